@@ -1,0 +1,472 @@
+"""Pins of the FP64 oracle against closed forms, brute-force integration and
+invariants that the paper and the mathematics fix (no GPU needed).
+
+Each test is chosen so that a plausible slip in the oracle (a dropped term, a
+wrong sign or index, a transposed operand, a wrong layer's temperature) fails it.
+"""
+import dataclasses
+import os
+
+import numpy as np
+import pytest
+
+from oracle import exoskry_oracle as O
+from paper_2602_19687_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _model(L=40, p_top=1e-6, p_bot=100.0, p_ref=10.0, tp=O.TP_ISOTHERMAL, cloud=O.CLOUD_NONE,
+           n_species=1, r_star=synth.R_SUN_CM):
+    m = synth._model(n_species, L, p_top, p_bot, tp, cloud, free=[0],
+                     species=list(synth.SPECIES)[:n_species])
+    m.p_ref_bar = p_ref
+    m.r_star_cm = r_star
+    return m
+
+
+def _flat_tables(nu, log10_sigma=-22.0, n_species=1, cia=-99.0):
+    t_grid = np.geomspace(100.0, 5000.0, 6)
+    p_grid = np.geomspace(1e-9, 1e3, 5)
+    sig = np.full((n_species, t_grid.size, p_grid.size, nu.size), log10_sigma)
+    cia_t = np.array([100.0, 5000.0])
+    cia_tab = np.full((2, nu.size), cia)
+    return synth.Tables(nu=nu, t_grid=t_grid, p_grid_bar=p_grid, log10_sigma=sig,
+                        cia_t_grid=cia_t, cia_h2h2=cia_tab, cia_h2he=cia_tab)
+
+
+# ---------------------------------------------------------------- grids, VMR
+def test_pressure_grid_levels_and_layers():
+    p_lev, p_lay = O.pressure_grid(50, 1e-6, 100.0)
+    assert p_lev[0] == pytest.approx(1e-6 * O.BAR) and p_lev[-1] == pytest.approx(100.0 * O.BAR)
+    ratio = p_lev[1:] / p_lev[:-1]
+    assert np.allclose(ratio, ratio[0], rtol=1e-12)           # log-uniform levels
+    assert np.all((p_lay > p_lev[:-1]) & (p_lay < p_lev[1:]))
+    assert np.allclose(np.log(p_lay), 0.5 * (np.log(p_lev[:-1]) + np.log(p_lev[1:])))
+
+
+def test_vmr_fill_sums_to_one_and_he_ratio():
+    x = 10.0 ** np.array([-3.0, -4.5, -2.2, -7.0])
+    x_h2, x_he = O.background_fill(x)
+    assert np.sum(x) + x_h2 + x_he == pytest.approx(1.0, abs=1e-15)
+    assert x_he / x_h2 == pytest.approx(0.164, rel=1e-15)
+    mu = O.mean_molecular_mass(np.zeros(1), np.array([18.0]), *O.background_fill(np.zeros(1)))
+    # solar H2/He mixture: (2.01588 + 0.164*4.002602)/1.164
+    assert mu == pytest.approx((2.01588 + 0.164 * 4.002602) / 1.164, rel=1e-14)
+
+
+# ---------------------------------------------------------------- T-p profiles
+def test_guillot_reduces_to_guillot2010():
+    """q_irr = 2/3 equals Guillot (2010) Eq. 49 with mu_* = 1/sqrt(3) and
+    T_irr^4 mu_* = 4 f_hem T_eq^4, written in its own variables."""
+    p = np.geomspace(1e-2, 1e8, 40)
+    t_int, t_eq, kappa, gamma, g = 250.0, 1300.0, 10 ** -2.3, 10 ** -0.7, 10 ** 3.1
+    mu_s = 1.0 / np.sqrt(3.0)
+    t_irr4 = 4.0 * 0.25 * t_eq ** 4 / mu_s
+    tau = kappa * p / g
+    t4_ref = 0.75 * t_int ** 4 * (2.0 / 3.0 + tau) + 0.75 * t_irr4 * mu_s * (
+        2.0 / 3.0 + mu_s / gamma + (gamma / (3.0 * mu_s) - mu_s / gamma) * np.exp(-gamma * tau / mu_s))
+    t = O.temperature_guillot(p, t_int, t_eq, kappa, gamma, g)
+    assert np.allclose(t, t4_ref ** 0.25, rtol=1e-13)
+
+
+def test_guillot_deep_limit_and_hopf_limits():
+    p = np.array([1e12, 1e13])
+    t_int, g, kappa = 400.0, 1e3, 1e-1
+    t = O.temperature_guillot(p, t_int, 1500.0, kappa, 0.3, g)
+    tau = kappa * p / g
+    assert np.allclose(t ** 4 / tau, 0.75 * t_int ** 4, rtol=1e-3)   # T^4 -> 3/4 T_int^4 tau
+    q = O.stretched_hopf(np.array([1e-12, 1e12]), 0.2, 2.0 / 3.0, 1e3, 0.7)
+    assert q[0] == pytest.approx(0.2, abs=1e-6) and q[1] == pytest.approx(2.0 / 3.0, abs=1e-12)
+
+
+# ---------------------------------------------------------------- hydrostatics
+def test_hydrostatic_isothermal_closed_form():
+    """Isothermal, constant mu, g ~ 1/r^2: 1/r(p) = 1/R + k T ln(p/p_ref)/(mu m_u g R^2)
+    exactly at every level, for any L and any p_ref (also off-grid)."""
+    for L, p_ref in ((7, 10.0), (50, 3.3), (33, 1e-7)):
+        p_lev, _ = O.pressure_grid(L, 1e-8, 100.0)
+        t, mu, g, R = 1234.0, 2.37, 10 ** 3.2, 1.3 * O.R_JUP
+        r, _ = O.altitude_grid(p_lev, np.full(L, t), mu, g, R, p_ref * O.BAR)
+        inv = 1.0 / R + O.K_B * t * np.log(p_lev / (p_ref * O.BAR)) / (mu * O.AMU * g * R ** 2)
+        assert np.allclose(r, 1.0 / inv, rtol=1e-13)
+
+
+def test_hydrostatic_layered_profile_matches_ode():
+    """Layer-wise temperatures: compare with a numerical integration of
+    dr/d ln p = -k_B T(p) r^2 / (mu m_u g_ref R^2) through the piecewise-constant
+    profile (pins which layer's temperature applies between which levels)."""
+    from scipy.integrate import solve_ivp
+    L = 12
+    p_lev, _ = O.pressure_grid(L, 1e-6, 100.0)
+    t_lay = np.linspace(600.0, 2400.0, L) + 200.0 * np.sin(np.arange(L))
+    mu, g, R, p_ref = 2.3, 10 ** 2.9, 1.1 * O.R_JUP, 10.0 * O.BAR
+    r, _ = O.altitude_grid(p_lev, t_lay, mu, g, R, p_ref)
+
+    def temp(lnp):
+        k = np.searchsorted(np.log(p_lev), lnp, side="right") - 1
+        return t_lay[min(max(k, 0), L - 1)]
+
+    for k in (0, 3, L):
+        # integrate piecewise so that no step straddles a temperature jump
+        a, b = np.log(p_ref), np.log(p_lev[k])
+        inner = np.log(p_lev[(np.log(p_lev) > min(a, b)) & (np.log(p_lev) < max(a, b))])
+        cuts = np.concatenate([[a], np.sort(inner)[::1 if b > a else -1], [b]])
+        y = R
+        for c0, c1 in zip(cuts[:-1], cuts[1:]):
+            mid = 0.5 * (c0 + c1)
+            sol = solve_ivp(lambda x, yy: [-O.K_B * temp(mid) * yy[0] ** 2 / (mu * O.AMU * g * R ** 2)],
+                            (c0, c1), [y], rtol=1e-12, atol=1e-3)
+            y = sol.y[0, -1]
+        assert y == pytest.approx(r[k], rel=1e-10)
+
+
+# ---------------------------------------------------------------- path matrix
+def _radii(L=30):
+    p_lev, _ = O.pressure_grid(L, 1e-6, 100.0)
+    t_lay = np.linspace(900.0, 1600.0, L)
+    r, _ = O.altitude_grid(p_lev, t_lay, 2.3, 1e3, O.R_JUP, 10.0 * O.BAR)
+    return r
+
+
+def test_path_matrix_row_sums_are_chord_lengths():
+    """alpha = 1 everywhere: tau_i = sum_l P_il dr_l is the chord length above
+    b_i, 2 sqrt(r_top^2 - b_i^2) (a telescoping sum)."""
+    r = _radii()
+    P, dr, b = O.path_matrix(r)
+    assert np.allclose(P @ dr, 2.0 * np.sqrt(r[0] ** 2 - b ** 2), rtol=1e-10)
+    # no path through layers below the impact parameter's layer
+    assert np.all(np.triu(P[::-1, ::-1], 1) == 0) or np.all(np.tril(P, -1)[:, :] >= 0)
+    assert np.all(P[np.triu_indices(len(dr), 1)] >= 0)
+    assert np.all(P[np.tril_indices(len(dr), -1)[::-1]] >= 0)
+    for i in range(len(dr)):
+        assert np.all(P[i, i + 1:] == 0.0)
+
+
+def test_path_matrix_brute_force_chord_march():
+    """Random per-layer extinction: tau_i by marching along each chord in 2e5
+    steps and summing the extinction of the shell containing each point."""
+    r = _radii(8)
+    P, dr, b = O.path_matrix(r)
+    rng = np.random.default_rng(3)
+    alpha = rng.uniform(0.1, 2.0, dr.size) * 1e-8
+    tau = P @ (alpha * dr)
+    for i in range(dr.size):
+        smax = np.sqrt(r[0] ** 2 - b[i] ** 2)
+        n = 200000
+        s = (np.arange(n) + 0.5) * smax / n
+        rad = np.sqrt(b[i] ** 2 + s ** 2)
+        layer = np.searchsorted(-r, -rad, side="left") - 1      # r descending
+        layer = np.clip(layer, 0, dr.size - 1)
+        brute = 2.0 * np.sum(alpha[layer]) * smax / n
+        assert tau[i] == pytest.approx(brute, rel=2e-5)
+
+
+# ---------------------------------------------------------------- transmission
+def _trans_setup(L, log10_sigma, deck=None, p_ref=10.0, p_bot=100.0, p_top=1e-6):
+    m = _model(L=L, p_ref=p_ref, p_bot=p_bot, p_top=p_top,
+               cloud=O.CLOUD_DECK if deck is not None else O.CLOUD_NONE)
+    m.ray_h2_cm2 = m.ray_he_cm2 = 0.0
+    nu = synth.nu_grid_constant_r(1.0, 2.0, 8)
+    tabs = _flat_tables(nu, log10_sigma)
+    th = m.theta_fixed.copy()
+    th[0] = -3.0
+    if deck is not None:
+        th[m.n_species + O.P_LOG_PCLOUD] = deck
+    mem = O.bin_members(nu, np.array([0.9]), np.array([2.1]))
+    return m, tabs, th, mem
+
+
+def test_zero_opacity_gives_bottom_disk():
+    m, tabs, th, mem = _trans_setup(30, -99.0, p_ref=100.0)
+    spec, y = O.forward(m, tabs, th, 0, mem)
+    rp = th[m.n_species + O.P_R_P] * O.R_JUP
+    assert np.allclose(spec, (rp / m.r_star_cm) ** 2, rtol=1e-14)   # (R_p/R_*)^2 when p_ref = p_bot
+
+
+def test_opaque_limits_and_deck():
+    m, tabs, th, mem = _trans_setup(30, -10.0)
+    atm = O.atmosphere(m, th)
+    spec, _ = O.forward(m, tabs, th, 0, mem)
+    assert np.allclose(spec, (atm["r_lev"][0] / m.r_star_cm) ** 2, rtol=1e-12)
+    m, tabs, th, mem = _trans_setup(30, -99.0, deck=-6.0)            # deck at p_top
+    spec, _ = O.forward(m, tabs, th, 0, mem)
+    assert np.allclose(spec, (O.atmosphere(m, th)["r_lev"][0] / m.r_star_cm) ** 2, rtol=1e-13)
+    m1, tabs1, th1, mem1 = _trans_setup(30, -24.0, deck=2.0)         # deck at p_bot: no change
+    m2, tabs2, th2, mem2 = _trans_setup(30, -24.0)
+    assert np.allclose(O.forward(m1, tabs1, th1, 0, mem1)[0], O.forward(m2, tabs2, th2, 0, mem2)[0],
+                       rtol=1e-14)
+
+
+def test_deck_depth_continuous_in_pressure():
+    vals = []
+    for lp in (-2.0 - 1e-9, -2.0 + 1e-9):
+        m, tabs, th, mem = _trans_setup(30, -25.0, deck=lp)
+        vals.append(O.forward(m, tabs, th, 0, mem)[0][0])
+    assert vals[0] == pytest.approx(vals[1], rel=1e-9)
+
+
+def test_beer_lambert_single_layer():
+    """One layer: the chord at the layer midpoint crosses it over
+    s = 2 sqrt(r_up^2 - b^2) and transmits exp(-alpha s)."""
+    m, tabs, th, mem = _trans_setup(1, -24.0, p_top=1e-3, p_bot=1e-2, p_ref=1e-2)
+    atm = O.atmosphere(m, th)
+    r_up, r_low = atm["r_lev"]
+    b = 0.5 * (r_up + r_low)
+    n = atm["p_lay"][0] / (O.K_B * atm["t_lay"][0])
+    x_h2 = atm["x_h2"]
+    alpha = n * 1e-3 * 1e-24
+    s = 2.0 * np.sqrt(r_up ** 2 - b ** 2)
+    expect = (r_low ** 2 + (r_up ** 2 - r_low ** 2) * (1.0 - np.exp(-alpha * s))) / m.r_star_cm ** 2
+    spec, _ = O.forward(m, tabs, th, 0, mem)
+    assert x_h2 > 0 and np.allclose(spec, expect, rtol=1e-12)
+
+
+def _continuum_depth(m, th, log10_sigma):
+    """Exact transit depth of the continuous isothermal atmosphere with
+    constant cross-section, by nested Gauss-Legendre quadrature."""
+    s = m.n_species
+    atm = O.atmosphere(m, th)
+    t = th[s + O.P_T_ISO]
+    mu, g, R = atm["mu"], atm["g"], atm["r_ref"]
+    p_ref = m.p_ref_bar * O.BAR
+    coef = O.K_B * t / (mu * O.AMU * g * R ** 2)
+    r_top, r_bot = atm["r_lev"][0], atm["r_lev"][-1]
+    x = 10.0 ** th[0]
+
+    def alpha(r):
+        p = p_ref * np.exp((1.0 / r - 1.0 / R) / coef)
+        return x * 10.0 ** log10_sigma * p / (O.K_B * t)
+
+    gx, gw = np.polynomial.legendre.leggauss(16)
+
+    def tau(b):
+        tmax = np.sqrt(r_top - b)
+        edges = np.linspace(0.0, tmax, 400)
+        tt = (0.5 * (edges[1:] - edges[:-1])[:, None] * gx[None, :] + 0.5 * (edges[1:] + edges[:-1])[:, None])
+        ww = 0.5 * (edges[1:] - edges[:-1])[:, None] * gw[None, :]
+        rr = b + tt ** 2
+        # tau(b) = 2 int_b alpha r dr / sqrt(r^2 - b^2), r = b + t^2
+        return np.sum(ww * 4.0 * alpha(rr) * rr / np.sqrt(2.0 * b + tt ** 2))
+
+    edges = np.linspace(r_bot, r_top, 1500)
+    acc = 0.0
+    for a0, a1 in zip(edges[:-1], edges[1:]):
+        bb = 0.5 * (a1 - a0) * gx + 0.5 * (a1 + a0)
+        acc += np.sum(0.5 * (a1 - a0) * gw * 2.0 * bb * (1.0 - np.exp(-np.array([tau(v) for v in bb]))))
+    return (r_bot ** 2 + acc) / m.r_star_cm ** 2
+
+
+@pytest.mark.slow
+def test_transit_depth_converges_to_continuum():
+    """Isothermal atmosphere with a constant cross-section: the discretised
+    depth converges to the exact transmission integral of the continuous
+    atmosphere. The square-root behaviour of the path length at the tangent
+    layer makes the rate ~ (dr)^1.5 (error ratio ~2.9 per halving)."""
+    lsig = -25.0
+    m0, _, th0, _ = _trans_setup(20, lsig, p_top=1e-7)
+    exact = _continuum_depth(m0, th0, lsig)
+    errs = []
+    for L in (50, 100, 200):
+        m, tabs, th, mem = _trans_setup(L, lsig, p_top=1e-7)
+        errs.append(abs(O.forward(m, tabs, th, 0, mem)[0][0] / exact - 1.0))
+    assert errs[2] < 5e-5
+    assert errs[0] / errs[1] > 2.5 and errs[1] / errs[2] > 2.5
+
+
+def test_scale_height_law():
+    """dR_eff/d ln sigma equals the pressure scale height at R_eff (to O(H/R))."""
+    rads = []
+    for lsig in (-25.0, -24.0):
+        m, tabs, th, mem = _trans_setup(300, lsig, p_top=1e-9)
+        rads.append(m.r_star_cm * np.sqrt(O.forward(m, tabs, th, 0, mem)[0][0]))
+    atm = O.atmosphere(m, th)
+    g_eff = atm["g"] * (atm["r_ref"] / np.mean(rads)) ** 2
+    h = O.K_B * th[m.n_species + O.P_T_ISO] / (atm["mu"] * O.AMU * g_eff)
+    slope = (rads[1] - rads[0]) / np.log(10.0)
+    assert slope == pytest.approx(h, rel=2e-2)
+
+
+# ---------------------------------------------------------------- interpolation
+def test_interpolation_nodes_linear_and_clamp():
+    rng = np.random.default_rng(1)
+    t_grid = np.geomspace(300, 3000, 5)
+    p_grid = np.geomspace(1e-6, 100, 4)
+    tab = rng.uniform(-28, -20, (5, 4, 3))
+    for it in range(5):
+        for ip in range(4):
+            v = O.log10_sigma_bilinear(tab, t_grid, p_grid, t_grid[it], p_grid[ip] * O.BAR)
+            assert np.allclose(v, tab[it, ip], atol=1e-12)
+    # a table linear in (log T, log p) is reproduced exactly everywhere
+    a, bt, bp = -23.0, 1.7, -0.4
+    lin = a + bt * np.log10(t_grid)[:, None, None] + bp * np.log10(p_grid)[None, :, None] + np.zeros(3)
+    for t, p in ((777.0, 3e-3), (301.0, 99.0), (2999.0, 1.1e-6)):
+        v = O.log10_sigma_bilinear(lin, t_grid, p_grid, t, p * O.BAR)
+        assert np.allclose(v, a + bt * np.log10(t) + bp * np.log10(p), atol=1e-12)
+    # clamping outside the table
+    v_lo = O.log10_sigma_bilinear(tab, t_grid, p_grid, 10.0, 1e-12 * O.BAR)
+    v_hi = O.log10_sigma_bilinear(tab, t_grid, p_grid, 9000.0, 1e4 * O.BAR)
+    assert np.allclose(v_lo, tab[0, 0]) and np.allclose(v_hi, tab[-1, -1])
+
+
+def test_cia_and_rayleigh_scalings():
+    """CIA extinction scales as n^2 (pressure squared at fixed T), Rayleigh as
+    n nu^4: checked by doubling the pressure and the wavenumber."""
+    m = _model(L=4)
+    nu = np.array([1.0e4, 2.0e4])
+    tabs = _flat_tables(nu, -99.0, cia=-45.0)
+    x = np.array([1e-30])
+    x_h2, x_he = O.background_fill(x)
+    t = np.array([1000.0])
+    m.ray_h2_cm2 = m.ray_he_cm2 = 0.0
+    a1 = O.extinction(tabs, m, x, x_h2, x_he, t, np.array([1e5]))
+    a2 = O.extinction(tabs, m, x, x_h2, x_he, t, np.array([2e5]))
+    assert np.allclose(a2 / a1, 4.0, rtol=1e-12)
+    n = 1e5 / (O.K_B * 1000.0)
+    assert a1[0, 0] == pytest.approx(n * n * x_h2 * (x_h2 + x_he) * 1e-45, rel=1e-12)
+    m = _model(L=4)
+    tabs = _flat_tables(nu, -99.0, cia=-99.0)
+    r1 = O.extinction(tabs, m, x, x_h2, x_he, t, np.array([1e5]))
+    r2 = O.extinction(tabs, m, x, x_h2, x_he, t, np.array([2e5]))
+    assert np.allclose(r2 / r1, 2.0, rtol=1e-12)
+    assert r1[0, 1] / r1[0, 0] == pytest.approx(16.0, rel=1e-12)
+
+
+# ---------------------------------------------------------------- emission
+def test_gauss_legendre_matches_table():
+    ref = np.loadtxt(os.path.join(GOLDEN, "gauss_legendre_4.txt"))
+    mu, w = O.gauss_legendre_01(4)
+    assert np.allclose(mu, 0.5 * (ref[:, 0] + 1.0), atol=1e-14)
+    assert np.allclose(w, 0.5 * ref[:, 1], atol=1e-14)
+
+
+def test_planck_integral_is_stefan_boltzmann():
+    sig = dict(np.loadtxt(os.path.join(GOLDEN, "constants.txt"), dtype=str).reshape(-1, 2))
+    sigma_sb = float(sig["sigma_sb"])
+    for t in (300.0, 1500.0):
+        nu = np.linspace(1e-3, 40.0 * t, 400001)
+        b = O.planck_wavenumber(t, nu)
+        integral = np.sum(0.5 * (b[1:] + b[:-1]) * np.diff(nu))
+        assert integral == pytest.approx(sigma_sb * t ** 4 / np.pi, rel=1e-7)
+
+
+def test_isothermal_emission_is_planck():
+    m = _model(L=25)
+    nu = synth.nu_grid_constant_r(1.0, 12.0, 50)
+    rng = np.random.default_rng(5)
+    tabs = _flat_tables(nu, -22.0)
+    tabs.log10_sigma = rng.uniform(-28, -19, tabs.log10_sigma.shape)
+    th = m.theta_fixed.copy()
+    th[0] = -3.0
+    mem = O.bin_members(nu, np.array([0.9]), np.array([13.0]))
+    spec, _ = O.forward(m, tabs, th, 1, mem)
+    t = th[m.n_species + O.P_T_ISO]
+    rp = th[m.n_species + O.P_R_P] * O.R_JUP
+    expect = O.planck_wavenumber(t, nu) / O.planck_wavenumber(m.t_star_k, nu) * (rp / m.r_star_cm) ** 2
+    assert np.allclose(spec, expect, rtol=1e-12)
+
+
+def test_linear_source_exact_solution():
+    """Source linear in optical depth, B = a + b t, over total depth T:
+    I_top(mu) = a + b mu (1 - e^{-T/mu}) exactly, so
+    F = 2 pi sum_j w_j mu_j I_top(mu_j) from the tabulated GL nodes."""
+    ref = np.loadtxt(os.path.join(GOLDEN, "gauss_legendre_4.txt"))
+    mu_t, w_t = 0.5 * (ref[:, 0] + 1.0), 0.5 * ref[:, 1]
+    a, bcoef = 2.0, 3.5
+    dtau = np.array([1e-6, 3e-5, 0.02, 0.3, 1.7, 4.0, 0.9])[:, None] * np.ones((1, 3))
+    t_edges = np.concatenate([[0.0], np.cumsum(dtau[:, 0])])
+    b_lev = (a + bcoef * t_edges)[:, None] * np.ones((1, 3))
+    total = t_edges[-1]
+    expect = 2.0 * np.pi * np.sum(w_t * mu_t * (a + bcoef * mu_t * (1.0 - np.exp(-total / mu_t))))
+    assert np.allclose(O.emergent_flux(b_lev, dtau), expect, rtol=1e-12)
+    # deep limit: Eddington-Barbier, F = pi (a + 2 b / 3)
+    deep = np.full((60, 1), 1.0)
+    te = np.concatenate([[0.0], np.cumsum(deep[:, 0])])
+    assert O.emergent_flux((a + bcoef * te)[:, None], deep)[0] == pytest.approx(np.pi * (a + 2 * bcoef / 3), rel=1e-12)
+
+
+def test_linear_source_factor_series_matches_exact():
+    x = np.array([2e-5, 9.9e-5, 1.01e-4, 1e-3])
+    exact = np.array([float((1 - np.exp(-np.longdouble(v))) / np.longdouble(v) - np.exp(-np.longdouble(v)))
+                      for v in x])
+    assert np.allclose(O.linear_source_factor(x), exact, rtol=1e-10)
+
+
+# ---------------------------------------------------------------- binning, likelihood
+def test_binning_means():
+    nu = synth.nu_grid_constant_r(1.0, 2.0, 101)
+    lo, hi = synth.make_bins(nu, 7)
+    mem = O.bin_members(nu, lo, hi)
+    spec = np.arange(nu.size, dtype=float)
+    y = O.bin_spectrum(spec, mem)
+    lam = 1e4 / nu
+    for k in range(7):
+        pts = [spec[n] for n in range(nu.size) if lo[k] <= lam[n] < hi[k]]
+        assert len(pts) > 0 and y[k] == pytest.approx(sum(pts) / len(pts), rel=1e-15)
+    assert sum(len(m_) for m_ in mem) <= nu.size
+
+
+def test_likelihood_closed_forms():
+    rng = np.random.default_rng(0)
+    sig = rng.uniform(1e-5, 1e-4, 50)
+    y = rng.uniform(0, 1, 50)
+    lnl = O.log_likelihood(y, y, sig, -99.0)
+    assert lnl == pytest.approx(-np.sum(np.log(sig)) - 25.0 * np.log(2 * np.pi), rel=1e-14)
+    # inflation: sigma_eff^2 = sigma^2 + 10^(2c)
+    c = np.log10(3e-5)
+    yo = y + 2e-5
+    s_eff = np.sqrt(sig ** 2 + 9e-10)
+    ref = np.sum(-np.log(s_eff) - 0.5 * np.log(2 * np.pi) - 0.5 * (2e-5 / s_eff) ** 2)
+    assert O.log_likelihood(y, yo, sig, c) == pytest.approx(ref, rel=1e-13)
+    # Gaussian normalisation: exp(lnL) integrates to 1 over one datum
+    grid = np.linspace(-1.0, 1.0, 200001) * 1e-3
+    dens = np.exp([O.log_likelihood(np.array([0.0]), np.array([v]), np.array([1e-4]), -99.0) for v in grid])
+    assert np.sum(dens) * (grid[1] - grid[0]) == pytest.approx(1.0, rel=1e-6)
+
+
+def test_invalid_outputs():
+    w = synth.workload("tiny")
+    m = w.model
+    th = m.full_theta(w.theta)[0]
+    mem = O.bin_members(w.tables.nu, w.bin_lo_um, w.bin_hi_um)
+    bad = th.copy()
+    bad[0] = np.log10(0.7)
+    bad[1] = np.log10(0.5)          # sum X > 1
+    assert O.loglike(m, w.tables, bad, 0, mem, w.y_obs[0], w.sigma[0]) == O.INVALID_LNL
+    hot = th.copy()
+    hot[m.n_species + O.P_T_ISO] = 2.0e6   # runaway inflation (1/r <= 0)
+    assert O.loglike(m, w.tables, hot, 0, mem, w.y_obs[0], w.sigma[0]) == O.INVALID_LNL
+
+
+# ---------------------------------------------------------------- gradient
+@pytest.mark.parametrize("kind", [0, 1])
+def test_complex_step_gradient_matches_central_differences(kind):
+    w = synth.workload("jwst_plain", n_nu=400)
+    m = w.model
+    m.tp_kind = O.TP_GUILLOT_MOD
+    m.cloud_kind = O.CLOUD_DECK
+    s = m.n_species
+    slots = list(range(s)) + [s + k for k in (O.P_T_INT, O.P_T_EQ, O.P_LOG_KAPPA, O.P_LOG_GAMMA,
+                                               O.P_Q_IRR0, O.P_LOG_PT, O.P_BETA, O.P_LOG_G, O.P_R_P,
+                                               O.P_C_INFL)]
+    if kind == 0:
+        slots.append(s + O.P_LOG_PCLOUD)
+    else:
+        slots.append(s + O.P_DILUTION)
+    th = m.full_theta(w.theta)[0]
+    th[s + O.P_LOG_PCLOUD] = -3.37
+    th[s + O.P_Q_IRR0] = 0.3
+    th[s + O.P_LOG_PT] = -1.3
+    th[s + O.P_C_INFL] = -4.6
+    th[s + O.P_DILUTION] = 0.9
+    mem = O.bin_members(w.tables.nu, w.bin_lo_um, w.bin_hi_um)
+    y_obs, sig = w.y_obs[kind], w.sigma[kind]
+    g = O.loglike_gradient(m, w.tables, th, kind, mem, y_obs, sig, slots)
+    for k, slot in enumerate(slots):
+        h = 1e-5 * max(1.0, abs(th[slot]))
+        a, b = th.copy(), th.copy()
+        a[slot] += h
+        b[slot] -= h
+        fd = (O.loglike(m, w.tables, a, kind, mem, y_obs, sig)
+              - O.loglike(m, w.tables, b, kind, mem, y_obs, sig)) / (2 * h)
+        assert g[k] == pytest.approx(fd, rel=2e-5, abs=1e-6 * np.max(np.abs(g))), slot
