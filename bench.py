@@ -1,0 +1,372 @@
+"""Benchmark: forward+gradient spectra/s of the batched forward model and
+log-likelihood on one GB300 (and N GPUs as independent shards, weak scaling).
+
+A step is one es_forward_backward over the whole batch (every stage of the
+path: setup, interpolation/extinction, chord optical depth / transit depth or
+emission RT, binning, ln L, and the full adjoint). Inputs are resident in HBM
+before the timed region; the per-step workspace (extinction, tau_bar,
+alpha_bar: ~37 GB at the default workload) is far larger than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   # the FP64 oracle on the host cores
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "forward+gradient spectra/sec per GB300 (batched vs plain) at ≤1e-5 rel err vs FP64"
+UNIT = "spectra/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="batched_trans")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--cpu-child", default=None, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- CPU oracle timing
+def oracle_sample_time(workload, n_sub, n_vec, seconds_cap=25.0):
+    """Time the FP64 oracle (forward + complex-step gradient) on a bounded
+    sample: the first `n_vec` valid parameter vectors of the workload on the
+    first `n_sub` wavenumbers (same tables, layers, species). Returns seconds
+    per full-resolution spectrum+gradient, scaled by N / n_sub."""
+    from oracle import exoskry_oracle as O
+    from paper_2602_19687_gb300 import synth
+    w = synth.workload(workload, batch=max(8, n_vec * 4), n_nu=None)
+    tabs = w.tables
+    full_n = tabs.nu.size
+    sub = synth.Tables(nu=tabs.nu[:n_sub], t_grid=tabs.t_grid, p_grid_bar=tabs.p_grid_bar,
+                       log10_sigma=tabs.log10_sigma[..., :n_sub], cia_t_grid=tabs.cia_t_grid,
+                       cia_h2h2=tabs.cia_h2h2[:, :n_sub], cia_h2he=tabs.cia_h2he[:, :n_sub])
+    if w.table_dtype == "bf16":
+        sub.log10_sigma = O.bf16_row_dequantized(sub.log10_sigma)
+    lam_sub = 1e4 / sub.nu
+    keep = (w.bin_hi_um <= lam_sub.max()) & (w.bin_lo_um >= lam_sub.min())
+    lo, hi = w.bin_lo_um[keep], w.bin_hi_um[keep]
+    mem = O.bin_members(sub.nu, lo, hi)
+    m = w.model
+    done, t0 = 0, time.perf_counter()
+    for b in range(w.theta.shape[0]):
+        kind = int(w.kind[b])
+        th = m.full_theta(w.theta[b])[0]
+        if not O.atmosphere(m, th)["valid"]:
+            continue
+        O.loglike_gradient(m, sub, th, kind, mem, w.y_obs[kind][keep], w.sigma[kind][keep],
+                           list(m.free_idx))
+        done += 1
+        if done >= n_vec or time.perf_counter() - t0 > seconds_cap:
+            break
+    dt = time.perf_counter() - t0
+    return dt / max(done, 1) * (full_n / n_sub), done, full_n
+
+
+def cpu_baseline(workload, n_sub=1500, n_vec=2):
+    """Run the oracle timing in a child process pinned to one thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-child", "%s:%d:%d" % (workload, n_sub, n_vec)]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-300:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": 1.0 / d["sec_per_spectrum"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d parameter vector(s) x first %d of %d wavenumbers, forward + complex-step gradient "
+                      "(%s), scaled to a full spectrum; host cores available %d"
+                      % (d["done"], n_sub, d["full_n"], workload, os.cpu_count() or 0)}
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r.split(",") for r in out.strip().splitlines() if r.strip()]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 4 + k and r[4 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- roofline
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def kernel_work(name, w, n_valid):
+    """Algorithmic work of one launch of each kernel at this workload:
+    (amount, unit, bound). Counts as stated in the design doc."""
+    m = w.model
+    B, L, S, N = n_valid, m.n_layers, m.n_species, w.tables.nu.size
+    tri = L * (L + 1) // 2
+    if name in ("k_extinction", "k_extinction_bwd"):
+        return B * L * (S + 2) * N, "ex2", "alu"
+    if name in ("k_transit", "k_transit_taubar", "k_transit_abar", "k_transit_lbar"):
+        return 2.0 * B * N * tri, "flop", "alu"
+    if name in ("k_emission", "k_emission_bwd"):
+        return B * N * L * 4, "layer-angle steps", "alu"
+    return None
+
+
+def alu_peak(kind, sm_mhz):
+    """Peaks from unit counts x clock (152 SMs): MUFU ex2 32/clk/SM on
+    GB300; FP32 FMA 128 lanes x 2 flop/clk/SM."""
+    clk = sm_mhz * 1e6
+    if kind == "ex2":
+        return 152 * 32 * clk
+    if kind == "flop":
+        return 152 * 128 * 2 * clk
+    return None
+
+
+# --------------------------------------------------------------------------- main arms
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2602_19687_gb300 import binding, synth
+    import __graft_entry__
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+        __graft_entry__.build()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    w = synth.workload(args.workload, seed=42 + rank)      # each rank: its own shard of vectors
+    ctx = binding.context_for(w, device=local)
+    B = w.theta.shape[0]
+    nfree = w.theta.shape[1]
+    theta = torch.tensor(w.theta, dtype=torch.float64, device=dev)
+    kind = torch.tensor(w.kind, dtype=torch.int32, device=dev)
+    ctx.es_set_batch(theta, kind)
+    lnl = torch.empty(B, dtype=torch.float64, device=dev)
+    grad = torch.empty((B, nfree), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        ctx.es_forward_backward(lnl, grad)
+    torch.cuda.synchronize(dev)
+    flags = torch.empty(B, dtype=torch.int32, device=dev)
+    ctx.es_get_flags(flags)
+    n_valid = int((flags == 0).sum().item())
+
+    # ---- timed region (device-resident inputs)
+    ctx.es_set_profiling(True)
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    launches = 0
+    for _ in range(args.steps):
+        ctx.es_forward_backward(lnl, grad)
+        launches += ctx.es_query(7)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    prof = ctx.es_get_profile()
+    ctx.es_set_profiling(False)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = B * world / (ms_max / 1e3)
+
+    # ---- end to end through the C ABI with host buffers (pinned)
+    th_host = torch.tensor(w.theta, dtype=torch.float64).pin_memory().numpy()
+    kd_host = np.ascontiguousarray(w.kind, np.int32)
+    lnl_h = torch.empty(B, dtype=torch.float64).pin_memory().numpy()
+    grad_h = torch.empty((B, nfree), dtype=torch.float64).pin_memory().numpy()
+    ctx.es_set_batch(th_host, kd_host)
+    ctx.es_forward_backward(lnl_h, grad_h)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.es_set_batch(th_host, kd_host)
+        ctx.es_forward_backward(lnl_h, grad_h)
+    t1 = time.perf_counter()
+    barrier()
+    e2e_ms = (t1 - t0) * 1e3 / args.steps
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = B * world / (float(te.item()) / 1e3)
+
+    # ---- roofline of the dominant kernel (live CUDA-event times)
+    peaks, peak_src = measured_peaks()
+    sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    per_kernel = {}
+    total_prof = sum(p[1] for p in prof) or 1.0
+    for name, tot, n in prof:
+        per_kernel[name] = {"ms_per_launch": tot / max(n, 1), "launches": n, "share": tot / total_prof}
+    top = max(prof, key=lambda p: p[1])[0] if prof else None
+    roof = None
+    if top is not None:
+        wk = kernel_work(top, w, n_valid)
+        ms_launch = per_kernel[top]["ms_per_launch"]
+        if wk is not None:
+            amount, unit_kind, bound = wk
+            achieved = amount / (ms_launch / 1e3)
+            peak = alu_peak(unit_kind, sm_mhz)
+            scale = 1e12
+            roof = {"kernel": top, "bound": bound, "achieved": achieved / scale,
+                    "peak": peak / scale if peak else None,
+                    "unit": "T%s/s" % unit_kind, "frac": (achieved / peak) if peak else None,
+                    "traffic": None, "ms_per_launch": ms_launch,
+                    "peak_source": "derived from unit counts x median SM clock %.0f MHz" % sm_mhz}
+
+    # ---- plain per-sample path (batched vs plain)
+    plain = None
+    if not args.no_plain and rank == 0:
+        wp = synth.workload("jwst_plain")
+        cp = binding.context_for(wp, device=local)
+        thp = torch.tensor(wp.theta, dtype=torch.float64, device=dev)
+        cp.es_set_batch(thp)
+        lp = torch.empty(1, dtype=torch.float64, device=dev)
+        gp = torch.empty_like(thp)
+        for _ in range(3):
+            cp.es_forward_backward(lp, gp)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 20
+        e0.record(stream)
+        for _ in range(reps):
+            cp.es_forward_backward(lp, gp)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        pms = e0.elapsed_time(e1) / reps
+        plain = {"value": 1e3 / pms, "unit": UNIT, "ms_per_spectrum": pms,
+                 "workload": "jwst_plain: " + wp.description + " (one vector per call, forward+gradient)"}
+        cp.es_destroy()
+
+    cpu = cpu_baseline(args.workload) if rank == 0 else None
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded tables, data and parameter batches)",
+            "config": {"workload": args.workload + ": " + w.description, "batch_per_gpu": B,
+                       "valid_vectors": n_valid, "n_nu": int(w.tables.nu.size), "layers": w.model.n_layers,
+                       "species": w.model.n_species, "free_params": nfree, "tables": w.table_dtype,
+                       "l2": "inputs larger than L2 (per-step workspace ~%.0f GB)" % (ctx.es_query(6) / 1e9),
+                       "parallelism": "independent shards, one process per GPU"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(B * nfree * 8 + B * 4),
+                    "d2h_bytes_per_step": int(B * 8 + B * nfree * 8)},
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "kernels": per_kernel,
+            "plain": plain,
+            "batched_over_plain": (value / world / plain["value"]) if plain else None,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "peaks_source": peak_src,
+        }
+        print(json.dumps(line))
+    ctx.es_destroy()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The FP64 oracle as it stands, timed on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per = []
+    for _ in range(args.warmup + args.steps):
+        sec, done, full_n = None, 0, 0
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1")
+        cmd = [sys.executable, os.path.abspath(__file__), "--cpu-child", "%s:%d:%d" % (args.workload, 600, 1)]
+        r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=600)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        per.append(d["sec_per_spectrum"])
+    timed = per[args.warmup:]
+    sps = 1.0 / float(np.mean(timed))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": sps, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(timed)) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload},
+        "cpu_baseline": {"value": sps, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "per step: 1 parameter vector x first 600 wavenumbers, forward + "
+                                   "complex-step gradient, scaled to a full spectrum"},
+        "e2e": {"value": sps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    args = parse()
+    if args.cpu_child:
+        name, n_sub, n_vec = args.cpu_child.split(":")
+        sec, done, full_n = oracle_sample_time(name, int(n_sub), int(n_vec))
+        print(json.dumps({"sec_per_spectrum": sec, "done": done, "full_n": full_n}))
+        return
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

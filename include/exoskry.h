@@ -1,0 +1,199 @@
+/*
+ * exoskry.h - C ABI of the GB300-native batched forward model, Gaussian
+ * log-likelihood and adjoint for sub-stellar atmospheric retrieval
+ * (Exo Skryer, arXiv 2602.19687).
+ *
+ * The problem statement the calls follow (Sect. 2, 2.3): a sampler proposes
+ * parameter vectors theta; the library evaluates the forward model spectrum
+ * for each vector and its Gaussian log-likelihood against binned data
+ * (Eq. lnL with residuals r_i and the error inflation of Eq. c_error);
+ * invalid forward-model output is assigned ln L = -1e300.
+ *
+ * Conventions shared by every entry point:
+ *  - Units are cgs; pressures in the API are in bar, wavelengths in micron,
+ *    wavenumbers in cm^-1.
+ *  - A context owns every device copy it makes (tables, grids, data, batch,
+ *    workspace). Host inputs are copied during the call; the caller keeps
+ *    ownership of its memory.
+ *  - `mem` arguments say where a caller buffer lives: ES_MEM_HOST (pageable
+ *    or pinned host memory; the call copies through the device and
+ *    synchronises `stream` before returning) or ES_MEM_DEVICE (device memory
+ *    of the context's GPU; the call is asynchronous on `stream`).
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream.
+ *  - Errors are returned as es_status; es_last_error() gives a message.
+ *    An invalid sample is not an error (it gets ln L = -1e300, zero
+ *    gradient and flag bit ES_FLAG_INVALID).
+ *  - One context must not be used from two host threads at once.
+ */
+#ifndef EXOSKRY_H
+#define EXOSKRY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct es_ctx es_ctx;
+typedef void *es_stream_t;
+
+typedef enum {
+    ES_OK = 0,
+    ES_EINVAL = 1,    /* bad argument, size or inconsistent description  */
+    ES_ENOMEM = 2,    /* device or host allocation failed                */
+    ES_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed     */
+    ES_ESTATE = 4,    /* call out of order (e.g. forward before tables)  */
+    ES_ETIMEOUT = 5   /* a bounded device-side wait gave up              */
+} es_status;
+
+enum { ES_TP_ISOTHERMAL = 0, ES_TP_GUILLOT = 1, ES_TP_GUILLOT_MOD = 2 };
+enum { ES_CLOUD_NONE = 0, ES_CLOUD_DECK = 1 };
+enum { ES_KIND_TRANSMISSION = 0, ES_KIND_EMISSION = 1 };
+enum { ES_TABLE_F32 = 0, ES_TABLE_BF16 = 1 };
+enum { ES_MEM_HOST = 0, ES_MEM_DEVICE = 1 };
+enum { ES_FLAG_INVALID = 1 };
+
+/*
+ * Canonical parameter vector. Slots 0..S-1 hold log10 of the S absorber
+ * volume mixing ratios (Sect. 3.1); the slots below follow at S + ES_P_*.
+ *   T_ISO        isothermal temperature [K]                  (Sect. 2.4.1)
+ *   T_INT, T_EQ  internal / equilibrium temperature [K]     (Sect. 2.4.4)
+ *   LOG_KAPPA_IR log10 infrared opacity [cm^2 g^-1]          (Sect. 2.4.3)
+ *   LOG_GAMMA_V  log10 visible-to-infrared opacity ratio     (Sect. 2.4.4)
+ *   Q_IRR0, LOG_P_T, BETA  stretched-exponential Hopf function
+ *                of the irradiation term, Eq. (q); p_t in bar (GUILLOT_MOD)
+ *   LOG_G        log10 reference gravity [cm s^-2]
+ *   R_P          planet radius at p_ref [Jupiter radii, 7.1492e9 cm]
+ *   LOG_P_CLOUD  log10 grey cloud-deck pressure [bar]        (ES_CLOUD_DECK)
+ *   C_INFL       error inflation c of Eq. c_error (-99: none)
+ *   DILUTION     dilution factor s of Sect. 5 (emission)
+ */
+enum {
+    ES_P_T_ISO = 0, ES_P_T_INT, ES_P_T_EQ, ES_P_LOG_KAPPA_IR, ES_P_LOG_GAMMA_V,
+    ES_P_Q_IRR0, ES_P_LOG_P_T, ES_P_BETA, ES_P_LOG_G, ES_P_R_P, ES_P_LOG_P_CLOUD,
+    ES_P_C_INFL, ES_P_DILUTION, ES_P_N_EXTRA
+};
+
+#define ES_MAX_SPECIES 16
+#define ES_MAX_LAYERS 112
+#define ES_MAX_PARAMS (ES_MAX_SPECIES + ES_P_N_EXTRA)
+
+/*
+ * Static model description (Sect. 2.4 profile choice, Sect. 3 absorbers,
+ * Sect. 4-5 geometry and star). Layers: n_layers (2..ES_MAX_LAYERS) with
+ * n_layers+1 levels log-spaced from p_top (top) to p_bot (bottom); a
+ * layer's pressure is the geometric mean of its levels. Hydrostatic
+ * balance with g(r) = g_ref (R_p/r)^2 is anchored at r(p_ref) = R_p.
+ * theta_fixed holds every canonical slot's value; the user's parameter
+ * vectors fill the n_free slots listed in free_idx (in that order).
+ * Rayleigh cross-sections are sigma(nu) = ray_*_cm2 (nu / ray_nu_ref)^4.
+ */
+typedef struct {
+    int n_layers;
+    double p_top_bar, p_bot_bar, p_ref_bar;
+    int tp_kind;                 /* ES_TP_*          */
+    int cloud_kind;              /* ES_CLOUD_*       */
+    int n_species;               /* S, 1..ES_MAX_SPECIES */
+    double species_mass_amu[ES_MAX_SPECIES];
+    double r_star_cm, t_star_k;
+    double ray_h2_cm2, ray_he_cm2, ray_nu_ref;
+    double theta_fixed[ES_MAX_PARAMS];
+    int n_free;
+    int free_idx[ES_MAX_PARAMS];
+} es_model_desc;
+
+/*
+ * Opacity tables (Sect. 3: opacity-sampled cross-sections on temperature
+ * and pressure grids; H2-H2 and H2-He CIA). All host pointers, row-major:
+ *   log10_sigma [n_species][n_t][n_p][n_nu]  log10 cm^2
+ *   cia_h2h2, cia_h2he [n_t_cia][n_nu]        log10 cm^5
+ * Grids strictly ascending; every species shares the wavenumber grid.
+ * storage = ES_TABLE_BF16 keeps each (species, T, p) row as BF16 residuals
+ * about an FP32 row offset (the row mean): value = bf16 + offset.
+ */
+typedef struct {
+    int n_nu;      const double *nu;          /* cm^-1, ascending          */
+    int n_t;       const double *t_grid;      /* K                          */
+    int n_p;       const double *p_grid_bar;  /* bar                        */
+    const float *log10_sigma;
+    int n_t_cia;   const double *cia_t_grid;  /* K                          */
+    const float *cia_h2h2;
+    const float *cia_h2he;
+    int storage;                              /* ES_TABLE_F32 | ES_TABLE_BF16 */
+} es_tables_desc;
+
+/* Create a context on CUDA device `device` for the model `desc`.
+ * Errors: ES_EINVAL (bad description), ES_ECUDA, ES_ENOMEM. */
+es_status es_create(es_ctx **out, int device, const es_model_desc *desc);
+
+/* Copy the opacity tables to the device (Sect. 3). Replaces earlier tables
+ * and invalidates the instrument grid. Errors: ES_EINVAL (sizes, grids not
+ * ascending, species count differs from the model), ES_ENOMEM, ES_ECUDA. */
+es_status es_load_tables(es_ctx *ctx, const es_tables_desc *tables);
+
+/* Instrument bins [lo, hi) in micron. The model of bin k is the equal-
+ * weight mean of the native points with lambda = 1e4/nu in [lo_k, hi_k).
+ * Bins must not share native points; a bin with no points is ES_EINVAL.
+ * Requires tables (ES_ESTATE). */
+es_status es_set_grid(es_ctx *ctx, const double *bin_lo_um, const double *bin_hi_um, int n_bins);
+
+/* Observed spectrum and 1-sigma errors for samples of `kind`
+ * (transit depth for transmission, Fp/F* for emission), n_bins values
+ * each, host memory (Sect. 2.3). Requires the grid (ES_ESTATE). */
+es_status es_set_data(es_ctx *ctx, int kind, const double *y_obs, const double *sigma, int n_bins);
+
+/* Set the batch: theta [batch][n_free] (the model's free slots, in
+ * free_idx order) and kind [batch] (ES_KIND_*; NULL = all transmission),
+ * both in `mem`. Grows the device workspace as needed (ES_ENOMEM). */
+es_status es_set_batch(es_ctx *ctx, const double *theta, const int32_t *kind, int batch,
+                       int mem, es_stream_t stream);
+
+/* Forward model for the current batch (Sects. 2.4-5) and its log-likelihood
+ * (Sect. 2.3). Any output may be NULL:
+ *   spectrum [batch][n_nu]  native-resolution transit depth or Fp/F* (float)
+ *   binned   [batch][n_bins] binned model (double)
+ *   lnL      [batch]          ln L (double); -1e300 for invalid samples
+ * Needs tables, grid, data for every kind present, and a batch. */
+es_status es_forward(es_ctx *ctx, float *spectrum, double *binned, double *lnL,
+                     int mem, es_stream_t stream);
+
+/* ln L only (the sampler's call). Same requirements as es_forward. */
+es_status es_loglike(es_ctx *ctx, double *lnL, int mem, es_stream_t stream);
+
+/* ln L and its gradient with respect to the free parameters,
+ * grad [batch][n_free] (double), by a hand-written adjoint that recomputes
+ * the interpolated opacities. Invalid samples get a zero gradient. */
+es_status es_forward_backward(es_ctx *ctx, double *lnL, double *grad, int mem,
+                              es_stream_t stream);
+
+/* Per-sample flags (ES_FLAG_INVALID) of the last forward, int32 [batch]. */
+es_status es_get_flags(es_ctx *ctx, int32_t *flags, int mem, es_stream_t stream);
+
+/* Sizes: 0 n_nu, 1 n_bins, 2 n_free, 3 batch, 4 n_layers, 5 n_species,
+ * 6 device workspace bytes, 7 kernel launches issued by the last call.
+ * Returns -1 for an unknown key or a NULL context. */
+int64_t es_query(const es_ctx *ctx, int key);
+
+/* Per-kernel timing with CUDA events recorded on the launching stream
+ * around every kernel launch of later calls (on = 1) or off (on = 0, the
+ * default). Turning it on or off clears the accumulated times. */
+es_status es_set_profiling(es_ctx *ctx, int on);
+
+/* Accumulated profile entry `index` (0-based, in first-launch order):
+ * copies the kernel's name (NUL-terminated, at most name_len bytes), its
+ * total device time in milliseconds and its launch count. Synchronises the
+ * device. Returns ES_EINVAL when index is past the last entry. */
+es_status es_get_profile(es_ctx *ctx, int index, char *name, int name_len, double *total_ms,
+                         int64_t *launches);
+
+/* Message for the last error on this context (never NULL). */
+const char *es_last_error(const es_ctx *ctx);
+
+/* Free every device and host resource of the context. NULL is a no-op. */
+void es_destroy(es_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EXOSKRY_H */

@@ -426,3 +426,20 @@ def loglike_gradient(model, tabs, theta, kind, members, y_obs, sigma, slots, h=1
         val = loglike(model, tabs, th, kind, members, y_obs, sigma)
         grad[k] = 0.0 if np.real(val) == INVALID_LNL else np.imag(val) / h
     return grad
+
+
+# --------------------------------------------------------------------------
+# BF16 table storage (the library's reduced-precision table format)
+# --------------------------------------------------------------------------
+def bf16_row_dequantized(log10_sigma):
+    """Values the BF16-table path interpolates: each (species, T, p) row is
+    stored as round-to-nearest-even BF16 of (value - offset) with an FP32
+    offset equal to the row mean (mean taken in FP64, rounded to FP32; the
+    residual formed in FP32). Returns the dequantized table in float64."""
+    tab = np.asarray(log10_sigma, dtype=np.float32)
+    off = np.mean(tab.astype(np.float64), axis=-1).astype(np.float32)
+    resid = (tab - off[..., None]).astype(np.float32)
+    bits = resid.view(np.uint32).astype(np.uint64)
+    rounded = ((bits + 0x7FFF + ((bits >> 16) & 1)) >> 16) << 16
+    q = rounded.astype(np.uint32).view(np.float32)
+    return q.astype(np.float64) + off[..., None].astype(np.float64)

@@ -1,0 +1,738 @@
+// C ABI of the library: context management, validation, device copies of
+// tables/grids/data, workspace, and the launch sequence of each call.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace es;
+
+struct es_ctx {
+    int device = 0;
+    es_model_desc desc{};
+    Model m{};
+    Work w{};
+    std::string err = "no error";
+    std::vector<void *> model_bufs;   // freed on destroy
+    std::vector<void *> table_bufs;   // replaced by es_load_tables
+    std::vector<void *> grid_bufs;    // replaced by es_set_grid
+    std::vector<void *> data_bufs;
+    std::vector<void *> work_bufs;    // forward workspace
+    std::vector<void *> bwd_bufs;     // adjoint workspace
+    bool have_tables = false, have_grid = false, have_data[2] = {false, false};
+    int cap_b = 0, cap_b_bwd = 0, batch = 0, n_kind[2] = {0, 0};
+    size_t ws_bytes = 0;
+    int64_t last_launches = 0;
+    std::vector<double> y_host[2], s_host[2];
+    std::vector<double> nu_host;      // FP64 wavenumber grid (bin membership)
+    size_t ymod_cap = 0;
+    double *d_data = nullptr;         // [2][nbins] y_obs then sigma
+    double *d_lnl = nullptr, *d_grad = nullptr;
+    // per-kernel CUDA-event profiling
+    struct ProfEntry { std::string name; double ms = 0.0; int64_t n = 0; };
+    struct Pending { int entry; cudaEvent_t a, b; };
+    bool prof_on = false;
+    std::vector<ProfEntry> prof;
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> ev_pool;
+    int open_entry = -1;
+    cudaEvent_t open_ev = nullptr;
+    Hook hook;
+};
+
+namespace {
+
+es_status fail(es_ctx *c, es_status s, const std::string &msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+es_status cuda_fail(es_ctx *c, cudaError_t e, const char *where) {
+    return fail(c, ES_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+template <class T>
+es_status dalloc(es_ctx *c, std::vector<void *> &owner, T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, ES_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
+    }
+    owner.push_back(q);
+    c->ws_bytes += count * sizeof(T);
+    *p = static_cast<T *>(q);
+    return ES_OK;
+}
+
+template <class T>
+es_status upload(es_ctx *c, std::vector<void *> &owner, T **p, const T *src, size_t count) {
+    es_status s = dalloc(c, owner, p, count);
+    if (s != ES_OK) return s;
+    cudaError_t e = cudaMemcpy(*p, src, count * sizeof(T), cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? ES_OK : cuda_fail(c, e, "cudaMemcpy");
+}
+
+void free_all(std::vector<void *> &v) {
+    for (void *p : v) cudaFree(p);
+    v.clear();
+}
+
+bool ascending(const double *g, int n) {
+    for (int i = 1; i < n; ++i)
+        if (!(g[i] > g[i - 1])) return false;
+    return true;
+}
+
+// same bracket convention as the device code, in double on the host
+void host_bracket(const double *grid, int n, double x, int &i, double &w) {
+    if (x <= grid[0]) x = grid[0];
+    if (x >= grid[n - 1]) x = grid[n - 1];
+    i = 0;
+    for (int q = 0; q < n; ++q)
+        if (grid[q] <= x) i = q;
+    if (i > n - 2) i = n - 2;
+    w = (x - grid[i]) / (grid[i + 1] - grid[i]);
+}
+
+uint16_t to_bf16_rne(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7FFFu + lsb;
+    return (uint16_t)(u >> 16);
+}
+
+double planck_host(double nu, double t) {
+    return TWO_HC2 * nu * nu * nu / std::expm1(C2_RAD * nu / t);
+}
+
+cudaEvent_t take_event(es_ctx *c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_begin(void *p, const char *name, cudaStream_t st) {
+    es_ctx *c = static_cast<es_ctx *>(p);
+    int idx = -1;
+    for (size_t k = 0; k < c->prof.size(); ++k)
+        if (c->prof[k].name == name) idx = (int)k;
+    if (idx < 0) {
+        c->prof.push_back(es_ctx::ProfEntry{name, 0.0, 0});
+        idx = (int)c->prof.size() - 1;
+    }
+    c->open_entry = idx;
+    c->open_ev = take_event(c);
+    cudaEventRecord(c->open_ev, st);
+}
+
+void prof_end(void *p, cudaStream_t st) {
+    es_ctx *c = static_cast<es_ctx *>(p);
+    cudaEvent_t e = take_event(c);
+    cudaEventRecord(e, st);
+    c->pending.push_back(es_ctx::Pending{c->open_entry, c->open_ev, e});
+    c->open_entry = -1;
+}
+
+void prof_resolve(es_ctx *c) {
+    for (auto &q : c->pending) {
+        cudaEventSynchronize(q.b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, q.a, q.b);
+        c->prof[q.entry].ms += ms;
+        c->prof[q.entry].n += 1;
+        c->ev_pool.push_back(q.a);
+        c->ev_pool.push_back(q.b);
+    }
+    c->pending.clear();
+}
+
+es_status check_launch(es_ctx *c, const char *what) {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? ES_OK : cuda_fail(c, e, what);
+}
+
+es_status alloc_forward(es_ctx *c, int B) {
+    if (B <= c->cap_b) return ES_OK;
+    free_all(c->work_bufs);
+    free_all(c->bwd_bufs);
+    c->cap_b_bwd = 0;
+    c->ws_bytes = 0;
+    const Model &m = c->m;
+    const size_t L = m.L, S = m.S, N = m.N;
+    Work &w = c->w;
+    es_status s = ES_OK;
+    double *theta_user;
+#define ALLOC(p, n) if ((s = dalloc(c, c->work_bufs, &(p), (size_t)(n))) != ES_OK) return s
+    ALLOC(theta_user, (size_t)B * m.nfree);
+    w.theta_user = theta_user;
+    ALLOC(w.theta, (size_t)B * m.nfull);
+    ALLOC(w.kind, B);
+    ALLOC(w.flags, B);
+    ALLOC(w.t_lay, B * L);
+    ALLOC(w.t_lev, B * (L + 1));
+    ALLOC(w.r_lev, B * (L + 1));
+    ALLOC(w.xs, B * (S + 2));
+    ALLOC(w.n_lay, B * L);
+    ALLOC(w.rc, B);
+    ALLOC(w.base, B);
+    ALLOC(w.scale, B);
+    ALLOC(w.lmat, B * L * L);
+    ALLOC(w.area, B * L);
+    ALLOC(w.dr, B * L);
+    ALLOC(w.w4, B * L);
+    ALLOC(w.it, B * L);
+    ALLOC(w.gt, B * L);
+    ALLOC(w.wtr, B * L);
+    ALLOC(w.coef, B * L * S);
+    ALLOC(w.itc, B * L);
+    ALLOC(w.wtc, B * L);
+    ALLOC(w.gtc, B * L);
+    ALLOC(w.ccia, B * L * 2);
+    ALLOC(w.ray, B * L);
+    ALLOC(w.alpha, (size_t)B * L * N);
+    ALLOC(w.spec, (size_t)B * N);
+    ALLOC(w.lnl, B);
+    ALLOC(w.misc, (size_t)B * 4);
+    ALLOC(c->d_lnl, B);
+#undef ALLOC
+    c->cap_b = B;
+    return ES_OK;
+}
+
+es_status alloc_backward(es_ctx *c) {
+    const int B = c->cap_b;
+    if (B <= c->cap_b_bwd) return ES_OK;
+    free_all(c->bwd_bufs);
+    const Model &m = c->m;
+    const size_t L = m.L, S = m.S, N = m.N;
+    Work &w = c->w;
+    es_status s = ES_OK;
+#define ALLOC(p, n) if ((s = dalloc(c, c->bwd_bufs, &(p), (size_t)(n))) != ES_OK) return s
+    ALLOC(w.dbar, (size_t)B * N);
+    ALLOC(w.taubar, (size_t)B * L * N);
+    ALLOC(w.abar, (size_t)B * L * N);
+    ALLOC(w.lbar, (size_t)B * L * L);
+    ALLOC(w.red, (size_t)B * L * (S + N_RED_EXTRA));
+    ALLOC(w.areabar, (size_t)B * L);
+    ALLOC(w.levbar, (size_t)B * (L + 1));
+    ALLOC(w.drbar, (size_t)B * L);
+    ALLOC(w.grad, (size_t)B * c->m.nfree);
+#undef ALLOC
+    c->cap_b_bwd = B;
+    return ES_OK;
+}
+
+es_status ready(es_ctx *c) {
+    if (!c->have_tables) return fail(c, ES_ESTATE, "tables not loaded");
+    if (!c->have_grid) return fail(c, ES_ESTATE, "instrument grid not set");
+    if (c->batch <= 0) return fail(c, ES_ESTATE, "no batch set");
+    for (int k = 0; k < 2; ++k)
+        if (c->n_kind[k] > 0 && !c->have_data[k])
+            return fail(c, ES_ESTATE, std::string("no data for ") + (k ? "emission" : "transmission") + " samples");
+    return ES_OK;
+}
+
+// forward sequence; adjoint=true also prepares dbar / misc for the backward
+es_status run_forward(es_ctx *c, bool adjoint, float *spec_out, double *binned_out, double *lnl_out,
+                      cudaStream_t st) {
+    Work w = c->w;
+    w.B = c->batch;
+    int launches = 0;
+    const Hook &h = c->hook;
+    launches += launch_setup(c->m, w, st, h);
+    launches += launch_extinction(c->m, w, st, h);
+    if (c->n_kind[0]) launches += launch_transit(c->m, w, st, h);
+    if (c->n_kind[1]) launches += launch_emission(c->m, w, st, h);
+    if (adjoint) {
+        cudaMemsetAsync(w.dbar, 0, sizeof(float) * (size_t)w.B * c->m.N, st);
+    }
+    launches += launch_bins(c->m, w, adjoint, spec_out, binned_out, lnl_out, st, h);
+    c->last_launches = launches;
+    return check_launch(c, "forward launch");
+}
+
+}  // namespace
+
+static es_status ensure_ymod(es_ctx *c) {
+    size_t need = (size_t)c->cap_b * c->m.nbins;
+    if (need <= c->ymod_cap) return ES_OK;
+    if (c->w.ymod) cudaFree(c->w.ymod);
+    c->w.ymod = nullptr;
+    c->ymod_cap = 0;
+    void *q = nullptr;
+    if (cudaMalloc(&q, need * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, ES_ENOMEM, "cudaMalloc of the binned-model buffer failed");
+    }
+    c->w.ymod = static_cast<double *>(q);
+    c->ymod_cap = need;
+    return ES_OK;
+}
+
+extern "C" {
+
+es_status es_create(es_ctx **out, int device, const es_model_desc *d) {
+    if (!out || !d) return ES_EINVAL;
+    *out = nullptr;
+    if (d->n_layers < 2 || d->n_layers > ES_MAX_LAYERS) return ES_EINVAL;
+    if (d->n_species < 1 || d->n_species > ES_MAX_SPECIES) return ES_EINVAL;
+    if (!(d->p_top_bar > 0) || !(d->p_bot_bar > d->p_top_bar) || !(d->p_ref_bar > 0)) return ES_EINVAL;
+    if (d->tp_kind < 0 || d->tp_kind > 2 || d->cloud_kind < 0 || d->cloud_kind > 1) return ES_EINVAL;
+    if (!(d->r_star_cm > 0) || !(d->t_star_k > 0)) return ES_EINVAL;
+    const int nfull = d->n_species + ES_P_N_EXTRA;
+    if (d->n_free < 1 || d->n_free > 32 || d->n_free > nfull) return ES_EINVAL;
+    for (int k = 0; k < d->n_free; ++k) {
+        if (d->free_idx[k] < 0 || d->free_idx[k] >= nfull) return ES_EINVAL;
+        for (int q = 0; q < k; ++q)
+            if (d->free_idx[q] == d->free_idx[k]) return ES_EINVAL;
+    }
+    for (int s = 0; s < d->n_species; ++s)
+        if (!(d->species_mass_amu[s] > 0)) return ES_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return ES_ECUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return ES_ECUDA;
+    es_ctx *c = new es_ctx();
+    c->device = device;
+    c->desc = *d;
+    Model &m = c->m;
+    m.L = d->n_layers;
+    m.S = d->n_species;
+    m.nfree = d->n_free;
+    m.nfull = nfull;
+    m.tp_kind = d->tp_kind;
+    m.cloud_kind = d->cloud_kind;
+    m.p_ref = d->p_ref_bar * BAR;
+    m.r_star = d->r_star_cm;
+    m.t_star = d->t_star_k;
+    m.ray_h2 = d->ray_h2_cm2;
+    m.ray_he = d->ray_he_cm2;
+    m.ray_nu_ref = d->ray_nu_ref > 0 ? d->ray_nu_ref : 1.0;
+    for (int s = 0; s < m.S; ++s) m.mass[s] = d->species_mass_amu[s];
+    for (int k = 0; k < nfull; ++k) m.theta_fixed[k] = d->theta_fixed[k];
+    for (int k = 0; k < m.nfree; ++k) m.free_idx[k] = d->free_idx[k];
+    // 4-point Gauss-Legendre on [0, 1]: x = +-sqrt(3/7 -+ 2/7 sqrt(6/5)),
+    // w = (18 +- sqrt(30))/36 on [-1, 1]
+    const double xa = std::sqrt(3.0 / 7.0 - 2.0 / 7.0 * std::sqrt(6.0 / 5.0));
+    const double xb = std::sqrt(3.0 / 7.0 + 2.0 / 7.0 * std::sqrt(6.0 / 5.0));
+    const double wa = (18.0 + std::sqrt(30.0)) / 36.0, wb = (18.0 - std::sqrt(30.0)) / 36.0;
+    const double xs[4] = {-xb, -xa, xa, xb}, ws[4] = {wb, wa, wa, wb};
+    for (int j = 0; j < 4; ++j) {
+        m.mu_gl[j] = 0.5 * (xs[j] + 1.0);
+        m.w_gl[j] = 0.5 * ws[j];
+    }
+    // pressure levels (top to bottom) and layers
+    std::vector<double> p_lev(m.L + 1), p_lay(m.L);
+    for (int k = 0; k <= m.L; ++k)
+        p_lev[k] = d->p_top_bar * std::pow(d->p_bot_bar / d->p_top_bar, (double)k / m.L) * BAR;
+    for (int l = 0; l < m.L; ++l) p_lay[l] = std::sqrt(p_lev[l] * p_lev[l + 1]);
+    double *dp;
+    es_status s;
+    if ((s = upload(c, c->model_bufs, &dp, p_lev.data(), p_lev.size())) != ES_OK) { es_destroy(c); return s; }
+    m.p_lev = dp;
+    if ((s = upload(c, c->model_bufs, &dp, p_lay.data(), p_lay.size())) != ES_OK) { es_destroy(c); return s; }
+    m.p_lay = dp;
+    c->ws_bytes = 0;
+    *out = c;
+    return ES_OK;
+}
+
+es_status es_load_tables(es_ctx *c, const es_tables_desc *t) {
+    if (!c) return ES_EINVAL;
+    if (!t || !t->nu || !t->t_grid || !t->p_grid_bar || !t->log10_sigma || !t->cia_t_grid || !t->cia_h2h2 ||
+        !t->cia_h2he)
+        return fail(c, ES_EINVAL, "null table pointer");
+    if (t->n_nu < 2 || t->n_t < 2 || t->n_p < 2 || t->n_t_cia < 2 || t->n_t > 64 || t->n_p > 64 || t->n_t_cia > 64)
+        return fail(c, ES_EINVAL, "table sizes out of range");
+    if (!ascending(t->nu, t->n_nu) || !ascending(t->t_grid, t->n_t) || !ascending(t->p_grid_bar, t->n_p) ||
+        !ascending(t->cia_t_grid, t->n_t_cia) || !(t->t_grid[0] > 0) || !(t->p_grid_bar[0] > 0) ||
+        !(t->nu[0] > 0))
+        return fail(c, ES_EINVAL, "grids must be positive and strictly ascending");
+    if (t->storage != ES_TABLE_F32 && t->storage != ES_TABLE_BF16) return fail(c, ES_EINVAL, "bad storage");
+    cudaSetDevice(c->device);
+    free_all(c->table_bufs);
+    free_all(c->grid_bufs);
+    c->have_tables = c->have_grid = false;
+    c->have_data[0] = c->have_data[1] = false;
+    c->cap_b = c->cap_b_bwd = 0;
+    free_all(c->work_bufs);
+    free_all(c->bwd_bufs);
+    Model &m = c->m;
+    m.N = t->n_nu;
+    m.NT = t->n_t;
+    m.NP = t->n_p;
+    m.NTc = t->n_t_cia;
+    m.bf16 = t->storage == ES_TABLE_BF16;
+    c->nu_host.assign(t->nu, t->nu + t->n_nu);
+    const size_t N = m.N, S = m.S, rows = S * m.NT * m.NP;
+    es_status s;
+    std::vector<float> off(rows, 0.f);
+    if (m.bf16) {
+        std::vector<uint16_t> q(rows * N);
+        for (size_t r = 0; r < rows; ++r) {
+            const float *src = t->log10_sigma + r * N;
+            double mean = 0.0;
+            for (size_t n = 0; n < N; ++n) mean += src[n];
+            float o = (float)(mean / (double)N);
+            off[r] = o;
+            for (size_t n = 0; n < N; ++n) q[r * N + n] = to_bf16_rne(src[n] - o);
+        }
+        uint16_t *d16;
+        if ((s = upload(c, c->table_bufs, &d16, q.data(), q.size())) != ES_OK) return s;
+        m.tab16 = d16;
+        m.tab32 = nullptr;
+    } else {
+        float *d32;
+        if ((s = upload(c, c->table_bufs, &d32, t->log10_sigma, rows * N)) != ES_OK) return s;
+        m.tab32 = d32;
+        m.tab16 = nullptr;
+    }
+    float *df;
+    if ((s = upload(c, c->table_bufs, &df, off.data(), rows)) != ES_OK) return s;
+    m.row_off = df;
+    std::vector<float> cia(2 * (size_t)m.NTc * N);
+    std::memcpy(cia.data(), t->cia_h2h2, sizeof(float) * m.NTc * N);
+    std::memcpy(cia.data() + (size_t)m.NTc * N, t->cia_h2he, sizeof(float) * m.NTc * N);
+    if ((s = upload(c, c->table_bufs, &df, cia.data(), cia.size())) != ES_OK) return s;
+    m.cia = df;
+    std::vector<float> nuf(N), ifs(N);
+    for (size_t n = 0; n < N; ++n) {
+        nuf[n] = (float)t->nu[n];
+        ifs[n] = (float)(1.0 / (PI * planck_host(t->nu[n], m.t_star)));
+    }
+    if ((s = upload(c, c->table_bufs, &df, nuf.data(), N)) != ES_OK) return s;
+    m.nu = df;
+    if ((s = upload(c, c->table_bufs, &df, ifs.data(), N)) != ES_OK) return s;
+    m.inv_fstar = df;
+    std::vector<double> logt(m.NT), logp(m.NP);
+    for (int i = 0; i < m.NT; ++i) logt[i] = std::log10(t->t_grid[i]);
+    for (int i = 0; i < m.NP; ++i) logp[i] = std::log10(t->p_grid_bar[i]);
+    double *dd;
+    if ((s = upload(c, c->table_bufs, &dd, logt.data(), logt.size())) != ES_OK) return s;
+    m.log_t = dd;
+    if ((s = upload(c, c->table_bufs, &dd, t->cia_t_grid, (size_t)m.NTc)) != ES_OK) return s;
+    m.cia_t = dd;
+    // fixed pressure bracket of every layer (log10 p in bar)
+    std::vector<int> ip(m.L);
+    std::vector<float> wp(m.L);
+    for (int l = 0; l < m.L; ++l) {
+        double pl = c->desc.p_top_bar * std::pow(c->desc.p_bot_bar / c->desc.p_top_bar, (double)l / m.L) * BAR;
+        double pu = c->desc.p_top_bar * std::pow(c->desc.p_bot_bar / c->desc.p_top_bar, (double)(l + 1) / m.L) * BAR;
+        double play = std::sqrt(pl * pu);
+        int i;
+        double wv;
+        host_bracket(logp.data(), m.NP, std::log10(play / BAR), i, wv);
+        ip[l] = i;
+        wp[l] = (float)wv;
+    }
+    int *di;
+    if ((s = upload(c, c->table_bufs, &di, ip.data(), ip.size())) != ES_OK) return s;
+    m.ip = di;
+    if ((s = upload(c, c->table_bufs, &df, wp.data(), wp.size())) != ES_OK) return s;
+    m.wp = df;
+    c->have_tables = true;
+    return ES_OK;
+}
+
+es_status es_set_grid(es_ctx *c, const double *lo, const double *hi, int nbins) {
+    if (!c) return ES_EINVAL;
+    if (!c->have_tables) return fail(c, ES_ESTATE, "load tables before the grid");
+    if (!lo || !hi || nbins < 1) return fail(c, ES_EINVAL, "bad bin arrays");
+    cudaSetDevice(c->device);
+    const int N = c->m.N;
+    // lambda = 1e4/nu decreases with the index, so each bin's members
+    // {n : lo <= lambda_n < hi} form one contiguous index range.
+    std::vector<double> lam(N);
+    for (int n = 0; n < N; ++n) lam[n] = 1.0e4 / c->nu_host[n];
+    std::vector<int> blo(nbins), bhi(nbins), owner(N, -1);
+    for (int k = 0; k < nbins; ++k) {
+        if (!(hi[k] > lo[k])) return fail(c, ES_EINVAL, "bin " + std::to_string(k) + ": hi <= lo");
+        int a = 0, b = N;   // first index with lam < hi
+        while (a < b) {
+            int mid = (a + b) / 2;
+            if (lam[mid] < hi[k]) b = mid; else a = mid + 1;
+        }
+        int first = a;
+        a = 0, b = N;       // first index with lam < lo
+        while (a < b) {
+            int mid = (a + b) / 2;
+            if (lam[mid] < lo[k]) b = mid; else a = mid + 1;
+        }
+        int end = a;
+        if (end <= first) return fail(c, ES_EINVAL, "bin " + std::to_string(k) + " holds no native point");
+        for (int n = first; n < end; ++n) {
+            if (owner[n] >= 0) return fail(c, ES_EINVAL, "bins " + std::to_string(owner[n]) + " and " +
+                                                           std::to_string(k) + " overlap");
+            owner[n] = k;
+        }
+        blo[k] = first;
+        bhi[k] = end;
+    }
+    free_all(c->grid_bufs);
+    free_all(c->data_bufs);
+    c->have_grid = false;
+    c->have_data[0] = c->have_data[1] = false;
+    es_status s;
+    int *di;
+    if ((s = upload(c, c->grid_bufs, &di, blo.data(), (size_t)nbins)) != ES_OK) return s;
+    c->m.bin_lo = di;
+    if ((s = upload(c, c->grid_bufs, &di, bhi.data(), (size_t)nbins)) != ES_OK) return s;
+    c->m.bin_hi = di;
+    if ((s = upload(c, c->grid_bufs, &di, owner.data(), (size_t)N)) != ES_OK) return s;
+    c->m.bin_of = di;
+    if ((s = dalloc(c, c->grid_bufs, &c->d_data, (size_t)4 * nbins)) != ES_OK) return s;
+    c->m.nbins = nbins;
+    c->m.y_obs = c->d_data;
+    c->m.sigma = c->d_data + 2 * (size_t)nbins;
+    for (int k = 0; k < 2; ++k) {
+        c->y_host[k].assign(nbins, 0.0);
+        c->s_host[k].assign(nbins, 1.0);
+    }
+    c->have_grid = true;
+    return ES_OK;
+}
+
+es_status es_set_data(es_ctx *c, int kind, const double *y_obs, const double *sigma, int nbins) {
+    if (!c) return ES_EINVAL;
+    if (!c->have_grid) return fail(c, ES_ESTATE, "set the instrument grid before the data");
+    if (kind != ES_KIND_TRANSMISSION && kind != ES_KIND_EMISSION) return fail(c, ES_EINVAL, "bad kind");
+    if (!y_obs || !sigma || nbins != c->m.nbins) return fail(c, ES_EINVAL, "data size differs from the grid");
+    for (int k = 0; k < nbins; ++k)
+        if (!(sigma[k] > 0) || !std::isfinite(y_obs[k])) return fail(c, ES_EINVAL, "sigma must be > 0, y finite");
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaMemcpy(c->d_data + (size_t)kind * nbins, y_obs, sizeof(double) * nbins,
+                               cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_data + (size_t)(2 + kind) * nbins, sigma, sizeof(double) * nbins,
+                       cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "es_set_data");
+    c->have_data[kind] = true;
+    return ES_OK;
+}
+
+es_status es_set_batch(es_ctx *c, const double *theta, const int32_t *kind, int batch, int mem,
+                       es_stream_t stream) {
+    if (!c) return ES_EINVAL;
+    if (!c->have_tables) return fail(c, ES_ESTATE, "load tables before the batch");
+    if (!theta || batch < 1 || (mem != ES_MEM_HOST && mem != ES_MEM_DEVICE))
+        return fail(c, ES_EINVAL, "bad batch arguments");
+    cudaSetDevice(c->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    es_status s = alloc_forward(c, batch);
+    if (s != ES_OK) return s;
+    const cudaMemcpyKind dir = mem == ES_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    cudaError_t e = cudaMemcpyAsync(const_cast<double *>(c->w.theta_user), theta,
+                                    sizeof(double) * (size_t)batch * c->m.nfree, dir, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "theta copy");
+    std::vector<int32_t> kh(batch, ES_KIND_TRANSMISSION);
+    if (kind) {
+        if (mem == ES_MEM_HOST) {
+            std::memcpy(kh.data(), kind, sizeof(int32_t) * batch);
+        } else {
+            e = cudaMemcpyAsync(kh.data(), kind, sizeof(int32_t) * batch, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return cuda_fail(c, e, "kind copy");
+        }
+    }
+    int nk[2] = {0, 0};
+    for (int b = 0; b < batch; ++b) {
+        if (kh[b] != ES_KIND_TRANSMISSION && kh[b] != ES_KIND_EMISSION)
+            return fail(c, ES_EINVAL, "kind must be 0 (transmission) or 1 (emission)");
+        nk[kh[b]]++;
+    }
+    e = cudaMemcpyAsync(c->w.kind, kh.data(), sizeof(int32_t) * batch, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && mem == ES_MEM_HOST) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && kind && mem == ES_MEM_DEVICE) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "kind upload");
+    if (mem == ES_MEM_DEVICE && !kind) {
+        e = cudaStreamSynchronize(st);   // the host vector kh goes out of scope
+        if (e != cudaSuccess) return cuda_fail(c, e, "kind upload");
+    }
+    c->batch = batch;
+    c->n_kind[0] = nk[0];
+    c->n_kind[1] = nk[1];
+    return ES_OK;
+}
+
+namespace {
+
+es_status copy_out(es_ctx *c, void *dst, const void *src, size_t bytes, cudaStream_t st) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st);
+    return e == cudaSuccess ? ES_OK : cuda_fail(c, e, "result copy");
+}
+
+es_status finish(es_ctx *c, int mem, cudaStream_t st) {
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && mem == ES_MEM_HOST) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? ES_OK : cuda_fail(c, e, "kernel execution");
+}
+
+}  // namespace
+
+es_status es_forward(es_ctx *c, float *spectrum, double *binned, double *lnl, int mem, es_stream_t stream) {
+    if (!c) return ES_EINVAL;
+    if (mem != ES_MEM_HOST && mem != ES_MEM_DEVICE) return fail(c, ES_EINVAL, "bad mem");
+    es_status s = ready(c);
+    if (s != ES_OK) return s;
+    cudaSetDevice(c->device);
+    if ((s = ensure_ymod(c)) != ES_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int B = c->batch;
+    float *d_spec = spectrum;
+    double *d_bin = binned, *d_lnl = lnl;
+    std::vector<void *> tmp;
+    if (mem == ES_MEM_HOST) {
+        d_lnl = lnl ? c->d_lnl : nullptr;
+        if (spectrum && (s = dalloc(c, tmp, &d_spec, (size_t)B * c->m.N)) != ES_OK) return s;
+        if (binned && (s = dalloc(c, tmp, &d_bin, (size_t)B * c->m.nbins)) != ES_OK) { free_all(tmp); return s; }
+    }
+    s = run_forward(c, false, d_spec, d_bin, d_lnl, st);
+    if (s == ES_OK && mem == ES_MEM_HOST) {
+        if (lnl) s = copy_out(c, lnl, d_lnl, sizeof(double) * B, st);
+        if (s == ES_OK && spectrum) s = copy_out(c, spectrum, d_spec, sizeof(float) * (size_t)B * c->m.N, st);
+        if (s == ES_OK && binned) s = copy_out(c, binned, d_bin, sizeof(double) * (size_t)B * c->m.nbins, st);
+    }
+    if (s == ES_OK) s = finish(c, mem, st);
+    if (!tmp.empty()) {
+        cudaStreamSynchronize(st);
+        free_all(tmp);
+    }
+    return s;
+}
+
+es_status es_loglike(es_ctx *c, double *lnl, int mem, es_stream_t stream) {
+    if (!lnl) return fail(c, ES_EINVAL, "lnL pointer is NULL");
+    return es_forward(c, nullptr, nullptr, lnl, mem, stream);
+}
+
+es_status es_forward_backward(es_ctx *c, double *lnl, double *grad, int mem, es_stream_t stream) {
+    if (!c) return ES_EINVAL;
+    if (mem != ES_MEM_HOST && mem != ES_MEM_DEVICE) return fail(c, ES_EINVAL, "bad mem");
+    es_status s = ready(c);
+    if (s != ES_OK) return s;
+    cudaSetDevice(c->device);
+    if ((s = ensure_ymod(c)) != ES_OK) return s;
+    if ((s = alloc_backward(c)) != ES_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int B = c->batch;
+    const Model &m = c->m;
+    Work w = c->w;
+    w.B = B;
+    double *d_lnl = (mem == ES_MEM_HOST || !lnl) ? c->d_lnl : lnl;
+    const size_t L = m.L, S = m.S;
+    cudaMemsetAsync(w.red, 0, sizeof(double) * B * L * (S + N_RED_EXTRA), st);
+    cudaMemsetAsync(w.areabar, 0, sizeof(double) * B * L, st);
+    cudaMemsetAsync(w.levbar, 0, sizeof(double) * B * (L + 1), st);
+    cudaMemsetAsync(w.drbar, 0, sizeof(double) * B * L, st);
+    cudaMemsetAsync(w.lbar, 0, sizeof(double) * B * L * L, st);
+    s = run_forward(c, true, nullptr, nullptr, d_lnl, st);
+    if (s != ES_OK) return s;
+    int launches = (int)c->last_launches;
+    const Hook &h = c->hook;
+    if (c->n_kind[0]) launches += launch_transit_backward(m, w, st, h);
+    if (c->n_kind[1]) launches += launch_emission_backward(m, w, st, h);
+    launches += launch_extinction_backward(m, w, st, h);
+    launches += launch_setup_backward(m, w, st, h);
+    c->last_launches = launches;
+    if ((s = check_launch(c, "backward launch")) != ES_OK) return s;
+    if (mem == ES_MEM_HOST) {
+        if (lnl) s = copy_out(c, lnl, d_lnl, sizeof(double) * B, st);
+        if (s == ES_OK && grad) s = copy_out(c, grad, w.grad, sizeof(double) * (size_t)B * m.nfree, st);
+    } else if (grad) {
+        cudaError_t e = cudaMemcpyAsync(grad, w.grad, sizeof(double) * (size_t)B * m.nfree,
+                                        cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "gradient copy");
+    }
+    if (s == ES_OK) s = finish(c, mem, st);
+    return s;
+}
+
+es_status es_get_flags(es_ctx *c, int32_t *flags, int mem, es_stream_t stream) {
+    if (!c) return ES_EINVAL;
+    if (!flags || c->batch <= 0) return fail(c, ES_EINVAL, "no batch or NULL flags");
+    cudaSetDevice(c->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(flags, c->w.flags, sizeof(int32_t) * c->batch,
+                                    mem == ES_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && mem == ES_MEM_HOST) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? ES_OK : cuda_fail(c, e, "flags copy");
+}
+
+int64_t es_query(const es_ctx *c, int key) {
+    if (!c) return -1;
+    switch (key) {
+        case 0: return c->m.N;
+        case 1: return c->m.nbins;
+        case 2: return c->m.nfree;
+        case 3: return c->batch;
+        case 4: return c->m.L;
+        case 5: return c->m.S;
+        case 6: return (int64_t)c->ws_bytes;
+        case 7: return c->last_launches;
+        default: return -1;
+    }
+}
+
+es_status es_set_profiling(es_ctx *c, int on) {
+    if (!c) return ES_EINVAL;
+    cudaSetDevice(c->device);
+    prof_resolve(c);
+    c->prof.clear();
+    c->prof_on = on != 0;
+    c->hook = Hook{};
+    if (c->prof_on) {
+        c->hook.ctx = c;
+        c->hook.begin = prof_begin;
+        c->hook.end = prof_end;
+    }
+    return ES_OK;
+}
+
+es_status es_get_profile(es_ctx *c, int index, char *name, int name_len, double *total_ms, int64_t *launches) {
+    if (!c) return ES_EINVAL;
+    cudaSetDevice(c->device);
+    prof_resolve(c);
+    if (index < 0 || index >= (int)c->prof.size()) return fail(c, ES_EINVAL, "no such profile entry");
+    const auto &e = c->prof[index];
+    if (name && name_len > 0) {
+        std::strncpy(name, e.name.c_str(), (size_t)name_len - 1);
+        name[name_len - 1] = 0;
+    }
+    if (total_ms) *total_ms = e.ms;
+    if (launches) *launches = e.n;
+    return ES_OK;
+}
+
+const char *es_last_error(const es_ctx *c) { return c ? c->err.c_str() : "NULL context"; }
+
+void es_destroy(es_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    free_all(c->bwd_bufs);
+    free_all(c->work_bufs);
+    free_all(c->data_bufs);
+    free_all(c->grid_bufs);
+    free_all(c->table_bufs);
+    free_all(c->model_bufs);
+    if (c->w.ymod) cudaFree(c->w.ymod);
+    prof_resolve(c);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,132 @@
+// Internal declarations shared by the C-ABI layer and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "exoskry.h"
+
+namespace es {
+
+// CODATA 2018 (cgs) and nominal radii
+constexpr double K_B = 1.380649e-16;
+constexpr double H_PLANCK = 6.62607015e-27;
+constexpr double C_LIGHT = 2.99792458e10;
+constexpr double AMU = 1.66053906660e-24;
+constexpr double R_JUP = 7.1492e9;
+constexpr double BAR = 1.0e6;
+constexpr double PI = 3.14159265358979323846;
+constexpr double LN10 = 2.302585092994045684;
+constexpr double LOG2_10 = 3.321928094887362348;
+// Sect. 3.1 background gas; Sect. 2.4.4 modified Guillot constants
+constexpr double HE_TO_H2 = 0.164;
+constexpr double M_H2 = 2.01588;
+constexpr double M_HE = 4.002602;
+constexpr double F_HEM = 0.25;
+constexpr double Q_INT = 2.0 / 3.0;
+constexpr double Q_IRR_INF = 2.0 / 3.0;
+// Sect. 2.3: invalid forward-model output
+constexpr double INVALID_LNL = -1.0e300;
+// second radiation constant h c / k_B [cm K] and 2 h c^2 [erg cm^2 s^-1]
+constexpr double C2_RAD = H_PLANCK * C_LIGHT / K_B;
+constexpr double TWO_HC2 = 2.0 * H_PLANCK * C_LIGHT * C_LIGHT;
+// number of Gauss-Legendre angles for the emission flux integral
+constexpr int N_MU = 4;
+// reductions per (sample, layer) in the extinction adjoint (after S species)
+constexpr int N_RED_EXTRA = 6;   // D, C1, C2, C1T, C2T, W4
+
+// Constant model data, passed by value to every kernel.
+struct Model {
+    int L, S, NT, NP, NTc, N, nbins, nfree, nfull;
+    int tp_kind, cloud_kind, bf16;
+    double p_ref;                 // dyn cm^-2
+    double r_star, t_star;
+    double ray_h2, ray_he, ray_nu_ref;
+    double mass[ES_MAX_SPECIES];
+    int free_idx[ES_MAX_PARAMS];
+    double theta_fixed[ES_MAX_PARAMS];
+    double mu_gl[N_MU], w_gl[N_MU];
+    // device arrays
+    const double *p_lev, *p_lay;  // [L+1], [L]
+    const int *ip;                // [L] pressure bracket of each layer
+    const float *wp;              // [L] pressure weight of each layer
+    const double *log_t;          // [NT] log10 of the temperature grid
+    const double *cia_t;          // [NTc]
+    const float *tab32;           // [S][NT][NP][N]
+    const uint16_t *tab16;        // [S][NT][NP][N] BF16 residuals
+    const float *row_off;         // [S][NT][NP] (zeros for FP32 tables)
+    const float *cia;             // [2][NTc][N] log10 k
+    const float *nu;              // [N]
+    const float *inv_fstar;       // [N] 1 / (pi B(T_*, nu))
+    const int *bin_lo, *bin_hi;   // [nbins] native index ranges [lo, hi)
+    const int *bin_of;            // [N] bin of each native point or -1
+    const double *y_obs, *sigma;  // [2][nbins]
+};
+
+// Per-batch device workspace.
+struct Work {
+    int B;
+    const double *theta_user;     // [B][nfree]
+    double *theta;                // [B][nfull]
+    int *kind, *flags;            // [B]
+    double *t_lay, *t_lev, *r_lev;// [B][L], [B][L+1], [B][L+1]
+    double *xs;                   // [B][S+2] X_s..., X_H2, X_He
+    double *n_lay;                // [B][L]
+    double *rc, *base, *scale;    // [B]
+    float *lmat;                  // [B][L][L] path lengths L_il = P_il dr_l
+    float *area;                  // [B][L] annulus area / R_*^2
+    float *dr;                    // [B][L]
+    float4 *w4;                   // [B][L] bilinear weights x log2(10)
+    int *it;                      // [B][L] temperature bracket
+    float *gt;                    // [B][L] 1/dlog10T of the bracket (0 if clamped)
+    float *wtr;                   // [B][L] raw temperature weight
+    float *coef;                  // [B][L][S] log2(X_s n_l) + offsets
+    int *itc;                     // [B][L] CIA temperature bracket
+    float *wtc, *gtc;             // [B][L] CIA weight, 1/dT (0 if clamped)
+    float *ccia;                  // [B][L][2] log2(n^2 X_H2 X_H2), log2(n^2 X_H2 X_He)
+    float *ray;                   // [B][L] n (X_H2 s_H2 + X_He s_He)
+    float *alpha;                 // [B][L][N]
+    float *spec;                  // [B][N] transmission: depth - base; emission: Fp/F*
+    double *ymod;                 // [B][nbins]
+    double *lnl;                  // [B]
+    // adjoint
+    float *dbar;                  // [B][N] d lnL / d spec
+    float *taubar;                // [B][L][N]
+    float *abar;                  // [B][L][N] d lnL / d alpha
+    double *lbar;                 // [B][L][L]
+    double *red;                  // [B][L][S+N_RED_EXTRA]
+    double *areabar;              // [B][L]
+    double *levbar;               // [B][L+1] d lnL / d T_lev (emission)
+    double *drbar;                // [B][L]   d lnL / d dr (emission)
+    double *misc;                 // [B][4] base_bar, scale_bar, c_bar, -
+    double *grad;                 // [B][nfree]
+};
+
+// Optional per-launch callbacks (CUDA-event profiling of each kernel).
+struct Hook {
+    void *ctx = nullptr;
+    void (*begin)(void *, const char *, cudaStream_t) = nullptr;
+    void (*end)(void *, cudaStream_t) = nullptr;
+    void on_begin(const char *name, cudaStream_t s) const { if (begin) begin(ctx, name, s); }
+    void on_end(cudaStream_t s) const { if (end) end(ctx, s); }
+};
+#define ES_LAUNCH(hook, name, st, ...) \
+    do {                                 \
+        (hook).on_begin(name, st);       \
+        __VA_ARGS__;                     \
+        (hook).on_end(st);               \
+    } while (0)
+
+// kernel launchers (each returns the number of kernels launched)
+int launch_setup(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
+int launch_extinction(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
+int launch_transit(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
+int launch_emission(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
+int launch_bins(const Model &m, const Work &w, bool want_adjoint, float *spectrum_out,
+                double *binned_out, double *lnl_out, cudaStream_t st, const Hook &h);
+int launch_transit_backward(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
+int launch_emission_backward(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
+int launch_extinction_backward(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
+int launch_setup_backward(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
+
+}  // namespace es

@@ -1,0 +1,103 @@
+"""C-ABI checks that need no GPU: the library builds and loads, exports every
+entry point that include/exoskry.h declares, the ctypes structures match the
+C layout, and host-side validation rejects bad arguments before any device
+call."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+import __graft_entry__ as entry
+from paper_2602_19687_gb300 import binding, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "exoskry.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    entry.build()
+    return binding.load_library()
+
+
+def header_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:es_status|int64_t|const char \*|void)\s*\**\s*(es_\w+)\(", text, re.M)))
+
+
+def test_header_declares_the_binding_exports():
+    assert header_functions() == sorted(binding.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", binding.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (es_\w+)$", out, re.M))
+    for name in header_functions():
+        assert name in exported, name
+        assert hasattr(lib, name)
+
+
+def test_struct_layout_matches_c_header():
+    src = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "exoskry.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(es_model_desc), offsetof(es_model_desc, theta_fixed),
+         offsetof(es_model_desc, free_idx), sizeof(es_tables_desc), offsetof(es_tables_desc, cia_h2he),
+         offsetof(es_tables_desc, storage));
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "layout.c")
+        exe = os.path.join(d, "layout")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
+    M, T = binding.es_model_desc, binding.es_tables_desc
+    assert vals == [ctypes.sizeof(M), M.theta_fixed.offset, M.free_idx.offset, ctypes.sizeof(T),
+                    T.cia_h2he.offset, T.storage.offset]
+
+
+def test_null_context_calls(lib):
+    assert lib.es_query(None, 0) == -1
+    assert lib.es_last_error(None) == b"NULL context"
+    lib.es_destroy(None)
+    assert lib.es_forward(None, None, None, None, 0, None) == binding.ES_EINVAL
+    assert lib.es_set_grid(None, None, None, 3) == binding.ES_EINVAL
+
+
+@pytest.mark.parametrize("field,value", [("n_layers", 1), ("n_layers", 113), ("n_species", 0),
+                                         ("n_species", 17), ("p_top_bar", -1.0), ("tp_kind", 7),
+                                         ("cloud_kind", 3), ("n_free", 0), ("r_star_cm", 0.0)])
+def test_create_rejects_bad_descriptions_before_touching_cuda(lib, field, value):
+    w = synth.workload("tiny", n_nu=64)
+    d = binding.model_desc(w.model)
+    setattr(d, field, value)
+    h = ctypes.c_void_p()
+    assert lib.es_create(ctypes.byref(h), 0, ctypes.byref(d)) == binding.ES_EINVAL
+    assert not h.value
+
+
+def test_create_rejects_duplicate_or_out_of_range_free_slots(lib):
+    w = synth.workload("tiny", n_nu=64)
+    d = binding.model_desc(w.model)
+    d.free_idx[1] = d.free_idx[0]
+    h = ctypes.c_void_p()
+    assert lib.es_create(ctypes.byref(h), 0, ctypes.byref(d)) == binding.ES_EINVAL
+    d = binding.model_desc(w.model)
+    d.free_idx[0] = 99
+    assert lib.es_create(ctypes.byref(h), 0, ctypes.byref(d)) == binding.ES_EINVAL
+
+
+def test_binding_refuses_to_run_without_the_library(tmp_path):
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        binding._lib = None
+        try:
+            binding.load_library(str(tmp_path / "missing.so"))
+        finally:
+            binding._lib = None
