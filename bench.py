@@ -37,7 +37,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="batched_trans")
-    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain per-sample comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
+    ap.add_argument("--batch", type=int, default=None, help="override the workload's batch size")
     ap.add_argument("--cpu-child", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -193,7 +195,7 @@ def run_gpu(args):
         if world > 1:
             dist.barrier()
 
-    w = synth.workload(args.workload, seed=42 + rank)      # each rank: its own shard of vectors
+    w = synth.workload(args.workload, batch=args.batch, seed=42 + rank)   # each rank: its own shard
     ctx = binding.context_for(w, device=local)
     B = w.theta.shape[0]
     nfree = w.theta.shape[1]
@@ -301,7 +303,7 @@ def run_gpu(args):
                  "workload": "jwst_plain: " + wp.description + " (one vector per call, forward+gradient)"}
         cp.es_destroy()
 
-    cpu = cpu_baseline(args.workload) if rank == 0 else None
+    cpu = cpu_baseline(args.workload) if (rank == 0 and not args.no_cpu) else None
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
