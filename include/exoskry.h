@@ -167,6 +167,25 @@ es_status es_loglike(es_ctx *ctx, double *lnL, int mem, es_stream_t stream);
 es_status es_forward_backward(es_ctx *ctx, double *lnL, double *grad, int mem,
                               es_stream_t stream);
 
+/* ln L of `batch` parameter vectors, like es_set_batch + es_loglike, but
+ * without allocating any device memory: all per-call workspace comes from
+ * one fixed array of 32 MiB built into the library (present on every GPU
+ * that loads the library, until the process exits). The paper has no
+ * counterpart; this is a library convenience for callers that must not call
+ * cudaMalloc on their hot path (code running during CUDA-graph stream
+ * capture, frameworks that own all device memory through their own pool,
+ * or long runs that must not risk an out-of-memory error mid-way).
+ *   theta [batch][n_free] device, kind [batch] device or NULL (all
+ *   transmission), lnL [batch] device; asynchronous on `stream`.
+ * Needs tables, grid and transmission data (and emission data when kind is
+ * given). A batch whose workspace exceeds 32 MiB is rejected with ES_EINVAL
+ * (the message gives the bytes needed). The first call on a device looks up
+ * the array's device address; make that first call before any stream
+ * capture. All calls on a device share the array and leave their contents in
+ * it: calls that overlap on the GPU race and must be serialised. */
+es_status es_loglike_noalloc(es_ctx *ctx, const double *theta, const int32_t *kind, int batch, double *lnL,
+                             es_stream_t stream);
+
 /* Per-sample flags (ES_FLAG_INVALID) of the last forward, int32 [batch]. */
 es_status es_get_flags(es_ctx *ctx, int32_t *flags, int mem, es_stream_t stream);
 

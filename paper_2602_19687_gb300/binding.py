@@ -25,7 +25,8 @@ ES_MAX_LAYERS = 112
 STATUS_NAMES = {0: "ES_OK", 1: "ES_EINVAL", 2: "ES_ENOMEM", 3: "ES_ECUDA", 4: "ES_ESTATE", 5: "ES_ETIMEOUT"}
 
 EXPORTS = ["es_create", "es_load_tables", "es_set_grid", "es_set_data", "es_set_batch", "es_forward",
-           "es_loglike", "es_forward_backward", "es_get_flags", "es_query", "es_set_profiling",
+           "es_loglike", "es_forward_backward", "es_loglike_noalloc", "es_get_flags", "es_query",
+           "es_set_profiling",
            "es_get_profile", "es_last_error", "es_destroy"]
 
 
@@ -71,6 +72,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.es_forward.argtypes = [vp, vp, vp, vp, ip, vp]
     lib.es_loglike.argtypes = [vp, vp, ip, vp]
     lib.es_forward_backward.argtypes = [vp, vp, vp, ip, vp]
+    lib.es_loglike_noalloc.argtypes = [vp, vp, vp, ip, vp, vp]
     lib.es_get_flags.argtypes = [vp, vp, ip, vp]
     lib.es_query.argtypes = [vp, ip]
     lib.es_query.restype = ctypes.c_int64
@@ -205,6 +207,11 @@ class Context:
     def es_forward_backward(self, lnl, grad, stream=None):
         self._check(self.lib.es_forward_backward(self.handle, _ptr(lnl), _ptr(grad), _mem(lnl),
                                                  _stream(stream)), "es_forward_backward")
+
+    def es_loglike_noalloc(self, theta, kind, lnl, stream=None):
+        """ln L without device allocation (theta, kind, lnl: CUDA tensors; kind may be None)."""
+        self._check(self.lib.es_loglike_noalloc(self.handle, _ptr(theta), _ptr(kind), int(theta.shape[0]),
+                                                _ptr(lnl), _stream(stream)), "es_loglike_noalloc")
 
     def es_get_flags(self, flags, stream=None):
         self._check(self.lib.es_get_flags(self.handle, _ptr(flags), _mem(flags), _stream(stream)),

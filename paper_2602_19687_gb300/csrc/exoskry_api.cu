@@ -6,42 +6,10 @@
 #include <string>
 #include <vector>
 
-#include "internal.cuh"
+#include "context.cuh"
 
 using namespace es;
 
-struct es_ctx {
-    int device = 0;
-    es_model_desc desc{};
-    Model m{};
-    Work w{};
-    std::string err = "no error";
-    std::vector<void *> model_bufs;   // freed on destroy
-    std::vector<void *> table_bufs;   // replaced by es_load_tables
-    std::vector<void *> grid_bufs;    // replaced by es_set_grid
-    std::vector<void *> data_bufs;
-    std::vector<void *> work_bufs;    // forward workspace
-    std::vector<void *> bwd_bufs;     // adjoint workspace
-    bool have_tables = false, have_grid = false, have_data[2] = {false, false};
-    int cap_b = 0, cap_b_bwd = 0, batch = 0, n_kind[2] = {0, 0};
-    size_t ws_bytes = 0;
-    int64_t last_launches = 0;
-    std::vector<double> y_host[2], s_host[2];
-    std::vector<double> nu_host;      // FP64 wavenumber grid (bin membership)
-    size_t ymod_cap = 0;
-    double *d_data = nullptr;         // [2][nbins] y_obs then sigma
-    double *d_lnl = nullptr, *d_grad = nullptr;
-    // per-kernel CUDA-event profiling
-    struct ProfEntry { std::string name; double ms = 0.0; int64_t n = 0; };
-    struct Pending { int entry; cudaEvent_t a, b; };
-    bool prof_on = false;
-    std::vector<ProfEntry> prof;
-    std::vector<Pending> pending;
-    std::vector<cudaEvent_t> ev_pool;
-    int open_entry = -1;
-    cudaEvent_t open_ev = nullptr;
-    Hook hook;
-};
 
 namespace {
 
