@@ -150,10 +150,13 @@ def kernel_work(name, w, n_valid):
     m = w.model
     B, L, S, N = n_valid, m.n_layers, m.n_species, w.tables.nu.size
     tri = L * (L + 1) // 2
+    n_t = int(np.sum((w.kind == 0)[:B])) if B else 0
+    n_e = B - n_t
     if name in ("k_extinction", "k_extinction_bwd"):
-        return B * L * (S + 2) * N, "ex2", "alu"
-    if name in ("k_transit", "k_transit_taubar", "k_transit_abar", "k_transit_lbar"):
-        return 2.0 * B * N * tri, "flop", "alu"
+        return n_e * L * (S + 2) * N, "ex2", "alu"
+    if name in ("k_trans_fwd", "k_trans_bwd"):
+        # one ex2 per (vector, layer, species or CIA pair, wavenumber) of the interpolation
+        return n_t * L * (S + 2) * N, "ex2", "alu"
     if name in ("k_emission", "k_emission_bwd"):
         return B * N * L * 4, "layer-angle steps", "alu"
     return None

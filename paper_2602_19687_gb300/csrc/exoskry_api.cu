@@ -169,7 +169,6 @@ es_status alloc_forward(es_ctx *c, int B) {
     ALLOC(w.gtc, B * L);
     ALLOC(w.ccia, B * L * 2);
     ALLOC(w.ray, B * L);
-    ALLOC(w.alpha, (size_t)B * L * N);
     ALLOC(w.spec, (size_t)B * N);
     ALLOC(w.lnl, B);
     ALLOC(w.misc, (size_t)B * 4);
@@ -188,17 +187,34 @@ es_status alloc_backward(es_ctx *c) {
     Work &w = c->w;
     es_status s = ES_OK;
 #define ALLOC(p, n) if ((s = dalloc(c, c->bwd_bufs, &(p), (size_t)(n))) != ES_OK) return s
-    ALLOC(w.dbar, (size_t)B * N);
-    ALLOC(w.taubar, (size_t)B * L * N);
-    ALLOC(w.abar, (size_t)B * L * N);
+    ALLOC(w.dbar, (size_t)B * m.Np);
     ALLOC(w.lbar, (size_t)B * L * L);
-    ALLOC(w.red, (size_t)B * L * (S + N_RED_EXTRA));
+    ALLOC(w.red, (size_t)B * L * N_RED);
+    ALLOC(w.qtot, (size_t)B * S);
     ALLOC(w.areabar, (size_t)B * L);
     ALLOC(w.levbar, (size_t)B * (L + 1));
     ALLOC(w.drbar, (size_t)B * L);
     ALLOC(w.grad, (size_t)B * c->m.nfree);
 #undef ALLOC
     c->cap_b_bwd = B;
+    return ES_OK;
+}
+
+// Large per-kind buffers, allocated on first need and kept until the batch
+// capacity grows: alpha/abar for emission samples, estore for the
+// transmission adjoint.
+es_status ensure_big(es_ctx *c, float **p, size_t &cap, size_t count) {
+    if (count <= cap && *p) return ES_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    cap = 0;
+    void *q = nullptr;
+    if (cudaMalloc(&q, count * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, ES_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(float)) + " bytes failed");
+    }
+    *p = static_cast<float *>(q);
+    cap = count;
     return ES_OK;
 }
 
@@ -215,16 +231,24 @@ es_status ready(es_ctx *c) {
 // forward sequence; adjoint=true also prepares dbar / misc for the backward
 es_status run_forward(es_ctx *c, bool adjoint, float *spec_out, double *binned_out, double *lnl_out,
                       cudaStream_t st) {
+    es_status s;
+    const size_t big = (size_t)c->batch * c->m.L * c->m.N;
+    if (c->n_kind[1] && (s = ensure_big(c, &c->w.alpha, c->alpha_cap, big)) != ES_OK) return s;
+    if (adjoint && c->n_kind[0] &&
+        (s = ensure_big(c, &c->w.estore, c->estore_cap, (size_t)c->batch * c->m.L * c->m.Np)) != ES_OK)
+        return s;
     Work w = c->w;
     w.B = c->batch;
     int launches = 0;
     const Hook &h = c->hook;
     launches += launch_setup(c->m, w, st, h);
-    launches += launch_extinction(c->m, w, st, h);
-    if (c->n_kind[0]) launches += launch_transit(c->m, w, st, h);
-    if (c->n_kind[1]) launches += launch_emission(c->m, w, st, h);
+    if (c->n_kind[0]) launches += launch_trans_fused_forward(c->m, w, adjoint, st, h);
+    if (c->n_kind[1]) {
+        launches += launch_extinction(c->m, w, ES_KIND_EMISSION, st, h);
+        launches += launch_emission(c->m, w, st, h);
+    }
     if (adjoint) {
-        cudaMemsetAsync(w.dbar, 0, sizeof(float) * (size_t)w.B * c->m.N, st);
+        cudaMemsetAsync(w.dbar, 0, sizeof(float) * (size_t)w.B * c->m.Np, st);
     }
     launches += launch_bins(c->m, w, adjoint, spec_out, binned_out, lnl_out, st, h);
     c->last_launches = launches;
@@ -346,45 +370,56 @@ es_status es_load_tables(es_ctx *c, const es_tables_desc *t) {
     m.NTc = t->n_t_cia;
     m.bf16 = t->storage == ES_TABLE_BF16;
     c->nu_host.assign(t->nu, t->nu + t->n_nu);
-    const size_t N = m.N, S = m.S, rows = S * m.NT * m.NP;
+    // device rows are padded to Np (a multiple of 128, the widest tile) by
+    // repeating the last value, so the last tile's loads stay inside their row
+    m.Np = (m.N + 127) / 128 * 128;
+    const size_t N = m.N, Np = m.Np, S = m.S, rows = S * m.NT * m.NP;
     es_status s;
     std::vector<float> off(rows, 0.f);
     if (m.bf16) {
-        std::vector<uint16_t> q(rows * N);
+        std::vector<uint16_t> q(rows * Np);
         for (size_t r = 0; r < rows; ++r) {
             const float *src = t->log10_sigma + r * N;
             double mean = 0.0;
             for (size_t n = 0; n < N; ++n) mean += src[n];
             float o = (float)(mean / (double)N);
             off[r] = o;
-            for (size_t n = 0; n < N; ++n) q[r * N + n] = to_bf16_rne(src[n] - o);
+            for (size_t n = 0; n < Np; ++n) q[r * Np + n] = to_bf16_rne(src[n < N ? n : N - 1] - o);
         }
         uint16_t *d16;
         if ((s = upload(c, c->table_bufs, &d16, q.data(), q.size())) != ES_OK) return s;
         m.tab16 = d16;
         m.tab32 = nullptr;
     } else {
+        std::vector<float> q(rows * Np);
+        for (size_t r = 0; r < rows; ++r)
+            for (size_t n = 0; n < Np; ++n) q[r * Np + n] = t->log10_sigma[r * N + (n < N ? n : N - 1)];
         float *d32;
-        if ((s = upload(c, c->table_bufs, &d32, t->log10_sigma, rows * N)) != ES_OK) return s;
+        if ((s = upload(c, c->table_bufs, &d32, q.data(), q.size())) != ES_OK) return s;
         m.tab32 = d32;
         m.tab16 = nullptr;
     }
     float *df;
     if ((s = upload(c, c->table_bufs, &df, off.data(), rows)) != ES_OK) return s;
     m.row_off = df;
-    std::vector<float> cia(2 * (size_t)m.NTc * N);
-    std::memcpy(cia.data(), t->cia_h2h2, sizeof(float) * m.NTc * N);
-    std::memcpy(cia.data() + (size_t)m.NTc * N, t->cia_h2he, sizeof(float) * m.NTc * N);
+    std::vector<float> cia(2 * (size_t)m.NTc * Np);
+    for (int pair = 0; pair < 2; ++pair) {
+        const float *src = pair ? t->cia_h2he : t->cia_h2h2;
+        for (size_t r = 0; r < (size_t)m.NTc; ++r)
+            for (size_t n = 0; n < Np; ++n)
+                cia[((size_t)pair * m.NTc + r) * Np + n] = src[r * N + (n < N ? n : N - 1)];
+    }
     if ((s = upload(c, c->table_bufs, &df, cia.data(), cia.size())) != ES_OK) return s;
     m.cia = df;
-    std::vector<float> nuf(N), ifs(N);
-    for (size_t n = 0; n < N; ++n) {
-        nuf[n] = (float)t->nu[n];
-        ifs[n] = (float)(1.0 / (PI * planck_host(t->nu[n], m.t_star)));
+    std::vector<float> nuf(Np), ifs(Np);
+    for (size_t n = 0; n < Np; ++n) {
+        const double nv = t->nu[n < N ? n : N - 1];
+        nuf[n] = (float)nv;
+        ifs[n] = (float)(1.0 / (PI * planck_host(nv, m.t_star)));
     }
-    if ((s = upload(c, c->table_bufs, &df, nuf.data(), N)) != ES_OK) return s;
+    if ((s = upload(c, c->table_bufs, &df, nuf.data(), Np)) != ES_OK) return s;
     m.nu = df;
-    if ((s = upload(c, c->table_bufs, &df, ifs.data(), N)) != ES_OK) return s;
+    if ((s = upload(c, c->table_bufs, &df, ifs.data(), Np)) != ES_OK) return s;
     m.inv_fstar = df;
     std::vector<double> logt(m.NT), logp(m.NP);
     for (int i = 0; i < m.NT; ++i) logt[i] = std::log10(t->t_grid[i]);
@@ -602,18 +637,24 @@ es_status es_forward_backward(es_ctx *c, double *lnl, double *grad, int mem, es_
     w.B = B;
     double *d_lnl = (mem == ES_MEM_HOST || !lnl) ? c->d_lnl : lnl;
     const size_t L = m.L, S = m.S;
-    cudaMemsetAsync(w.red, 0, sizeof(double) * B * L * (S + N_RED_EXTRA), st);
+    cudaMemsetAsync(w.red, 0, sizeof(double) * B * L * N_RED, st);
+    cudaMemsetAsync(w.qtot, 0, sizeof(double) * B * S, st);
     cudaMemsetAsync(w.areabar, 0, sizeof(double) * B * L, st);
     cudaMemsetAsync(w.levbar, 0, sizeof(double) * B * (L + 1), st);
     cudaMemsetAsync(w.drbar, 0, sizeof(double) * B * L, st);
     cudaMemsetAsync(w.lbar, 0, sizeof(double) * B * L * L, st);
+    if (c->n_kind[1] && (s = ensure_big(c, &c->w.abar, c->abar_cap, (size_t)B * L * m.N)) != ES_OK) return s;
     s = run_forward(c, true, nullptr, nullptr, d_lnl, st);
     if (s != ES_OK) return s;
+    w = c->w;
+    w.B = B;
     int launches = (int)c->last_launches;
     const Hook &h = c->hook;
-    if (c->n_kind[0]) launches += launch_transit_backward(m, w, st, h);
-    if (c->n_kind[1]) launches += launch_emission_backward(m, w, st, h);
-    launches += launch_extinction_backward(m, w, st, h);
+    if (c->n_kind[0]) launches += launch_trans_fused_backward(m, w, st, h);
+    if (c->n_kind[1]) {
+        launches += launch_emission_backward(m, w, st, h);
+        launches += launch_extinction_backward(m, w, ES_KIND_EMISSION, st, h);
+    }
     launches += launch_setup_backward(m, w, st, h);
     c->last_launches = launches;
     if ((s = check_launch(c, "backward launch")) != ES_OK) return s;
@@ -698,6 +739,9 @@ void es_destroy(es_ctx *c) {
     free_all(c->table_bufs);
     free_all(c->model_bufs);
     if (c->w.ymod) cudaFree(c->w.ymod);
+    if (c->w.alpha) cudaFree(c->w.alpha);
+    if (c->w.abar) cudaFree(c->w.abar);
+    if (c->w.estore) cudaFree(c->w.estore);
     prof_resolve(c);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;

@@ -58,7 +58,7 @@ struct Carver {
 };
 
 // Lay out the forward workspace of a batch of B vectors; returns bytes needed.
-size_t carve(const es::Model &m, int B, unsigned char *base, es::Work &w, int **kind_slot) {
+size_t carve(const es::Model &m, int B, bool emission, unsigned char *base, es::Work &w, int **kind_slot) {
     Carver c{base};
     const size_t L = m.L, S = m.S, N = m.N;
     w.B = B;
@@ -86,7 +86,7 @@ size_t carve(const es::Model &m, int B, unsigned char *base, es::Work &w, int **
     w.gtc = c.take<float>(B * L);
     w.ccia = c.take<float>(B * L * 2);
     w.ray = c.take<float>(B * L);
-    w.alpha = c.take<float>((size_t)B * L * N);
+    w.alpha = emission ? c.take<float>((size_t)B * L * N) : nullptr;   // extinction of emission samples
     w.spec = c.take<float>((size_t)B * N);
     w.ymod = c.take<double>((size_t)B * m.nbins);
     w.lnl = c.take<double>(B);
@@ -112,7 +112,7 @@ extern "C" es_status es_loglike_noalloc(es_ctx *c, const double *theta, const in
     if (c->device < 0 || c->device >= MAX_DEVICES) return fail(c, ES_EINVAL, "device ordinal too large");
     es::Work w{};
     int *kind_slot = nullptr;
-    const size_t need = carve(c->m, batch, nullptr, w, &kind_slot);
+    const size_t need = carve(c->m, batch, kind != nullptr, nullptr, w, &kind_slot);
     if (need > NOALLOC_SCRATCH_BYTES)
         return fail(c, ES_EINVAL,
                     "es_loglike_noalloc: batch of " + std::to_string(batch) + " needs " + std::to_string(need) +
@@ -122,7 +122,7 @@ extern "C" es_status es_loglike_noalloc(es_ctx *c, const double *theta, const in
     unsigned char *base = nullptr;
     if (e == cudaSuccess) e = scratch_address(c->device, &base);
     if (e != cudaSuccess) return fail(c, ES_ECUDA, std::string("scratch address: ") + cudaGetErrorString(e));
-    carve(c->m, batch, base, w, &kind_slot);
+    carve(c->m, batch, kind != nullptr, base, w, &kind_slot);
     w.theta_user = theta;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (kind) {
@@ -135,9 +135,11 @@ extern "C" es_status es_loglike_noalloc(es_ctx *c, const double *theta, const in
     const es::Hook none{};
     int launches = 0;
     launches += es::launch_setup(c->m, w, st, none);
-    launches += es::launch_extinction(c->m, w, st, none);
-    launches += es::launch_transit(c->m, w, st, none);
-    if (kind) launches += es::launch_emission(c->m, w, st, none);
+    launches += es::launch_trans_fused_forward(c->m, w, false, st, none);
+    if (kind) {
+        launches += es::launch_extinction(c->m, w, ES_KIND_EMISSION, st, none);
+        launches += es::launch_emission(c->m, w, st, none);
+    }
     launches += es::launch_bins(c->m, w, false, nullptr, nullptr, lnl, st, none);
     c->last_launches = launches;
     e = cudaGetLastError();

@@ -1,0 +1,325 @@
+// Building blocks of the fused per-tile kernels: warp-level BF16 tensor-core
+// MMA (split-precision), packed FP32x2 arithmetic, and the register-cached
+// opacity interpolation of one 64-wavenumber tile.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+
+namespace es {
+
+constexpr int FT = 64;            // wavenumbers per tile
+constexpr int FWARPS = 8;         // warps per fused block
+constexpr int FTHREADS = FWARPS * 32;
+constexpr int LP = 112;           // layers padded to 7 x 16 (tensor-core K/M blocks)
+constexpr int LPW = 14;           // max layers per warp (LP / FWARPS)
+constexpr int SCH = 4;            // species per register-cached chunk
+constexpr float KSHIFT = 64.f;    // log2 scale folded into the species exponents
+constexpr int L_PITCH = 120;      // bf16 pitch of [112][112] path-matrix rows (240 B: 15 x 16 B)
+constexpr int R_PITCH = 72;       // bf16 pitch of [row][64 nu] operand rows (144 B: 9 x 16 B)
+
+// ------------------------------------------------------------ packed FP32x2
+#ifndef ES_PACKED_F32X2
+#define ES_PACKED_F32X2 1
+#endif
+#if ES_PACKED_F32X2
+__device__ __forceinline__ unsigned long long pk(float2 a) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+    return r;
+}
+__device__ __forceinline__ float2 upk(unsigned long long v) {
+    float2 a;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(v));
+    return a;
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)), "l"(pk(c)));
+    return upk(d);
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+    return upk(d);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+    return upk(d);
+}
+#else
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return make_float2(a.x * b.x, a.y * b.y); }
+#endif
+__device__ __forceinline__ float ex2f(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float2 ex2x2(float2 x) { return make_float2(ex2f(x.x), ex2f(x.y)); }
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+
+// ------------------------------------------------------------ BF16 split and tensor cores
+// x = hi + lo with hi, lo BF16 (hi round-to-nearest, lo the rounded residual)
+__device__ __forceinline__ void split2(float2 x, uint32_t &hi, uint32_t &lo) {
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(x.y), "f"(x.x));
+    float hx = __uint_as_float(hi << 16), hy = __uint_as_float(hi & 0xffff0000u);
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(x.y - hy), "f"(x.x - hx));
+}
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void ldsm_x4(uint32_t a, uint32_t (&r)[4]) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t a, uint32_t (&r)[4]) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t a, uint32_t (&r)[2]) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2_t(uint32_t a, uint32_t (&r)[2]) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];"
+                 : "=r"(r[0]), "=r"(r[1]) : "r"(a));
+}
+// D += A B, m16n8k16, BF16 inputs, FP32 accumulation
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+// split-precision product: (Ah + Al)(Bh + Bl) ~ Ah Bh + Ah Bl + Al Bh
+__device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4],
+                                     const uint32_t (&bh)[2], const uint32_t (&bl)[2]) {
+    mma16816(d, al, bh);
+    mma16816(d, ah, bl);
+    mma16816(d, ah, bh);
+}
+
+// Address of lane's ldmatrix row for an A fragment (m16 x k16) of a row-major
+// [m][k] BF16 array with `pitch` elements per row.
+__device__ __forceinline__ uint32_t a_addr(uint32_t base, int pitch, int m0, int k0, int lane) {
+    return base + 2u * (uint32_t)((m0 + (lane & 15)) * pitch + k0 + ((lane >> 4) << 3));
+}
+// A fragment (m16 x k16) of A = S^T where S is stored row-major [k][m] (ldmatrix .trans)
+__device__ __forceinline__ uint32_t at_addr(uint32_t base, int pitch, int m0, int k0, int lane) {
+    const int q = lane >> 3, r = lane & 7;   // matrix q: (k half, m half) = (q>>1, q&1)
+    return base + 2u * (uint32_t)((k0 + ((q >> 1) << 3) + r) * pitch + m0 + ((q & 1) << 3));
+}
+// B fragment (k16 x n8) from a row-major [n][k] array (ldmatrix, non-trans)
+__device__ __forceinline__ uint32_t b_addr(uint32_t base, int pitch, int n0, int k0, int lane) {
+    const int l = lane & 15;
+    return base + 2u * (uint32_t)((n0 + (l & 7)) * pitch + k0 + ((l >> 3) << 3));
+}
+// B fragment (k16 x n8) from a row-major [k][n] array (ldmatrix .trans)
+__device__ __forceinline__ uint32_t bt_addr(uint32_t base, int pitch, int n0, int k0, int lane) {
+    const int l = lane & 15;
+    return base + 2u * (uint32_t)((k0 + l) * pitch + n0);
+}
+
+// ------------------------------------------------------------ per-sample constants
+struct __align__(16) LayerConst {
+    int it, ip, itc, cell;   // temperature / pressure / CIA brackets; cell = it * NP + ip
+    float wt, wp, wtc;       // raw interpolation weights
+    float nsc;               // n_l 2^-KSHIFT
+    float cc1, cc2;          // log2(n^2 X_H2^2), log2(n^2 X_H2 X_He)
+    float ray;               // n (X_H2 s_H2 + X_He s_He) / nu_ref^4
+    float gt, gtc;           // 1/dlog10T and 1/dT of the brackets (0 where clamped)
+    float pad[3];
+};
+
+struct SampleConst {
+    LayerConst lay[ES_MAX_LAYERS];
+    float lx[ES_MAX_SPECIES];   // log2 X_s + KSHIFT
+};
+
+// All threads of the block: per-layer constants of sample b into shared memory.
+__device__ inline void stage_sample(const Model &m, const Work &w, int b, SampleConst &sc) {
+    const float ry = (float)(1.0 / ((double)m.ray_nu_ref * m.ray_nu_ref * m.ray_nu_ref * m.ray_nu_ref));
+    for (int l = threadIdx.x; l < m.L; l += blockDim.x) {
+        const size_t bl = (size_t)b * m.L + l;
+        LayerConst c;
+        c.it = w.it[bl];
+        c.ip = m.ip[l];
+        c.itc = w.itc[bl];
+        c.cell = c.it * m.NP + c.ip;
+        c.wt = w.wtr[bl];
+        c.wp = m.wp[l];
+        c.wtc = w.wtc[bl];
+        c.nsc = (float)(w.n_lay[bl] * 5.421010862427522e-20);   // 2^-64
+        c.cc1 = w.ccia[2 * bl];
+        c.cc2 = w.ccia[2 * bl + 1];
+        c.ray = w.ray[bl] * ry;
+        c.gt = w.gt[bl];
+        c.gtc = w.gtc[bl];
+        c.pad[0] = c.pad[1] = c.pad[2] = 0.f;
+        sc.lay[l] = c;
+    }
+    for (int s = threadIdx.x; s < m.S; s += blockDim.x) {
+        const double x = w.xs[(size_t)b * (m.S + 2) + s];
+        sc.lx[s] = (x > 0.0) ? (float)(log2(x) + KSHIFT) : -1000.f;
+    }
+}
+
+// Layers handled by warp `warp` (contiguous ranges; at most LPW each).
+__device__ __forceinline__ void warp_layers(int L, int warp, int &lb, int &le) {
+    const int per = (L + FWARPS - 1) / FWARPS;
+    lb = warp * per;
+    le = min(L, lb + per);
+}
+
+// ------------------------------------------------------------ interpolation
+template <bool BF16>
+__device__ __forceinline__ float2 tab_pair(const Model &m, size_t idx) {
+    if (BF16) {
+        const uint32_t v = __ldg(reinterpret_cast<const unsigned int *>(m.tab16 + idx));
+        return make_float2(__uint_as_float(v << 16), __uint_as_float(v & 0xffff0000u));
+    }
+    return __ldg(reinterpret_cast<const float2 *>(m.tab32 + idx));
+}
+
+// Species-exponent coefficients of one cell for the lane's wavenumber pair:
+//   e = a0 + wp a1 + wt (a2 + wp a3) = log2(X_s sigma) + KSHIFT
+template <bool BF16>
+__device__ __forceinline__ void load_cell(const Model &m, int s, int it, int ip, int n, float lx, float2 &a0,
+                                          float2 &a1, float2 &a2, float2 &a3) {
+    const size_t row = ((size_t)s * m.NT + it) * m.NP + ip;
+    const size_t st = (size_t)m.Np;
+    const size_t r00 = row * st + n, r01 = r00 + st, r10 = r00 + (size_t)m.NP * st, r11 = r10 + st;
+    const float *off = m.row_off + row;
+    const float o00 = __ldg(off), o01 = __ldg(off + 1), o10 = __ldg(off + m.NP), o11 = __ldg(off + m.NP + 1);
+    float2 v00 = tab_pair<BF16>(m, r00), v01 = tab_pair<BF16>(m, r01);
+    float2 v10 = tab_pair<BF16>(m, r10), v11 = tab_pair<BF16>(m, r11);
+    v00 = add2(v00, f2(o00));
+    v01 = add2(v01, f2(o01));
+    v10 = add2(v10, f2(o10));
+    v11 = add2(v11, f2(o11));
+    const float2 c = f2((float)LOG2_10);
+    const float2 d0 = add2(v01, make_float2(-v00.x, -v00.y));
+    a0 = fma2(c, v00, f2(lx));
+    a1 = mul2(c, d0);
+    a2 = mul2(c, add2(v10, make_float2(-v00.x, -v00.y)));
+    a3 = mul2(c, add2(add2(v11, make_float2(-v10.x, -v10.y)), make_float2(-d0.x, -d0.y)));
+}
+
+// CIA coefficients of one temperature bracket: e = b + wtc d + cc
+__device__ __forceinline__ void load_cia(const Model &m, int pair, int itc, int n, float2 &b, float2 &d) {
+    const size_t st = (size_t)m.Np;
+    const float *base = m.cia + ((size_t)pair * m.NTc + itc) * st + n;
+    const float2 k0 = __ldg(reinterpret_cast<const float2 *>(base));
+    const float2 k1 = __ldg(reinterpret_cast<const float2 *>(base + st));
+    const float2 c = f2((float)LOG2_10);
+    b = mul2(c, k0);
+    d = mul2(c, add2(k1, make_float2(-k0.x, -k0.y)));
+}
+
+constexpr int SCACHE = 8;   // species whose cell coefficients stay in registers
+
+// Per-lane interpolation state for one sample and one wavenumber pair: the
+// coefficients of the current (T, p) cell for the first SCACHE species and of
+// the current CIA temperature bracket. Cells change only every few layers.
+template <bool BF16>
+struct PairInterp {
+    float2 a0[SCACHE], a1[SCACHE], a2[SCACHE], a3[SCACHE];
+    float2 b1, d1, b2, d2, nu4;
+    int cell = -1, itc = -1;
+
+    __device__ __forceinline__ void init(const Model &m, int n) {
+        const float2 nu = __ldg(reinterpret_cast<const float2 *>(m.nu + n));
+        const float2 nu2 = mul2(nu, nu);
+        nu4 = mul2(nu2, nu2);
+        cell = itc = -1;
+    }
+    // L1 prefetch of the table rows of the next layer's cell when it differs
+    __device__ __forceinline__ void prefetch(const Model &m, const LayerConst &cur, const LayerConst &next, int n) const {
+        if (next.cell == cur.cell) return;
+        const size_t st = (size_t)m.Np;
+        const size_t esz = m.bf16 ? 2 : 4;
+        const char *base = m.bf16 ? reinterpret_cast<const char *>(m.tab16) : reinterpret_cast<const char *>(m.tab32);
+#pragma unroll
+        for (int j = 0; j < SCACHE; ++j) {
+            if (j < m.S) {
+                const size_t r00 = (((size_t)j * m.NT + next.it) * m.NP + next.ip) * st + n;
+                const size_t r10 = r00 + (size_t)m.NP * st;
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(base + r00 * esz));
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(base + (r00 + st) * esz));
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(base + r10 * esz));
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(base + (r10 + st) * esz));
+            }
+        }
+    }
+    __device__ __forceinline__ void update(const Model &m, const SampleConst &sc, const LayerConst &lc, int n) {
+        if (lc.cell != cell) {
+            cell = lc.cell;
+#pragma unroll
+            for (int j = 0; j < SCACHE; ++j)
+                if (j < m.S) load_cell<BF16>(m, j, lc.it, lc.ip, n, sc.lx[j], a0[j], a1[j], a2[j], a3[j]);
+        }
+        if (lc.itc != itc) {
+            itc = lc.itc;
+            load_cia(m, 0, lc.itc, n, b1, d1);
+            load_cia(m, 1, lc.itc, n, b2, d2);
+        }
+    }
+    // exponent of species j (cached): e = a0 + wp a1 + wt (a2 + wp a3); t = de/dwt
+    __device__ __forceinline__ float2 expo(int j, float2 wp, float2 wt, float2 &t) const {
+        t = fma2(wp, a3[j], a2[j]);
+        return fma2(wt, t, fma2(wp, a1[j], a0[j]));
+    }
+};
+
+// Exponent of an uncached species (s >= SCACHE), loading its cell each call.
+template <bool BF16>
+__device__ __forceinline__ float2 expo_uncached(const Model &m, const SampleConst &sc, const LayerConst &lc, int s,
+                                                int n, float2 wp, float2 wt, float2 &t) {
+    float2 a0, a1, a2, a3;
+    load_cell<BF16>(m, s, lc.it, lc.ip, n, sc.lx[s], a0, a1, a2, a3);
+    t = fma2(wp, a3, a2);
+    return fma2(wt, t, fma2(wp, a1, a0));
+}
+
+// Extinction alpha_l(nu) at the lane's wavenumber pair for the warp's layers
+// [lb, le):  alpha = n 2^-K sum_s 2^e_s + CIA_H2H2 + CIA_H2He + Rayleigh.
+// Calls out(l, alpha) for each layer.
+template <bool BF16, class Out>
+__device__ __forceinline__ void extinction_pair(const Model &m, const SampleConst &sc, int lb, int le, int n,
+                                                Out &&out) {
+    PairInterp<BF16> pi;
+    pi.init(m, n);
+    for (int l = lb; l < le; ++l) {
+        const LayerConst &lc = sc.lay[l];
+        pi.update(m, sc, lc, n);
+        if (l + 1 < le) pi.prefetch(m, lc, sc.lay[l + 1], n);
+        const float2 wp = f2(lc.wp), wt = f2(lc.wt);
+        float2 sum = f2(0.f), t;
+#pragma unroll
+        for (int j = 0; j < SCACHE; ++j)
+            if (j < m.S) sum = add2(sum, ex2x2(pi.expo(j, wp, wt, t)));
+        for (int s = SCACHE; s < m.S; ++s) sum = add2(sum, ex2x2(expo_uncached<BF16>(m, sc, lc, s, n, wp, wt, t)));
+        const float2 wc = f2(lc.wtc);
+        const float2 c1 = ex2x2(fma2(wc, pi.d1, add2(pi.b1, f2(lc.cc1))));
+        const float2 c2 = ex2x2(fma2(wc, pi.d2, add2(pi.b2, f2(lc.cc2))));
+        const float2 base = fma2(f2(lc.ray), pi.nu4, add2(c1, c2));
+        out(l, fma2(sum, f2(lc.nsc), base));
+    }
+}
+
+// Adjoint reductions of one layer for the lane's pair, with abar = d lnL / d alpha:
+// Q_s = sum abar e_s (species), D = sum abar sum_s e_s dlog10(sigma_s)/dlog10 T,
+// C1, C2, C1T, C2T (CIA and their temperature slopes), W4 = sum abar (nu/nu_ref)^4.
+// Values are reduced over the warp and added to red[l][*] (shared, one warp per layer).
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace es

@@ -32,12 +32,15 @@ constexpr double C2_RAD = H_PLANCK * C_LIGHT / K_B;
 constexpr double TWO_HC2 = 2.0 * H_PLANCK * C_LIGHT * C_LIGHT;
 // number of Gauss-Legendre angles for the emission flux integral
 constexpr int N_MU = 4;
-// reductions per (sample, layer) in the extinction adjoint (after S species)
-constexpr int N_RED_EXTRA = 6;   // D, C1, C2, C1T, C2T, W4
+// reductions per (sample, layer) in the extinction adjoint:
+// QS (sum over species of Q_s), D, C1, C2, C1T, C2T, W4; per-species totals
+// over layers go to Work::qtot
+constexpr int N_RED = 7;
 
 // Constant model data, passed by value to every kernel.
 struct Model {
     int L, S, NT, NP, NTc, N, nbins, nfree, nfull;
+    int Np;                       // padded row stride of tables and per-wavenumber arrays (N rounded up to 128)
     int tp_kind, cloud_kind, bf16;
     double p_ref;                 // dyn cm^-2
     double r_star, t_star;
@@ -52,12 +55,12 @@ struct Model {
     const float *wp;              // [L] pressure weight of each layer
     const double *log_t;          // [NT] log10 of the temperature grid
     const double *cia_t;          // [NTc]
-    const float *tab32;           // [S][NT][NP][N]
-    const uint16_t *tab16;        // [S][NT][NP][N] BF16 residuals
+    const float *tab32;           // [S][NT][NP][Np]
+    const uint16_t *tab16;        // [S][NT][NP][Np] BF16 residuals
     const float *row_off;         // [S][NT][NP] (zeros for FP32 tables)
-    const float *cia;             // [2][NTc][N] log10 k
-    const float *nu;              // [N]
-    const float *inv_fstar;       // [N] 1 / (pi B(T_*, nu))
+    const float *cia;             // [2][NTc][Np] log10 k
+    const float *nu;              // [Np]
+    const float *inv_fstar;       // [Np] 1 / (pi B(T_*, nu))
     const int *bin_lo, *bin_hi;   // [nbins] native index ranges [lo, hi)
     const int *bin_of;            // [N] bin of each native point or -1
     const double *y_obs, *sigma;  // [2][nbins]
@@ -85,16 +88,17 @@ struct Work {
     float *wtc, *gtc;             // [B][L] CIA weight, 1/dT (0 if clamped)
     float *ccia;                  // [B][L][2] log2(n^2 X_H2 X_H2), log2(n^2 X_H2 X_He)
     float *ray;                   // [B][L] n (X_H2 s_H2 + X_He s_He)
-    float *alpha;                 // [B][L][N]
+    float *alpha;                 // [B][L][N] (emission samples)
     float *spec;                  // [B][N] transmission: depth - base; emission: Fp/F*
     double *ymod;                 // [B][nbins]
     double *lnl;                  // [B]
     // adjoint
-    float *dbar;                  // [B][N] d lnL / d spec
-    float *taubar;                // [B][L][N]
-    float *abar;                  // [B][L][N] d lnL / d alpha
+    float *dbar;                  // [B][Np] d lnL / d spec (zero beyond N)
+    float *estore;                // [B][L][Np] exp(-tau) of the forward (transmission adjoint)
+    float *abar;                  // [B][L][N] d lnL / d alpha (emission samples)
     double *lbar;                 // [B][L][L]
-    double *red;                  // [B][L][S+N_RED_EXTRA]
+    double *red;                  // [B][L][N_RED]
+    double *qtot;                 // [B][S] per-species reductions summed over layers
     double *areabar;              // [B][L]
     double *levbar;               // [B][L+1] d lnL / d T_lev (emission)
     double *drbar;                // [B][L]   d lnL / d dr (emission)
@@ -119,14 +123,14 @@ struct Hook {
 
 // kernel launchers (each returns the number of kernels launched)
 int launch_setup(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
-int launch_extinction(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
-int launch_transit(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
+int launch_extinction(const Model &m, const Work &w, int only_kind, cudaStream_t st, const Hook &h);
+int launch_trans_fused_forward(const Model &m, const Work &w, bool store_e, cudaStream_t st, const Hook &h);
+int launch_trans_fused_backward(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
 int launch_emission(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
 int launch_bins(const Model &m, const Work &w, bool want_adjoint, float *spectrum_out,
                 double *binned_out, double *lnl_out, cudaStream_t st, const Hook &h);
-int launch_transit_backward(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
 int launch_emission_backward(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
-int launch_extinction_backward(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
+int launch_extinction_backward(const Model &m, const Work &w, int only_kind, cudaStream_t st, const Hook &h);
 int launch_setup_backward(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
 
 }  // namespace es

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(BIN_THREADS) k_bins(Model m, Work w, int adjoi
             const int lo = m.bin_lo[k], hi = m.bin_hi[k];
             const double se2 = sg[k] * sg[k] + infl;
             const float g = (float)((yo[k] - w.ymod[(size_t)b * m.nbins + k]) / se2 / (double)(hi - lo));
-            for (int n = lo; n < hi; ++n) w.dbar[(size_t)b * N + n] = g;
+            for (int n = lo; n < hi; ++n) w.dbar[(size_t)b * m.Np + n] = g;
         }
     }
     if (spec_out)

@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(EM_THREADS) k_emission_bwd(Model m, Work w) {
     float flux = 0.f;
 #pragma unroll
     for (int j = 0; j < N_MU; ++j) flux = fmaf((float)(2.0 * PI * m.w_gl[j] * m.mu_gl[j]), ist[0][j], flux);
-    const float db = live ? w.dbar[(size_t)b * N + n] : 0.f;
+    const float db = live ? w.dbar[(size_t)b * m.Np + n] : 0.f;
     const float sc = (float)w.scale[b];
     const float fbar = db * sc * m.inv_fstar[nn];
     float sbar = db * flux * m.inv_fstar[nn];

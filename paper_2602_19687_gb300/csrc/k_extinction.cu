@@ -28,8 +28,9 @@ __device__ __forceinline__ float tab_load(const Model &m, size_t idx) {
 }
 
 template <bool BF16>
-__global__ void __launch_bounds__(EXT_THREADS) k_extinction(Model m, Work w) {
+__global__ void __launch_bounds__(EXT_THREADS) k_extinction(Model m, Work w, int only_kind) {
     const int b = blockIdx.y;
+    if (only_kind >= 0 && w.kind[b] != only_kind) return;
     const int n = blockIdx.x * EXT_THREADS + threadIdx.x;
     const int L = m.L, S = m.S, N = m.N;
     __shared__ float4 s_w4[ES_MAX_LAYERS];
@@ -52,8 +53,8 @@ __global__ void __launch_bounds__(EXT_THREADS) k_extinction(Model m, Work w) {
     if (n >= N) return;
     const float nf = m.nu[n] / (float)m.ray_nu_ref;
     const float nu4 = (nf * nf) * (nf * nf);
-    const size_t strideP = N, strideT = (size_t)m.NP * N, strideS = (size_t)m.NT * strideT;
-    const float *cia1 = m.cia + n, *cia2 = m.cia + (size_t)m.NTc * N + n;
+    const size_t strideP = m.Np, strideT = (size_t)m.NP * m.Np, strideS = (size_t)m.NT * strideT;
+    const float *cia1 = m.cia + n, *cia2 = m.cia + (size_t)m.NTc * m.Np + n;
     float *out = w.alpha + (size_t)b * L * N + n;
     for (int l = 0; l < L; ++l) {
         const float4 wv = s_w4[l];
@@ -66,11 +67,11 @@ __global__ void __launch_bounds__(EXT_THREADS) k_extinction(Model m, Work w) {
             float e = fmaf(wv.x, q00, fmaf(wv.y, q01, fmaf(wv.z, q10, fmaf(wv.w, q11, s_coef[l * S + s]))));
             acc += ex2(e);
         }
-        const size_t c = (size_t)s_itc[l] * N;
-        float k0 = __ldg(cia1 + c), k1 = __ldg(cia1 + c + N);
+        const size_t c = (size_t)s_itc[l] * m.Np;
+        float k0 = __ldg(cia1 + c), k1 = __ldg(cia1 + c + m.Np);
         acc += ex2(fmaf((float)LOG2_10, fmaf(s_wtc[l], k1 - k0, k0), s_cc[2 * l]));
         k0 = __ldg(cia2 + c);
-        k1 = __ldg(cia2 + c + N);
+        k1 = __ldg(cia2 + c + m.Np);
         acc += ex2(fmaf((float)LOG2_10, fmaf(s_wtc[l], k1 - k0, k0), s_cc[2 * l + 1]));
         acc = fmaf(s_ray[l], nu4, acc);
         out[(size_t)l * N] = acc;
@@ -97,19 +98,20 @@ __device__ __forceinline__ float block_sum(float v, float *scratch) {
 //   C2T = sum abar c2 dlog10k2/dT, W4 = sum abar (nu/nu_ref)^4,
 // where e_s, c1, c2 are the species and CIA extinction terms.
 template <bool BF16>
-__global__ void __launch_bounds__(EXT_THREADS) k_extinction_bwd(Model m, Work w) {
+__global__ void __launch_bounds__(EXT_THREADS) k_extinction_bwd(Model m, Work w, int only_kind) {
     const int b = blockIdx.y;
-    const int L = m.L, S = m.S, N = m.N, NR = S + N_RED_EXTRA;
+    if (only_kind >= 0 && w.kind[b] != only_kind) return;
+    const int L = m.L, S = m.S, N = m.N, NR = S + N_RED - 1;
     const int n0 = blockIdx.x * EXT_THREADS * BWD_NU_PER_THREAD + threadIdx.x;
     __shared__ float scratch[EXT_THREADS / 32];
-    const size_t strideP = N, strideT = (size_t)m.NP * N, strideS = (size_t)m.NT * strideT;
+    const size_t strideP = m.Np, strideT = (size_t)m.NP * m.Np, strideS = (size_t)m.NT * strideT;
     for (int l = 0; l < L; ++l) {
         const size_t bl = (size_t)b * L + l;
         const float4 wv = w.w4[bl];
         const int it = w.it[bl], ip = m.ip[l], itc = w.itc[bl];
         const float wp = m.wp[l], gt = w.gt[bl], wtc = w.wtc[bl], gtc = w.gtc[bl];
         const float cc1 = w.ccia[2 * bl], cc2 = w.ccia[2 * bl + 1];
-        float acc[ES_MAX_SPECIES + N_RED_EXTRA];
+        float acc[ES_MAX_SPECIES + N_RED - 1];
         for (int q = 0; q < NR; ++q) acc[q] = 0.f;
         const float *abar = w.abar + bl * N;
         for (int k = 0; k < BWD_NU_PER_THREAD; ++k) {
@@ -131,13 +133,13 @@ __global__ void __launch_bounds__(EXT_THREADS) k_extinction_bwd(Model m, Work w)
                 dsum = fmaf(ae, slope, dsum);
             }
             acc[S] += dsum;
-            const size_t c = (size_t)itc * N + n;
-            float k0 = __ldg(m.cia + c), k1 = __ldg(m.cia + c + N);
+            const size_t c = (size_t)itc * m.Np + n;
+            float k0 = __ldg(m.cia + c), k1 = __ldg(m.cia + c + m.Np);
             float c1 = ex2(fmaf((float)LOG2_10, fmaf(wtc, k1 - k0, k0), cc1));
             float sl1 = gtc * (k1 - k0);
-            const size_t c2i = c + (size_t)m.NTc * N;
+            const size_t c2i = c + (size_t)m.NTc * m.Np;
             k0 = __ldg(m.cia + c2i);
-            k1 = __ldg(m.cia + c2i + N);
+            k1 = __ldg(m.cia + c2i + m.Np);
             float c2 = ex2(fmaf((float)LOG2_10, fmaf(wtc, k1 - k0, k0), cc2));
             float sl2 = gtc * (k1 - k0);
             acc[S + 1] += a * c1;
@@ -147,27 +149,38 @@ __global__ void __launch_bounds__(EXT_THREADS) k_extinction_bwd(Model m, Work w)
             const float nf = m.nu[n] / (float)m.ray_nu_ref;
             acc[S + 5] += a * (nf * nf) * (nf * nf);
         }
+        // species: per-species totals (qtot) and their sum for this layer (red[0]);
+        // then D, C1, C2, C1T, C2T, W4 into red[1..6]
+        float qs = 0.f;
         for (int q = 0; q < NR; ++q) {
             float t = block_sum(acc[q], scratch);
-            if (threadIdx.x == 0 && t != 0.f) atomicAdd(w.red + bl * NR + q, (double)t);
+            if (threadIdx.x == 0) {
+                if (q < S) {
+                    qs += t;
+                    if (t != 0.f) atomicAdd(w.qtot + (size_t)b * S + q, (double)t);
+                } else if (t != 0.f) {
+                    atomicAdd(w.red + bl * N_RED + 1 + (q - S), (double)t);
+                }
+            }
         }
+        if (threadIdx.x == 0 && qs != 0.f) atomicAdd(w.red + bl * N_RED, (double)qs);
     }
 }
 
 }  // namespace
 
-int launch_extinction(const Model &m, const Work &w, cudaStream_t st, const Hook &h) {
+int launch_extinction(const Model &m, const Work &w, int only_kind, cudaStream_t st, const Hook &h) {
     dim3 grid((m.N + EXT_THREADS - 1) / EXT_THREADS, w.B);
-    if (m.bf16) ES_LAUNCH(h, "k_extinction", st, k_extinction<true><<<grid, EXT_THREADS, 0, st>>>(m, w));
-    else ES_LAUNCH(h, "k_extinction", st, k_extinction<false><<<grid, EXT_THREADS, 0, st>>>(m, w));
+    if (m.bf16) ES_LAUNCH(h, "k_extinction", st, k_extinction<true><<<grid, EXT_THREADS, 0, st>>>(m, w, only_kind));
+    else ES_LAUNCH(h, "k_extinction", st, k_extinction<false><<<grid, EXT_THREADS, 0, st>>>(m, w, only_kind));
     return 1;
 }
 
-int launch_extinction_backward(const Model &m, const Work &w, cudaStream_t st, const Hook &h) {
+int launch_extinction_backward(const Model &m, const Work &w, int only_kind, cudaStream_t st, const Hook &h) {
     const int per_block = EXT_THREADS * BWD_NU_PER_THREAD;
     dim3 grid((m.N + per_block - 1) / per_block, w.B);
-    if (m.bf16) ES_LAUNCH(h, "k_extinction_bwd", st, k_extinction_bwd<true><<<grid, EXT_THREADS, 0, st>>>(m, w));
-    else ES_LAUNCH(h, "k_extinction_bwd", st, k_extinction_bwd<false><<<grid, EXT_THREADS, 0, st>>>(m, w));
+    if (m.bf16) ES_LAUNCH(h, "k_extinction_bwd", st, k_extinction_bwd<true><<<grid, EXT_THREADS, 0, st>>>(m, w, only_kind));
+    else ES_LAUNCH(h, "k_extinction_bwd", st, k_extinction_bwd<false><<<grid, EXT_THREADS, 0, st>>>(m, w, only_kind));
     return 1;
 }
 

@@ -1,0 +1,548 @@
+// Fused transmission kernels (Sect. 3 opacities -> Sect. 4 chord optical
+// depth and transit depth), persistent over (sample, wavenumber-chunk) items.
+//
+// Forward, per 64-wavenumber tile: the extinction alpha[l][nu] of every
+// layer is interpolated into shared memory as a split BF16 pair, the chord
+// optical depth tau[i][nu] = sum_l L_il alpha_l(nu) runs on the tensor cores
+// (mma.sync m16n8k16, hi*hi + hi*lo + lo*hi, FP32 accumulation; only the
+// lower-triangular blocks of L), and the epilogue forms
+// delta(nu) - base = sum_i A_i (1 - exp(-tau_i)); exp(-tau) is optionally
+// stored for the adjoint.
+//
+// Backward, per tile: tau_bar = dbar A_i exp(-tau) (split BF16 in shared
+// memory), alpha_bar = L^T tau_bar on the tensor cores, the interpolation is
+// recomputed and reduced against alpha_bar (per-layer sums over wavenumber),
+// and L_bar += tau_bar alpha^T on the tensor cores, accumulated in registers
+// across the item's tiles.
+#include <algorithm>
+
+#include "fused_common.cuh"
+
+namespace es {
+
+namespace {
+
+constexpr int RB_PITCH = 152;                 // bf16 pitch of the backward row buffer (304 B)
+constexpr int RB_LO = 72;                     // bf16 offset of the lo half in a row (144 B)
+constexpr float LOG2E_F = 1.4426950408889634f;
+
+struct TransFwdSmem {
+    SampleConst sc;
+    __nv_bfloat16 lh[LP * L_PITCH], ll[LP * L_PITCH];   // path lengths [i][l]
+    __nv_bfloat16 ah[LP * R_PITCH], al[LP * R_PITCH];   // extinction [l][nu]
+    float area[LP];
+};
+
+// Backward block: 16 warps, 128-wavenumber tiles.
+constexpr int BW_WARPS = 16;
+constexpr int BW_THREADS = BW_WARPS * 32;
+constexpr int BT = 128;              // wavenumbers per backward tile
+constexpr int T2_PITCH = 136;        // bf16 pitch of tau_bar rows [i][128 nu] (272 B: 17 x 16 B)
+constexpr int RB2_BYTES = 528;       // bytes per row buffer row (33 x 16 B): two 256-B halves
+// Row buffer, per layer and per 64-wavenumber half h (bytes [256 h, 256 h + 256)):
+// first alpha_bar as 64 FP32, then overwritten by the extinction as BF16 hi
+// (bytes 0..127 of the half) and lo (bytes 128..255). Each half belongs to one
+// warp, so the overwrite only needs a warp barrier.
+
+struct TransBwdSmem {
+    SampleConst sc;
+    __nv_bfloat16 lh[LP * L_PITCH], ll[LP * L_PITCH];   // path lengths [i][l]
+    __nv_bfloat16 th[LP * T2_PITCH], tl[LP * T2_PITCH]; // tau_bar [i][nu]
+    unsigned char rb[LP * RB2_BYTES];                   // alpha_bar / alpha rows
+    float area[LP];
+    float area_acc[LP];                                 // area_bar of the current sample
+    float red[ES_MAX_LAYERS * N_RED];                   // per-layer reductions of the current sample
+    float qtot[ES_MAX_SPECIES];                         // per-species totals of the current sample
+};
+
+// Path-length matrix of sample b as split BF16 [i][l] (zero-padded to LP x LP).
+__device__ void stage_lmat(const Model &m, const Work &w, int b, __nv_bfloat16 *lh, __nv_bfloat16 *ll, float *area) {
+    const int L = m.L;
+    const float *src = w.lmat + (size_t)b * L * L;
+    for (int idx = threadIdx.x; idx < LP * (LP / 2); idx += FTHREADS) {
+        const int i = idx / (LP / 2), l = 2 * (idx % (LP / 2));
+        float2 v = make_float2(0.f, 0.f);
+        if (i < L) {
+            if (l < L) v.x = src[(size_t)i * L + l];
+            if (l + 1 < L) v.y = src[(size_t)i * L + l + 1];
+        }
+        uint32_t hi, lo;
+        split2(v, hi, lo);
+        *reinterpret_cast<uint32_t *>(lh + i * L_PITCH + l) = hi;
+        *reinterpret_cast<uint32_t *>(ll + i * L_PITCH + l) = lo;
+    }
+    for (int i = threadIdx.x; i < LP; i += FTHREADS) area[i] = (i < L) ? w.area[(size_t)b * L + i] : 0.f;
+}
+
+template <bool BF16, bool STORE_E>
+__global__ void __launch_bounds__(FTHREADS, 2) k_trans_fwd(Model m, Work w, int chunk_tiles) {
+    extern __shared__ float4 smem4[];
+    TransFwdSmem &sm = *reinterpret_cast<TransFwdSmem *>(smem4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int L = m.L, N = m.N;
+    const int ntiles = (N + FT - 1) / FT;
+    const int nchunks = (ntiles + chunk_tiles - 1) / chunk_tiles;
+    const long long total = (long long)w.B * nchunks;
+    // extinction rows of the padding layers stay zero
+    for (int idx = threadIdx.x; idx < (LP - L) * R_PITCH; idx += FTHREADS) {
+        sm.ah[L * R_PITCH + idx] = __float2bfloat16_rn(0.f);
+        sm.al[L * R_PITCH + idx] = __float2bfloat16_rn(0.f);
+    }
+    int lb, le;
+    warp_layers(L, warp, lb, le);
+    const uint32_t blh = smem_u32(sm.lh), bll = smem_u32(sm.ll), bah = smem_u32(sm.ah), bal = smem_u32(sm.al);
+    const int ksmax = (L + 15) / 16;
+    int cur_b = -1;
+    for (long long item = blockIdx.x; item < total; item += gridDim.x) {
+        // chunk-major order: blocks running together share a wavenumber window,
+        // so its slice of the opacity tables stays resident in L2
+        const int c = (int)(item / w.B), b = (int)(item % w.B);
+        if (w.kind[b] != ES_KIND_TRANSMISSION) continue;
+        if (b != cur_b) {
+            __syncthreads();
+            stage_sample(m, w, b, sm.sc);
+            stage_lmat(m, w, b, sm.lh, sm.ll, sm.area);
+            cur_b = b;
+            __syncthreads();
+        }
+        const int t1 = min(ntiles, (c + 1) * chunk_tiles);
+        for (int t = c * chunk_tiles; t < t1; ++t) {
+            const int nt0 = t * FT;
+            extinction_pair<BF16>(m, sm.sc, lb, le, nt0 + 2 * lane, [&](int l, float2 a) {
+                uint32_t hi, lo;
+                split2(a, hi, lo);
+                *reinterpret_cast<uint32_t *>(sm.ah + l * R_PITCH + 2 * lane) = hi;
+                *reinterpret_cast<uint32_t *>(sm.al + l * R_PITCH + 2 * lane) = lo;
+            });
+            __syncthreads();
+            // tau[i][nu] for this warp's 8 wavenumbers, lower-triangular blocks only
+            float acc[7][4];
+#pragma unroll
+            for (int mi = 0; mi < 7; ++mi) acc[mi][0] = acc[mi][1] = acc[mi][2] = acc[mi][3] = 0.f;
+#pragma unroll
+            for (int ks = 0; ks < 7; ++ks) {
+                if (ks < ksmax) {
+                    uint32_t bh[2], bl[2];
+                    ldsm_x2_t(bt_addr(bah, R_PITCH, 8 * warp, 16 * ks, lane), bh);
+                    ldsm_x2_t(bt_addr(bal, R_PITCH, 8 * warp, 16 * ks, lane), bl);
+#pragma unroll
+                    for (int mi = ks; mi < 7; ++mi) {
+                        uint32_t ah[4], al[4];
+                        ldsm_x4(a_addr(blh, L_PITCH, 16 * mi, 16 * ks, lane), ah);
+                        ldsm_x4(a_addr(bll, L_PITCH, 16 * mi, 16 * ks, lane), al);
+                        mma3(acc[mi], ah, al, bh, bl);
+                    }
+                }
+            }
+            // epilogue: sum_i A_i (1 - exp(-tau_i)); lane holds rows r, r+8 and columns c, c+1
+            const int col = 8 * warp + 2 * (lane & 3), r = lane >> 2;
+            const int n0 = nt0 + col;
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+            for (int mi = 0; mi < 7; ++mi) {
+                const int i0 = 16 * mi + r, i1 = i0 + 8;
+                const float e00 = ex2f(-acc[mi][0] * LOG2E_F), e01 = ex2f(-acc[mi][1] * LOG2E_F);
+                const float e10 = ex2f(-acc[mi][2] * LOG2E_F), e11 = ex2f(-acc[mi][3] * LOG2E_F);
+                const float a0 = sm.area[i0], a1 = sm.area[i1];
+                s0 += a0 * (1.f - e00) + a1 * (1.f - e10);
+                s1 += a0 * (1.f - e01) + a1 * (1.f - e11);
+                if (STORE_E) {   // padding wavenumbers too: the adjoint multiplies them by dbar = 0
+                    float *eb = w.estore + (size_t)b * L * m.Np + n0;
+                    if (i0 < L) *reinterpret_cast<float2 *>(eb + (size_t)i0 * m.Np) = make_float2(e00, e01);
+                    if (i1 < L) *reinterpret_cast<float2 *>(eb + (size_t)i1 * m.Np) = make_float2(e10, e11);
+                }
+            }
+#pragma unroll
+            for (int o = 4; o < 32; o <<= 1) {
+                s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            }
+            if (r == 0) {
+                float *sp = w.spec + (size_t)b * N;
+                if (n0 < N) sp[n0] = s0;
+                if (n0 + 1 < N) sp[n0 + 1] = s1;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Warp transpose-reduction of 16 values: on return lane holds the warp-wide
+// sum of v[idx] with idx = 8 b4 + 4 b3 + 2 b2 + b1 (bk = bit k of the lane).
+__device__ __forceinline__ float transpose_reduce16(float (&v)[16], int lane) {
+    float a[8], c[4], d[2];
+    {
+        const bool up = lane & 16;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float send = up ? v[k] : v[k + 8], keep = up ? v[k + 8] : v[k];
+            a[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        }
+    }
+    {
+        const bool up = lane & 8;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float send = up ? a[k] : a[k + 4], keep = up ? a[k + 4] : a[k];
+            c[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        }
+    }
+    {
+        const bool up = lane & 4;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const float send = up ? c[k] : c[k + 2], keep = up ? c[k + 2] : c[k];
+            d[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+        }
+    }
+    const bool up = lane & 2;
+    float e = (up ? d[1] : d[0]) + __shfl_xor_sync(0xffffffffu, up ? d[0] : d[1], 2);
+    e += __shfl_xor_sync(0xffffffffu, e, 1);
+    return e;
+}
+
+// Lower-triangular block pair p (0..55) of L_bar: i-block mi (0..6), l-block nj <= 2 mi + 1.
+__device__ __forceinline__ void decode_pair(int p, int &mi, int &nj) {
+    mi = 0;
+    while (p >= 2 * mi + 2) {
+        p -= 2 * mi + 2;
+        ++mi;
+    }
+    nj = p;
+}
+
+__device__ __forceinline__ int reduce_index(int lane) {
+    return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+}
+
+// Warp transpose-reduction of 8 values: on return lane holds the warp-wide
+// sum of v[idx] with idx = 4 b4 + 2 b3 + b2 (bk = bit k of the lane).
+__device__ __forceinline__ float transpose_reduce8(const float (&v)[8], int lane) {
+    float a[4], c[2];
+    {
+        const bool up = lane & 16;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            a[k] = (up ? v[k + 4] : v[k]) + __shfl_xor_sync(0xffffffffu, up ? v[k] : v[k + 4], 16);
+    }
+    {
+        const bool up = lane & 8;
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+            c[k] = (up ? a[k + 2] : a[k]) + __shfl_xor_sync(0xffffffffu, up ? a[k] : a[k + 2], 8);
+    }
+    const bool up = lane & 4;
+    float e = (up ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, up ? c[0] : c[1], 4);
+    e += __shfl_xor_sync(0xffffffffu, e, 2);
+    e += __shfl_xor_sync(0xffffffffu, e, 1);
+    return e;
+}
+
+__device__ __forceinline__ int reduce_index8(int lane) {
+    return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+}
+
+// Backward interpolation for one warp: layers [lb, le), wavenumber pair n, n+1
+// (the warp's 64-wavenumber half `half` of its row-buffer rows). Reads
+// alpha_bar, adds per-layer reductions to red[l][*] and per-species totals to
+// qtot[s], then overwrites its half-rows with the extinction as split BF16.
+// Per layer, summed over wavenumber: QS = sum abar sum_s e_s,
+// D = sum abar sum_s e_s dlog10(sigma_s)/dlog10 T, C1, C2 = sum abar c1, c2,
+// C1T, C2T = sum abar c dlog10 k/dT, W4 = sum abar (nu/nu_ref)^4; per species
+// Q_s = sum_l sum abar e_s (e_s, c1, c2 the species and CIA extinction terms).
+template <bool BF16>
+__device__ void interp_backward(const Model &m, const SampleConst &sc, int lb, int le, int n, int lane, int half,
+                                unsigned char *rb, float *red, float *qtot) {
+    const int S = m.S;
+    const int ridx = reduce_index8(lane);
+    const bool writer = (lane & 3) == 0;
+    const float inv_l2 = (float)(1.0 / LOG2_10);
+    const float ray_ref = (float)(1.0 / ((double)m.ray_nu_ref * m.ray_nu_ref * m.ray_nu_ref * m.ray_nu_ref));
+    PairInterp<BF16> pi;
+    pi.init(m, n);
+    float qa[SCACHE], qx[SCACHE];
+#pragma unroll
+    for (int j = 0; j < SCACHE; ++j) qa[j] = qx[j] = 0.f;
+    for (int l = lb; l < le; ++l) {
+        const LayerConst &lc = sc.lay[l];
+        pi.update(m, sc, lc, n);
+        if (l + 1 < le) pi.prefetch(m, lc, sc.lay[l + 1], n);
+        unsigned char *hrow = rb + (size_t)l * RB2_BYTES + 256 * half;
+        const float2 ab = *reinterpret_cast<const float2 *>(hrow + 8 * lane);
+        const float2 wp = f2(lc.wp), wt = f2(lc.wt);
+        float2 sum = f2(0.f), dsum = f2(0.f), t;
+        float qs = 0.f;
+#pragma unroll
+        for (int j = 0; j < SCACHE; ++j) {
+            if (j < S) {
+                const float2 p = ex2x2(pi.expo(j, wp, wt, t));
+                sum = add2(sum, p);
+                const float2 ap = mul2(ab, p);
+                const float q = (ap.x + ap.y) * lc.nsc;
+                qa[j] += q;
+                qs += q;
+                dsum = fma2(ap, t, dsum);
+            }
+        }
+        for (int s = SCACHE; s < S; ++s) {
+            const float2 p = ex2x2(expo_uncached<BF16>(m, sc, lc, s, n, wp, wt, t));
+            sum = add2(sum, p);
+            const float2 ap = mul2(ab, p);
+            const float q = (ap.x + ap.y) * lc.nsc;
+#pragma unroll
+            for (int k = 0; k < SCACHE; ++k)
+                if (k == s - SCACHE) qx[k] += q;
+            qs += q;
+            dsum = fma2(ap, t, dsum);
+        }
+        const float2 wc = f2(lc.wtc);
+        const float2 c1 = ex2x2(fma2(wc, pi.d1, add2(pi.b1, f2(lc.cc1))));
+        const float2 c2 = ex2x2(fma2(wc, pi.d2, add2(pi.b2, f2(lc.cc2))));
+        const float2 ac1 = mul2(ab, c1), ac2 = mul2(ab, c2);
+        const float2 t1 = mul2(ac1, pi.d1), t2 = mul2(ac2, pi.d2), t4 = mul2(ab, pi.nu4);
+        float v[8];
+        v[0] = qs;
+        v[1] = (dsum.x + dsum.y) * (lc.nsc * lc.gt * inv_l2);
+        v[2] = ac1.x + ac1.y;
+        v[3] = ac2.x + ac2.y;
+        v[4] = (t1.x + t1.y) * (lc.gtc * inv_l2);
+        v[5] = (t2.x + t2.y) * (lc.gtc * inv_l2);
+        v[6] = (t4.x + t4.y) * ray_ref;
+        v[7] = 0.f;
+        const float tot = transpose_reduce8(v, lane);
+        if (writer && ridx < N_RED && tot != 0.f) atomicAdd(red + l * N_RED + ridx, tot);
+        const float2 base = fma2(f2(lc.ray), pi.nu4, add2(c1, c2));
+        const float2 alpha = fma2(sum, f2(lc.nsc), base);
+        uint32_t hi, lo;
+        split2(alpha, hi, lo);
+        __syncwarp();
+        *reinterpret_cast<uint32_t *>(hrow + 4 * lane) = hi;
+        *reinterpret_cast<uint32_t *>(hrow + 128 + 4 * lane) = lo;
+    }
+    const float tq = transpose_reduce8(qa, lane);
+    if (writer && ridx < S && tq != 0.f) atomicAdd(qtot + ridx, tq);
+    if (S > SCACHE) {
+        const float tx = transpose_reduce8(qx, lane);
+        if (writer && SCACHE + ridx < S && tx != 0.f) atomicAdd(qtot + SCACHE + ridx, tx);
+    }
+}
+
+// B fragment (k16 x n8) of alpha^T for L_bar = tau_bar alpha^T: rows l of the
+// row buffer, wavenumbers [16 ks, 16 ks + 16) of the tile; lo = false/true.
+__device__ __forceinline__ uint32_t rb_addr(uint32_t base, int n0, int ks, bool lo, int lane) {
+    const int l = lane & 15;
+    const int half = ks >> 2, kin = (ks & 3) * 16 + ((l >> 3) << 3);
+    return base + (uint32_t)((n0 + (l & 7)) * RB2_BYTES + 256 * half + (lo ? 128 : 0) + 2 * kin);
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, int chunk_tiles) {
+    extern __shared__ float4 smem4[];
+    TransBwdSmem &sm = *reinterpret_cast<TransBwdSmem *>(smem4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int L = m.L, N = m.N, S = m.S;
+    const int ntiles = (N + BT - 1) / BT;
+    const int nchunks = (ntiles + chunk_tiles - 1) / chunk_tiles;
+    const long long total = (long long)w.B * nchunks;
+    const int half = warp & 1, group = warp >> 1;       // interpolation: layer group, wavenumber half
+    int lb, le;
+    warp_layers(L, group, lb, le);
+    // padding rows (impact parameters / layers >= L) of tau_bar and the row buffer stay zero
+    for (int idx = threadIdx.x; idx < (LP - L) * T2_PITCH; idx += BW_THREADS) {
+        sm.th[L * T2_PITCH + idx] = __float2bfloat16_rn(0.f);
+        sm.tl[L * T2_PITCH + idx] = __float2bfloat16_rn(0.f);
+    }
+    for (int idx = threadIdx.x; idx < (LP - L) * RB2_BYTES; idx += BW_THREADS) sm.rb[L * RB2_BYTES + idx] = 0;
+    const uint32_t blh = smem_u32(sm.lh), bll = smem_u32(sm.ll), bth = smem_u32(sm.th), btl = smem_u32(sm.tl);
+    const uint32_t brb = smem_u32(sm.rb);
+    const int ksmax = (L + 15) / 16;
+    float lacc[4][4];
+    int cur_b = -1;
+    auto flush = [&](int b) {
+        // L_bar, reductions, per-species totals and area_bar of sample b (FP64 atomics)
+        double *lbar = w.lbar + (size_t)b * L * L;
+        const int r = lane >> 2, col = 2 * (lane & 3);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int p = warp + BW_WARPS * k;
+            if (p < 56) {
+                int mi, nj;
+                decode_pair(p, mi, nj);
+                const int i0 = 16 * mi + r, l0 = 8 * nj + col;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int ii = i0 + ((e >> 1) << 3), ll = l0 + (e & 1);
+                    if (ii < L && ll <= ii && lacc[k][e] != 0.f) atomicAdd(lbar + (size_t)ii * L + ll, (double)lacc[k][e]);
+                }
+            }
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < L * N_RED; idx += BW_THREADS) {
+            const float v = sm.red[idx];
+            if (v != 0.f) atomicAdd(w.red + (size_t)b * L * N_RED + idx, (double)v);
+        }
+        for (int i = threadIdx.x; i < L; i += BW_THREADS)
+            if (sm.area_acc[i] != 0.f) atomicAdd(w.areabar + (size_t)b * L + i, (double)sm.area_acc[i]);
+        for (int s2 = threadIdx.x; s2 < S; s2 += BW_THREADS)
+            if (sm.qtot[s2] != 0.f) atomicAdd(w.qtot + (size_t)b * S + s2, (double)sm.qtot[s2]);
+    };
+    for (long long item = blockIdx.x; item < total; item += gridDim.x) {
+        // chunk-major order: blocks running together share a wavenumber window
+        const int c = (int)(item / w.B), b = (int)(item % w.B);
+        if (w.kind[b] != ES_KIND_TRANSMISSION || w.flags[b]) continue;
+        if (b != cur_b) {
+            if (cur_b >= 0) flush(cur_b);
+            __syncthreads();
+            stage_sample(m, w, b, sm.sc);
+            stage_lmat(m, w, b, sm.lh, sm.ll, sm.area);
+            for (int idx = threadIdx.x; idx < L * N_RED; idx += BW_THREADS) sm.red[idx] = 0.f;
+            for (int i = threadIdx.x; i < LP; i += BW_THREADS) sm.area_acc[i] = 0.f;
+            for (int s2 = threadIdx.x; s2 < ES_MAX_SPECIES; s2 += BW_THREADS) sm.qtot[s2] = 0.f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) lacc[k][0] = lacc[k][1] = lacc[k][2] = lacc[k][3] = 0.f;
+            cur_b = b;
+            __syncthreads();
+        }
+        const int t1 = min(ntiles, (c + 1) * chunk_tiles);
+        for (int t = c * chunk_tiles; t < t1; ++t) {
+            const int nt0 = t * BT;
+            const int n = nt0 + 2 * (lane + 32 * half);
+            // tau_bar = dbar A_i exp(-tau); area_bar += dbar (1 - exp(-tau))
+            {
+                const float2 db = *reinterpret_cast<const float2 *>(w.dbar + (size_t)b * m.Np + n);
+                const float *eb = w.estore + (size_t)b * L * m.Np + n;
+                float av[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    av[k] = 0.f;
+                    const int i = group + 8 * k;
+                    if (k < 14 && i < L) {
+                        const float2 e = *reinterpret_cast<const float2 *>(eb + (size_t)i * m.Np);
+                        const float a = sm.area[i];
+                        uint32_t hi, lo;
+                        split2(make_float2(db.x * a * e.x, db.y * a * e.y), hi, lo);
+                        const int col = 2 * (lane + 32 * half);
+                        *reinterpret_cast<uint32_t *>(sm.th + i * T2_PITCH + col) = hi;
+                        *reinterpret_cast<uint32_t *>(sm.tl + i * T2_PITCH + col) = lo;
+                        av[k] = db.x * (1.f - e.x) + db.y * (1.f - e.y);
+                    }
+                }
+                const float tot = transpose_reduce16(av, lane);
+                const int k = reduce_index(lane), i = group + 8 * k;
+                if ((lane & 1) == 0 && k < 14 && i < L && tot != 0.f) atomicAdd(sm.area_acc + i, tot);
+            }
+            __syncthreads();
+            // alpha_bar[l][nu] = sum_{i >= l} L_il tau_bar_i(nu), this warp's 8 wavenumbers
+            {
+                float acc[7][4];
+#pragma unroll
+                for (int ml = 0; ml < 7; ++ml) acc[ml][0] = acc[ml][1] = acc[ml][2] = acc[ml][3] = 0.f;
+#pragma unroll
+                for (int ks = 0; ks < 7; ++ks) {
+                    if (ks < ksmax) {
+                        uint32_t bh[2], bl[2];
+                        ldsm_x2_t(bt_addr(bth, T2_PITCH, 8 * warp, 16 * ks, lane), bh);
+                        ldsm_x2_t(bt_addr(btl, T2_PITCH, 8 * warp, 16 * ks, lane), bl);
+#pragma unroll
+                        for (int ml = 0; ml <= ks; ++ml) {
+                            uint32_t ah[4], al[4];
+                            ldsm_x4_t(at_addr(blh, L_PITCH, 16 * ml, 16 * ks, lane), ah);
+                            ldsm_x4_t(at_addr(bll, L_PITCH, 16 * ml, 16 * ks, lane), al);
+                            mma3(acc[ml], ah, al, bh, bl);
+                        }
+                    }
+                }
+                const int colt = 8 * warp + 2 * (lane & 3), r = lane >> 2;
+                const int h = colt >> 6, cin = colt & 63;
+#pragma unroll
+                for (int ml = 0; ml < 7; ++ml) {
+                    const int l0 = 16 * ml + r, l1 = l0 + 8;
+                    if (l0 < L)
+                        *reinterpret_cast<float2 *>(sm.rb + (size_t)l0 * RB2_BYTES + 256 * h + 4 * cin) =
+                            make_float2(acc[ml][0], acc[ml][1]);
+                    if (l1 < L)
+                        *reinterpret_cast<float2 *>(sm.rb + (size_t)l1 * RB2_BYTES + 256 * h + 4 * cin) =
+                            make_float2(acc[ml][2], acc[ml][3]);
+                }
+            }
+            __syncthreads();
+            interp_backward<BF16>(m, sm.sc, lb, le, n, lane, half, sm.rb, sm.red, sm.qtot);
+            __syncthreads();
+            // L_bar[i][l] += sum_nu tau_bar[i][nu] alpha[l][nu] over this tile (8 k-steps)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int p = warp + BW_WARPS * k;
+                if (p < 56) {
+                    int mi, nj;
+                    decode_pair(p, mi, nj);
+#pragma unroll
+                    for (int ks = 0; ks < BT / 16; ++ks) {
+                        uint32_t ah[4], al[4], bh[2], bl[2];
+                        ldsm_x4(a_addr(bth, T2_PITCH, 16 * mi, 16 * ks, lane), ah);
+                        ldsm_x4(a_addr(btl, T2_PITCH, 16 * mi, 16 * ks, lane), al);
+                        ldsm_x2(rb_addr(brb, 8 * nj, ks, false, lane), bh);
+                        ldsm_x2(rb_addr(brb, 8 * nj, ks, true, lane), bl);
+                        mma3(lacc[k], ah, al, bh, bl);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (cur_b >= 0) flush(cur_b);
+}
+
+size_t fwd_smem() { return sizeof(TransFwdSmem); }
+size_t bwd_smem() { return sizeof(TransBwdSmem); }
+
+int sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+}  // namespace
+
+// Tiles per work item: up to 16 (amortises staging the sample), fewer when the
+// batch is small so that every resident block gets items.
+int chunk_tiles(const Model &m, int B, int blocks) {
+    const int ntiles = (m.N + FT - 1) / FT;
+    long long c = ((long long)ntiles * B) / (4LL * blocks);
+    return (int)std::max<long long>(1, std::min<long long>(16, c));
+}
+
+int launch_trans_fused_forward(const Model &m, const Work &w, bool store_e, cudaStream_t st, const Hook &h) {
+    const int ntiles = (m.N + FT - 1) / FT;
+    const int chunk = chunk_tiles(m, w.B, 2 * sm_count());
+    const long long items = (long long)w.B * ((ntiles + chunk - 1) / chunk);
+    const int grid = (int)std::min<long long>(items, 2LL * sm_count());
+    const size_t sm = fwd_smem();
+#define ES_FWD(BF, SE)                                                                          \
+    do {                                                                                        \
+        cudaFuncSetAttribute(k_trans_fwd<BF, SE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+        ES_LAUNCH(h, "k_trans_fwd", st, k_trans_fwd<BF, SE><<<grid, FTHREADS, sm, st>>>(m, w, chunk)); \
+    } while (0)
+    if (m.bf16) { if (store_e) ES_FWD(true, true); else ES_FWD(true, false); }
+    else { if (store_e) ES_FWD(false, true); else ES_FWD(false, false); }
+#undef ES_FWD
+    return 1;
+}
+
+int launch_trans_fused_backward(const Model &m, const Work &w, cudaStream_t st, const Hook &h) {
+    const int ntiles = (m.N + BT - 1) / BT;
+    const int chunk = std::max(1, chunk_tiles(m, w.B, sm_count()) / 2);
+    const long long items = (long long)w.B * ((ntiles + chunk - 1) / chunk);
+    const int grid = (int)std::min<long long>(items, (long long)sm_count());
+    const size_t sm = bwd_smem();
+    if (m.bf16) {
+        cudaFuncSetAttribute(k_trans_bwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        ES_LAUNCH(h, "k_trans_bwd", st, k_trans_bwd<true><<<grid, BW_THREADS, sm, st>>>(m, w, chunk));
+    } else {
+        cudaFuncSetAttribute(k_trans_bwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        ES_LAUNCH(h, "k_trans_bwd", st, k_trans_bwd<false><<<grid, BW_THREADS, sm, st>>>(m, w, chunk));
+    }
+    return 1;
+}
+
+}  // namespace es

@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup(Model m, Work w) {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(SETUP_THREADS) k_setup_bwd(Model m, Work w) {
     const int b = blockIdx.x, tid = threadIdx.x;
-    const int L = m.L, S = m.S, NR = S + N_RED_EXTRA;
+    const int L = m.L, S = m.S;
     __shared__ double rl[ES_MAX_LAYERS + 1], rbar[ES_MAX_LAYERS + 1], tvbar[ES_MAX_LAYERS + 1];
     __shared__ double tlbar[ES_MAX_LAYERS];
     __shared__ double xbar[ES_MAX_SPECIES + 2], xs[ES_MAX_SPECIES + 2];
@@ -205,15 +205,12 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup_bwd(Model m, Work w) {
         }
     }
     // extinction reductions -> layer temperature and VMR adjoints
+    if (!bad && tid < S) atomicAdd(&xbar[tid], w.qtot[(size_t)b * S + tid] / xs[tid]);
     for (int l = tid; l < L; l += blockDim.x) {
-        const double *rd = w.red + ((size_t)b * L + l) * NR;
+        const double *rd = w.red + ((size_t)b * L + l) * N_RED;
         double n = w.n_lay[(size_t)b * L + l], t = w.t_lay[(size_t)b * L + l];
-        double qsum = 0.0;
-        for (int s = 0; s < S; ++s) {
-            qsum += rd[s];
-            if (!bad) atomicAdd(&xbar[s], rd[s] / xs[s]);
-        }
-        double dd = rd[S], c1 = rd[S + 1], c2 = rd[S + 2], c1t = rd[S + 3], c2t = rd[S + 4], w4 = rd[S + 5];
+        const double qsum = rd[0];
+        double dd = rd[1], c1 = rd[2], c2 = rd[3], c1t = rd[4], c2t = rd[5], w4 = rd[6];
         double nbar = 0.0, tb = 0.0;
         if (!bad) {
             nbar = (qsum + 2.0 * (c1 + c2)) / n + (xs[S] * m.ray_h2 + xs[S + 1] * m.ray_he) * w4;

@@ -56,9 +56,9 @@ def test_no_alloc_mixed_kinds_twice():
 
 
 def test_no_alloc_rejects_a_batch_beyond_the_fixed_workspace():
-    w = synth.workload("jwst_plain", batch=8, n_nu=20000)
+    w = synth.workload("jwst_plain", batch=400, n_nu=20000)    # ~130 kB per vector: 52 MB > 32 MiB
     ctx = binding.context_for(w)
     theta = torch.tensor(w.theta, dtype=torch.float64, device=DEV)
-    out = torch.empty(8, dtype=torch.float64, device=DEV)
+    out = torch.empty(400, dtype=torch.float64, device=DEV)
     with pytest.raises(binding.ExoskryError, match="EINVAL.*bytes of workspace"):
         ctx.es_loglike_noalloc(theta, None, out)
