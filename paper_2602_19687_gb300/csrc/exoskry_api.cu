@@ -447,6 +447,16 @@ es_status es_load_tables(es_ctx *c, const es_tables_desc *t) {
     m.ip = di;
     if ((s = upload(c, c->table_bufs, &df, wp.data(), wp.size())) != ES_OK) return s;
     m.wp = df;
+    // per-cell bilinear coefficients used by the fused kernels
+    float4 *coef;
+    const size_t ncoef = (size_t)(m.NT - 1) * (m.NP - 1) * m.S * m.Np;
+    if ((s = dalloc(c, c->table_bufs, &coef, ncoef)) != ES_OK) return s;
+    m.coef4 = nullptr;
+    launch_build_coef(m, coef, nullptr);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "coefficient table");
+    m.coef4 = coef;
     c->have_tables = true;
     return ES_OK;
 }

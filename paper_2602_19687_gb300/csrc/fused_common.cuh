@@ -127,7 +127,7 @@ __device__ __forceinline__ uint32_t bt_addr(uint32_t base, int pitch, int n0, in
 
 // ------------------------------------------------------------ per-sample constants
 struct __align__(16) LayerConst {
-    int it, ip, itc, cell;   // temperature / pressure / CIA brackets; cell = it * NP + ip
+    int it, ip, itc, cell;   // temperature / pressure / CIA brackets; cell = it * (NP - 1) + ip
     float wt, wp, wtc;       // raw interpolation weights
     float nsc;               // n_l 2^-KSHIFT
     float cc1, cc2;          // log2(n^2 X_H2^2), log2(n^2 X_H2 X_He)
@@ -150,7 +150,7 @@ __device__ inline void stage_sample(const Model &m, const Work &w, int b, Sample
         c.it = w.it[bl];
         c.ip = m.ip[l];
         c.itc = w.itc[bl];
-        c.cell = c.it * m.NP + c.ip;
+        c.cell = c.it * (m.NP - 1) + c.ip;
         c.wt = w.wtr[bl];
         c.wp = m.wp[l];
         c.wtc = w.wtc[bl];
@@ -177,37 +177,16 @@ __device__ __forceinline__ void warp_layers(int L, int warp, int &lb, int &le) {
 }
 
 // ------------------------------------------------------------ interpolation
-template <bool BF16>
-__device__ __forceinline__ float2 tab_pair(const Model &m, size_t idx) {
-    if (BF16) {
-        const uint32_t v = __ldg(reinterpret_cast<const unsigned int *>(m.tab16 + idx));
-        return make_float2(__uint_as_float(v << 16), __uint_as_float(v & 0xffff0000u));
-    }
-    return __ldg(reinterpret_cast<const float2 *>(m.tab32 + idx));
-}
-
-// Species-exponent coefficients of one cell for the lane's wavenumber pair:
-//   e = a0 + wp a1 + wt (a2 + wp a3) = log2(X_s sigma) + KSHIFT
-template <bool BF16>
-__device__ __forceinline__ void load_cell(const Model &m, int s, int it, int ip, int n, float lx, float2 &a0,
-                                          float2 &a1, float2 &a2, float2 &a3) {
-    const size_t row = ((size_t)s * m.NT + it) * m.NP + ip;
-    const size_t st = (size_t)m.Np;
-    const size_t r00 = row * st + n, r01 = r00 + st, r10 = r00 + (size_t)m.NP * st, r11 = r10 + st;
-    const float *off = m.row_off + row;
-    const float o00 = __ldg(off), o01 = __ldg(off + 1), o10 = __ldg(off + m.NP), o11 = __ldg(off + m.NP + 1);
-    float2 v00 = tab_pair<BF16>(m, r00), v01 = tab_pair<BF16>(m, r01);
-    float2 v10 = tab_pair<BF16>(m, r10), v11 = tab_pair<BF16>(m, r11);
-    v00 = add2(v00, f2(o00));
-    v01 = add2(v01, f2(o01));
-    v10 = add2(v10, f2(o10));
-    v11 = add2(v11, f2(o11));
-    const float2 c = f2((float)LOG2_10);
-    const float2 d0 = add2(v01, make_float2(-v00.x, -v00.y));
-    a0 = fma2(c, v00, f2(lx));
-    a1 = mul2(c, d0);
-    a2 = mul2(c, add2(v10, make_float2(-v00.x, -v00.y)));
-    a3 = mul2(c, add2(add2(v11, make_float2(-v10.x, -v10.y)), make_float2(-d0.x, -d0.y)));
+// Coefficients of species s in cell `cell` for the lane's wavenumber pair n, n+1,
+// with log2 X_s + KSHIFT folded into a0:  e = a0 + wp a1 + wt (a2 + wp a3).
+__device__ __forceinline__ void load_cell(const Model &m, int s, int cell, int n, float lx, float2 &a0, float2 &a1,
+                                          float2 &a2, float2 &a3) {
+    const float4 *p = m.coef4 + ((size_t)cell * m.S + s) * m.Np + n;
+    const float4 c0 = __ldg(p), c1 = __ldg(p + 1);
+    a0 = add2(make_float2(c0.x, c1.x), f2(lx));
+    a1 = make_float2(c0.y, c1.y);
+    a2 = make_float2(c0.z, c1.z);
+    a3 = make_float2(c0.w, c1.w);
 }
 
 // CIA coefficients of one temperature bracket: e = b + wtc d + cc
@@ -238,30 +217,20 @@ struct PairInterp {
         nu4 = mul2(nu2, nu2);
         cell = itc = -1;
     }
-    // L1 prefetch of the table rows of the next layer's cell when it differs
+    // L1 prefetch of the next layer's cell coefficients when the cell changes
     __device__ __forceinline__ void prefetch(const Model &m, const LayerConst &cur, const LayerConst &next, int n) const {
         if (next.cell == cur.cell) return;
-        const size_t st = (size_t)m.Np;
-        const size_t esz = m.bf16 ? 2 : 4;
-        const char *base = m.bf16 ? reinterpret_cast<const char *>(m.tab16) : reinterpret_cast<const char *>(m.tab32);
 #pragma unroll
-        for (int j = 0; j < SCACHE; ++j) {
-            if (j < m.S) {
-                const size_t r00 = (((size_t)j * m.NT + next.it) * m.NP + next.ip) * st + n;
-                const size_t r10 = r00 + (size_t)m.NP * st;
-                asm volatile("prefetch.global.L1 [%0];" ::"l"(base + r00 * esz));
-                asm volatile("prefetch.global.L1 [%0];" ::"l"(base + (r00 + st) * esz));
-                asm volatile("prefetch.global.L1 [%0];" ::"l"(base + r10 * esz));
-                asm volatile("prefetch.global.L1 [%0];" ::"l"(base + (r10 + st) * esz));
-            }
-        }
+        for (int j = 0; j < SCACHE; ++j)
+            if (j < m.S)
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(m.coef4 + ((size_t)next.cell * m.S + j) * m.Np + n));
     }
     __device__ __forceinline__ void update(const Model &m, const SampleConst &sc, const LayerConst &lc, int n) {
         if (lc.cell != cell) {
             cell = lc.cell;
 #pragma unroll
             for (int j = 0; j < SCACHE; ++j)
-                if (j < m.S) load_cell<BF16>(m, j, lc.it, lc.ip, n, sc.lx[j], a0[j], a1[j], a2[j], a3[j]);
+                if (j < m.S) load_cell(m, j, lc.cell, n, sc.lx[j], a0[j], a1[j], a2[j], a3[j]);
         }
         if (lc.itc != itc) {
             itc = lc.itc;
@@ -281,7 +250,7 @@ template <bool BF16>
 __device__ __forceinline__ float2 expo_uncached(const Model &m, const SampleConst &sc, const LayerConst &lc, int s,
                                                 int n, float2 wp, float2 wt, float2 &t) {
     float2 a0, a1, a2, a3;
-    load_cell<BF16>(m, s, lc.it, lc.ip, n, sc.lx[s], a0, a1, a2, a3);
+    load_cell(m, s, lc.cell, n, sc.lx[s], a0, a1, a2, a3);
     t = fma2(wp, a3, a2);
     return fma2(wt, t, fma2(wp, a1, a0));
 }

@@ -58,6 +58,8 @@ struct Model {
     const float *tab32;           // [S][NT][NP][Np]
     const uint16_t *tab16;        // [S][NT][NP][Np] BF16 residuals
     const float *row_off;         // [S][NT][NP] (zeros for FP32 tables)
+    const float4 *coef4;          // [(NT-1)(NP-1) cells][S][Np] bilinear coefficients (log2 units):
+                                  // (v00, v01 - v00, v10 - v00, v11 - v10 - v01 + v00) x log2(10)
     const float *cia;             // [2][NTc][Np] log10 k
     const float *nu;              // [Np]
     const float *inv_fstar;       // [Np] 1 / (pi B(T_*, nu))
@@ -122,6 +124,7 @@ struct Hook {
     } while (0)
 
 // kernel launchers (each returns the number of kernels launched)
+int launch_build_coef(const Model &m, float4 *coef, cudaStream_t st);
 int launch_setup(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
 int launch_extinction(const Model &m, const Work &w, int only_kind, cudaStream_t st, const Hook &h);
 int launch_trans_fused_forward(const Model &m, const Work &w, bool store_e, cudaStream_t st, const Hook &h);
