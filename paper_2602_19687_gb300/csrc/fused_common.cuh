@@ -13,49 +13,15 @@ constexpr int FT = 64;            // wavenumbers per tile
 constexpr int FWARPS = 8;         // warps per fused block
 constexpr int FTHREADS = FWARPS * 32;
 constexpr int LP = 112;           // layers padded to 7 x 16 (tensor-core K/M blocks)
-constexpr int LPW = 14;           // max layers per warp (LP / FWARPS)
-constexpr int SCH = 4;            // species per register-cached chunk
 constexpr float KSHIFT = 64.f;    // log2 scale folded into the species exponents
 constexpr int L_PITCH = 120;      // bf16 pitch of [112][112] path-matrix rows (240 B: 15 x 16 B)
 constexpr int R_PITCH = 72;       // bf16 pitch of [row][64 nu] operand rows (144 B: 9 x 16 B)
 
 // ------------------------------------------------------------ packed FP32x2
-#ifndef ES_PACKED_F32X2
-#define ES_PACKED_F32X2 1
-#endif
-#if ES_PACKED_F32X2
-__device__ __forceinline__ unsigned long long pk(float2 a) {
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
-    return r;
-}
-__device__ __forceinline__ float2 upk(unsigned long long v) {
-    float2 a;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(v));
-    return a;
-}
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
-    unsigned long long d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)), "l"(pk(c)));
-    return upk(d);
-}
-__device__ __forceinline__ float2 add2(float2 a, float2 b) {
-    unsigned long long d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
-    return upk(d);
-}
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
-    unsigned long long d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
-    return upk(d);
-}
-#else
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
-    return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
-}
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return make_float2(a.x * b.x, a.y * b.y); }
-#endif
+// Two FP32 lanes per instruction (sm_100+ FFMA2/FADD2/FMUL2 builtins).
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float ex2f(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -163,30 +129,34 @@ __device__ inline void stage_sample(const Model &m, const Work &w, int b, Sample
         c.pad[0] = c.pad[1] = c.pad[2] = 0.f;
         sc.lay[l] = c;
     }
-    for (int s = threadIdx.x; s < m.S; s += blockDim.x) {
-        const double x = w.xs[(size_t)b * (m.S + 2) + s];
-        sc.lx[s] = (x > 0.0) ? (float)(log2(x) + KSHIFT) : -1000.f;
+    // absent species (s >= S, padding of the per-lane species slots) get a
+    // log2 weight so low that their terms are exactly zero
+    for (int s = threadIdx.x; s < ES_MAX_SPECIES; s += blockDim.x) {
+        const double x = (s < m.S) ? w.xs[(size_t)b * (m.S + 2) + s] : 0.0;
+        sc.lx[s] = (x > 0.0) ? (float)(log2(x) + KSHIFT) : -1.0e4f;
     }
 }
 
-// Layers handled by warp `warp` (contiguous ranges; at most LPW each).
-__device__ __forceinline__ void warp_layers(int L, int warp, int &lb, int &le) {
-    const int per = (L + FWARPS - 1) / FWARPS;
-    lb = warp * per;
+// Layers of layer group `g` out of `ng` (contiguous ranges).
+__device__ __forceinline__ void group_layers(int L, int g, int ng, int &lb, int &le) {
+    const int per = (L + ng - 1) / ng;
+    lb = g * per;
     le = min(L, lb + per);
 }
 
 // ------------------------------------------------------------ interpolation
-// Coefficients of species s in cell `cell` for the lane's wavenumber pair n, n+1,
-// with log2 X_s + KSHIFT folded into a0:  e = a0 + wp a1 + wt (a2 + wp a3).
+// Coefficient table layout (see k_tables.cu): per (cell, species) and
+// wavenumber pair, two float4: (a0, a0', a1, a1') and (a2, a2', a3, a3') for
+// the pair's two wavenumbers, so each coefficient loads straight into an
+// aligned register pair.
 __device__ __forceinline__ void load_cell(const Model &m, int s, int cell, int n, float lx, float2 &a0, float2 &a1,
                                           float2 &a2, float2 &a3) {
-    const float4 *p = m.coef4 + ((size_t)cell * m.S + s) * m.Np + n;
+    const float4 *p = m.coef4 + (((size_t)cell * m.S + s) * (m.Np >> 1) + (n >> 1)) * 2;
     const float4 c0 = __ldg(p), c1 = __ldg(p + 1);
-    a0 = add2(make_float2(c0.x, c1.x), f2(lx));
-    a1 = make_float2(c0.y, c1.y);
-    a2 = make_float2(c0.z, c1.z);
-    a3 = make_float2(c0.w, c1.w);
+    a0 = add2(make_float2(c0.x, c0.y), f2(lx));
+    a1 = make_float2(c0.z, c0.w);
+    a2 = make_float2(c1.x, c1.y);
+    a3 = make_float2(c1.z, c1.w);
 }
 
 // CIA coefficients of one temperature bracket: e = b + wtc d + cc
@@ -200,69 +170,73 @@ __device__ __forceinline__ void load_cia(const Model &m, int pair, int itc, int 
     d = mul2(c, add2(k1, make_float2(-k0.x, -k0.y)));
 }
 
-constexpr int SCACHE = 8;   // species whose cell coefficients stay in registers
-
-// Per-lane interpolation state for one sample and one wavenumber pair: the
-// coefficients of the current (T, p) cell for the first SCACHE species and of
-// the current CIA temperature bracket. Cells change only every few layers.
-template <bool BF16>
+// Per-lane interpolation state for SPL species per lane. A wavenumber pair is
+// shared by two lanes (h = lane & 1): lane h interpolates species SPL h ..
+// SPL h + SPL - 1 (slots beyond S read species S-1 with a zero weight) and
+// CIA pair h, keeping the current (T, p) cell's coefficients in registers;
+// cells change only every few layers.
+template <int SPL>
 struct PairInterp {
-    float2 a0[SCACHE], a1[SCACHE], a2[SCACHE], a3[SCACHE];
-    float2 b1, d1, b2, d2, nu4;
-    int cell = -1, itc = -1;
+    float2 a0[SPL], a1[SPL], a2[SPL], a3[SPL];
+    float2 b, d, nu4;
+    int cell = -1, itc = -1, h = 0;
 
-    __device__ __forceinline__ void init(const Model &m, int n) {
+    __device__ __forceinline__ void init(const Model &m, int n, int half) {
         const float2 nu = __ldg(reinterpret_cast<const float2 *>(m.nu + n));
         const float2 nu2 = mul2(nu, nu);
         nu4 = mul2(nu2, nu2);
         cell = itc = -1;
+        h = half;
     }
+    __device__ __forceinline__ int slot(int j) const { return SPL * h + j; }
+    __device__ __forceinline__ int table_species(const Model &m, int j) const { return min(slot(j), m.S - 1); }
     // L1 prefetch of the next layer's cell coefficients when the cell changes
     __device__ __forceinline__ void prefetch(const Model &m, const LayerConst &cur, const LayerConst &next, int n) const {
         if (next.cell == cur.cell) return;
 #pragma unroll
-        for (int j = 0; j < SCACHE; ++j)
-            if (j < m.S)
-                asm volatile("prefetch.global.L1 [%0];" ::"l"(m.coef4 + ((size_t)next.cell * m.S + j) * m.Np + n));
+        for (int j = 0; j < SPL; ++j)
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(
+                m.coef4 + (((size_t)next.cell * m.S + table_species(m, j)) * (m.Np >> 1) + (n >> 1)) * 2));
     }
     __device__ __forceinline__ void update(const Model &m, const SampleConst &sc, const LayerConst &lc, int n) {
         if (lc.cell != cell) {
             cell = lc.cell;
 #pragma unroll
-            for (int j = 0; j < SCACHE; ++j)
-                if (j < m.S) load_cell(m, j, lc.cell, n, sc.lx[j], a0[j], a1[j], a2[j], a3[j]);
+            for (int j = 0; j < SPL; ++j)
+                load_cell(m, table_species(m, j), lc.cell, n, sc.lx[slot(j)], a0[j], a1[j], a2[j], a3[j]);
         }
         if (lc.itc != itc) {
             itc = lc.itc;
-            load_cia(m, 0, lc.itc, n, b1, d1);
-            load_cia(m, 1, lc.itc, n, b2, d2);
+            load_cia(m, h, lc.itc, n, b, d);
         }
     }
-    // exponent of species j (cached): e = a0 + wp a1 + wt (a2 + wp a3); t = de/dwt
+    // exponent of species slot j: e = a0 + wp a1 + wt (a2 + wp a3); t = de/dwt
     __device__ __forceinline__ float2 expo(int j, float2 wp, float2 wt, float2 &t) const {
         t = fma2(wp, a3[j], a2[j]);
         return fma2(wt, t, fma2(wp, a1[j], a0[j]));
     }
+    // CIA term of this lane's pair
+    __device__ __forceinline__ float2 cia(const LayerConst &lc) const {
+        return ex2x2(fma2(f2(lc.wtc), d, add2(b, f2(h ? lc.cc2 : lc.cc1))));
+    }
 };
 
-// Exponent of an uncached species (s >= SCACHE), loading its cell each call.
-template <bool BF16>
-__device__ __forceinline__ float2 expo_uncached(const Model &m, const SampleConst &sc, const LayerConst &lc, int s,
-                                                int n, float2 wp, float2 wt, float2 &t) {
-    float2 a0, a1, a2, a3;
-    load_cell(m, s, lc.cell, n, sc.lx[s], a0, a1, a2, a3);
-    t = fma2(wp, a3, a2);
-    return fma2(wt, t, fma2(wp, a1, a0));
+// Species slots per lane for S species (two lanes per wavenumber pair).
+__host__ __device__ constexpr int spl_for(int S) { return S <= 4 ? 2 : (S <= 8 ? 4 : 8); }
+
+__device__ __forceinline__ float2 shfl_xor2(float2 v, int o) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
 }
 
-// Extinction alpha_l(nu) at the lane's wavenumber pair for the warp's layers
-// [lb, le):  alpha = n 2^-K sum_s 2^e_s + CIA_H2H2 + CIA_H2He + Rayleigh.
-// Calls out(l, alpha) for each layer.
-template <bool BF16, class Out>
+// Extinction alpha_l(nu) at wavenumber pair n, n+1 for layers [lb, le), the
+// lane pair (lane, lane ^ 1) splitting species and CIA pairs:
+//   alpha = n 2^-K sum_s 2^e_s + CIA_H2H2 + CIA_H2He + Rayleigh.
+// Calls out(l, alpha) on both lanes of the pair.
+template <int SPL, class Out>
 __device__ __forceinline__ void extinction_pair(const Model &m, const SampleConst &sc, int lb, int le, int n,
-                                                Out &&out) {
-    PairInterp<BF16> pi;
-    pi.init(m, n);
+                                                int half, Out &&out) {
+    PairInterp<SPL> pi;
+    pi.init(m, n, half);
     for (int l = lb; l < le; ++l) {
         const LayerConst &lc = sc.lay[l];
         pi.update(m, sc, lc, n);
@@ -270,14 +244,10 @@ __device__ __forceinline__ void extinction_pair(const Model &m, const SampleCons
         const float2 wp = f2(lc.wp), wt = f2(lc.wt);
         float2 sum = f2(0.f), t;
 #pragma unroll
-        for (int j = 0; j < SCACHE; ++j)
-            if (j < m.S) sum = add2(sum, ex2x2(pi.expo(j, wp, wt, t)));
-        for (int s = SCACHE; s < m.S; ++s) sum = add2(sum, ex2x2(expo_uncached<BF16>(m, sc, lc, s, n, wp, wt, t)));
-        const float2 wc = f2(lc.wtc);
-        const float2 c1 = ex2x2(fma2(wc, pi.d1, add2(pi.b1, f2(lc.cc1))));
-        const float2 c2 = ex2x2(fma2(wc, pi.d2, add2(pi.b2, f2(lc.cc2))));
-        const float2 base = fma2(f2(lc.ray), pi.nu4, add2(c1, c2));
-        out(l, fma2(sum, f2(lc.nsc), base));
+        for (int j = 0; j < SPL; ++j) sum = add2(sum, ex2x2(pi.expo(j, wp, wt, t)));
+        float2 mine = fma2(sum, f2(lc.nsc), pi.cia(lc));
+        if (half == 0) mine = fma2(f2(lc.ray), pi.nu4, mine);
+        out(l, add2(mine, shfl_xor2(mine, 1)));
     }
 }
 

@@ -38,11 +38,11 @@ constexpr int BW_WARPS = 16;
 constexpr int BW_THREADS = BW_WARPS * 32;
 constexpr int BT = 128;              // wavenumbers per backward tile
 constexpr int T2_PITCH = 136;        // bf16 pitch of tau_bar rows [i][128 nu] (272 B: 17 x 16 B)
-constexpr int RB2_BYTES = 528;       // bytes per row buffer row (33 x 16 B): two 256-B halves
-// Row buffer, per layer and per 64-wavenumber half h (bytes [256 h, 256 h + 256)):
-// first alpha_bar as 64 FP32, then overwritten by the extinction as BF16 hi
-// (bytes 0..127 of the half) and lo (bytes 128..255). Each half belongs to one
-// warp, so the overwrite only needs a warp barrier.
+constexpr int RB2_BYTES = 528;       // bytes per row buffer row (33 x 16 B): four 128-B quarters
+// Row buffer, per layer and per 32-wavenumber quarter k (bytes [128 k, 128 k + 128)):
+// first alpha_bar as 32 FP32, then overwritten by the extinction as BF16 hi
+// (bytes 0..63 of the quarter) and lo (bytes 64..127). Each quarter of a row
+// belongs to one warp, so the overwrite only needs a warp barrier.
 
 struct TransBwdSmem {
     SampleConst sc;
@@ -74,7 +74,7 @@ __device__ void stage_lmat(const Model &m, const Work &w, int b, __nv_bfloat16 *
     for (int i = threadIdx.x; i < LP; i += FTHREADS) area[i] = (i < L) ? w.area[(size_t)b * L + i] : 0.f;
 }
 
-template <bool BF16, bool STORE_E>
+template <int SPL, bool STORE_E>
 __global__ void __launch_bounds__(FTHREADS, 2) k_trans_fwd(Model m, Work w, int chunk_tiles) {
     extern __shared__ float4 smem4[];
     TransFwdSmem &sm = *reinterpret_cast<TransFwdSmem *>(smem4);
@@ -88,8 +88,11 @@ __global__ void __launch_bounds__(FTHREADS, 2) k_trans_fwd(Model m, Work w, int 
         sm.ah[L * R_PITCH + idx] = __float2bfloat16_rn(0.f);
         sm.al[L * R_PITCH + idx] = __float2bfloat16_rn(0.f);
     }
+    // interpolation: 4 layer groups x 2 halves (32 wavenumbers) of the tile; a
+    // wavenumber pair is shared by a lane pair splitting the species
+    const int half = lane & 1, pair = 16 * (warp & 1) + (lane >> 1);
     int lb, le;
-    warp_layers(L, warp, lb, le);
+    group_layers(L, warp >> 1, FWARPS / 2, lb, le);
     const uint32_t blh = smem_u32(sm.lh), bll = smem_u32(sm.ll), bah = smem_u32(sm.ah), bal = smem_u32(sm.al);
     const int ksmax = (L + 15) / 16;
     int cur_b = -1;
@@ -108,11 +111,10 @@ __global__ void __launch_bounds__(FTHREADS, 2) k_trans_fwd(Model m, Work w, int 
         const int t1 = min(ntiles, (c + 1) * chunk_tiles);
         for (int t = c * chunk_tiles; t < t1; ++t) {
             const int nt0 = t * FT;
-            extinction_pair<BF16>(m, sm.sc, lb, le, nt0 + 2 * lane, [&](int l, float2 a) {
+            extinction_pair<SPL>(m, sm.sc, lb, le, nt0 + 2 * pair, half, [&](int l, float2 a) {
                 uint32_t hi, lo;
                 split2(a, hi, lo);
-                *reinterpret_cast<uint32_t *>(sm.ah + l * R_PITCH + 2 * lane) = hi;
-                *reinterpret_cast<uint32_t *>(sm.al + l * R_PITCH + 2 * lane) = lo;
+                *reinterpret_cast<uint32_t *>((half ? sm.al : sm.ah) + l * R_PITCH + 2 * pair) = half ? lo : hi;
             });
             __syncthreads();
             // tau[i][nu] for this warp's 8 wavenumbers, lower-triangular blocks only
@@ -243,87 +245,77 @@ __device__ __forceinline__ int reduce_index8(int lane) {
 }
 
 // Backward interpolation for one warp: layers [lb, le), wavenumber pair n, n+1
-// (the warp's 64-wavenumber half `half` of its row-buffer rows). Reads
-// alpha_bar, adds per-layer reductions to red[l][*] and per-species totals to
-// qtot[s], then overwrites its half-rows with the extinction as split BF16.
-// Per layer, summed over wavenumber: QS = sum abar sum_s e_s,
+// shared by the lane pair (lane, lane ^ 1) that splits the species; `quarter`
+// points at the warp's 32-wavenumber quarter of row 0 of the row buffer.
+// Reads alpha_bar, adds per-layer reductions to red[l][*] and per-species
+// totals to qtot[s], then overwrites the quarter-rows with the extinction as
+// split BF16. Per layer, summed over wavenumber: QS = sum abar sum_s e_s,
 // D = sum abar sum_s e_s dlog10(sigma_s)/dlog10 T, C1, C2 = sum abar c1, c2,
 // C1T, C2T = sum abar c dlog10 k/dT, W4 = sum abar (nu/nu_ref)^4; per species
 // Q_s = sum_l sum abar e_s (e_s, c1, c2 the species and CIA extinction terms).
-template <bool BF16>
-__device__ void interp_backward(const Model &m, const SampleConst &sc, int lb, int le, int n, int lane, int half,
-                                unsigned char *rb, float *red, float *qtot) {
-    const int S = m.S;
+template <int SPL>
+__device__ void interp_backward(const Model &m, const SampleConst &sc, int lb, int le, int n, int half, int lane,
+                                unsigned char *quarter, float *red, float *qtot) {
+    const int S = m.S, q = lane >> 1;
     const int ridx = reduce_index8(lane);
     const bool writer = (lane & 3) == 0;
     const float inv_l2 = (float)(1.0 / LOG2_10);
     const float ray_ref = (float)(1.0 / ((double)m.ray_nu_ref * m.ray_nu_ref * m.ray_nu_ref * m.ray_nu_ref));
-    PairInterp<BF16> pi;
-    pi.init(m, n);
-    float qa[SCACHE], qx[SCACHE];
+    PairInterp<SPL> pi;
+    pi.init(m, n, half);
+    float2 qa[SPL];
 #pragma unroll
-    for (int j = 0; j < SCACHE; ++j) qa[j] = qx[j] = 0.f;
+    for (int j = 0; j < SPL; ++j) qa[j] = f2(0.f);
     for (int l = lb; l < le; ++l) {
         const LayerConst &lc = sc.lay[l];
         pi.update(m, sc, lc, n);
         if (l + 1 < le) pi.prefetch(m, lc, sc.lay[l + 1], n);
-        unsigned char *hrow = rb + (size_t)l * RB2_BYTES + 256 * half;
-        const float2 ab = *reinterpret_cast<const float2 *>(hrow + 8 * lane);
+        unsigned char *row = quarter + (size_t)l * RB2_BYTES;
+        const float2 ab = *reinterpret_cast<const float2 *>(row + 8 * q);
+        const float2 abn = mul2(ab, f2(lc.nsc));
         const float2 wp = f2(lc.wp), wt = f2(lc.wt);
-        float2 sum = f2(0.f), dsum = f2(0.f), t;
-        float qs = 0.f;
+        float2 sum = f2(0.f), pt = f2(0.f), t;
 #pragma unroll
-        for (int j = 0; j < SCACHE; ++j) {
-            if (j < S) {
-                const float2 p = ex2x2(pi.expo(j, wp, wt, t));
-                sum = add2(sum, p);
-                const float2 ap = mul2(ab, p);
-                const float q = (ap.x + ap.y) * lc.nsc;
-                qa[j] += q;
-                qs += q;
-                dsum = fma2(ap, t, dsum);
-            }
-        }
-        for (int s = SCACHE; s < S; ++s) {
-            const float2 p = ex2x2(expo_uncached<BF16>(m, sc, lc, s, n, wp, wt, t));
+        for (int j = 0; j < SPL; ++j) {
+            const float2 p = ex2x2(pi.expo(j, wp, wt, t));
             sum = add2(sum, p);
-            const float2 ap = mul2(ab, p);
-            const float q = (ap.x + ap.y) * lc.nsc;
-#pragma unroll
-            for (int k = 0; k < SCACHE; ++k)
-                if (k == s - SCACHE) qx[k] += q;
-            qs += q;
-            dsum = fma2(ap, t, dsum);
+            qa[j] = fma2(abn, p, qa[j]);
+            pt = fma2(p, t, pt);
         }
-        const float2 wc = f2(lc.wtc);
-        const float2 c1 = ex2x2(fma2(wc, pi.d1, add2(pi.b1, f2(lc.cc1))));
-        const float2 c2 = ex2x2(fma2(wc, pi.d2, add2(pi.b2, f2(lc.cc2))));
-        const float2 ac1 = mul2(ab, c1), ac2 = mul2(ab, c2);
-        const float2 t1 = mul2(ac1, pi.d1), t2 = mul2(ac2, pi.d2), t4 = mul2(ab, pi.nu4);
+        const float2 c = pi.cia(lc);
+        const float2 ac = mul2(ab, c);
+        const float2 act = mul2(ac, pi.d);
+        const float cs = ac.x + ac.y, cts = (act.x + act.y) * (lc.gtc * inv_l2);
         float v[8];
-        v[0] = qs;
-        v[1] = (dsum.x + dsum.y) * (lc.nsc * lc.gt * inv_l2);
-        v[2] = ac1.x + ac1.y;
-        v[3] = ac2.x + ac2.y;
-        v[4] = (t1.x + t1.y) * (lc.gtc * inv_l2);
-        v[5] = (t2.x + t2.y) * (lc.gtc * inv_l2);
-        v[6] = (t4.x + t4.y) * ray_ref;
+        v[0] = abn.x * sum.x + abn.y * sum.y;
+        v[1] = (abn.x * pt.x + abn.y * pt.y) * (lc.gt * inv_l2);
+        v[2] = half ? 0.f : cs;
+        v[3] = half ? cs : 0.f;
+        v[4] = half ? 0.f : cts;
+        v[5] = half ? cts : 0.f;
+        v[6] = half ? 0.f : (ab.x * pi.nu4.x + ab.y * pi.nu4.y) * ray_ref;
         v[7] = 0.f;
         const float tot = transpose_reduce8(v, lane);
         if (writer && ridx < N_RED && tot != 0.f) atomicAdd(red + l * N_RED + ridx, tot);
-        const float2 base = fma2(f2(lc.ray), pi.nu4, add2(c1, c2));
-        const float2 alpha = fma2(sum, f2(lc.nsc), base);
+        float2 mine = fma2(sum, f2(lc.nsc), c);
+        if (half == 0) mine = fma2(f2(lc.ray), pi.nu4, mine);
+        const float2 alpha = add2(mine, shfl_xor2(mine, 1));
         uint32_t hi, lo;
         split2(alpha, hi, lo);
         __syncwarp();
-        *reinterpret_cast<uint32_t *>(hrow + 4 * lane) = hi;
-        *reinterpret_cast<uint32_t *>(hrow + 128 + 4 * lane) = lo;
+        *reinterpret_cast<uint32_t *>(row + (half ? 64 : 0) + 4 * q) = half ? lo : hi;
     }
-    const float tq = transpose_reduce8(qa, lane);
-    if (writer && ridx < S && tq != 0.f) atomicAdd(qtot + ridx, tq);
-    if (S > SCACHE) {
-        const float tx = transpose_reduce8(qx, lane);
-        if (writer && SCACHE + ridx < S && tx != 0.f) atomicAdd(qtot + SCACHE + ridx, tx);
+    // per-species totals: slot j of lane half h is species SPL h + j
+#pragma unroll
+    for (int c0 = 0; c0 < 2 * SPL; c0 += 8) {
+        float v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int sl = c0 + k;
+            v[k] = (sl < 2 * SPL && sl / SPL == half) ? qa[sl % SPL].x + qa[sl % SPL].y : 0.f;
+        }
+        const float tq = transpose_reduce8(v, lane);
+        if (writer && c0 + ridx < S && tq != 0.f) atomicAdd(qtot + c0 + ridx, tq);
     }
 }
 
@@ -331,11 +323,11 @@ __device__ void interp_backward(const Model &m, const SampleConst &sc, int lb, i
 // row buffer, wavenumbers [16 ks, 16 ks + 16) of the tile; lo = false/true.
 __device__ __forceinline__ uint32_t rb_addr(uint32_t base, int n0, int ks, bool lo, int lane) {
     const int l = lane & 15;
-    const int half = ks >> 2, kin = (ks & 3) * 16 + ((l >> 3) << 3);
-    return base + (uint32_t)((n0 + (l & 7)) * RB2_BYTES + 256 * half + (lo ? 128 : 0) + 2 * kin);
+    const int qt = ks >> 1, kin = (ks & 1) * 16 + ((l >> 3) << 3);
+    return base + (uint32_t)((n0 + (l & 7)) * RB2_BYTES + 128 * qt + (lo ? 64 : 0) + 2 * kin);
 }
 
-template <bool BF16>
+template <int SPL>
 __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, int chunk_tiles) {
     extern __shared__ float4 smem4[];
     TransBwdSmem &sm = *reinterpret_cast<TransBwdSmem *>(smem4);
@@ -344,9 +336,11 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
     const int ntiles = (N + BT - 1) / BT;
     const int nchunks = (ntiles + chunk_tiles - 1) / chunk_tiles;
     const long long total = (long long)w.B * nchunks;
-    const int half = warp & 1, group = warp >> 1;       // interpolation: layer group, wavenumber half
+    const int group = warp >> 1;                        // tau_bar phase: rows i = group + 8 k
+    // interpolation: 4 layer groups x 4 quarters (32 wavenumbers); lane pairs split species
+    const int half = lane & 1, vq = warp & 3, pair = 16 * vq + (lane >> 1);
     int lb, le;
-    warp_layers(L, group, lb, le);
+    group_layers(L, warp >> 2, 4, lb, le);
     // padding rows (impact parameters / layers >= L) of tau_bar and the row buffer stay zero
     for (int idx = threadIdx.x; idx < (LP - L) * T2_PITCH; idx += BW_THREADS) {
         sm.th[L * T2_PITCH + idx] = __float2bfloat16_rn(0.f);
@@ -406,11 +400,11 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
         const int t1 = min(ntiles, (c + 1) * chunk_tiles);
         for (int t = c * chunk_tiles; t < t1; ++t) {
             const int nt0 = t * BT;
-            const int n = nt0 + 2 * (lane + 32 * half);
             // tau_bar = dbar A_i exp(-tau); area_bar += dbar (1 - exp(-tau))
             {
-                const float2 db = *reinterpret_cast<const float2 *>(w.dbar + (size_t)b * m.Np + n);
-                const float *eb = w.estore + (size_t)b * L * m.Np + n;
+                const int nl = nt0 + 2 * (lane + 32 * (warp & 1));
+                const float2 db = *reinterpret_cast<const float2 *>(w.dbar + (size_t)b * m.Np + nl);
+                const float *eb = w.estore + (size_t)b * L * m.Np + nl;
                 float av[16];
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
@@ -421,7 +415,7 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
                         const float a = sm.area[i];
                         uint32_t hi, lo;
                         split2(make_float2(db.x * a * e.x, db.y * a * e.y), hi, lo);
-                        const int col = 2 * (lane + 32 * half);
+                        const int col = 2 * (lane + 32 * (warp & 1));
                         *reinterpret_cast<uint32_t *>(sm.th + i * T2_PITCH + col) = hi;
                         *reinterpret_cast<uint32_t *>(sm.tl + i * T2_PITCH + col) = lo;
                         av[k] = db.x * (1.f - e.x) + db.y * (1.f - e.y);
@@ -453,20 +447,20 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
                     }
                 }
                 const int colt = 8 * warp + 2 * (lane & 3), r = lane >> 2;
-                const int h = colt >> 6, cin = colt & 63;
+                const int qt = colt >> 5, cin = colt & 31;
 #pragma unroll
                 for (int ml = 0; ml < 7; ++ml) {
                     const int l0 = 16 * ml + r, l1 = l0 + 8;
                     if (l0 < L)
-                        *reinterpret_cast<float2 *>(sm.rb + (size_t)l0 * RB2_BYTES + 256 * h + 4 * cin) =
+                        *reinterpret_cast<float2 *>(sm.rb + (size_t)l0 * RB2_BYTES + 128 * qt + 4 * cin) =
                             make_float2(acc[ml][0], acc[ml][1]);
                     if (l1 < L)
-                        *reinterpret_cast<float2 *>(sm.rb + (size_t)l1 * RB2_BYTES + 256 * h + 4 * cin) =
+                        *reinterpret_cast<float2 *>(sm.rb + (size_t)l1 * RB2_BYTES + 128 * qt + 4 * cin) =
                             make_float2(acc[ml][2], acc[ml][3]);
                 }
             }
             __syncthreads();
-            interp_backward<BF16>(m, sm.sc, lb, le, n, lane, half, sm.rb, sm.red, sm.qtot);
+            interp_backward<SPL>(m, sm.sc, lb, le, nt0 + 2 * pair, half, lane, sm.rb + 128 * vq, sm.red, sm.qtot);
             __syncthreads();
             // L_bar[i][l] += sum_nu tau_bar[i][nu] alpha[l][nu] over this tile (8 k-steps)
 #pragma unroll
@@ -518,13 +512,15 @@ int launch_trans_fused_forward(const Model &m, const Work &w, bool store_e, cuda
     const long long items = (long long)w.B * ((ntiles + chunk - 1) / chunk);
     const int grid = (int)std::min<long long>(items, 2LL * sm_count());
     const size_t sm = fwd_smem();
-#define ES_FWD(BF, SE)                                                                          \
+#define ES_FWD(SPL, SE)                                                                         \
     do {                                                                                        \
-        cudaFuncSetAttribute(k_trans_fwd<BF, SE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-        ES_LAUNCH(h, "k_trans_fwd", st, k_trans_fwd<BF, SE><<<grid, FTHREADS, sm, st>>>(m, w, chunk)); \
+        cudaFuncSetAttribute(k_trans_fwd<SPL, SE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+        ES_LAUNCH(h, "k_trans_fwd", st, k_trans_fwd<SPL, SE><<<grid, FTHREADS, sm, st>>>(m, w, chunk)); \
     } while (0)
-    if (m.bf16) { if (store_e) ES_FWD(true, true); else ES_FWD(true, false); }
-    else { if (store_e) ES_FWD(false, true); else ES_FWD(false, false); }
+    const int spl = spl_for(m.S);
+    if (spl == 2) { if (store_e) ES_FWD(2, true); else ES_FWD(2, false); }
+    else if (spl == 4) { if (store_e) ES_FWD(4, true); else ES_FWD(4, false); }
+    else { if (store_e) ES_FWD(8, true); else ES_FWD(8, false); }
 #undef ES_FWD
     return 1;
 }
@@ -535,13 +531,16 @@ int launch_trans_fused_backward(const Model &m, const Work &w, cudaStream_t st, 
     const long long items = (long long)w.B * ((ntiles + chunk - 1) / chunk);
     const int grid = (int)std::min<long long>(items, (long long)sm_count());
     const size_t sm = bwd_smem();
-    if (m.bf16) {
-        cudaFuncSetAttribute(k_trans_bwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        ES_LAUNCH(h, "k_trans_bwd", st, k_trans_bwd<true><<<grid, BW_THREADS, sm, st>>>(m, w, chunk));
-    } else {
-        cudaFuncSetAttribute(k_trans_bwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        ES_LAUNCH(h, "k_trans_bwd", st, k_trans_bwd<false><<<grid, BW_THREADS, sm, st>>>(m, w, chunk));
-    }
+#define ES_BWD(SPL)                                                                             \
+    do {                                                                                        \
+        cudaFuncSetAttribute(k_trans_bwd<SPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+        ES_LAUNCH(h, "k_trans_bwd", st, k_trans_bwd<SPL><<<grid, BW_THREADS, sm, st>>>(m, w, chunk)); \
+    } while (0)
+    const int spl = spl_for(m.S);
+    if (spl == 2) ES_BWD(2);
+    else if (spl == 4) ES_BWD(4);
+    else ES_BWD(8);
+#undef ES_BWD
     return 1;
 }
 

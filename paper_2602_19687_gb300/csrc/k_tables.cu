@@ -6,7 +6,8 @@
 //   c0 = L v00, c1 = L (v01 - v00), c2 = L (v10 - v00),
 //   c3 = L ((v11 - v10) - (v01 - v00)),  L = log2(10),
 // identical to bilinear interpolation with weights (1-wt)(1-wp), (1-wt) wp,
-// wt (1-wp), wt wp. Stored [cell][s][Np] as float4.
+// wt (1-wp), wt wp. Stored per (cell, s) and wavenumber pair as two float4
+// (c0, c0', c1, c1'), (c2, c2', c3, c3') (primes: the pair's second wavenumber).
 #include "internal.cuh"
 
 namespace es {
@@ -31,7 +32,11 @@ __global__ void k_build_coef(Model m, float4 *coef) {
     const float v00 = table_value<BF16>(m, row, n), v01 = table_value<BF16>(m, row + 1, n);
     const float v10 = table_value<BF16>(m, row + m.NP, n), v11 = table_value<BF16>(m, row + m.NP + 1, n);
     const float l = (float)LOG2_10, d0 = v01 - v00;
-    coef[(size_t)cs * m.Np + n] = make_float4(l * v00, l * d0, l * (v10 - v00), l * ((v11 - v10) - d0));
+    float *out = reinterpret_cast<float *>(coef + ((size_t)cs * (m.Np >> 1) + (n >> 1)) * 2) + (n & 1);
+    out[0] = l * v00;
+    out[2] = l * d0;
+    out[4] = l * (v10 - v00);
+    out[6] = l * ((v11 - v10) - d0);
 }
 
 }  // namespace
