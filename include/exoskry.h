@@ -163,9 +163,34 @@ es_status es_loglike(es_ctx *ctx, double *lnL, int mem, es_stream_t stream);
 
 /* ln L and its gradient with respect to the free parameters,
  * grad [batch][n_free] (double), by a hand-written adjoint that recomputes
- * the interpolated opacities. Invalid samples get a zero gradient. */
+ * the interpolated opacities. Invalid samples get a zero gradient.
+ * lnL or grad may be NULL (not copied out).
+ *
+ * CUDA-graph replay (es_loglike and es_forward_backward): the first call
+ * after the batch shape, the tables, the grid or a buffer changed runs its
+ * kernels directly; the next one captures the whole launch sequence into a
+ * CUDA graph, and later calls replay it. Inputs and outputs go through the
+ * context's own device buffers, so the graph stays valid when only theta
+ * values (es_set_batch with the same batch and kind counts), data or output
+ * pointers change. The graph runs on a private stream ordered after all
+ * earlier work on `stream` by events, and later work on `stream` waits for
+ * it. Disabled while profiling is on, or by es_set_graphs(ctx, 0). */
 es_status es_forward_backward(es_ctx *ctx, double *lnL, double *grad, int mem,
                               es_stream_t stream);
+
+/* Time the fused transmission kernels at several work-item sizes
+ * (wavenumber tiles per persistent work item) on the current batch and keep
+ * the fastest for later calls of this context; the results are readable
+ * through es_query keys 8 and 9. Runs a full forward + adjoint plus about
+ * twenty timed kernel launches on `stream` and synchronises it; leaves the
+ * context's outputs undefined until the next es_loglike /
+ * es_forward_backward. A batch with no transmission samples is a no-op.
+ * Not a step of the paper's method: launch-shape tuning for this GPU. */
+es_status es_autotune(es_ctx *ctx, es_stream_t stream);
+
+/* CUDA-graph replay of es_loglike / es_forward_backward on (1, default) or
+ * off (0). Either way drops any captured graph. */
+es_status es_set_graphs(es_ctx *ctx, int on);
 
 /* ln L of `batch` parameter vectors, like es_set_batch + es_loglike, but
  * without allocating any device memory: all per-call workspace comes from
@@ -190,7 +215,10 @@ es_status es_loglike_noalloc(es_ctx *ctx, const double *theta, const int32_t *ki
 es_status es_get_flags(es_ctx *ctx, int32_t *flags, int mem, es_stream_t stream);
 
 /* Sizes: 0 n_nu, 1 n_bins, 2 n_free, 3 batch, 4 n_layers, 5 n_species,
- * 6 device workspace bytes, 7 kernel launches issued by the last call.
+ * 6 device workspace bytes, 7 kernel launches issued by the last call (a
+ * replayed graph counts the launches it holds), 8 / 9 work-item size of the
+ * fused transmission forward / adjoint kernel (0: built-in heuristic),
+ * 10 graph replay enabled (1) or not (0).
  * Returns -1 for an unknown key or a NULL context. */
 int64_t es_query(const es_ctx *ctx, int key);
 

@@ -25,8 +25,8 @@ ES_MAX_LAYERS = 112
 STATUS_NAMES = {0: "ES_OK", 1: "ES_EINVAL", 2: "ES_ENOMEM", 3: "ES_ECUDA", 4: "ES_ESTATE", 5: "ES_ETIMEOUT"}
 
 EXPORTS = ["es_create", "es_load_tables", "es_set_grid", "es_set_data", "es_set_batch", "es_forward",
-           "es_loglike", "es_forward_backward", "es_loglike_noalloc", "es_get_flags", "es_query",
-           "es_set_profiling",
+           "es_loglike", "es_forward_backward", "es_loglike_noalloc", "es_autotune", "es_set_graphs",
+           "es_get_flags", "es_query", "es_set_profiling",
            "es_get_profile", "es_last_error", "es_destroy"]
 
 
@@ -74,6 +74,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.es_forward_backward.argtypes = [vp, vp, vp, ip, vp]
     lib.es_loglike_noalloc.argtypes = [vp, vp, vp, ip, vp, vp]
     lib.es_get_flags.argtypes = [vp, vp, ip, vp]
+    lib.es_autotune.argtypes = [vp, vp]
+    lib.es_set_graphs.argtypes = [vp, ip]
     lib.es_query.argtypes = [vp, ip]
     lib.es_query.restype = ctypes.c_int64
     lib.es_set_profiling.argtypes = [vp, ip]
@@ -212,6 +214,14 @@ class Context:
         """ln L without device allocation (theta, kind, lnl: CUDA tensors; kind may be None)."""
         self._check(self.lib.es_loglike_noalloc(self.handle, _ptr(theta), _ptr(kind), int(theta.shape[0]),
                                                 _ptr(lnl), _stream(stream)), "es_loglike_noalloc")
+
+    def es_autotune(self, stream=None):
+        """Pick the fused transmission kernels' work-item sizes by timing them on the current batch."""
+        self._check(self.lib.es_autotune(self.handle, _stream(stream)), "es_autotune")
+        return self.es_query(8), self.es_query(9)
+
+    def es_set_graphs(self, on):
+        self._check(self.lib.es_set_graphs(self.handle, 1 if on else 0), "es_set_graphs")
 
     def es_get_flags(self, flags, stream=None):
         self._check(self.lib.es_get_flags(self.handle, _ptr(flags), _mem(flags), _stream(stream)),

@@ -37,4 +37,15 @@ struct es_ctx {
     int open_entry = -1;
     cudaEvent_t open_ev = nullptr;
     es::Hook hook;
+    // tuned work-item sizes of the fused transmission kernels (0: heuristic)
+    int fwd_chunk = 0, bwd_chunk = 0;
+    // CUDA-graph replay of es_loglike / es_forward_backward
+    bool use_graph = true;
+    int graph_epoch = 0;
+    cudaStream_t gstream = nullptr;   // private stream the graphs run on
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;              // bumped whenever buffers or the batch shape change
+    struct GraphSlot {
+        cudaGraphExec_t exec = nullptr;
+        int epoch = -1, calls = 0;
+    } graph_fb, graph_ll;
 };

@@ -131,8 +131,62 @@ es_status check_launch(es_ctx *c, const char *what) {
     return e == cudaSuccess ? ES_OK : cuda_fail(c, e, what);
 }
 
+void drop_graph(es_ctx::GraphSlot &g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    g.epoch = -1;
+    g.calls = 0;
+}
+
+// Run `enqueue(stream)` eagerly, or, from the second call with an unchanged
+// batch shape and buffers on, capture it once into a CUDA graph and replay it.
+// The graph is captured and launched on a private non-blocking stream joined
+// to the caller's stream by events, so callers on the legacy default stream
+// get replay too. Profiling runs stay eager (their events are per launch).
+template <class F>
+es_status launch_or_replay(es_ctx *c, es_ctx::GraphSlot &g, cudaStream_t st, F &&enqueue) {
+    if (!c->use_graph || c->prof_on) return enqueue(st);
+    if (g.epoch != c->graph_epoch) {
+        drop_graph(g);
+        g.epoch = c->graph_epoch;
+    }
+    if (!g.exec) {
+        if (g.calls++ == 0) return enqueue(st);   // first call eager: sets attributes, warms caches
+        cudaError_t e = cudaSuccess;
+        if (!c->gstream) {
+            e = cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+            if (e != cudaSuccess) return cuda_fail(c, e, "graph stream");
+        }
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(c, e, "graph capture");
+        es_status s = enqueue(c->gstream);
+        e = cudaStreamEndCapture(c->gstream, &graph);
+        if (s != ES_OK || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return s != ES_OK ? s : cuda_fail(c, e, "graph capture");
+        }
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            g.exec = nullptr;
+            return cuda_fail(c, e, "graph instantiate");
+        }
+    }
+    cudaError_t e = cudaEventRecord(c->ev_fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->gstream, c->ev_fork, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(g.exec, c->gstream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->gstream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->ev_join, 0);
+    return e == cudaSuccess ? ES_OK : cuda_fail(c, e, "graph launch");
+}
+
 es_status alloc_forward(es_ctx *c, int B) {
     if (B <= c->cap_b) return ES_OK;
+    ++c->graph_epoch;
     free_all(c->work_bufs);
     free_all(c->bwd_bufs);
     c->cap_b_bwd = 0;
@@ -181,6 +235,7 @@ es_status alloc_forward(es_ctx *c, int B) {
 es_status alloc_backward(es_ctx *c) {
     const int B = c->cap_b;
     if (B <= c->cap_b_bwd) return ES_OK;
+    ++c->graph_epoch;
     free_all(c->bwd_bufs);
     const Model &m = c->m;
     const size_t L = m.L, S = m.S, N = m.N;
@@ -205,6 +260,7 @@ es_status alloc_backward(es_ctx *c) {
 // transmission adjoint.
 es_status ensure_big(es_ctx *c, float **p, size_t &cap, size_t count) {
     if (count <= cap && *p) return ES_OK;
+    ++c->graph_epoch;
     if (*p) cudaFree(*p);
     *p = nullptr;
     cap = 0;
@@ -228,21 +284,47 @@ es_status ready(es_ctx *c) {
     return ES_OK;
 }
 
-// forward sequence; adjoint=true also prepares dbar / misc for the backward
-es_status run_forward(es_ctx *c, bool adjoint, float *spec_out, double *binned_out, double *lnl_out,
-                      cudaStream_t st) {
+es_status ensure_ymod(es_ctx *c) {
+    size_t need = (size_t)c->cap_b * c->m.nbins;
+    if (need <= c->ymod_cap) return ES_OK;
+    ++c->graph_epoch;
+    if (c->w.ymod) cudaFree(c->w.ymod);
+    c->w.ymod = nullptr;
+    c->ymod_cap = 0;
+    void *q = nullptr;
+    if (cudaMalloc(&q, need * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, ES_ENOMEM, "cudaMalloc of the binned-model buffer failed");
+    }
+    c->w.ymod = static_cast<double *>(q);
+    c->ymod_cap = need;
+    return ES_OK;
+}
+
+// Device buffers a call needs (allocated before any launch or capture).
+es_status prepare(es_ctx *c, bool adjoint) {
     es_status s;
     const size_t big = (size_t)c->batch * c->m.L * c->m.N;
+    if ((s = ensure_ymod(c)) != ES_OK) return s;
     if (c->n_kind[1] && (s = ensure_big(c, &c->w.alpha, c->alpha_cap, big)) != ES_OK) return s;
-    if (adjoint && c->n_kind[0] &&
-        (s = ensure_big(c, &c->w.estore, c->estore_cap, (size_t)c->batch * c->m.L * c->m.Np)) != ES_OK)
-        return s;
+    if (adjoint) {
+        if ((s = alloc_backward(c)) != ES_OK) return s;
+        if (c->n_kind[0] &&
+            (s = ensure_big(c, &c->w.estore, c->estore_cap, (size_t)c->batch * c->m.L * c->m.Np)) != ES_OK)
+            return s;
+        if (c->n_kind[1] && (s = ensure_big(c, &c->w.abar, c->abar_cap, big)) != ES_OK) return s;
+    }
+    return ES_OK;
+}
+
+es_status run_forward(es_ctx *c, bool adjoint, float *spec_out, double *binned_out, double *lnl_out,
+                      cudaStream_t st) {
     Work w = c->w;
     w.B = c->batch;
     int launches = 0;
     const Hook &h = c->hook;
     launches += launch_setup(c->m, w, st, h);
-    if (c->n_kind[0]) launches += launch_trans_fused_forward(c->m, w, adjoint, st, h);
+    if (c->n_kind[0]) launches += launch_trans_fused_forward(c->m, w, adjoint, c->fwd_chunk, st, h);
     if (c->n_kind[1]) {
         launches += launch_extinction(c->m, w, ES_KIND_EMISSION, st, h);
         launches += launch_emission(c->m, w, st, h);
@@ -256,22 +338,6 @@ es_status run_forward(es_ctx *c, bool adjoint, float *spec_out, double *binned_o
 }
 
 }  // namespace
-
-static es_status ensure_ymod(es_ctx *c) {
-    size_t need = (size_t)c->cap_b * c->m.nbins;
-    if (need <= c->ymod_cap) return ES_OK;
-    if (c->w.ymod) cudaFree(c->w.ymod);
-    c->w.ymod = nullptr;
-    c->ymod_cap = 0;
-    void *q = nullptr;
-    if (cudaMalloc(&q, need * sizeof(double)) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(c, ES_ENOMEM, "cudaMalloc of the binned-model buffer failed");
-    }
-    c->w.ymod = static_cast<double *>(q);
-    c->ymod_cap = need;
-    return ES_OK;
-}
 
 extern "C" {
 
@@ -458,6 +524,7 @@ es_status es_load_tables(es_ctx *c, const es_tables_desc *t) {
     if (e != cudaSuccess) return cuda_fail(c, e, "coefficient table");
     m.coef4 = coef;
     c->have_tables = true;
+    ++c->graph_epoch;
     return ES_OK;
 }
 
@@ -516,6 +583,7 @@ es_status es_set_grid(es_ctx *c, const double *lo, const double *hi, int nbins) 
         c->s_host[k].assign(nbins, 1.0);
     }
     c->have_grid = true;
+    ++c->graph_epoch;
     return ES_OK;
 }
 
@@ -575,6 +643,7 @@ es_status es_set_batch(es_ctx *c, const double *theta, const int32_t *kind, int 
         e = cudaStreamSynchronize(st);   // the host vector kh goes out of scope
         if (e != cudaSuccess) return cuda_fail(c, e, "kind upload");
     }
+    if (batch != c->batch || nk[0] != c->n_kind[0] || nk[1] != c->n_kind[1]) ++c->graph_epoch;
     c->batch = batch;
     c->n_kind[0] = nk[0];
     c->n_kind[1] = nk[1];
@@ -602,7 +671,7 @@ es_status es_forward(es_ctx *c, float *spectrum, double *binned, double *lnl, in
     es_status s = ready(c);
     if (s != ES_OK) return s;
     cudaSetDevice(c->device);
-    if ((s = ensure_ymod(c)) != ES_OK) return s;
+    if ((s = prepare(c, false)) != ES_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int B = c->batch;
     float *d_spec = spectrum;
@@ -628,8 +697,48 @@ es_status es_forward(es_ctx *c, float *spectrum, double *binned, double *lnl, in
 }
 
 es_status es_loglike(es_ctx *c, double *lnl, int mem, es_stream_t stream) {
+    if (!c) return ES_EINVAL;
     if (!lnl) return fail(c, ES_EINVAL, "lnL pointer is NULL");
-    return es_forward(c, nullptr, nullptr, lnl, mem, stream);
+    if (mem != ES_MEM_HOST && mem != ES_MEM_DEVICE) return fail(c, ES_EINVAL, "bad mem");
+    es_status s = ready(c);
+    if (s != ES_OK) return s;
+    cudaSetDevice(c->device);
+    if ((s = prepare(c, false)) != ES_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    s = launch_or_replay(c, c->graph_ll, st,
+                         [&](cudaStream_t q) { return run_forward(c, false, nullptr, nullptr, c->d_lnl, q); });
+    if (s != ES_OK) return s;
+    cudaError_t e = cudaMemcpyAsync(lnl, c->d_lnl, sizeof(double) * c->batch,
+                                    mem == ES_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lnL copy");
+    return finish(c, mem, st);
+}
+
+// Forward + adjoint into the context's buffers (lnL in d_lnl, gradient in w.grad).
+es_status enqueue_forward_backward(es_ctx *c, cudaStream_t st) {
+    const int B = c->batch;
+    const Model &m = c->m;
+    Work w = c->w;
+    w.B = B;
+    const size_t L = m.L, S = m.S;
+    cudaMemsetAsync(w.red, 0, sizeof(double) * B * L * N_RED, st);
+    cudaMemsetAsync(w.qtot, 0, sizeof(double) * B * S, st);
+    cudaMemsetAsync(w.areabar, 0, sizeof(double) * B * L, st);
+    cudaMemsetAsync(w.levbar, 0, sizeof(double) * B * (L + 1), st);
+    cudaMemsetAsync(w.drbar, 0, sizeof(double) * B * L, st);
+    cudaMemsetAsync(w.lbar, 0, sizeof(double) * B * L * L, st);
+    es_status s = run_forward(c, true, nullptr, nullptr, c->d_lnl, st);
+    if (s != ES_OK) return s;
+    int launches = (int)c->last_launches;
+    const Hook &h = c->hook;
+    if (c->n_kind[0]) launches += launch_trans_fused_backward(m, w, c->bwd_chunk, st, h);
+    if (c->n_kind[1]) {
+        launches += launch_emission_backward(m, w, st, h);
+        launches += launch_extinction_backward(m, w, ES_KIND_EMISSION, st, h);
+    }
+    launches += launch_setup_backward(m, w, st, h);
+    c->last_launches = launches;
+    return check_launch(c, "backward launch");
 }
 
 es_status es_forward_backward(es_ctx *c, double *lnl, double *grad, int mem, es_stream_t stream) {
@@ -638,46 +747,72 @@ es_status es_forward_backward(es_ctx *c, double *lnl, double *grad, int mem, es_
     es_status s = ready(c);
     if (s != ES_OK) return s;
     cudaSetDevice(c->device);
-    if ((s = ensure_ymod(c)) != ES_OK) return s;
-    if ((s = alloc_backward(c)) != ES_OK) return s;
+    if ((s = prepare(c, true)) != ES_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int B = c->batch;
-    const Model &m = c->m;
-    Work w = c->w;
-    w.B = B;
-    double *d_lnl = (mem == ES_MEM_HOST || !lnl) ? c->d_lnl : lnl;
-    const size_t L = m.L, S = m.S;
-    cudaMemsetAsync(w.red, 0, sizeof(double) * B * L * N_RED, st);
-    cudaMemsetAsync(w.qtot, 0, sizeof(double) * B * S, st);
-    cudaMemsetAsync(w.areabar, 0, sizeof(double) * B * L, st);
-    cudaMemsetAsync(w.levbar, 0, sizeof(double) * B * (L + 1), st);
-    cudaMemsetAsync(w.drbar, 0, sizeof(double) * B * L, st);
-    cudaMemsetAsync(w.lbar, 0, sizeof(double) * B * L * L, st);
-    if (c->n_kind[1] && (s = ensure_big(c, &c->w.abar, c->abar_cap, (size_t)B * L * m.N)) != ES_OK) return s;
-    s = run_forward(c, true, nullptr, nullptr, d_lnl, st);
+    s = launch_or_replay(c, c->graph_fb, st, [&](cudaStream_t q) { return enqueue_forward_backward(c, q); });
     if (s != ES_OK) return s;
-    w = c->w;
-    w.B = B;
-    int launches = (int)c->last_launches;
-    const Hook &h = c->hook;
-    if (c->n_kind[0]) launches += launch_trans_fused_backward(m, w, st, h);
-    if (c->n_kind[1]) {
-        launches += launch_emission_backward(m, w, st, h);
-        launches += launch_extinction_backward(m, w, ES_KIND_EMISSION, st, h);
+    const int B = c->batch;
+    const cudaMemcpyKind dir = mem == ES_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    cudaError_t e = cudaSuccess;
+    if (lnl) e = cudaMemcpyAsync(lnl, c->d_lnl, sizeof(double) * B, dir, st);
+    if (e == cudaSuccess && grad)
+        e = cudaMemcpyAsync(grad, c->w.grad, sizeof(double) * (size_t)B * c->m.nfree, dir, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "result copy");
+    return finish(c, mem, st);
+}
+
+es_status es_autotune(es_ctx *c, es_stream_t stream) {
+    if (!c) return ES_EINVAL;
+    es_status s = ready(c);
+    if (s != ES_OK) return s;
+    cudaSetDevice(c->device);
+    if ((s = prepare(c, true)) != ES_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!c->n_kind[0]) return ES_OK;   // only the fused transmission kernels have tunables
+    // one full pass so the forward's exp(-tau) and dbar the backward reads are valid
+    c->fwd_chunk = c->bwd_chunk = 0;
+    if ((s = enqueue_forward_backward(c, st)) != ES_OK) return s;
+    Work w = c->w;
+    w.B = c->batch;
+    const Hook none{};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto time_it = [&](auto &&launch) {
+        float best = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+            cudaEventRecord(e0, st);
+            launch();
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            best = std::min(best, ms);
+        }
+        return best;
+    };
+    const int fwd_cand[] = {1, 2, 4, 8, 16, 32}, bwd_cand[] = {1, 2, 4, 8, 16};
+    float best = 1e30f;
+    for (int ch : fwd_cand) {
+        const float ms = time_it([&]() { launch_trans_fused_forward(c->m, w, true, ch, st, none); });
+        if (ms < best) { best = ms; c->fwd_chunk = ch; }
     }
-    launches += launch_setup_backward(m, w, st, h);
-    c->last_launches = launches;
-    if ((s = check_launch(c, "backward launch")) != ES_OK) return s;
-    if (mem == ES_MEM_HOST) {
-        if (lnl) s = copy_out(c, lnl, d_lnl, sizeof(double) * B, st);
-        if (s == ES_OK && grad) s = copy_out(c, grad, w.grad, sizeof(double) * (size_t)B * m.nfree, st);
-    } else if (grad) {
-        cudaError_t e = cudaMemcpyAsync(grad, w.grad, sizeof(double) * (size_t)B * m.nfree,
-                                        cudaMemcpyDeviceToDevice, st);
-        if (e != cudaSuccess) return cuda_fail(c, e, "gradient copy");
+    best = 1e30f;
+    for (int ch : bwd_cand) {
+        const float ms = time_it([&]() { launch_trans_fused_backward(c->m, w, ch, st, none); });
+        if (ms < best) { best = ms; c->bwd_chunk = ch; }
     }
-    if (s == ES_OK) s = finish(c, mem, st);
-    return s;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ++c->graph_epoch;
+    return check_launch(c, "autotune");
+}
+
+es_status es_set_graphs(es_ctx *c, int on) {
+    if (!c) return ES_EINVAL;
+    c->use_graph = on != 0;
+    ++c->graph_epoch;
+    return ES_OK;
 }
 
 es_status es_get_flags(es_ctx *c, int32_t *flags, int mem, es_stream_t stream) {
@@ -700,8 +835,13 @@ int64_t es_query(const es_ctx *c, int key) {
         case 3: return c->batch;
         case 4: return c->m.L;
         case 5: return c->m.S;
-        case 6: return (int64_t)c->ws_bytes;
+        case 6:
+            return (int64_t)(c->ws_bytes + sizeof(float) * (c->alpha_cap + c->abar_cap + c->estore_cap) +
+                             sizeof(double) * c->ymod_cap);
         case 7: return c->last_launches;
+        case 8: return c->fwd_chunk;
+        case 9: return c->bwd_chunk;
+        case 10: return c->use_graph ? 1 : 0;
         default: return -1;
     }
 }
@@ -748,6 +888,14 @@ void es_destroy(es_ctx *c) {
     free_all(c->grid_bufs);
     free_all(c->table_bufs);
     free_all(c->model_bufs);
+    drop_graph(c->graph_fb);
+    drop_graph(c->graph_ll);
+    if (c->gstream) {
+        cudaStreamSynchronize(c->gstream);
+        cudaStreamDestroy(c->gstream);
+        cudaEventDestroy(c->ev_fork);
+        cudaEventDestroy(c->ev_join);
+    }
     if (c->w.ymod) cudaFree(c->w.ymod);
     if (c->w.alpha) cudaFree(c->w.alpha);
     if (c->w.abar) cudaFree(c->w.abar);

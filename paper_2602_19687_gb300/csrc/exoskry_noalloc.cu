@@ -135,7 +135,7 @@ extern "C" es_status es_loglike_noalloc(es_ctx *c, const double *theta, const in
     const es::Hook none{};
     int launches = 0;
     launches += es::launch_setup(c->m, w, st, none);
-    launches += es::launch_trans_fused_forward(c->m, w, false, st, none);
+    launches += es::launch_trans_fused_forward(c->m, w, false, 0, st, none);
     if (kind) {
         launches += es::launch_extinction(c->m, w, ES_KIND_EMISSION, st, none);
         launches += es::launch_emission(c->m, w, st, none);

@@ -127,8 +127,9 @@ struct Hook {
 int launch_build_coef(const Model &m, float4 *coef, cudaStream_t st);
 int launch_setup(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
 int launch_extinction(const Model &m, const Work &w, int only_kind, cudaStream_t st, const Hook &h);
-int launch_trans_fused_forward(const Model &m, const Work &w, bool store_e, cudaStream_t st, const Hook &h);
-int launch_trans_fused_backward(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
+// chunk: wavenumber tiles per persistent work item (<= 0: built-in heuristic)
+int launch_trans_fused_forward(const Model &m, const Work &w, bool store_e, int chunk, cudaStream_t st, const Hook &h);
+int launch_trans_fused_backward(const Model &m, const Work &w, int chunk, cudaStream_t st, const Hook &h);
 int launch_emission(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
 int launch_bins(const Model &m, const Work &w, bool want_adjoint, float *spectrum_out,
                 double *binned_out, double *lnl_out, cudaStream_t st, const Hook &h);

@@ -506,9 +506,10 @@ int chunk_tiles(const Model &m, int B, int blocks) {
     return (int)std::max<long long>(1, std::min<long long>(16, c));
 }
 
-int launch_trans_fused_forward(const Model &m, const Work &w, bool store_e, cudaStream_t st, const Hook &h) {
+int launch_trans_fused_forward(const Model &m, const Work &w, bool store_e, int chunk_req, cudaStream_t st,
+                               const Hook &h) {
     const int ntiles = (m.N + FT - 1) / FT;
-    const int chunk = chunk_tiles(m, w.B, 2 * sm_count());
+    const int chunk = chunk_req > 0 ? chunk_req : chunk_tiles(m, w.B, 2 * sm_count());
     const long long items = (long long)w.B * ((ntiles + chunk - 1) / chunk);
     const int grid = (int)std::min<long long>(items, 2LL * sm_count());
     const size_t sm = fwd_smem();
@@ -525,9 +526,9 @@ int launch_trans_fused_forward(const Model &m, const Work &w, bool store_e, cuda
     return 1;
 }
 
-int launch_trans_fused_backward(const Model &m, const Work &w, cudaStream_t st, const Hook &h) {
+int launch_trans_fused_backward(const Model &m, const Work &w, int chunk_req, cudaStream_t st, const Hook &h) {
     const int ntiles = (m.N + BT - 1) / BT;
-    const int chunk = std::max(1, chunk_tiles(m, w.B, sm_count()) / 2);
+    const int chunk = chunk_req > 0 ? chunk_req : std::max(1, chunk_tiles(m, w.B, sm_count()) / 2);
     const long long items = (long long)w.B * ((ntiles + chunk - 1) / chunk);
     const int grid = (int)std::min<long long>(items, (long long)sm_count());
     const size_t sm = bwd_smem();
