@@ -246,6 +246,7 @@ es_status alloc_backward(es_ctx *c) {
     ALLOC(w.lbar, (size_t)B * L * L);
     ALLOC(w.red, (size_t)B * L * N_RED);
     ALLOC(w.qtot, (size_t)B * S);
+    ALLOC(w.zbar, (size_t)B * L);
     ALLOC(w.areabar, (size_t)B * L);
     ALLOC(w.levbar, (size_t)B * (L + 1));
     ALLOC(w.drbar, (size_t)B * L);
@@ -477,6 +478,25 @@ es_status es_load_tables(es_ctx *c, const es_tables_desc *t) {
     }
     if ((s = upload(c, c->table_bufs, &df, cia.data(), cia.size())) != ES_OK) return s;
     m.cia = df;
+    // CIA interpolation coefficients per temperature bracket and wavenumber pair
+    {
+        const size_t np2 = Np / 2, nb = (size_t)m.NTc - 1;
+        std::vector<float> c4(2 * nb * np2 * 4);
+        for (int pair = 0; pair < 2; ++pair)
+            for (size_t r = 0; r < nb; ++r)
+                for (size_t q = 0; q < np2; ++q)
+                    for (int k = 0; k < 2; ++k) {
+                        const double k0 = cia[((size_t)pair * m.NTc + r) * Np + 2 * q + k];
+                        const double k1 = cia[((size_t)pair * m.NTc + r + 1) * Np + 2 * q + k];
+                        float *o = &c4[((r * np2 + q) * 2 + pair) * 4];
+                        o[k] = (float)(LOG2_10 * k0);
+                        o[2 + k] = (float)(LOG2_10 * (k1 - k0));
+                    }
+        float4 *d4;
+        if ((s = upload(c, c->table_bufs, &d4, reinterpret_cast<const float4 *>(c4.data()), c4.size() / 4)) != ES_OK)
+            return s;
+        m.cia4 = d4;
+    }
     std::vector<float> nuf(Np), ifs(Np);
     for (size_t n = 0; n < Np; ++n) {
         const double nv = t->nu[n < N ? n : N - 1];
@@ -515,11 +535,14 @@ es_status es_load_tables(es_ctx *c, const es_tables_desc *t) {
     m.wp = df;
     // per-cell bilinear coefficients used by the fused kernels
     float4 *coef;
-    const size_t ncoef = (size_t)(m.NT - 1) * (m.NP - 1) * m.S * m.Np;
+    m.SP = 2 * spl_for(m.S);
+    const size_t ncoef = (size_t)(m.NT - 1) * (m.NP - 1) * m.SP * m.Np;
     if ((s = dalloc(c, c->table_bufs, &coef, ncoef)) != ES_OK) return s;
     m.coef4 = nullptr;
+    cudaError_t e = cudaMemset(coef, 0, ncoef * sizeof(float4));
+    if (e != cudaSuccess) return cuda_fail(c, e, "coefficient table");
     launch_build_coef(m, coef, nullptr);
-    cudaError_t e = cudaDeviceSynchronize();
+    e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "coefficient table");
     m.coef4 = coef;
@@ -723,6 +746,7 @@ es_status enqueue_forward_backward(es_ctx *c, cudaStream_t st) {
     const size_t L = m.L, S = m.S;
     cudaMemsetAsync(w.red, 0, sizeof(double) * B * L * N_RED, st);
     cudaMemsetAsync(w.qtot, 0, sizeof(double) * B * S, st);
+    cudaMemsetAsync(w.zbar, 0, sizeof(double) * B * L, st);
     cudaMemsetAsync(w.areabar, 0, sizeof(double) * B * L, st);
     cudaMemsetAsync(w.levbar, 0, sizeof(double) * B * (L + 1), st);
     cudaMemsetAsync(w.drbar, 0, sizeof(double) * B * L, st);

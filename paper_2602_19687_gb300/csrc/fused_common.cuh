@@ -92,14 +92,17 @@ __device__ __forceinline__ uint32_t bt_addr(uint32_t base, int pitch, int n0, in
 }
 
 // ------------------------------------------------------------ per-sample constants
+// Per-layer constants, with the operands of packed FP32x2 instructions stored
+// as duplicated pairs so that the layer loop needs no register moves.
 struct __align__(16) LayerConst {
-    int it, ip, itc, cell;   // temperature / pressure / CIA brackets; cell = it * (NP - 1) + ip
-    float wt, wp, wtc;       // raw interpolation weights
-    float nsc;               // n_l 2^-KSHIFT
-    float cc1, cc2;          // log2(n^2 X_H2^2), log2(n^2 X_H2 X_He)
-    float ray;               // n (X_H2 s_H2 + X_He s_He) / nu_ref^4
-    float gt, gtc;           // 1/dlog10T and 1/dT of the brackets (0 where clamped)
-    float pad[3];
+    float2 wp, wt;       // pressure / temperature interpolation weights
+    float2 nsc, wtc;     // n_l 2^-KSHIFT; CIA temperature weight
+    float2 cc[2];        // log2(n^2 X_H2^2), log2(n^2 X_H2 X_He): CIA pair 0 / 1
+    float2 ray;          // n (X_H2 s_H2 + X_He s_He) / nu_ref^4
+    float gts, gtcs;     // d/dlog10 T of the log2 exponents: gt / log2(10), gtc / log2(10)
+    int cell, itc;       // (T, p) table cell = it * (NP - 1) + ip; CIA temperature bracket
+    int run_end;         // first layer after l whose (cell, itc) differs (or L)
+    int pad;
 };
 
 struct SampleConst {
@@ -110,23 +113,28 @@ struct SampleConst {
 // All threads of the block: per-layer constants of sample b into shared memory.
 __device__ inline void stage_sample(const Model &m, const Work &w, int b, SampleConst &sc) {
     const float ry = (float)(1.0 / ((double)m.ray_nu_ref * m.ray_nu_ref * m.ray_nu_ref * m.ray_nu_ref));
-    for (int l = threadIdx.x; l < m.L; l += blockDim.x) {
-        const size_t bl = (size_t)b * m.L + l;
+    const float il2 = (float)(1.0 / LOG2_10);
+    const int L = m.L;
+    const size_t b0 = (size_t)b * L;
+    for (int l = threadIdx.x; l < L; l += blockDim.x) {
+        const size_t bl = b0 + l;
         LayerConst c;
-        c.it = w.it[bl];
-        c.ip = m.ip[l];
-        c.itc = w.itc[bl];
-        c.cell = c.it * (m.NP - 1) + c.ip;
-        c.wt = w.wtr[bl];
-        c.wp = m.wp[l];
-        c.wtc = w.wtc[bl];
-        c.nsc = (float)(w.n_lay[bl] * 5.421010862427522e-20);   // 2^-64
-        c.cc1 = w.ccia[2 * bl];
-        c.cc2 = w.ccia[2 * bl + 1];
-        c.ray = w.ray[bl] * ry;
-        c.gt = w.gt[bl];
-        c.gtc = w.gtc[bl];
-        c.pad[0] = c.pad[1] = c.pad[2] = 0.f;
+        const int it = w.it[bl], itc = w.itc[bl];
+        c.cell = it * (m.NP - 1) + m.ip[l];
+        c.itc = itc;
+        int r = l + 1;   // runs are a few layers long: a short forward scan
+        while (r < L && w.it[b0 + r] == it && m.ip[r] == m.ip[l] && w.itc[b0 + r] == itc) ++r;
+        c.run_end = r;
+        c.pad = 0;
+        c.wp = f2(m.wp[l]);
+        c.wt = f2(w.wtr[bl]);
+        c.wtc = f2(w.wtc[bl]);
+        c.nsc = f2((float)(w.n_lay[bl] * 5.421010862427522e-20));   // 2^-64
+        c.cc[0] = f2(w.ccia[2 * bl]);
+        c.cc[1] = f2(w.ccia[2 * bl + 1]);
+        c.ray = f2(w.ray[bl] * ry);
+        c.gts = w.gt[bl] * il2;
+        c.gtcs = w.gtc[bl] * il2;
         sc.lay[l] = c;
     }
     // absent species (s >= S, padding of the per-lane species slots) get a
@@ -145,70 +153,70 @@ __device__ __forceinline__ void group_layers(int L, int g, int ng, int &lb, int 
 }
 
 // ------------------------------------------------------------ interpolation
-// Coefficient table layout (see k_tables.cu): per (cell, species) and
-// wavenumber pair, two float4: (a0, a0', a1, a1') and (a2, a2', a3, a3') for
-// the pair's two wavenumbers, so each coefficient loads straight into an
-// aligned register pair.
-__device__ __forceinline__ void load_cell(const Model &m, int s, int cell, int n, float lx, float2 &a0, float2 &a1,
-                                          float2 &a2, float2 &a3) {
-    const float4 *p = m.coef4 + (((size_t)cell * m.S + s) * (m.Np >> 1) + (n >> 1)) * 2;
-    const float4 c0 = __ldg(p), c1 = __ldg(p + 1);
-    a0 = add2(make_float2(c0.x, c0.y), f2(lx));
-    a1 = make_float2(c0.z, c0.w);
-    a2 = make_float2(c1.x, c1.y);
-    a3 = make_float2(c1.z, c1.w);
-}
-
-// CIA coefficients of one temperature bracket: e = b + wtc d + cc
-__device__ __forceinline__ void load_cia(const Model &m, int pair, int itc, int n, float2 &b, float2 &d) {
-    const size_t st = (size_t)m.Np;
-    const float *base = m.cia + ((size_t)pair * m.NTc + itc) * st + n;
-    const float2 k0 = __ldg(reinterpret_cast<const float2 *>(base));
-    const float2 k1 = __ldg(reinterpret_cast<const float2 *>(base + st));
-    const float2 c = f2((float)LOG2_10);
-    b = mul2(c, k0);
-    d = mul2(c, add2(k1, make_float2(-k0.x, -k0.y)));
-}
+// Coefficient table layout (k_tables.cu): per (cell, wavenumber pair) the SP
+// species slots, each as two float4 (a0, a0', a1, a1'), (a2, a2', a3, a3'),
+// so a lane's SPL slots are one contiguous 32 SPL-byte block and each
+// coefficient loads straight into an aligned register pair.
 
 // Per-lane interpolation state for SPL species per lane. A wavenumber pair is
 // shared by two lanes (h = lane & 1): lane h interpolates species SPL h ..
 // SPL h + SPL - 1 (slots beyond S read species S-1 with a zero weight) and
-// CIA pair h, keeping the current (T, p) cell's coefficients in registers;
-// cells change only every few layers.
+// CIA pair h, keeping the current (T, p) cell's coefficients in registers.
+// The layer loops run over runs of layers with one (cell, CIA bracket), so
+// coefficients are loaded once per run and the per-layer body has no tests.
 template <int SPL>
 struct PairInterp {
     float2 a0[SPL], a1[SPL], a2[SPL], a3[SPL];
-    float2 b, d, nu4;
-    int cell = -1, itc = -1, h = 0;
+    float2 b, d;
+    float2 nu4;          // nu^4 on lane h = 0, zero on h = 1 (Rayleigh counted once per pair)
+    int h = 0;
+    const float4 *cp;    // this lane's slot j = 0, c = 0 of its wavenumber pair in cell 0
+    const float4 *pfp;   // the line this lane prefetches for the warp, in cell 0
+    const float4 *ciap;  // this lane's CIA pair at bracket 0
+    size_t cstride;      // float4 per cell
+    int jstride;         // float4 between (j, c) blocks: Np (= 2 x pairs x halves / 2)
+    int cia_stride;      // float4 per CIA temperature bracket
 
-    __device__ __forceinline__ void init(const Model &m, int n, int half) {
+    // n: the pair's first wavenumber; the warp's lanes 2q, 2q + 1 cover 16
+    // consecutive pairs, the first at n - 2 q
+    __device__ __forceinline__ void init(const Model &m, int n, int half, int lane) {
+        const int n_warp = n - (lane & 30);
         const float2 nu = __ldg(reinterpret_cast<const float2 *>(m.nu + n));
         const float2 nu2 = mul2(nu, nu);
-        nu4 = mul2(nu2, nu2);
-        cell = itc = -1;
+        nu4 = half ? f2(0.f) : mul2(nu2, nu2);
         h = half;
+        jstride = m.Np;
+        cstride = (size_t)m.Np * m.SP;
+        cp = m.coef4 + (size_t)n + half;            // ((pair) * 2 + h) with pair = n / 2
+        // the warp's 2 SPL (j, c) blocks of 512 B = 4 lines each: lane -> one line
+        const int blk = (lane >> 2) & ((2 * SPL < 8 ? 2 * SPL : 8) - 1);
+        pfp = m.coef4 + (size_t)blk * m.Np + n_warp + 8 * (lane & 3);
+        cia_stride = m.Np;
+        ciap = m.cia4 + (size_t)n + half;
     }
-    __device__ __forceinline__ int slot(int j) const { return SPL * h + j; }
-    __device__ __forceinline__ int table_species(const Model &m, int j) const { return min(slot(j), m.S - 1); }
-    // L1 prefetch of the next layer's cell coefficients when the cell changes
-    __device__ __forceinline__ void prefetch(const Model &m, const LayerConst &cur, const LayerConst &next, int n) const {
-        if (next.cell == cur.cell) return;
+    // coefficients of a run: this lane's species slots in `cell`, CIA pair h in bracket itc
+    __device__ __forceinline__ void load(const SampleConst &sc, int cell, int itc) {
+        const float4 *p = cp + (size_t)cell * cstride;
 #pragma unroll
-        for (int j = 0; j < SPL; ++j)
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(
-                m.coef4 + (((size_t)next.cell * m.S + table_species(m, j)) * (m.Np >> 1) + (n >> 1)) * 2));
+        for (int j = 0; j < SPL; ++j) {
+            const float4 c0 = __ldg(p + (2 * j) * jstride), c1 = __ldg(p + (2 * j + 1) * jstride);
+            a0[j] = add2(make_float2(c0.x, c0.y), f2(sc.lx[SPL * h + j]));
+            a1[j] = make_float2(c0.z, c0.w);
+            a2[j] = make_float2(c1.x, c1.y);
+            a3[j] = make_float2(c1.z, c1.w);
+        }
+        const float4 k = __ldg(ciap + (size_t)itc * cia_stride);
+        b = make_float2(k.x, k.y);
+        d = make_float2(k.z, k.w);
     }
-    __device__ __forceinline__ void update(const Model &m, const SampleConst &sc, const LayerConst &lc, int n) {
-        if (lc.cell != cell) {
-            cell = lc.cell;
+    // L1 prefetch of the next run's coefficients: the warp's 2 SPL x 512 B,
+    // one 128-B line per lane (two for SPL = 8), and the lane's CIA entry
+    __device__ __forceinline__ void prefetch(int cell, int itc) const {
+        const float4 *p = pfp + (size_t)cell * cstride;
 #pragma unroll
-            for (int j = 0; j < SPL; ++j)
-                load_cell(m, table_species(m, j), lc.cell, n, sc.lx[slot(j)], a0[j], a1[j], a2[j], a3[j]);
-        }
-        if (lc.itc != itc) {
-            itc = lc.itc;
-            load_cia(m, h, lc.itc, n, b, d);
-        }
+        for (int k = 0; k < (2 * SPL * 4 + 31) / 32; ++k)
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(p + (size_t)k * 8 * jstride));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(ciap + (size_t)itc * cia_stride));
     }
     // exponent of species slot j: e = a0 + wp a1 + wt (a2 + wp a3); t = de/dwt
     __device__ __forceinline__ float2 expo(int j, float2 wp, float2 wt, float2 &t) const {
@@ -217,12 +225,9 @@ struct PairInterp {
     }
     // CIA term of this lane's pair
     __device__ __forceinline__ float2 cia(const LayerConst &lc) const {
-        return ex2x2(fma2(f2(lc.wtc), d, add2(b, f2(h ? lc.cc2 : lc.cc1))));
+        return ex2x2(fma2(lc.wtc, d, add2(b, lc.cc[h])));
     }
 };
-
-// Species slots per lane for S species (two lanes per wavenumber pair).
-__host__ __device__ constexpr int spl_for(int S) { return S <= 4 ? 2 : (S <= 8 ? 4 : 8); }
 
 __device__ __forceinline__ float2 shfl_xor2(float2 v, int o) {
     return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
@@ -236,18 +241,19 @@ template <int SPL, class Out>
 __device__ __forceinline__ void extinction_pair(const Model &m, const SampleConst &sc, int lb, int le, int n,
                                                 int half, Out &&out) {
     PairInterp<SPL> pi;
-    pi.init(m, n, half);
-    for (int l = lb; l < le; ++l) {
-        const LayerConst &lc = sc.lay[l];
-        pi.update(m, sc, lc, n);
-        if (l + 1 < le) pi.prefetch(m, lc, sc.lay[l + 1], n);
-        const float2 wp = f2(lc.wp), wt = f2(lc.wt);
-        float2 sum = f2(0.f), t;
+    pi.init(m, n, half, threadIdx.x & 31);
+    for (int l = lb; l < le;) {
+        const int end = min(sc.lay[l].run_end, le);
+        pi.load(sc, sc.lay[l].cell, sc.lay[l].itc);
+        if (end < le) pi.prefetch(sc.lay[end].cell, sc.lay[end].itc);
+        for (; l < end; ++l) {
+            const LayerConst &lc = sc.lay[l];
+            float2 t, sum = ex2x2(pi.expo(0, lc.wp, lc.wt, t));
 #pragma unroll
-        for (int j = 0; j < SPL; ++j) sum = add2(sum, ex2x2(pi.expo(j, wp, wt, t)));
-        float2 mine = fma2(sum, f2(lc.nsc), pi.cia(lc));
-        if (half == 0) mine = fma2(f2(lc.ray), pi.nu4, mine);
-        out(l, add2(mine, shfl_xor2(mine, 1)));
+            for (int j = 1; j < SPL; ++j) sum = add2(sum, ex2x2(pi.expo(j, lc.wp, lc.wt, t)));
+            const float2 mine = fma2(lc.ray, pi.nu4, fma2(sum, lc.nsc, pi.cia(lc)));
+            out(l, add2(mine, shfl_xor2(mine, 1)));
+        }
     }
 }
 

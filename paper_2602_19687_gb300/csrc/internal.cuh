@@ -30,17 +30,24 @@ constexpr double INVALID_LNL = -1.0e300;
 // second radiation constant h c / k_B [cm K] and 2 h c^2 [erg cm^2 s^-1]
 constexpr double C2_RAD = H_PLANCK * C_LIGHT / K_B;
 constexpr double TWO_HC2 = 2.0 * H_PLANCK * C_LIGHT * C_LIGHT;
+// Species slots per lane in the fused transmission kernels (two lanes share a
+// wavenumber pair and split the species between them).
+__host__ __device__ constexpr int spl_for(int S) { return S <= 4 ? 2 : (S <= 8 ? 4 : 8); }
 // number of Gauss-Legendre angles for the emission flux integral
 constexpr int N_MU = 4;
-// reductions per (sample, layer) in the extinction adjoint:
-// QS (sum over species of Q_s), D, C1, C2, C1T, C2T, W4; per-species totals
-// over layers go to Work::qtot
-constexpr int N_RED = 7;
+// reductions per (sample, layer) in the extinction adjoint, each a sum over
+// wavenumber of alpha_bar times a part of d alpha: 0/1 QS (species sum; two
+// partial sums added by the reader), 2/3 D (temperature slope of the species
+// sum; two partials), 4 C1, 5 C2 (CIA terms), 6 C1T, 7 C2T (their temperature
+// slopes), 8 W4 (Rayleigh weight). Per-species totals over layers go to
+// Work::qtot; for transmission, W4 comes from Work::zbar instead of slot 8.
+constexpr int N_RED = 9;
 
 // Constant model data, passed by value to every kernel.
 struct Model {
     int L, S, NT, NP, NTc, N, nbins, nfree, nfull;
     int Np;                       // padded row stride of tables and per-wavenumber arrays (N rounded up to 128)
+    int SP;                       // species slots per coefficient-table entry (2 spl_for(S) >= S)
     int tp_kind, cloud_kind, bf16;
     double p_ref;                 // dyn cm^-2
     double r_star, t_star;
@@ -58,8 +65,12 @@ struct Model {
     const float *tab32;           // [S][NT][NP][Np]
     const uint16_t *tab16;        // [S][NT][NP][Np] BF16 residuals
     const float *row_off;         // [S][NT][NP] (zeros for FP32 tables)
-    const float4 *coef4;          // [(NT-1)(NP-1) cells][S][Np] bilinear coefficients (log2 units):
-                                  // (v00, v01 - v00, v10 - v00, v11 - v10 - v01 + v00) x log2(10)
+    const float4 *coef4;          // [(NT-1)(NP-1) cells][SP/2 j][2 c][Np/2 pairs][2 h] bilinear coefficients
+                                  // (log2 units) (v00, v01 - v00, v10 - v00, v11 - v10 - v01 + v00) x log2(10)
+                                  // of species slot s = h SP/2 + j: c = 0 (c0, c0', c1, c1'), c = 1
+                                  // (c2, c2', c3, c3') for a wavenumber pair; slots >= S zero
+    const float4 *cia4;           // [NTc-1][Np/2 pairs][2 CIA pairs] (b, b', d, d'): b = log2(10) log10 k(T_i),
+                                  // d = log2(10) (log10 k(T_i+1) - log10 k(T_i))
     const float *cia;             // [2][NTc][Np] log10 k
     const float *nu;              // [Np]
     const float *inv_fstar;       // [Np] 1 / (pi B(T_*, nu))
@@ -101,6 +112,7 @@ struct Work {
     double *lbar;                 // [B][L][L]
     double *red;                  // [B][L][N_RED]
     double *qtot;                 // [B][S] per-species reductions summed over layers
+    double *zbar;                 // [B][L] transmission: sum_nu tau_bar_i(nu) (nu/nu_ref)^4
     double *areabar;              // [B][L]
     double *levbar;               // [B][L+1] d lnL / d T_lev (emission)
     double *drbar;                // [B][L]   d lnL / d dr (emission)

@@ -101,7 +101,7 @@ template <bool BF16>
 __global__ void __launch_bounds__(EXT_THREADS) k_extinction_bwd(Model m, Work w, int only_kind) {
     const int b = blockIdx.y;
     if (only_kind >= 0 && w.kind[b] != only_kind) return;
-    const int L = m.L, S = m.S, N = m.N, NR = S + N_RED - 1;
+    const int L = m.L, S = m.S, N = m.N, NR = S + 6;   // species, then D, C1, C2, C1T, C2T, W4
     const int n0 = blockIdx.x * EXT_THREADS * BWD_NU_PER_THREAD + threadIdx.x;
     __shared__ float scratch[EXT_THREADS / 32];
     const size_t strideP = m.Np, strideT = (size_t)m.NP * m.Np, strideS = (size_t)m.NT * strideT;
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(EXT_THREADS) k_extinction_bwd(Model m, Work w,
         const int it = w.it[bl], ip = m.ip[l], itc = w.itc[bl];
         const float wp = m.wp[l], gt = w.gt[bl], wtc = w.wtc[bl], gtc = w.gtc[bl];
         const float cc1 = w.ccia[2 * bl], cc2 = w.ccia[2 * bl + 1];
-        float acc[ES_MAX_SPECIES + N_RED - 1];
+        float acc[ES_MAX_SPECIES + 6];
         for (int q = 0; q < NR; ++q) acc[q] = 0.f;
         const float *abar = w.abar + bl * N;
         for (int k = 0; k < BWD_NU_PER_THREAD; ++k) {
@@ -149,8 +149,8 @@ __global__ void __launch_bounds__(EXT_THREADS) k_extinction_bwd(Model m, Work w,
             const float nf = m.nu[n] / (float)m.ray_nu_ref;
             acc[S + 5] += a * (nf * nf) * (nf * nf);
         }
-        // species: per-species totals (qtot) and their sum for this layer (red[0]);
-        // then D, C1, C2, C1T, C2T, W4 into red[1..6]
+        // species: per-species totals (qtot) and their sum for this layer (red
+        // slot 0); then D, C1, C2, C1T, C2T, W4 into slots 2, 4, 5, 6, 7, 8
         float qs = 0.f;
         for (int q = 0; q < NR; ++q) {
             float t = block_sum(acc[q], scratch);
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(EXT_THREADS) k_extinction_bwd(Model m, Work w,
                     qs += t;
                     if (t != 0.f) atomicAdd(w.qtot + (size_t)b * S + q, (double)t);
                 } else if (t != 0.f) {
-                    atomicAdd(w.red + bl * N_RED + 1 + (q - S), (double)t);
+                    atomicAdd(w.red + bl * N_RED + (q == S ? 2 : 3 + (q - S)), (double)t);
                 }
             }
         }

@@ -39,16 +39,20 @@ constexpr int BW_THREADS = BW_WARPS * 32;
 constexpr int BT = 128;              // wavenumbers per backward tile
 constexpr int T2_PITCH = 136;        // bf16 pitch of tau_bar rows [i][128 nu] (272 B: 17 x 16 B)
 constexpr int RB2_BYTES = 528;       // bytes per row buffer row (33 x 16 B): four 128-B quarters
+constexpr int LPR = 120;             // row buffer rows: LP layers, plus row L (the Rayleigh weight), to 8
 // Row buffer, per layer and per 32-wavenumber quarter k (bytes [128 k, 128 k + 128)):
 // first alpha_bar as 32 FP32, then overwritten by the extinction as BF16 hi
 // (bytes 0..63 of the quarter) and lo (bytes 64..127). Each quarter of a row
-// belongs to one warp, so the overwrite only needs a warp barrier.
+// belongs to one warp, so the overwrite only needs a warp barrier. Row L holds
+// w(nu) = (nu/nu_ref)^4 as split BF16, so that the L_bar product also yields
+// z_i = sum_nu tau_bar_i(nu) w(nu), from which the Rayleigh reduction
+// W4_l = sum_nu alpha_bar_l(nu) w(nu) = sum_i L_il z_i follows.
 
 struct TransBwdSmem {
     SampleConst sc;
     __nv_bfloat16 lh[LP * L_PITCH], ll[LP * L_PITCH];   // path lengths [i][l]
     __nv_bfloat16 th[LP * T2_PITCH], tl[LP * T2_PITCH]; // tau_bar [i][nu]
-    unsigned char rb[LP * RB2_BYTES];                   // alpha_bar / alpha rows
+    unsigned char rb[LPR * RB2_BYTES];                  // alpha_bar / alpha rows, Rayleigh weight row
     float area[LP];
     float area_acc[LP];                                 // area_bar of the current sample
     float red[ES_MAX_LAYERS * N_RED];                   // per-layer reductions of the current sample
@@ -95,6 +99,8 @@ __global__ void __launch_bounds__(FTHREADS, 2) k_trans_fwd(Model m, Work w, int 
     group_layers(L, warp >> 1, FWARPS / 2, lb, le);
     const uint32_t blh = smem_u32(sm.lh), bll = smem_u32(sm.ll), bah = smem_u32(sm.ah), bal = smem_u32(sm.al);
     const int ksmax = (L + 15) / 16;
+    // lane half 0 stores the hi parts of its pair's extinction, half 1 the lo parts
+    uint32_t *const a_dst = reinterpret_cast<uint32_t *>((half ? sm.al : sm.ah) + 2 * pair);
     int cur_b = -1;
     for (long long item = blockIdx.x; item < total; item += gridDim.x) {
         // chunk-major order: blocks running together share a wavenumber window,
@@ -114,7 +120,7 @@ __global__ void __launch_bounds__(FTHREADS, 2) k_trans_fwd(Model m, Work w, int 
             extinction_pair<SPL>(m, sm.sc, lb, le, nt0 + 2 * pair, half, [&](int l, float2 a) {
                 uint32_t hi, lo;
                 split2(a, hi, lo);
-                *reinterpret_cast<uint32_t *>((half ? sm.al : sm.ah) + l * R_PITCH + 2 * pair) = half ? lo : hi;
+                a_dst[l * (R_PITCH / 2)] = half ? lo : hi;
             });
             __syncthreads();
             // tau[i][nu] for this warp's 8 wavenumbers, lower-triangular blocks only
@@ -213,6 +219,19 @@ __device__ __forceinline__ void decode_pair(int p, int &mi, int &nj) {
     nj = p;
 }
 
+// Block pair p (0..63) of the L_bar product: the 56 lower-triangular pairs,
+// then (mi, L/8) for the i-blocks whose lower triangle stops short of column
+// L (the Rayleigh weight row). False for unused slots.
+__device__ __forceinline__ bool lbar_pair(int p, int L, int &mi, int &nj) {
+    if (p < 56) {
+        decode_pair(p, mi, nj);
+        return true;
+    }
+    mi = p - 56;
+    nj = L >> 3;
+    return mi < 7 && nj > 2 * mi + 1;
+}
+
 __device__ __forceinline__ int reduce_index(int lane) {
     return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
 }
@@ -244,66 +263,85 @@ __device__ __forceinline__ int reduce_index8(int lane) {
     return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
 }
 
+// Warp reduction of 4 values per lane that keeps the two lane parities
+// apart: on return lane holds the sum of v[2 b4 + b3] over the 16 lanes of its
+// parity (bk = bit k of the lane).
+__device__ __forceinline__ float reduce4_parity(const float (&v)[4], int lane) {
+    float a[2];
+    {
+        const bool up = lane & 16;
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+            a[k] = (up ? v[k + 2] : v[k]) + __shfl_xor_sync(0xffffffffu, up ? v[k] : v[k + 2], 16);
+    }
+    const bool up = lane & 8;
+    float e = (up ? a[1] : a[0]) + __shfl_xor_sync(0xffffffffu, up ? a[0] : a[1], 8);
+    e += __shfl_xor_sync(0xffffffffu, e, 4);
+    e += __shfl_xor_sync(0xffffffffu, e, 2);
+    return e;
+}
+
 // Backward interpolation for one warp: layers [lb, le), wavenumber pair n, n+1
 // shared by the lane pair (lane, lane ^ 1) that splits the species; `quarter`
 // points at the warp's 32-wavenumber quarter of row 0 of the row buffer.
 // Reads alpha_bar, adds per-layer reductions to red[l][*] and per-species
 // totals to qtot[s], then overwrites the quarter-rows with the extinction as
-// split BF16. Per layer, summed over wavenumber: QS = sum abar sum_s e_s,
-// D = sum abar sum_s e_s dlog10(sigma_s)/dlog10 T, C1, C2 = sum abar c1, c2,
-// C1T, C2T = sum abar c dlog10 k/dT, W4 = sum abar (nu/nu_ref)^4; per species
-// Q_s = sum_l sum abar e_s (e_s, c1, c2 the species and CIA extinction terms).
+// split BF16. Per layer, summed over wavenumber, with lane half h's species
+// and CIA pair h: QS_h = sum abar n sum_s e_s, D_h = sum abar n sum_s e_s
+// dlog2(sigma_s)/dlog10 T, C_h = sum abar c_h, CT_h = sum abar c_h dlog2 k_h/dT
+// (red slots 0/1, 2/3, 4/5, 6/7 for h = 0/1); per species Q_s = sum_l sum
+// abar n e_s. The Rayleigh sum over wavenumber comes from the L_bar product.
 template <int SPL>
 __device__ void interp_backward(const Model &m, const SampleConst &sc, int lb, int le, int n, int half, int lane,
                                 unsigned char *quarter, float *red, float *qtot) {
     const int S = m.S, q = lane >> 1;
     const int ridx = reduce_index8(lane);
     const bool writer = (lane & 3) == 0;
-    const float inv_l2 = (float)(1.0 / LOG2_10);
-    const float ray_ref = (float)(1.0 / ((double)m.ray_nu_ref * m.ray_nu_ref * m.ray_nu_ref * m.ray_nu_ref));
+    // after reduce4_parity: lanes with bits 2, 1 clear write slot 2 (2 b4 + b3) + b0
+    const bool rwriter = (lane & 6) == 0;
+    const int rslot = 2 * (2 * ((lane >> 4) & 1) + ((lane >> 3) & 1)) + (lane & 1);
     PairInterp<SPL> pi;
-    pi.init(m, n, half);
+    pi.init(m, n, half, lane);
     float2 qa[SPL];
 #pragma unroll
     for (int j = 0; j < SPL; ++j) qa[j] = f2(0.f);
-    for (int l = lb; l < le; ++l) {
-        const LayerConst &lc = sc.lay[l];
-        pi.update(m, sc, lc, n);
-        if (l + 1 < le) pi.prefetch(m, lc, sc.lay[l + 1], n);
-        unsigned char *row = quarter + (size_t)l * RB2_BYTES;
-        const float2 ab = *reinterpret_cast<const float2 *>(row + 8 * q);
-        const float2 abn = mul2(ab, f2(lc.nsc));
-        const float2 wp = f2(lc.wp), wt = f2(lc.wt);
-        float2 sum = f2(0.f), pt = f2(0.f), t;
+    const int st_off = (half ? 64 : 0) + 4 * q;
+    for (int l = lb; l < le;) {
+        const int end = min(sc.lay[l].run_end, le);
+        pi.load(sc, sc.lay[l].cell, sc.lay[l].itc);
+        if (end < le) pi.prefetch(sc.lay[end].cell, sc.lay[end].itc);
+        for (; l < end; ++l) {
+            const LayerConst &lc = sc.lay[l];
+            unsigned char *row = quarter + (size_t)l * RB2_BYTES;
+            const float2 ab = *reinterpret_cast<const float2 *>(row + 8 * q);
+            const float2 abn = mul2(ab, lc.nsc);
+            float2 t, p = ex2x2(pi.expo(0, lc.wp, lc.wt, t));
+            float2 sum = p, pt = mul2(p, t);
+            qa[0] = fma2(abn, p, qa[0]);
 #pragma unroll
-        for (int j = 0; j < SPL; ++j) {
-            const float2 p = ex2x2(pi.expo(j, wp, wt, t));
-            sum = add2(sum, p);
-            qa[j] = fma2(abn, p, qa[j]);
-            pt = fma2(p, t, pt);
+            for (int j = 1; j < SPL; ++j) {
+                p = ex2x2(pi.expo(j, lc.wp, lc.wt, t));
+                sum = add2(sum, p);
+                qa[j] = fma2(abn, p, qa[j]);
+                pt = fma2(p, t, pt);
+            }
+            const float2 c = pi.cia(lc);
+            const float2 ac = mul2(ab, c);
+            const float2 act = mul2(ac, pi.d);
+            float v[4];
+            v[0] = fmaf(abn.x, sum.x, abn.y * sum.y);
+            v[1] = fmaf(abn.x, pt.x, abn.y * pt.y) * lc.gts;
+            v[2] = ac.x + ac.y;
+            v[3] = (act.x + act.y) * lc.gtcs;
+            const float tot = reduce4_parity(v, lane);
+            if (rwriter) atomicAdd(red + l * N_RED + rslot, tot);
+            const float2 mine = fma2(lc.ray, pi.nu4, fma2(sum, lc.nsc, c));
+            const float2 alpha = add2(mine, shfl_xor2(mine, 1));
+            uint32_t hi, lo;
+            split2(alpha, hi, lo);
+            __syncwarp();
+            *reinterpret_cast<uint32_t *>(row + st_off) = half ? lo : hi;
         }
-        const float2 c = pi.cia(lc);
-        const float2 ac = mul2(ab, c);
-        const float2 act = mul2(ac, pi.d);
-        const float cs = ac.x + ac.y, cts = (act.x + act.y) * (lc.gtc * inv_l2);
-        float v[8];
-        v[0] = abn.x * sum.x + abn.y * sum.y;
-        v[1] = (abn.x * pt.x + abn.y * pt.y) * (lc.gt * inv_l2);
-        v[2] = half ? 0.f : cs;
-        v[3] = half ? cs : 0.f;
-        v[4] = half ? 0.f : cts;
-        v[5] = half ? cts : 0.f;
-        v[6] = half ? 0.f : (ab.x * pi.nu4.x + ab.y * pi.nu4.y) * ray_ref;
-        v[7] = 0.f;
-        const float tot = transpose_reduce8(v, lane);
-        if (writer && ridx < N_RED && tot != 0.f) atomicAdd(red + l * N_RED + ridx, tot);
-        float2 mine = fma2(sum, f2(lc.nsc), c);
-        if (half == 0) mine = fma2(f2(lc.ray), pi.nu4, mine);
-        const float2 alpha = add2(mine, shfl_xor2(mine, 1));
-        uint32_t hi, lo;
-        split2(alpha, hi, lo);
-        __syncwarp();
-        *reinterpret_cast<uint32_t *>(row + (half ? 64 : 0) + 4 * q) = half ? lo : hi;
     }
     // per-species totals: slot j of lane half h is species SPL h + j
 #pragma unroll
@@ -346,7 +384,8 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
         sm.th[L * T2_PITCH + idx] = __float2bfloat16_rn(0.f);
         sm.tl[L * T2_PITCH + idx] = __float2bfloat16_rn(0.f);
     }
-    for (int idx = threadIdx.x; idx < (LP - L) * RB2_BYTES; idx += BW_THREADS) sm.rb[L * RB2_BYTES + idx] = 0;
+    for (int idx = threadIdx.x; idx < (LPR - L) * RB2_BYTES; idx += BW_THREADS) sm.rb[L * RB2_BYTES + idx] = 0;
+    const float ray_ref = (float)(1.0 / ((double)m.ray_nu_ref * m.ray_nu_ref * m.ray_nu_ref * m.ray_nu_ref));
     const uint32_t blh = smem_u32(sm.lh), bll = smem_u32(sm.ll), bth = smem_u32(sm.th), btl = smem_u32(sm.tl);
     const uint32_t brb = smem_u32(sm.rb);
     const int ksmax = (L + 15) / 16;
@@ -354,19 +393,20 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
     int cur_b = -1;
     auto flush = [&](int b) {
         // L_bar, reductions, per-species totals and area_bar of sample b (FP64 atomics)
-        double *lbar = w.lbar + (size_t)b * L * L;
+        double *lbar = w.lbar + (size_t)b * L * L, *zbar = w.zbar + (size_t)b * L;
         const int r = lane >> 2, col = 2 * (lane & 3);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const int p = warp + BW_WARPS * k;
-            if (p < 56) {
-                int mi, nj;
-                decode_pair(p, mi, nj);
+            int mi, nj;
+            if (lbar_pair(warp + BW_WARPS * k, L, mi, nj)) {
                 const int i0 = 16 * mi + r, l0 = 8 * nj + col;
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int ii = i0 + ((e >> 1) << 3), ll = l0 + (e & 1);
-                    if (ii < L && ll <= ii && lacc[k][e] != 0.f) atomicAdd(lbar + (size_t)ii * L + ll, (double)lacc[k][e]);
+                    const float v = lacc[k][e];
+                    if (ii >= L || v == 0.f) continue;
+                    if (ll == L) atomicAdd(zbar + ii, (double)v);
+                    else if (ll <= ii) atomicAdd(lbar + (size_t)ii * L + ll, (double)v);
                 }
             }
         }
@@ -400,6 +440,17 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
         const int t1 = min(ntiles, (c + 1) * chunk_tiles);
         for (int t = c * chunk_tiles; t < t1; ++t) {
             const int nt0 = t * BT;
+            // Rayleigh weight row w(nu) for the L_bar product
+            if (threadIdx.x < BT / 2) {
+                const int t2 = threadIdx.x;
+                const float2 nu = __ldg(reinterpret_cast<const float2 *>(m.nu + nt0 + 2 * t2));
+                const float2 nu2 = mul2(nu, nu);
+                uint32_t hi, lo;
+                split2(mul2(mul2(nu2, nu2), f2(ray_ref)), hi, lo);
+                unsigned char *rw = sm.rb + (size_t)L * RB2_BYTES + 128 * (t2 >> 4) + 4 * (t2 & 15);
+                *reinterpret_cast<uint32_t *>(rw) = hi;
+                *reinterpret_cast<uint32_t *>(rw + 64) = lo;
+            }
             // tau_bar = dbar A_i exp(-tau); area_bar += dbar (1 - exp(-tau))
             {
                 const int nl = nt0 + 2 * (lane + 32 * (warp & 1));
@@ -465,10 +516,8 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
             // L_bar[i][l] += sum_nu tau_bar[i][nu] alpha[l][nu] over this tile (8 k-steps)
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const int p = warp + BW_WARPS * k;
-                if (p < 56) {
-                    int mi, nj;
-                    decode_pair(p, mi, nj);
+                int mi, nj;
+                if (lbar_pair(warp + BW_WARPS * k, L, mi, nj)) {
 #pragma unroll
                     for (int ks = 0; ks < BT / 16; ++ks) {
                         uint32_t ah[4], al[4], bh[2], bl[2];

@@ -209,8 +209,13 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup_bwd(Model m, Work w) {
     for (int l = tid; l < L; l += blockDim.x) {
         const double *rd = w.red + ((size_t)b * L + l) * N_RED;
         double n = w.n_lay[(size_t)b * L + l], t = w.t_lay[(size_t)b * L + l];
-        const double qsum = rd[0];
-        double dd = rd[1], c1 = rd[2], c2 = rd[3], c1t = rd[4], c2t = rd[5], w4 = rd[6];
+        const double qsum = rd[0] + rd[1];
+        double dd = rd[2] + rd[3], c1 = rd[4], c2 = rd[5], c1t = rd[6], c2t = rd[7], w4 = rd[8];
+        if (!emis && !bad) {   // W4_l = sum_nu alpha_bar_l w = sum_i L_il z_i
+            const float *lm = w.lmat + (size_t)b * L * L + l;
+            const double *z = w.zbar + (size_t)b * L;
+            for (int i = 0; i < L; ++i) w4 += (double)lm[(size_t)i * L] * z[i];
+        }
         double nbar = 0.0, tb = 0.0;
         if (!bad) {
             nbar = (qsum + 2.0 * (c1 + c2)) / n + (xs[S] * m.ray_h2 + xs[S + 1] * m.ray_he) * w4;

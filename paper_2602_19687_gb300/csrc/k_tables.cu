@@ -6,8 +6,11 @@
 //   c0 = L v00, c1 = L (v01 - v00), c2 = L (v10 - v00),
 //   c3 = L ((v11 - v10) - (v01 - v00)),  L = log2(10),
 // identical to bilinear interpolation with weights (1-wt)(1-wp), (1-wt) wp,
-// wt (1-wp), wt wp. Stored per (cell, s) and wavenumber pair as two float4
-// (c0, c0', c1, c1'), (c2, c2', c3, c3') (primes: the pair's second wavenumber).
+// wt (1-wp), wt wp. Species slot s = h SP/2 + j of a wavenumber pair is
+// read by the lane of half h of the pair; its two float4 (c0, c0', c1, c1')
+// and (c2, c2', c3, c3') (primes: the pair's second wavenumber) sit at
+// [cell][j][c][pair][h], so that for fixed (j, c) the lanes of a warp read
+// consecutive float4. Slots s >= S stay zero (the caller clears the table).
 #include "internal.cuh"
 
 namespace es {
@@ -32,11 +35,16 @@ __global__ void k_build_coef(Model m, float4 *coef) {
     const float v00 = table_value<BF16>(m, row, n), v01 = table_value<BF16>(m, row + 1, n);
     const float v10 = table_value<BF16>(m, row + m.NP, n), v11 = table_value<BF16>(m, row + m.NP + 1, n);
     const float l = (float)LOG2_10, d0 = v01 - v00;
-    float *out = reinterpret_cast<float *>(coef + ((size_t)cs * (m.Np >> 1) + (n >> 1)) * 2) + (n & 1);
-    out[0] = l * v00;
-    out[2] = l * d0;
-    out[4] = l * (v10 - v00);
-    out[6] = l * ((v11 - v10) - d0);
+    const int spl = m.SP >> 1, h = s / spl, j = s % spl;
+    const size_t np2 = (size_t)(m.Np >> 1);
+    const size_t i0 = ((((size_t)cell * spl + j) * 2 + 0) * np2 + (n >> 1)) * 2 + h;
+    const size_t i1 = i0 + 2 * np2;   // c = 1
+    float *o0 = reinterpret_cast<float *>(coef + i0) + (n & 1);
+    float *o1 = reinterpret_cast<float *>(coef + i1) + (n & 1);
+    o0[0] = l * v00;
+    o0[2] = l * d0;
+    o1[0] = l * (v10 - v00);
+    o1[2] = l * ((v11 - v10) - d0);
 }
 
 }  // namespace
