@@ -815,7 +815,7 @@ es_status es_autotune(es_ctx *c, es_stream_t stream) {
         }
         return best;
     };
-    const int fwd_cand[] = {1, 2, 4, 8, 16, 32}, bwd_cand[] = {1, 2, 4, 8, 16};
+    const int fwd_cand[] = {2, 4, 8, 16, 32, 64, 128}, bwd_cand[] = {2, 4, 8, 16, 32, 64};
     float best = 1e30f;
     for (int ch : fwd_cand) {
         const float ms = time_it([&]() { launch_trans_fused_forward(c->m, w, true, ch, st, none); });

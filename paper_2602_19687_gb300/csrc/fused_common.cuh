@@ -27,7 +27,24 @@ __device__ __forceinline__ float ex2f(float x) {
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-__device__ __forceinline__ float2 ex2x2(float2 x) { return make_float2(ex2f(x.x), ex2f(x.y)); }
+// float2 <-> 64-bit register pair (no data movement: keeps the two lanes of
+// a packed operand in one aligned pair across inline asm and shuffles)
+__device__ __forceinline__ unsigned long long f2_bits(float2 v) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
+    return r;
+}
+__device__ __forceinline__ float2 bits_f2(unsigned long long r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+__device__ __forceinline__ float2 ex2x2(float2 x) {
+    unsigned long long r;
+    asm("{\n\t.reg .f32 a, b;\n\tex2.approx.ftz.f32 a, %1;\n\tex2.approx.ftz.f32 b, %2;\n\tmov.b64 %0, {a, b};\n\t}"
+        : "=l"(r) : "f"(x.x), "f"(x.y));
+    return bits_f2(r);
+}
 __device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
 
 // ------------------------------------------------------------ BF16 split and tensor cores
@@ -230,7 +247,7 @@ struct PairInterp {
 };
 
 __device__ __forceinline__ float2 shfl_xor2(float2 v, int o) {
-    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+    return bits_f2(__shfl_xor_sync(0xffffffffu, f2_bits(v), o));
 }
 
 // Extinction alpha_l(nu) at wavenumber pair n, n+1 for layers [lb, le), the

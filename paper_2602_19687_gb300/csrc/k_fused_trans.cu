@@ -156,8 +156,9 @@ __global__ void __launch_bounds__(FTHREADS, 2) k_trans_fwd(Model m, Work w, int 
                 s1 += a0 * (1.f - e01) + a1 * (1.f - e11);
                 if (STORE_E) {   // padding wavenumbers too: the adjoint multiplies them by dbar = 0
                     float *eb = w.estore + (size_t)b * L * m.Np + n0;
-                    if (i0 < L) *reinterpret_cast<float2 *>(eb + (size_t)i0 * m.Np) = make_float2(e00, e01);
-                    if (i1 < L) *reinterpret_cast<float2 *>(eb + (size_t)i1 * m.Np) = make_float2(e10, e11);
+                    // streaming stores: keep the opacity coefficients, not these, in L2
+                    if (i0 < L) __stcs(reinterpret_cast<float2 *>(eb + (size_t)i0 * m.Np), make_float2(e00, e01));
+                    if (i1 < L) __stcs(reinterpret_cast<float2 *>(eb + (size_t)i1 * m.Np), make_float2(e10, e11));
                 }
             }
 #pragma unroll
@@ -420,6 +421,26 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
         for (int s2 = threadIdx.x; s2 < S; s2 += BW_THREADS)
             if (sm.qtot[s2] != 0.f) atomicAdd(w.qtot + (size_t)b * S + s2, (double)sm.qtot[s2]);
     };
+    // L2 prefetch of the exp(-tau) rows and dbar of tile t of sample b (the
+    // tau_bar phase reads them straight from HBM otherwise, with every warp
+    // of the block waiting on the same loads)
+    uint64_t evict_first;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(evict_first));
+    auto prefetch_tile = [&](int pb, int pt) {
+        if (threadIdx.x < L) {   // read once: evict-first, the coefficient table stays resident
+            const float *src = w.estore + ((size_t)pb * L + threadIdx.x) * m.Np + (size_t)pt * BT;
+            asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;" ::"l"(src), "r"(BT * 4),
+                         "l"(evict_first)
+                         : "memory");
+        } else if (threadIdx.x == L) {
+            const float *src = w.dbar + (size_t)pb * m.Np + (size_t)pt * BT;
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(BT * 4) : "memory");
+        }
+    };
+    if (blockIdx.x < total) {
+        const long long it0 = blockIdx.x;
+        prefetch_tile((int)(it0 % w.B), (int)(it0 / w.B) * chunk_tiles);
+    }
     for (long long item = blockIdx.x; item < total; item += gridDim.x) {
         // chunk-major order: blocks running together share a wavenumber window
         const int c = (int)(item / w.B), b = (int)(item % w.B);
@@ -440,6 +461,12 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
         const int t1 = min(ntiles, (c + 1) * chunk_tiles);
         for (int t = c * chunk_tiles; t < t1; ++t) {
             const int nt0 = t * BT;
+            if (t + 1 < t1) {
+                prefetch_tile(b, t + 1);
+            } else if (item + gridDim.x < total) {   // first tile of this block's next item
+                const long long nx = item + gridDim.x;
+                prefetch_tile((int)(nx % w.B), (int)(nx / w.B) * chunk_tiles);
+            }
             // Rayleigh weight row w(nu) for the L_bar product
             if (threadIdx.x < BT / 2) {
                 const int t2 = threadIdx.x;
