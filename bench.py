@@ -155,8 +155,12 @@ def kernel_work(name, w, n_valid):
     n_e = B - n_t
     if name in ("k_extinction", "k_extinction_bwd"):
         return n_e * L * (S + 2) * N, "ex2", "alu"
-    if name in ("k_trans_fwd", "k_trans_bwd"):
-        # one ex2 per (vector, layer, species or CIA pair, wavenumber) of the interpolation
+    if name == "k_trans_fwd":
+        # one ex2 per (vector, layer, species or CIA pair, wavenumber) of the
+        # interpolation, plus exp(-tau_i) per (vector, impact parameter, wavenumber)
+        return n_t * L * (S + 3) * N, "ex2", "alu"
+    if name == "k_trans_bwd":
+        # the adjoint recomputes the interpolation's exponentials
         return n_t * L * (S + 2) * N, "ex2", "alu"
     if name in ("k_emission", "k_emission_bwd"):
         return B * N * L * 4, "layer-angle steps", "alu"
@@ -175,6 +179,28 @@ def alu_peak(kind, sm_mhz):
 
 
 # --------------------------------------------------------------------------- main arms
+# --------------------------------------------------------------------------- sharding
+def shard_seed(rank):
+    """Each rank evaluates its own batch of parameter vectors (weak scaling:
+    independent shards, no data-path collective)."""
+    return 42 + rank
+
+
+def max_over_ranks(x, world, device):
+    """The slowest rank's time: all-reduce MAX (identity at world == 1)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(batch_per_rank, world, ms_max):
+    """Whole-job spectra/s: the units all ranks processed over the slowest rank's time."""
+    return batch_per_rank * world / (ms_max / 1e3)
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -199,7 +225,7 @@ def run_gpu(args):
         if world > 1:
             dist.barrier()
 
-    w = synth.workload(args.workload, batch=args.batch, seed=42 + rank)   # each rank: its own shard
+    w = synth.workload(args.workload, batch=args.batch, seed=shard_seed(rank))   # each rank: its own shard
     ctx = binding.context_for(w, device=local)
     B = w.theta.shape[0]
     nfree = w.theta.shape[1]
@@ -246,11 +272,8 @@ def run_gpu(args):
     ms_profiled = ep0.elapsed_time(ep1) / args.steps
     prof = ctx.es_get_profile()
     ctx.es_set_profiling(False)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = B * world / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, world, dev)
+    value = job_throughput(B, world, ms_max)
 
     # ---- end to end through the C ABI with host buffers (pinned)
     th_host = torch.tensor(w.theta, dtype=torch.float64).pin_memory().numpy()
@@ -267,13 +290,11 @@ def run_gpu(args):
     t1 = time.perf_counter()
     barrier()
     e2e_ms = (t1 - t0) * 1e3 / args.steps
-    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = B * world / (float(te.item()) / 1e3)
+    e2e_value = job_throughput(B, world, max_over_ranks(e2e_ms, world, dev))
 
     # ---- roofline of the dominant kernel (live CUDA-event times)
     peaks, peak_src = measured_peaks()
+    ex2_rate, ffma2_rate = binding.probe_rates(local)
     sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     per_kernel = {}
     total_prof = sum(p[1] for p in prof) or 1.0
@@ -287,13 +308,16 @@ def run_gpu(args):
         if wk is not None:
             amount, unit_kind, bound = wk
             achieved = amount / (ms_launch / 1e3)
-            peak = alu_peak(unit_kind, sm_mhz)
+            peak = ex2_rate if unit_kind == "ex2" else alu_peak(unit_kind, sm_mhz)
             scale = 1e12
             roof = {"kernel": top, "bound": bound, "achieved": achieved / scale,
                     "peak": peak / scale if peak else None,
                     "unit": "T%s/s" % unit_kind, "frac": (achieved / peak) if peak else None,
                     "traffic": None, "ms_per_launch": ms_launch,
-                    "peak_source": "derived from unit counts x median SM clock %.0f MHz" % sm_mhz}
+                    "peak_source": ("measured: es_probe_rates MUFU ex2 throughput on this GPU"
+                                    if unit_kind == "ex2" else
+                                    "derived from unit counts x median SM clock %.0f MHz" % sm_mhz),
+                    "nominal_peak": alu_peak(unit_kind, sm_mhz) / scale if alu_peak(unit_kind, sm_mhz) else None}
 
     # ---- plain per-sample path (batched vs plain)
     plain = None
@@ -343,6 +367,7 @@ def run_gpu(args):
             "cpu_baseline": cpu,
             "clocks": clk,
             "peaks_source": peak_src,
+            "probe": {"ex2_per_s": ex2_rate, "ffma2_per_s": ffma2_rate},
         }
         print(json.dumps(line))
     ctx.es_destroy()

@@ -234,6 +234,14 @@ es_status es_set_profiling(es_ctx *ctx, int on);
 es_status es_get_profile(es_ctx *ctx, int index, char *name, int name_len, double *total_ms,
                          int64_t *launches);
 
+/* Throughput probe of GPU `device` (not a step of the paper's method; a
+ * measured ceiling for the ALU roofline of the interpolation kernels):
+ * ex2.approx.ftz.f32 instructions per second and packed FP32x2 FMA
+ * instructions per second, each from a kernel of independent dependency
+ * chains at full occupancy (best of three ~ms runs). Synchronous; allocates
+ * and frees 1 KB. ES_EINVAL for NULL outputs, ES_ECUDA for a bad device. */
+es_status es_probe_rates(int device, double *ex2_per_s, double *ffma2_per_s);
+
 /* Message for the last error on this context (never NULL). */
 const char *es_last_error(const es_ctx *ctx);
 

@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "ES_OK", 1: "ES_EINVAL", 2: "ES_ENOMEM", 3: "ES_ECUDA", 4: "E
 
 EXPORTS = ["es_create", "es_load_tables", "es_set_grid", "es_set_data", "es_set_batch", "es_forward",
            "es_loglike", "es_forward_backward", "es_loglike_noalloc", "es_autotune", "es_set_graphs",
-           "es_get_flags", "es_query", "es_set_profiling",
+           "es_get_flags", "es_query", "es_set_profiling", "es_probe_rates",
            "es_get_profile", "es_last_error", "es_destroy"]
 
 
@@ -75,6 +75,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.es_loglike_noalloc.argtypes = [vp, vp, vp, ip, vp, vp]
     lib.es_get_flags.argtypes = [vp, vp, ip, vp]
     lib.es_autotune.argtypes = [vp, vp]
+    lib.es_probe_rates.argtypes = [ip, ctypes.POINTER(dp), ctypes.POINTER(dp)]
     lib.es_set_graphs.argtypes = [vp, ip]
     lib.es_query.argtypes = [vp, ip]
     lib.es_query.restype = ctypes.c_int64
@@ -254,6 +255,16 @@ class Context:
             self.es_destroy()
         except Exception:
             pass
+
+
+def probe_rates(device: int = 0):
+    """(ex2 instructions/s, packed FP32x2 FMA instructions/s) measured on `device`."""
+    lib = load_library()
+    e, f = ctypes.c_double(), ctypes.c_double()
+    st = lib.es_probe_rates(int(device), ctypes.byref(e), ctypes.byref(f))
+    if st != ES_OK:
+        raise RuntimeError("es_probe_rates failed with status %d" % st)
+    return e.value, f.value
 
 
 def context_for(workload, device: int = 0) -> Context:

@@ -71,6 +71,7 @@ def test_null_context_calls(lib):
     assert lib.es_set_grid(None, None, None, 3) == binding.ES_EINVAL
     assert lib.es_autotune(None, None) == binding.ES_EINVAL
     assert lib.es_set_graphs(None, 1) == binding.ES_EINVAL
+    assert lib.es_probe_rates(0, None, None) == binding.ES_EINVAL
 
 
 @pytest.mark.parametrize("field,value", [("n_layers", 1), ("n_layers", 113), ("n_species", 0),

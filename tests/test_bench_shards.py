@@ -1,0 +1,50 @@
+"""Multi-process logic of bench.py on CPU (gloo, world size 2): every rank
+gets its own shard of parameter vectors, the reported time is the slowest
+rank's, and the job throughput counts the units of all ranks."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+import bench  # noqa: E402
+from paper_2602_19687_gb300 import synth  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        w = synth.workload("batched_trans", batch=4, seed=bench.shard_seed(rank), n_nu=200)
+        ms = 10.0 + 5.0 * rank                      # rank 1 is the slow one
+        ms_max = bench.max_over_ranks(ms, world, "cpu")
+        out[rank] = (w.theta.copy(), ms_max, bench.job_throughput(4, world, ms_max))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_shards_and_max_over_ranks():
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        out = mgr.dict()
+        mp.start_processes(_rank_main, args=(2, _free_port(), out), nprocs=2, join=True, start_method="spawn")
+        res = dict(out)
+    (th0, ms0, v0), (th1, ms1, v1) = res[0], res[1]
+    assert not np.allclose(th0, th1)                 # distinct shards
+    assert ms0 == ms1 == 15.0                        # the slowest rank's time on every rank
+    assert v0 == v1 == pytest.approx(2 * 4 / 15e-3)  # units of both ranks / that time
+
+
+def test_single_rank_is_identity():
+    assert bench.max_over_ranks(3.5, 1, "cpu") == 3.5
+    assert bench.job_throughput(1024, 1, 80.0) == pytest.approx(12800.0)
