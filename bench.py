@@ -167,6 +167,23 @@ def kernel_work(name, w, n_valid):
     return None
 
 
+def measured_traffic(name, n_vectors):
+    """DRAM bytes per launch of `name` from the committed ncu capture, scaled
+    from its batch to n_vectors transmission vectors; None when the kernel
+    sources changed since the capture."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic_k_trans_b128.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    for rel, digest in d["sources_sha256"].items():
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != digest:
+                return None
+    b = d["dram_bytes_per_launch"].get(name)
+    return None if b is None else b * n_vectors / d["capture_vectors"]
+
+
 def alu_peak(kind, sm_mhz):
     """Peaks from unit counts x clock (152 SMs): MUFU ex2 32/clk/SM on
     GB300; FP32 FMA 128 lanes x 2 flop/clk/SM."""
@@ -313,7 +330,9 @@ def run_gpu(args):
             roof = {"kernel": top, "bound": bound, "achieved": achieved / scale,
                     "peak": peak / scale if peak else None,
                     "unit": "T%s/s" % unit_kind, "frac": (achieved / peak) if peak else None,
-                    "traffic": None, "ms_per_launch": ms_launch,
+                    "traffic": measured_traffic(top, int(np.sum(w.kind[:n_valid] == 0))),
+                    "traffic_unit": "bytes per launch (ncu capture at B=128, scaled by vectors)",
+                    "ms_per_launch": ms_launch,
                     "peak_source": ("measured: es_probe_rates MUFU ex2 throughput on this GPU"
                                     if unit_kind == "ex2" else
                                     "derived from unit counts x median SM clock %.0f MHz" % sm_mhz),
