@@ -218,7 +218,8 @@ es_status es_get_flags(es_ctx *ctx, int32_t *flags, int mem, es_stream_t stream)
  * 6 device workspace bytes, 7 kernel launches issued by the last call (a
  * replayed graph counts the launches it holds), 8 / 9 work-item size of the
  * fused transmission forward / adjoint kernel (0: built-in heuristic),
- * 10 graph replay enabled (1) or not (0).
+ * 10 graph replay enabled (1) or not (0), 11 device status word (0; nonzero
+ * once a tensor-core kernel gave up on a bounded wait; synchronises).
  * Returns -1 for an unknown key or a NULL context. */
 int64_t es_query(const es_ctx *ctx, int key);
 

@@ -202,6 +202,7 @@ es_status alloc_forward(es_ctx *c, int B) {
     ALLOC(w.theta, (size_t)B * m.nfull);
     ALLOC(w.kind, B);
     ALLOC(w.flags, B);
+    ALLOC(w.err, 1);
     ALLOC(w.t_lay, B * L);
     ALLOC(w.t_lev, B * (L + 1));
     ALLOC(w.r_lev, B * (L + 1));
@@ -228,6 +229,7 @@ es_status alloc_forward(es_ctx *c, int B) {
     ALLOC(w.misc, (size_t)B * 4);
     ALLOC(c->d_lnl, B);
 #undef ALLOC
+    if (cudaMemset(w.err, 0, sizeof(int)) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "status word");
     c->cap_b = B;
     return ES_OK;
 }
@@ -866,6 +868,11 @@ int64_t es_query(const es_ctx *c, int key) {
         case 8: return c->fwd_chunk;
         case 9: return c->bwd_chunk;
         case 10: return c->use_graph ? 1 : 0;
+        case 11: {
+            int v = -1;
+            if (!c->w.err || cudaMemcpy(&v, c->w.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+            return v;
+        }
         default: return -1;
     }
 }

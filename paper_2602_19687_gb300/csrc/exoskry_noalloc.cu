@@ -65,6 +65,7 @@ size_t carve(const es::Model &m, int B, bool emission, unsigned char *base, es::
     w.theta = c.take<double>((size_t)B * m.nfull);
     *kind_slot = c.take<int>(B);
     w.flags = c.take<int>(B);
+    w.err = c.take<int>(1);
     w.t_lay = c.take<double>(B * L);
     w.t_lev = c.take<double>(B * (L + 1));
     w.r_lev = c.take<double>(B * (L + 1));
@@ -132,6 +133,8 @@ extern "C" es_status es_loglike_noalloc(es_ctx *c, const double *theta, const in
         e = cudaMemsetAsync(kind_slot, 0, sizeof(int) * (size_t)batch, st);
         if (e != cudaSuccess) return fail(c, ES_ECUDA, std::string("kind fill: ") + cudaGetErrorString(e));
     }
+    e = cudaMemsetAsync(w.err, 0, sizeof(int), st);
+    if (e != cudaSuccess) return fail(c, ES_ECUDA, std::string("status word: ") + cudaGetErrorString(e));
     const es::Hook none{};
     int launches = 0;
     launches += es::launch_setup(c->m, w, st, none);

@@ -85,6 +85,7 @@ struct Work {
     const double *theta_user;     // [B][nfree]
     double *theta;                // [B][nfull]
     int *kind, *flags;            // [B]
+    int *err;                     // [1] nonzero once a kernel gave up on a bounded wait (sticky)
     double *t_lay, *t_lev, *r_lev;// [B][L], [B][L+1], [B][L+1]
     double *xs;                   // [B][S+2] X_s..., X_H2, X_He
     double *n_lay;                // [B][L]

@@ -17,53 +17,69 @@
 #include <algorithm>
 
 #include "fused_common.cuh"
+#include "tc_common.cuh"
 
 namespace es {
 
 namespace {
 
-constexpr int RB_PITCH = 152;                 // bf16 pitch of the backward row buffer (304 B)
-constexpr int RB_LO = 72;                     // bf16 offset of the lo half in a row (144 B)
 constexpr float LOG2E_F = 1.4426950408889634f;
+
+// Forward block: 16 warps, 128-wavenumber tiles; the chord product runs on
+// the tcgen05 tensor cores with the accumulator in TMEM (double-buffered so
+// the epilogue of tile t overlaps the product of tile t + 1).
+constexpr int FT2 = 128;                          // wavenumbers per forward tile (the MMA's M)
+constexpr int F2_WARPS = 16;
+constexpr int F2_THREADS = F2_WARPS * 32;
+constexpr int SBO_NU = (FT2 / 8) * CORE_STRIDE;   // 8-row group stride of [row][128 nu] operands (2304 B)
+constexpr int SBO_LP = (LP / 8) * CORE_STRIDE;    // 8-row group stride of [row][112 layers] operands (2016 B)
+constexpr int F2_TMEM_COLS = 256;                 // two 112-column accumulators
 
 struct TransFwdSmem {
     SampleConst sc;
-    __nv_bfloat16 lh[LP * L_PITCH], ll[LP * L_PITCH];   // path lengths [i][l]
-    __nv_bfloat16 ah[LP * R_PITCH], al[LP * R_PITCH];   // extinction [l][nu]
+    alignas(128) unsigned char lh[(LP / 8) * SBO_LP], ll[(LP / 8) * SBO_LP];    // L[i][l], split BF16
+    alignas(128) unsigned char ah[(LP / 8) * SBO_NU], al[(LP / 8) * SBO_NU];    // alpha[l][nu], split BF16
     float area[LP];
+    float part[4][FT2];                            // per-column-chunk partial transit sums
+    alignas(8) uint64_t mbar;
+    uint32_t tmem_base;
+    int abort;
 };
 
-// Backward block: 16 warps, 128-wavenumber tiles.
+// Backward block: 16 warps, 128-wavenumber tiles; both products on the
+// tcgen05 tensor cores: alpha_bar^T = tau_bar^T L into TMEM columns [0, 112)
+// (read there by the interpolation warps) and L_bar = tau_bar alpha^T
+// accumulated over the sample's tiles in TMEM columns [128, 256).
 constexpr int BW_WARPS = 16;
 constexpr int BW_THREADS = BW_WARPS * 32;
 constexpr int BT = 128;              // wavenumbers per backward tile
-constexpr int T2_PITCH = 136;        // bf16 pitch of tau_bar rows [i][128 nu] (272 B: 17 x 16 B)
-constexpr int RB2_BYTES = 528;       // bytes per row buffer row (33 x 16 B): four 128-B quarters
-constexpr int LPR = 120;             // row buffer rows: LP layers, plus row L (the Rayleigh weight), to 8
-// Row buffer, per layer and per 32-wavenumber quarter k (bytes [128 k, 128 k + 128)):
-// first alpha_bar as 32 FP32, then overwritten by the extinction as BF16 hi
-// (bytes 0..63 of the quarter) and lo (bytes 64..127). Each quarter of a row
-// belongs to one warp, so the overwrite only needs a warp barrier. Row L holds
-// w(nu) = (nu/nu_ref)^4 as split BF16, so that the L_bar product also yields
-// z_i = sum_nu tau_bar_i(nu) w(nu), from which the Rayleigh reduction
-// W4_l = sum_nu alpha_bar_l(nu) w(nu) = sum_i L_il z_i follows.
+constexpr int LB_ROWS = 128;         // rows of the alpha operand: layers, the Rayleigh weight row (L), zeros
+// The alpha operand's row L holds w(nu) = (nu/nu_ref)^4 as split BF16, so
+// the L_bar product also yields z_i = sum_nu tau_bar_i(nu) w(nu), from which
+// the Rayleigh reduction W4_l = sum_nu alpha_bar_l(nu) w(nu) = sum_i L_il z_i
+// follows.
 
 struct TransBwdSmem {
     SampleConst sc;
-    __nv_bfloat16 lh[LP * L_PITCH], ll[LP * L_PITCH];   // path lengths [i][l]
-    __nv_bfloat16 th[LP * T2_PITCH], tl[LP * T2_PITCH]; // tau_bar [i][nu]
-    unsigned char rb[LPR * RB2_BYTES];                  // alpha_bar / alpha rows, Rayleigh weight row
+    alignas(128) unsigned char lh[(LP / 8) * SBO_LP], ll[(LP / 8) * SBO_LP];      // L[i][l]
+    alignas(128) unsigned char th[(LP / 8) * SBO_NU], tl[(LP / 8) * SBO_NU];      // tau_bar[i][nu]
+    alignas(128) unsigned char ah[(LB_ROWS / 8) * SBO_NU], al[(LB_ROWS / 8) * SBO_NU];   // alpha[l][nu]
     float area[LP];
     float area_acc[LP];                                 // area_bar of the current sample
     float red[ES_MAX_LAYERS * N_RED];                   // per-layer reductions of the current sample
     float qtot[ES_MAX_SPECIES];                         // per-species totals of the current sample
+    alignas(8) uint64_t mbar_a, mbar_l;
+    uint32_t tmem_base;
+    int abort;
 };
 
-// Path-length matrix of sample b as split BF16 [i][l] (zero-padded to LP x LP).
-__device__ void stage_lmat(const Model &m, const Work &w, int b, __nv_bfloat16 *lh, __nv_bfloat16 *ll, float *area) {
+// Path-length matrix of sample b as the split BF16 tensor-core operand
+// L[i][l] (112 x 112, zero-padded, core-matrix layout) and the annulus areas.
+__device__ void stage_lmat_tc(const Model &m, const Work &w, int b, unsigned char *lh, unsigned char *ll,
+                              float *area) {
     const int L = m.L;
     const float *src = w.lmat + (size_t)b * L * L;
-    for (int idx = threadIdx.x; idx < LP * (LP / 2); idx += FTHREADS) {
+    for (int idx = threadIdx.x; idx < LP * (LP / 2); idx += blockDim.x) {
         const int i = idx / (LP / 2), l = 2 * (idx % (LP / 2));
         float2 v = make_float2(0.f, 0.f);
         if (i < L) {
@@ -72,108 +88,163 @@ __device__ void stage_lmat(const Model &m, const Work &w, int b, __nv_bfloat16 *
         }
         uint32_t hi, lo;
         split2(v, hi, lo);
-        *reinterpret_cast<uint32_t *>(lh + i * L_PITCH + l) = hi;
-        *reinterpret_cast<uint32_t *>(ll + i * L_PITCH + l) = lo;
+        const uint32_t o = op_off(i, l, SBO_LP);
+        *reinterpret_cast<uint32_t *>(lh + o) = hi;
+        *reinterpret_cast<uint32_t *>(ll + o) = lo;
     }
-    for (int i = threadIdx.x; i < LP; i += FTHREADS) area[i] = (i < L) ? w.area[(size_t)b * L + i] : 0.f;
+    for (int i = threadIdx.x; i < LP; i += blockDim.x) area[i] = (i < L) ? w.area[(size_t)b * L + i] : 0.f;
 }
 
 template <int SPL, bool STORE_E>
-__global__ void __launch_bounds__(FTHREADS, 2) k_trans_fwd(Model m, Work w, int chunk_tiles) {
+__global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, int chunk_tiles) {
     extern __shared__ float4 smem4[];
     TransFwdSmem &sm = *reinterpret_cast<TransFwdSmem *>(smem4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int L = m.L, N = m.N;
-    const int ntiles = (N + FT - 1) / FT;
+    const int ntiles = (N + FT2 - 1) / FT2;
     const int nchunks = (ntiles + chunk_tiles - 1) / chunk_tiles;
     const long long total = (long long)w.B * nchunks;
     // extinction rows of the padding layers stay zero
-    for (int idx = threadIdx.x; idx < (LP - L) * R_PITCH; idx += FTHREADS) {
-        sm.ah[L * R_PITCH + idx] = __float2bfloat16_rn(0.f);
-        sm.al[L * R_PITCH + idx] = __float2bfloat16_rn(0.f);
+    for (int idx = threadIdx.x; idx < (LP - L) * (FT2 / 2); idx += F2_THREADS) {
+        const uint32_t o = op_off(L + idx / (FT2 / 2), 2 * (idx % (FT2 / 2)), SBO_NU);
+        *reinterpret_cast<uint32_t *>(sm.ah + o) = 0u;
+        *reinterpret_cast<uint32_t *>(sm.al + o) = 0u;
     }
-    // interpolation: 4 layer groups x 2 halves (32 wavenumbers) of the tile; a
-    // wavenumber pair is shared by a lane pair splitting the species
-    const int half = lane & 1, pair = 16 * (warp & 1) + (lane >> 1);
+    const uint32_t mbar = smem_u32(&sm.mbar);
+    if (threadIdx.x == 0) {
+        mbar_init(mbar, 1);
+        sm.abort = 0;
+    }
+    if (warp == 0) tmem_alloc(smem_u32(&sm.tmem_base), F2_TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm.tmem_base;
+    // interpolation: 4 layer groups x 4 quarters (32 wavenumbers) of the tile;
+    // a wavenumber pair is shared by a lane pair splitting the species. Lane
+    // half 0 stores the hi parts of its pair's extinction, half 1 the lo parts.
+    const int half = lane & 1, vq = warp & 3, pair = 16 * vq + (lane >> 1);
     int lb, le;
-    group_layers(L, warp >> 1, FWARPS / 2, lb, le);
-    const uint32_t blh = smem_u32(sm.lh), bll = smem_u32(sm.ll), bah = smem_u32(sm.ah), bal = smem_u32(sm.al);
-    const int ksmax = (L + 15) / 16;
-    // lane half 0 stores the hi parts of its pair's extinction, half 1 the lo parts
-    uint32_t *const a_dst = reinterpret_cast<uint32_t *>((half ? sm.al : sm.ah) + 2 * pair);
-    int cur_b = -1;
-    for (long long item = blockIdx.x; item < total; item += gridDim.x) {
+    group_layers(L, warp >> 2, 4, lb, le);
+    unsigned char *const a_dst = (half ? sm.al : sm.ah) + op_off(0, 2 * pair, SBO_NU);
+    // epilogue: TMEM lane quadrant vq (wavenumber 32 vq + lane), impact parameters [28 ck, 28 ck + 28)
+    const int ck = warp >> 2;
+    // tau^T[nu][i] = sum_l alpha^T[nu][l] L^T[l][i]: M = 128 wavenumbers, N = 112, K = 112;
+    // A = alpha (stored [l][nu]: MN-major), B = L (stored [i][l]: K-major)
+    const uint32_t idesc = idesc_bf16(FT2, LP, true, false);
+    const uint32_t ah_s = smem_u32(sm.ah), al_s = smem_u32(sm.al), lh_s = smem_u32(sm.lh), ll_s = smem_u32(sm.ll);
+    uint32_t phase = 0;
+    int issued = 0, cur_b = -1;
+    int pend_b = -1, pend_t = 0, pend_buf = 0;
+    bool abort = false;
+
+    auto epilogue = [&](int pb, int pt, int buf) {
+        const int nl = 32 * vq + lane;
+        const uint32_t taddr = tmem + (uint32_t)(buf * 128 + 28 * ck) + ((uint32_t)(32 * vq) << 16);
+        float v16[16], v8[8], v4[4];
+        tmem_ld16(taddr, v16);
+        tmem_ld8(taddr + 16, v8);
+        tmem_ld4(taddr + 24, v4);
+        tmem_wait_ld();
+        float *eb = w.estore + (size_t)pb * L * m.Np + (size_t)pt * FT2 + nl;
+        float s = 0.f;
+        auto term = [&](int i, float tau) {
+            if (i < L) {
+                const float e = ex2f(-tau * LOG2E_F);
+                s = fmaf(sm.area[i], 1.f - e, s);
+                // streaming store: keep the opacity coefficients, not these, in L2
+                if (STORE_E) __stcs(eb + (size_t)i * m.Np, e);
+            }
+        };
+#pragma unroll
+        for (int k = 0; k < 16; ++k) term(28 * ck + k, v16[k]);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) term(28 * ck + 16 + k, v8[k]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) term(28 * ck + 24 + k, v4[k]);
+        sm.part[ck][nl] = s;
+    };
+    auto write_spec = [&](int pb, int pt) {
+        if (threadIdx.x < FT2) {
+            const int n = pt * FT2 + threadIdx.x;
+            if (n < N)
+                w.spec[(size_t)pb * N + n] = (sm.part[0][threadIdx.x] + sm.part[1][threadIdx.x]) +
+                                             (sm.part[2][threadIdx.x] + sm.part[3][threadIdx.x]);
+        }
+    };
+
+    for (long long item = blockIdx.x; item < total && !abort; item += gridDim.x) {
         // chunk-major order: blocks running together share a wavenumber window,
-        // so its slice of the opacity tables stays resident in L2
+        // so its slice of the opacity coefficients stays resident in L2
         const int c = (int)(item / w.B), b = (int)(item % w.B);
         if (w.kind[b] != ES_KIND_TRANSMISSION) continue;
         if (b != cur_b) {
+            if (pend_b >= 0) {   // the previous sample's last tile, before its constants are replaced
+                epilogue(pend_b, pend_t, pend_buf);
+                __syncthreads();
+                write_spec(pend_b, pend_t);
+                pend_b = -1;
+            }
+            tc_fence_before();
             __syncthreads();
             stage_sample(m, w, b, sm.sc);
-            stage_lmat(m, w, b, sm.lh, sm.ll, sm.area);
+            stage_lmat_tc(m, w, b, sm.lh, sm.ll, sm.area);
             cur_b = b;
+            fence_async_smem();
             __syncthreads();
         }
         const int t1 = min(ntiles, (c + 1) * chunk_tiles);
         for (int t = c * chunk_tiles; t < t1; ++t) {
-            const int nt0 = t * FT;
+            const int nt0 = t * FT2;
             extinction_pair<SPL>(m, sm.sc, lb, le, nt0 + 2 * pair, half, [&](int l, float2 a) {
                 uint32_t hi, lo;
                 split2(a, hi, lo);
-                a_dst[l * (R_PITCH / 2)] = half ? lo : hi;
+                *reinterpret_cast<uint32_t *>(a_dst + (l >> 3) * SBO_NU + (l & 7) * 16) = half ? lo : hi;
             });
+            fence_async_smem();
             __syncthreads();
-            // tau[i][nu] for this warp's 8 wavenumbers, lower-triangular blocks only
-            float acc[7][4];
-#pragma unroll
-            for (int mi = 0; mi < 7; ++mi) acc[mi][0] = acc[mi][1] = acc[mi][2] = acc[mi][3] = 0.f;
-#pragma unroll
-            for (int ks = 0; ks < 7; ++ks) {
-                if (ks < ksmax) {
-                    uint32_t bh[2], bl[2];
-                    ldsm_x2_t(bt_addr(bah, R_PITCH, 8 * warp, 16 * ks, lane), bh);
-                    ldsm_x2_t(bt_addr(bal, R_PITCH, 8 * warp, 16 * ks, lane), bl);
-#pragma unroll
-                    for (int mi = ks; mi < 7; ++mi) {
-                        uint32_t ah[4], al[4];
-                        ldsm_x4(a_addr(blh, L_PITCH, 16 * mi, 16 * ks, lane), ah);
-                        ldsm_x4(a_addr(bll, L_PITCH, 16 * mi, 16 * ks, lane), al);
-                        mma3(acc[mi], ah, al, bh, bl);
-                    }
+            const int buf = issued & 1;
+            if (threadIdx.x == 0) {   // 7 k-steps x (hi hi + hi lo + lo hi)
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(buf * 128);
+#pragma unroll 1
+                for (int k = 0; k < LP / 16; ++k) {
+                    const uint64_t a_h = desc_mn_major(ah_s + k * 2 * SBO_NU, SBO_NU);
+                    const uint64_t a_l = desc_mn_major(al_s + k * 2 * SBO_NU, SBO_NU);
+                    const uint64_t b_h = desc_k_major(lh_s + k * 2 * CORE_STRIDE, SBO_LP);
+                    const uint64_t b_l = desc_k_major(ll_s + k * 2 * CORE_STRIDE, SBO_LP);
+                    tc_mma(d, a_h, b_h, idesc, k > 0);
+                    tc_mma(d, a_h, b_l, idesc, true);
+                    tc_mma(d, a_l, b_h, idesc, true);
                 }
+                tc_commit(mbar);
             }
-            // epilogue: sum_i A_i (1 - exp(-tau_i)); lane holds rows r, r+8 and columns c, c+1
-            const int col = 8 * warp + 2 * (lane & 3), r = lane >> 2;
-            const int n0 = nt0 + col;
-            float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-            for (int mi = 0; mi < 7; ++mi) {
-                const int i0 = 16 * mi + r, i1 = i0 + 8;
-                const float e00 = ex2f(-acc[mi][0] * LOG2E_F), e01 = ex2f(-acc[mi][1] * LOG2E_F);
-                const float e10 = ex2f(-acc[mi][2] * LOG2E_F), e11 = ex2f(-acc[mi][3] * LOG2E_F);
-                const float a0 = sm.area[i0], a1 = sm.area[i1];
-                s0 += a0 * (1.f - e00) + a1 * (1.f - e10);
-                s1 += a0 * (1.f - e01) + a1 * (1.f - e11);
-                if (STORE_E) {   // padding wavenumbers too: the adjoint multiplies them by dbar = 0
-                    float *eb = w.estore + (size_t)b * L * m.Np + n0;
-                    // streaming stores: keep the opacity coefficients, not these, in L2
-                    if (i0 < L) __stcs(reinterpret_cast<float2 *>(eb + (size_t)i0 * m.Np), make_float2(e00, e01));
-                    if (i1 < L) __stcs(reinterpret_cast<float2 *>(eb + (size_t)i1 * m.Np), make_float2(e10, e11));
-                }
-            }
-#pragma unroll
-            for (int o = 4; o < 32; o <<= 1) {
-                s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-            }
-            if (r == 0) {
-                float *sp = w.spec + (size_t)b * N;
-                if (n0 < N) sp[n0] = s0;
-                if (n0 + 1 < N) sp[n0 + 1] = s1;
-            }
+            if (pend_b >= 0) epilogue(pend_b, pend_t, pend_buf);   // overlaps the product just issued
+            tc_fence_before();
+            if (!mbar_wait(mbar, phase)) sm.abort = 1;
+            phase ^= 1;
+            tc_fence_after();
             __syncthreads();
+            if (sm.abort) {
+                abort = true;
+                break;
+            }
+            if (pend_b >= 0) write_spec(pend_b, pend_t);
+            pend_b = b;
+            pend_t = t;
+            pend_buf = buf;
+            ++issued;
         }
     }
+    if (pend_b >= 0 && !abort) {
+        epilogue(pend_b, pend_t, pend_buf);
+        __syncthreads();
+        write_spec(pend_b, pend_t);
+    }
+    if (abort && threadIdx.x == 0) atomicOr(w.err, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_free(tmem, F2_TMEM_COLS);
 }
 
 // Warp transpose-reduction of 16 values: on return lane holds the warp-wide
@@ -208,29 +279,6 @@ __device__ __forceinline__ float transpose_reduce16(float (&v)[16], int lane) {
     float e = (up ? d[1] : d[0]) + __shfl_xor_sync(0xffffffffu, up ? d[0] : d[1], 2);
     e += __shfl_xor_sync(0xffffffffu, e, 1);
     return e;
-}
-
-// Lower-triangular block pair p (0..55) of L_bar: i-block mi (0..6), l-block nj <= 2 mi + 1.
-__device__ __forceinline__ void decode_pair(int p, int &mi, int &nj) {
-    mi = 0;
-    while (p >= 2 * mi + 2) {
-        p -= 2 * mi + 2;
-        ++mi;
-    }
-    nj = p;
-}
-
-// Block pair p (0..63) of the L_bar product: the 56 lower-triangular pairs,
-// then (mi, L/8) for the i-blocks whose lower triangle stops short of column
-// L (the Rayleigh weight row). False for unused slots.
-__device__ __forceinline__ bool lbar_pair(int p, int L, int &mi, int &nj) {
-    if (p < 56) {
-        decode_pair(p, mi, nj);
-        return true;
-    }
-    mi = p - 56;
-    nj = L >> 3;
-    return mi < 7 && nj > 2 * mi + 1;
 }
 
 __device__ __forceinline__ int reduce_index(int lane) {
@@ -282,20 +330,30 @@ __device__ __forceinline__ float reduce4_parity(const float (&v)[4], int lane) {
     return e;
 }
 
+// One TMEM column of this warp's lane quadrant: thread i <- lane i. The
+// value is bound to the wait so that no use is scheduled before it.
+__device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
+    uint32_t r;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r)::"memory");
+    return __uint_as_float(r);
+}
+
 // Backward interpolation for one warp: layers [lb, le), wavenumber pair n, n+1
-// shared by the lane pair (lane, lane ^ 1) that splits the species; `quarter`
-// points at the warp's 32-wavenumber quarter of row 0 of the row buffer.
-// Reads alpha_bar, adds per-layer reductions to red[l][*] and per-species
-// totals to qtot[s], then overwrites the quarter-rows with the extinction as
-// split BF16. Per layer, summed over wavenumber, with lane half h's species
-// and CIA pair h: QS_h = sum abar n sum_s e_s, D_h = sum abar n sum_s e_s
-// dlog2(sigma_s)/dlog10 T, C_h = sum abar c_h, CT_h = sum abar c_h dlog2 k_h/dT
-// (red slots 0/1, 2/3, 4/5, 6/7 for h = 0/1); per species Q_s = sum_l sum
-// abar n e_s. The Rayleigh sum over wavenumber comes from the L_bar product.
+// shared by the lane pair (lane, lane ^ 1) that splits the species. Reads
+// alpha_bar from TMEM (`abar_t`: column 0 of the warp's lane quadrant, lane =
+// wavenumber), adds per-layer reductions to red[l][*] and per-species totals
+// to qtot[s], and writes the extinction as split BF16 into the alpha operand
+// (`a_dst`: row 0 at this lane's column, hi for half 0, lo for half 1).
+// Per layer, summed over wavenumber, with lane half h's species and CIA pair
+// h: QS_h = sum abar n sum_s e_s, D_h = sum abar n sum_s e_s dlog2(sigma_s)/
+// dlog10 T, C_h = sum abar c_h, CT_h = sum abar c_h dlog2 k_h/dT (red slots
+// 0/1, 2/3, 4/5, 6/7 for h = 0/1); per species Q_s = sum_l sum abar n e_s.
+// The Rayleigh sum over wavenumber comes from the L_bar product.
 template <int SPL>
 __device__ void interp_backward(const Model &m, const SampleConst &sc, int lb, int le, int n, int half, int lane,
-                                unsigned char *quarter, float *red, float *qtot) {
-    const int S = m.S, q = lane >> 1;
+                                uint32_t abar_t, unsigned char *a_dst, float *red, float *qtot) {
+    const int S = m.S;
     const int ridx = reduce_index8(lane);
     const bool writer = (lane & 3) == 0;
     // after reduce4_parity: lanes with bits 2, 1 clear write slot 2 (2 b4 + b3) + b0
@@ -306,15 +364,15 @@ __device__ void interp_backward(const Model &m, const SampleConst &sc, int lb, i
     float2 qa[SPL];
 #pragma unroll
     for (int j = 0; j < SPL; ++j) qa[j] = f2(0.f);
-    const int st_off = (half ? 64 : 0) + 4 * q;
     for (int l = lb; l < le;) {
         const int end = min(sc.lay[l].run_end, le);
         pi.load(sc, sc.lay[l].cell, sc.lay[l].itc);
         if (end < le) pi.prefetch(sc.lay[end].cell, sc.lay[end].itc);
         for (; l < end; ++l) {
             const LayerConst &lc = sc.lay[l];
-            unsigned char *row = quarter + (size_t)l * RB2_BYTES;
-            const float2 ab = *reinterpret_cast<const float2 *>(row + 8 * q);
+            const float own = tmem_ld1(abar_t + (uint32_t)l);
+            const float other = __shfl_xor_sync(0xffffffffu, own, 1);
+            const float2 ab = half ? make_float2(other, own) : make_float2(own, other);
             const float2 abn = mul2(ab, lc.nsc);
             float2 t, p = ex2x2(pi.expo(0, lc.wp, lc.wt, t));
             float2 sum = p, pt = mul2(p, t);
@@ -340,8 +398,7 @@ __device__ void interp_backward(const Model &m, const SampleConst &sc, int lb, i
             const float2 alpha = add2(mine, shfl_xor2(mine, 1));
             uint32_t hi, lo;
             split2(alpha, hi, lo);
-            __syncwarp();
-            *reinterpret_cast<uint32_t *>(row + st_off) = half ? lo : hi;
+            *reinterpret_cast<uint32_t *>(a_dst + (l >> 3) * SBO_NU + (l & 7) * 16) = half ? lo : hi;
         }
     }
     // per-species totals: slot j of lane half h is species SPL h + j
@@ -358,14 +415,6 @@ __device__ void interp_backward(const Model &m, const SampleConst &sc, int lb, i
     }
 }
 
-// B fragment (k16 x n8) of alpha^T for L_bar = tau_bar alpha^T: rows l of the
-// row buffer, wavenumbers [16 ks, 16 ks + 16) of the tile; lo = false/true.
-__device__ __forceinline__ uint32_t rb_addr(uint32_t base, int n0, int ks, bool lo, int lane) {
-    const int l = lane & 15;
-    const int qt = ks >> 1, kin = (ks & 1) * 16 + ((l >> 3) << 3);
-    return base + (uint32_t)((n0 + (l & 7)) * RB2_BYTES + 128 * qt + (lo ? 64 : 0) + 2 * kin);
-}
-
 template <int SPL>
 __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, int chunk_tiles) {
     extern __shared__ float4 smem4[];
@@ -380,37 +429,72 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
     const int half = lane & 1, vq = warp & 3, pair = 16 * vq + (lane >> 1);
     int lb, le;
     group_layers(L, warp >> 2, 4, lb, le);
-    // padding rows (impact parameters / layers >= L) of tau_bar and the row buffer stay zero
-    for (int idx = threadIdx.x; idx < (LP - L) * T2_PITCH; idx += BW_THREADS) {
-        sm.th[L * T2_PITCH + idx] = __float2bfloat16_rn(0.f);
-        sm.tl[L * T2_PITCH + idx] = __float2bfloat16_rn(0.f);
+    const int NL = (L + 1 + 15) & ~15;                  // L_bar product N: layers and the weight row
+    // padding rows stay zero: tau_bar rows [L, 112), alpha rows [L + 1, 128)
+    for (int idx = threadIdx.x; idx < (LP - L) * (BT / 2); idx += BW_THREADS) {
+        const uint32_t o = op_off(L + idx / (BT / 2), 2 * (idx % (BT / 2)), SBO_NU);
+        *reinterpret_cast<uint32_t *>(sm.th + o) = 0u;
+        *reinterpret_cast<uint32_t *>(sm.tl + o) = 0u;
     }
-    for (int idx = threadIdx.x; idx < (LPR - L) * RB2_BYTES; idx += BW_THREADS) sm.rb[L * RB2_BYTES + idx] = 0;
+    for (int idx = threadIdx.x; idx < (LB_ROWS - L - 1) * (BT / 2); idx += BW_THREADS) {
+        const uint32_t o = op_off(L + 1 + idx / (BT / 2), 2 * (idx % (BT / 2)), SBO_NU);
+        *reinterpret_cast<uint32_t *>(sm.ah + o) = 0u;
+        *reinterpret_cast<uint32_t *>(sm.al + o) = 0u;
+    }
     const float ray_ref = (float)(1.0 / ((double)m.ray_nu_ref * m.ray_nu_ref * m.ray_nu_ref * m.ray_nu_ref));
-    const uint32_t blh = smem_u32(sm.lh), bll = smem_u32(sm.ll), bth = smem_u32(sm.th), btl = smem_u32(sm.tl);
-    const uint32_t brb = smem_u32(sm.rb);
-    const int ksmax = (L + 15) / 16;
-    float lacc[4][4];
+    const uint32_t mbar_a = smem_u32(&sm.mbar_a), mbar_l = smem_u32(&sm.mbar_l);
+    if (threadIdx.x == 0) {
+        mbar_init(mbar_a, 1);
+        mbar_init(mbar_l, 1);
+        sm.abort = 0;
+    }
+    if (warp == 0) tmem_alloc(smem_u32(&sm.tmem_base), 256);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm.tmem_base;
+    // alpha_bar^T[nu][l] = sum_i tau_bar^T[nu][i] L[i][l]: M = 128 wavenumbers, N = 112, K = 112;
+    // A = tau_bar (stored [i][nu]: MN-major), B = L (stored [i][l]: MN-major)
+    const uint32_t idesc_a = idesc_bf16(BT, LP, true, true);
+    // L_bar[i][l] += sum_nu tau_bar[i][nu] alpha[l][nu]: M = 128, N = NL, K = 128; both K-major
+    const uint32_t idesc_l = idesc_bf16(LB_ROWS, NL, false, false);
+    const uint32_t lh_s = smem_u32(sm.lh), ll_s = smem_u32(sm.ll), th_s = smem_u32(sm.th), tl_s = smem_u32(sm.tl);
+    const uint32_t ah_s = smem_u32(sm.ah), al_s = smem_u32(sm.al);
+    const uint32_t abar_t = tmem + ((uint32_t)(32 * vq) << 16);
+    unsigned char *const a_dst = (half ? sm.al : sm.ah) + op_off(0, 2 * pair, SBO_NU);
+    uint32_t pa = 0, pl = 0;
+    bool l_pending = false, l_started = false, abort = false;
     int cur_b = -1;
+
+    auto wait_lbar = [&]() {
+        if (l_pending) {
+            if (!mbar_wait(mbar_l, pl)) sm.abort = 1;
+            pl ^= 1;
+            l_pending = false;
+            tc_fence_after();
+        }
+    };
     auto flush = [&](int b) {
-        // L_bar, reductions, per-species totals and area_bar of sample b (FP64 atomics)
+        // L_bar (TMEM: lane i, column 128 + l) and z, the reductions, per-species
+        // totals and area_bar of sample b, by FP64 atomics
         double *lbar = w.lbar + (size_t)b * L * L, *zbar = w.zbar + (size_t)b * L;
-        const int r = lane >> 2, col = 2 * (lane & 3);
+        const int ck = warp >> 2, ii = 32 * vq + lane;
+        float v0[16], v1[16];
+        const uint32_t ta = tmem + (uint32_t)(128 + 32 * ck) + ((uint32_t)(32 * vq) << 16);
+        tmem_ld16(ta, v0);
+        tmem_ld16(ta + 16, v1);
+        tmem_wait_ld();
+        if (ii < L) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            int mi, nj;
-            if (lbar_pair(warp + BW_WARPS * k, L, mi, nj)) {
-                const int i0 = 16 * mi + r, l0 = 8 * nj + col;
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int ii = i0 + ((e >> 1) << 3), ll = l0 + (e & 1);
-                    const float v = lacc[k][e];
-                    if (ii >= L || v == 0.f) continue;
-                    if (ll == L) atomicAdd(zbar + ii, (double)v);
-                    else if (ll <= ii) atomicAdd(lbar + (size_t)ii * L + ll, (double)v);
-                }
+            for (int j = 0; j < 32; ++j) {
+                const int ll = 32 * ck + j;
+                const float v = j < 16 ? v0[j] : v1[j - 16];
+                if (v == 0.f) continue;
+                if (ll == L) atomicAdd(zbar + ii, (double)v);
+                else if (ll <= ii) atomicAdd(lbar + (size_t)ii * L + ll, (double)v);
             }
         }
+        tc_fence_before();
         __syncthreads();
         for (int idx = threadIdx.x; idx < L * N_RED; idx += BW_THREADS) {
             const float v = sm.red[idx];
@@ -441,21 +525,25 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
         const long long it0 = blockIdx.x;
         prefetch_tile((int)(it0 % w.B), (int)(it0 / w.B) * chunk_tiles);
     }
-    for (long long item = blockIdx.x; item < total; item += gridDim.x) {
+    for (long long item = blockIdx.x; item < total && !abort; item += gridDim.x) {
         // chunk-major order: blocks running together share a wavenumber window
         const int c = (int)(item / w.B), b = (int)(item % w.B);
         if (w.kind[b] != ES_KIND_TRANSMISSION || w.flags[b]) continue;
         if (b != cur_b) {
-            if (cur_b >= 0) flush(cur_b);
+            if (cur_b >= 0) {
+                wait_lbar();
+                flush(cur_b);
+            }
+            tc_fence_before();
             __syncthreads();
             stage_sample(m, w, b, sm.sc);
-            stage_lmat(m, w, b, sm.lh, sm.ll, sm.area);
+            stage_lmat_tc(m, w, b, sm.lh, sm.ll, sm.area);
             for (int idx = threadIdx.x; idx < L * N_RED; idx += BW_THREADS) sm.red[idx] = 0.f;
             for (int i = threadIdx.x; i < LP; i += BW_THREADS) sm.area_acc[i] = 0.f;
             for (int s2 = threadIdx.x; s2 < ES_MAX_SPECIES; s2 += BW_THREADS) sm.qtot[s2] = 0.f;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) lacc[k][0] = lacc[k][1] = lacc[k][2] = lacc[k][3] = 0.f;
             cur_b = b;
+            l_started = false;
+            fence_async_smem();
             __syncthreads();
         }
         const int t1 = min(ntiles, (c + 1) * chunk_tiles);
@@ -467,20 +555,22 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
                 const long long nx = item + gridDim.x;
                 prefetch_tile((int)(nx % w.B), (int)(nx / w.B) * chunk_tiles);
             }
-            // Rayleigh weight row w(nu) for the L_bar product
+            wait_lbar();   // the previous tile's L_bar product still reads tau_bar and alpha
+            // Rayleigh weight row w(nu) of the alpha operand
             if (threadIdx.x < BT / 2) {
                 const int t2 = threadIdx.x;
                 const float2 nu = __ldg(reinterpret_cast<const float2 *>(m.nu + nt0 + 2 * t2));
                 const float2 nu2 = mul2(nu, nu);
                 uint32_t hi, lo;
                 split2(mul2(mul2(nu2, nu2), f2(ray_ref)), hi, lo);
-                unsigned char *rw = sm.rb + (size_t)L * RB2_BYTES + 128 * (t2 >> 4) + 4 * (t2 & 15);
-                *reinterpret_cast<uint32_t *>(rw) = hi;
-                *reinterpret_cast<uint32_t *>(rw + 64) = lo;
+                const uint32_t o = op_off(L, 2 * t2, SBO_NU);
+                *reinterpret_cast<uint32_t *>(sm.ah + o) = hi;
+                *reinterpret_cast<uint32_t *>(sm.al + o) = lo;
             }
             // tau_bar = dbar A_i exp(-tau); area_bar += dbar (1 - exp(-tau))
             {
-                const int nl = nt0 + 2 * (lane + 32 * (warp & 1));
+                const int col = 2 * (lane + 32 * (warp & 1));
+                const int nl = nt0 + col;
                 const float2 db = *reinterpret_cast<const float2 *>(w.dbar + (size_t)b * m.Np + nl);
                 const float *eb = w.estore + (size_t)b * L * m.Np + nl;
                 float av[16];
@@ -493,9 +583,9 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
                         const float a = sm.area[i];
                         uint32_t hi, lo;
                         split2(make_float2(db.x * a * e.x, db.y * a * e.y), hi, lo);
-                        const int col = 2 * (lane + 32 * (warp & 1));
-                        *reinterpret_cast<uint32_t *>(sm.th + i * T2_PITCH + col) = hi;
-                        *reinterpret_cast<uint32_t *>(sm.tl + i * T2_PITCH + col) = lo;
+                        const uint32_t o = op_off(i, col, SBO_NU);
+                        *reinterpret_cast<uint32_t *>(sm.th + o) = hi;
+                        *reinterpret_cast<uint32_t *>(sm.tl + o) = lo;
                         av[k] = db.x * (1.f - e.x) + db.y * (1.f - e.y);
                     }
                 }
@@ -503,63 +593,64 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
                 const int k = reduce_index(lane), i = group + 8 * k;
                 if ((lane & 1) == 0 && k < 14 && i < L && tot != 0.f) atomicAdd(sm.area_acc + i, tot);
             }
+            fence_async_smem();
             __syncthreads();
-            // alpha_bar[l][nu] = sum_{i >= l} L_il tau_bar_i(nu), this warp's 8 wavenumbers
-            {
-                float acc[7][4];
-#pragma unroll
-                for (int ml = 0; ml < 7; ++ml) acc[ml][0] = acc[ml][1] = acc[ml][2] = acc[ml][3] = 0.f;
-#pragma unroll
-                for (int ks = 0; ks < 7; ++ks) {
-                    if (ks < ksmax) {
-                        uint32_t bh[2], bl[2];
-                        ldsm_x2_t(bt_addr(bth, T2_PITCH, 8 * warp, 16 * ks, lane), bh);
-                        ldsm_x2_t(bt_addr(btl, T2_PITCH, 8 * warp, 16 * ks, lane), bl);
-#pragma unroll
-                        for (int ml = 0; ml <= ks; ++ml) {
-                            uint32_t ah[4], al[4];
-                            ldsm_x4_t(at_addr(blh, L_PITCH, 16 * ml, 16 * ks, lane), ah);
-                            ldsm_x4_t(at_addr(bll, L_PITCH, 16 * ml, 16 * ks, lane), al);
-                            mma3(acc[ml], ah, al, bh, bl);
-                        }
-                    }
-                }
-                const int colt = 8 * warp + 2 * (lane & 3), r = lane >> 2;
-                const int qt = colt >> 5, cin = colt & 31;
-#pragma unroll
-                for (int ml = 0; ml < 7; ++ml) {
-                    const int l0 = 16 * ml + r, l1 = l0 + 8;
-                    if (l0 < L)
-                        *reinterpret_cast<float2 *>(sm.rb + (size_t)l0 * RB2_BYTES + 128 * qt + 4 * cin) =
-                            make_float2(acc[ml][0], acc[ml][1]);
-                    if (l1 < L)
-                        *reinterpret_cast<float2 *>(sm.rb + (size_t)l1 * RB2_BYTES + 128 * qt + 4 * cin) =
-                            make_float2(acc[ml][2], acc[ml][3]);
-                }
+            if (sm.abort) {
+                abort = true;
+                break;
             }
-            __syncthreads();
-            interp_backward<SPL>(m, sm.sc, lb, le, nt0 + 2 * pair, half, lane, sm.rb + 128 * vq, sm.red, sm.qtot);
-            __syncthreads();
-            // L_bar[i][l] += sum_nu tau_bar[i][nu] alpha[l][nu] over this tile (8 k-steps)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                int mi, nj;
-                if (lbar_pair(warp + BW_WARPS * k, L, mi, nj)) {
-#pragma unroll
-                    for (int ks = 0; ks < BT / 16; ++ks) {
-                        uint32_t ah[4], al[4], bh[2], bl[2];
-                        ldsm_x4(a_addr(bth, T2_PITCH, 16 * mi, 16 * ks, lane), ah);
-                        ldsm_x4(a_addr(btl, T2_PITCH, 16 * mi, 16 * ks, lane), al);
-                        ldsm_x2(rb_addr(brb, 8 * nj, ks, false, lane), bh);
-                        ldsm_x2(rb_addr(brb, 8 * nj, ks, true, lane), bl);
-                        mma3(lacc[k], ah, al, bh, bl);
-                    }
+            if (threadIdx.x == 0) {   // alpha_bar: 7 k-steps over impact parameters x 3 split terms
+                tc_fence_after();
+#pragma unroll 1
+                for (int k = 0; k < LP / 16; ++k) {
+                    const uint64_t a_h = desc_mn_major(th_s + k * 2 * SBO_NU, SBO_NU);
+                    const uint64_t a_l = desc_mn_major(tl_s + k * 2 * SBO_NU, SBO_NU);
+                    const uint64_t b_h = desc_mn_major(lh_s + k * 2 * SBO_LP, SBO_LP);
+                    const uint64_t b_l = desc_mn_major(ll_s + k * 2 * SBO_LP, SBO_LP);
+                    tc_mma(tmem, a_h, b_h, idesc_a, k > 0);
+                    tc_mma(tmem, a_h, b_l, idesc_a, true);
+                    tc_mma(tmem, a_l, b_h, idesc_a, true);
                 }
+                tc_commit(mbar_a);
             }
+            if (!mbar_wait(mbar_a, pa)) sm.abort = 1;
+            pa ^= 1;
+            tc_fence_after();
+            interp_backward<SPL>(m, sm.sc, lb, le, nt0 + 2 * pair, half, lane, abar_t, a_dst, sm.red, sm.qtot);
+            tc_fence_before();
+            fence_async_smem();
             __syncthreads();
+            if (sm.abort) {
+                abort = true;
+                break;
+            }
+            if (threadIdx.x == 0) {   // L_bar: 8 k-steps over the tile's wavenumbers x 3 split terms
+                tc_fence_after();
+                const uint32_t d = tmem + 128u;
+#pragma unroll 1
+                for (int k = 0; k < BT / 16; ++k) {
+                    const uint64_t a_h = desc_k_major(th_s + k * 2 * CORE_STRIDE, SBO_NU);
+                    const uint64_t a_l = desc_k_major(tl_s + k * 2 * CORE_STRIDE, SBO_NU);
+                    const uint64_t b_h = desc_k_major(ah_s + k * 2 * CORE_STRIDE, SBO_NU);
+                    const uint64_t b_l = desc_k_major(al_s + k * 2 * CORE_STRIDE, SBO_NU);
+                    tc_mma(d, a_h, b_h, idesc_l, l_started || k > 0);
+                    tc_mma(d, a_h, b_l, idesc_l, true);
+                    tc_mma(d, a_l, b_h, idesc_l, true);
+                }
+                tc_commit(mbar_l);
+            }
+            l_pending = true;
+            l_started = true;
         }
     }
-    if (cur_b >= 0) flush(cur_b);
+    if (cur_b >= 0 && !abort) {
+        wait_lbar();
+        flush(cur_b);
+    }
+    if ((abort || sm.abort) && threadIdx.x == 0) atomicOr(w.err, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_free(tmem, 256);
 }
 
 size_t fwd_smem() { return sizeof(TransFwdSmem); }
@@ -574,25 +665,25 @@ int sm_count() {
 
 }  // namespace
 
-// Tiles per work item: up to 16 (amortises staging the sample), fewer when the
-// batch is small so that every resident block gets items.
-int chunk_tiles(const Model &m, int B, int blocks) {
-    const int ntiles = (m.N + FT - 1) / FT;
+// Tiles of `tile` wavenumbers per work item: up to 16 (amortises staging the
+// sample), fewer when the batch is small so that every resident block gets items.
+int chunk_tiles(const Model &m, int B, int blocks, int tile) {
+    const int ntiles = (m.N + tile - 1) / tile;
     long long c = ((long long)ntiles * B) / (4LL * blocks);
     return (int)std::max<long long>(1, std::min<long long>(16, c));
 }
 
 int launch_trans_fused_forward(const Model &m, const Work &w, bool store_e, int chunk_req, cudaStream_t st,
                                const Hook &h) {
-    const int ntiles = (m.N + FT - 1) / FT;
-    const int chunk = chunk_req > 0 ? chunk_req : chunk_tiles(m, w.B, 2 * sm_count());
+    const int ntiles = (m.N + FT2 - 1) / FT2;
+    const int chunk = chunk_req > 0 ? chunk_req : chunk_tiles(m, w.B, sm_count(), FT2);
     const long long items = (long long)w.B * ((ntiles + chunk - 1) / chunk);
-    const int grid = (int)std::min<long long>(items, 2LL * sm_count());
+    const int grid = (int)std::min<long long>(items, (long long)sm_count());
     const size_t sm = fwd_smem();
 #define ES_FWD(SPL, SE)                                                                         \
     do {                                                                                        \
         cudaFuncSetAttribute(k_trans_fwd<SPL, SE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-        ES_LAUNCH(h, "k_trans_fwd", st, k_trans_fwd<SPL, SE><<<grid, FTHREADS, sm, st>>>(m, w, chunk)); \
+        ES_LAUNCH(h, "k_trans_fwd", st, k_trans_fwd<SPL, SE><<<grid, F2_THREADS, sm, st>>>(m, w, chunk)); \
     } while (0)
     const int spl = spl_for(m.S);
     if (spl == 2) { if (store_e) ES_FWD(2, true); else ES_FWD(2, false); }
@@ -604,7 +695,7 @@ int launch_trans_fused_forward(const Model &m, const Work &w, bool store_e, int 
 
 int launch_trans_fused_backward(const Model &m, const Work &w, int chunk_req, cudaStream_t st, const Hook &h) {
     const int ntiles = (m.N + BT - 1) / BT;
-    const int chunk = chunk_req > 0 ? chunk_req : std::max(1, chunk_tiles(m, w.B, sm_count()) / 2);
+    const int chunk = chunk_req > 0 ? chunk_req : chunk_tiles(m, w.B, sm_count(), BT);
     const long long items = (long long)w.B * ((ntiles + chunk - 1) / chunk);
     const int grid = (int)std::min<long long>(items, (long long)sm_count());
     const size_t sm = bwd_smem();

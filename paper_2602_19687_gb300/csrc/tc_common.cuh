@@ -1,0 +1,134 @@
+// Fifth-generation tensor cores (tcgen05) for the chord contractions:
+// TMEM allocation, shared-memory matrix descriptors, the kind::f16 MMA with
+// FP32 accumulation in TMEM, commit to an mbarrier, TMEM loads, fences, and
+// bounded mbarrier waits.
+//
+// Operand layout in shared memory (no swizzle): a matrix X[r][c] of BF16 is
+// stored as 8 x 8 core matrices of 8 rows x 16 bytes (128 contiguous bytes);
+// core matrices adjacent in c are CORE_STRIDE bytes apart, groups of 8 rows
+// `sbo` bytes apart. Without swizzling, a descriptor's leading byte offset is
+// the stride between core matrices along K and its stride byte offset the
+// stride along M/N, for both major-nesses. So the same bytes serve as a
+// K-major operand (K = c: leading = CORE_STRIDE, stride = sbo) or as an
+// MN-major operand (M or N = c: leading = sbo, stride = CORE_STRIDE), and one
+// layout feeds both uses of tau_bar, alpha and L. A
+// CORE_STRIDE of 144 bytes (16 mod 128) makes the 4-byte stores of a warp
+// that writes 32 consecutive columns of one row conflict-free.
+#pragma once
+
+#include <cstdint>
+
+#include "internal.cuh"
+
+namespace es {
+
+constexpr int CORE_STRIDE = 144;
+
+__device__ __forceinline__ uint32_t op_off(int r, int c, int sbo) {
+    return (uint32_t)((c >> 3) * CORE_STRIDE + (r >> 3) * sbo + (r & 7) * 16 + (c & 7) * 2);
+}
+
+// Shared-memory matrix descriptor (tcgen05 format, no swizzle):
+// start >> 4 in bits 0-13, leading byte offset >> 4 in 16-29, stride byte
+// offset >> 4 in 32-45, descriptor version 1 in 46-47, layout type 0.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+
+// operand X[r][c] with K along c / with M or N along c
+__device__ __forceinline__ uint64_t desc_k_major(uint32_t saddr, uint32_t sbo) {
+    return smem_desc(saddr, CORE_STRIDE, sbo);
+}
+__device__ __forceinline__ uint64_t desc_mn_major(uint32_t saddr, uint32_t sbo) {
+    return smem_desc(saddr, sbo, CORE_STRIDE);
+}
+
+// Instruction descriptor of kind::f16 with BF16 A and B and FP32 D:
+// D format bits 4-5 = 1 (F32), A format bits 7-9 = 1 (BF16), B format bits
+// 10-12 = 1 (BF16), A / B major-ness bits 15 / 16 (0 K-major, 1 MN-major),
+// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn, bool b_mn) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// D[tmem] (+)= A B, issued by one thread.
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, bool acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"((int)acc)
+        : "memory");
+}
+
+// Arrive on the mbarrier once all MMAs issued so far by this thread are complete.
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// generic-proxy shared-memory writes become visible to the tensor cores
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Whole warp: allocate `ncols` TMEM columns, base address written to *dst (shared).
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_free(uint32_t base, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(ncols) : "memory");
+}
+
+// Whole warp: 32 lanes x N consecutive 32-bit columns (thread i <- lane i of the warp's quadrant).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = __uint_as_float(r[k]);
+}
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = __uint_as_float(r[k]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ------------------------------------------------------------ mbarrier
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+// Wait for the phase with parity `parity` to complete; false after ~2^24
+// polls (seconds) without completion.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    for (uint32_t it = 0; it < (1u << 24); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+}  // namespace es

@@ -50,6 +50,7 @@ def gpu_eval(ctx, w, theta, kind, backward=True):
     ctx.es_get_flags(flags)
     out["flags"] = flags.cpu().numpy()
     torch.cuda.synchronize()
+    assert ctx.es_query(11) == 0, "a tensor-core kernel gave up on a bounded wait"
     return out
 
 
