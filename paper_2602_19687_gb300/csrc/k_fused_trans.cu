@@ -555,7 +555,20 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
                 const long long nx = item + gridDim.x;
                 prefetch_tile((int)(nx % w.B), (int)(nx / w.B) * chunk_tiles);
             }
-            wait_lbar();   // the previous tile's L_bar product still reads tau_bar and alpha
+            // tau_bar = dbar A_i exp(-tau); area_bar += dbar (1 - exp(-tau)). The
+            // loads are issued before waiting for the previous tile's L_bar
+            // product, which still reads tau_bar and alpha.
+            const int col = 2 * (lane + 32 * (warp & 1));
+            const int nl = nt0 + col;
+            const float2 db = *reinterpret_cast<const float2 *>(w.dbar + (size_t)b * m.Np + nl);
+            const float *eb = w.estore + (size_t)b * L * m.Np + nl;
+            float2 ev[14];
+#pragma unroll
+            for (int k = 0; k < 14; ++k) {
+                const int i = group + 8 * k;
+                ev[k] = (i < L) ? *reinterpret_cast<const float2 *>(eb + (size_t)i * m.Np) : make_float2(1.f, 1.f);
+            }
+            wait_lbar();
             // Rayleigh weight row w(nu) of the alpha operand
             if (threadIdx.x < BT / 2) {
                 const int t2 = threadIdx.x;
@@ -567,19 +580,14 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
                 *reinterpret_cast<uint32_t *>(sm.ah + o) = hi;
                 *reinterpret_cast<uint32_t *>(sm.al + o) = lo;
             }
-            // tau_bar = dbar A_i exp(-tau); area_bar += dbar (1 - exp(-tau))
             {
-                const int col = 2 * (lane + 32 * (warp & 1));
-                const int nl = nt0 + col;
-                const float2 db = *reinterpret_cast<const float2 *>(w.dbar + (size_t)b * m.Np + nl);
-                const float *eb = w.estore + (size_t)b * L * m.Np + nl;
                 float av[16];
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
                     av[k] = 0.f;
                     const int i = group + 8 * k;
                     if (k < 14 && i < L) {
-                        const float2 e = *reinterpret_cast<const float2 *>(eb + (size_t)i * m.Np);
+                        const float2 e = ev[k];
                         const float a = sm.area[i];
                         uint32_t hi, lo;
                         split2(make_float2(db.x * a * e.x, db.y * a * e.y), hi, lo);
