@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
     ap.add_argument("--batch", type=int, default=None, help="override the workload's batch size")
     ap.add_argument("--no-tune", action="store_true", help="keep the built-in work-item sizes")
+    ap.add_argument("--no-extra", action="store_true", help="skip the emission and high-resolution lines")
     ap.add_argument("--cpu-child", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -196,6 +197,38 @@ def alu_peak(kind, sm_mhz):
 
 
 # --------------------------------------------------------------------------- main arms
+# --------------------------------------------------------------------------- other workloads
+def measure_workload(name, device, steps=5, warmup=3):
+    """Forward+gradient throughput of another synthetic workload (graph
+    replay, device-resident inputs, CUDA events): spectra/s and ms/step."""
+    import torch
+    from paper_2602_19687_gb300 import binding, synth
+    w = synth.workload(name)
+    ctx = binding.context_for(w, device=device)
+    dev = torch.device("cuda", device)
+    B = w.theta.shape[0]
+    th = torch.tensor(w.theta, dtype=torch.float64, device=dev)
+    ctx.es_set_batch(th, torch.tensor(w.kind, dtype=torch.int32, device=dev))
+    lnl = torch.empty(B, dtype=torch.float64, device=dev)
+    grad = torch.empty_like(th)
+    ctx.es_autotune()
+    for _ in range(warmup):
+        ctx.es_forward_backward(lnl, grad)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream(dev)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.es_forward_backward(lnl, grad)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    n_em = int(np.sum(w.kind == 1))
+    ctx.es_destroy()
+    return {"workload": name + ": " + w.description, "vectors": B, "emission_vectors": n_em,
+            "value": B / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps, "warmup": warmup}
+
+
 # --------------------------------------------------------------------------- sharding
 def shard_seed(rank):
     """Each rank evaluates its own batch of parameter vectors (weak scaling:
@@ -362,6 +395,9 @@ def run_gpu(args):
                  "workload": "jwst_plain: " + wp.description + " (one vector per call, forward+gradient)"}
         cp.es_destroy()
 
+    extra = None
+    if rank == 0 and not args.no_extra:
+        extra = [measure_workload(n, local) for n in ("batched_emis", "highres")]
     cpu = cpu_baseline(args.workload) if (rank == 0 and not args.no_cpu) else None
     if rank == 0:
         line = {
@@ -384,6 +420,7 @@ def run_gpu(args):
             "plain": plain,
             "batched_over_plain": (value / world / plain["value"]) if plain else None,
             "cpu_baseline": cpu,
+            "other_workloads": extra,
             "clocks": clk,
             "peaks_source": peak_src,
             "probe": {"ex2_per_s": ex2_rate, "ffma2_per_s": ffma2_rate},

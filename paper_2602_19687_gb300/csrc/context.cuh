@@ -24,7 +24,7 @@ struct es_ctx {
     int64_t last_launches = 0;
     std::vector<double> y_host[2], s_host[2];
     std::vector<double> nu_host;      // FP64 wavenumber grid (bin membership)
-    size_t ymod_cap = 0, alpha_cap = 0, abar_cap = 0, estore_cap = 0;
+    size_t ymod_cap = 0, alpha_cap = 0, estore_cap = 0;   // alpha_cap: the emission I_toa store
     double *d_data = nullptr;         // [2][nbins] y_obs then sigma
     double *d_lnl = nullptr, *d_grad = nullptr;
     // per-kernel CUDA-event profiling

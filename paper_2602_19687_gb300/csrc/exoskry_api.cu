@@ -214,11 +214,9 @@ es_status alloc_forward(es_ctx *c, int B) {
     ALLOC(w.lmat, B * L * L);
     ALLOC(w.area, B * L);
     ALLOC(w.dr, B * L);
-    ALLOC(w.w4, B * L);
     ALLOC(w.it, B * L);
     ALLOC(w.gt, B * L);
     ALLOC(w.wtr, B * L);
-    ALLOC(w.coef, B * L * S);
     ALLOC(w.itc, B * L);
     ALLOC(w.wtc, B * L);
     ALLOC(w.gtc, B * L);
@@ -309,13 +307,15 @@ es_status prepare(es_ctx *c, bool adjoint) {
     es_status s;
     const size_t big = (size_t)c->batch * c->m.L * c->m.N;
     if ((s = ensure_ymod(c)) != ES_OK) return s;
-    if (c->n_kind[1] && (s = ensure_big(c, &c->w.alpha, c->alpha_cap, big)) != ES_OK) return s;
+
     if (adjoint) {
         if ((s = alloc_backward(c)) != ES_OK) return s;
         if (c->n_kind[0] &&
             (s = ensure_big(c, &c->w.estore, c->estore_cap, (size_t)c->batch * c->m.L * c->m.Np)) != ES_OK)
             return s;
-        if (c->n_kind[1] && (s = ensure_big(c, &c->w.abar, c->abar_cap, big)) != ES_OK) return s;
+        if (c->n_kind[1] &&
+            (s = ensure_big(c, &c->w.itop, c->alpha_cap, (size_t)c->batch * c->m.Np * N_MU)) != ES_OK)
+            return s;
     }
     return ES_OK;
 }
@@ -329,8 +329,7 @@ es_status run_forward(es_ctx *c, bool adjoint, float *spec_out, double *binned_o
     launches += launch_setup(c->m, w, st, h);
     if (c->n_kind[0]) launches += launch_trans_fused_forward(c->m, w, adjoint, c->fwd_chunk, st, h);
     if (c->n_kind[1]) {
-        launches += launch_extinction(c->m, w, ES_KIND_EMISSION, st, h);
-        launches += launch_emission(c->m, w, st, h);
+        launches += launch_emis_fused_forward(c->m, w, adjoint, st, h);
     }
     if (adjoint) {
         cudaMemsetAsync(w.dbar, 0, sizeof(float) * (size_t)w.B * c->m.Np, st);
@@ -759,8 +758,7 @@ es_status enqueue_forward_backward(es_ctx *c, cudaStream_t st) {
     const Hook &h = c->hook;
     if (c->n_kind[0]) launches += launch_trans_fused_backward(m, w, c->bwd_chunk, st, h);
     if (c->n_kind[1]) {
-        launches += launch_emission_backward(m, w, st, h);
-        launches += launch_extinction_backward(m, w, ES_KIND_EMISSION, st, h);
+        launches += launch_emis_fused_backward(m, w, st, h);
     }
     launches += launch_setup_backward(m, w, st, h);
     c->last_launches = launches;
@@ -862,7 +860,7 @@ int64_t es_query(const es_ctx *c, int key) {
         case 4: return c->m.L;
         case 5: return c->m.S;
         case 6:
-            return (int64_t)(c->ws_bytes + sizeof(float) * (c->alpha_cap + c->abar_cap + c->estore_cap) +
+            return (int64_t)(c->ws_bytes + sizeof(float) * (c->alpha_cap + c->estore_cap) +
                              sizeof(double) * c->ymod_cap);
         case 7: return c->last_launches;
         case 8: return c->fwd_chunk;
@@ -928,8 +926,7 @@ void es_destroy(es_ctx *c) {
         cudaEventDestroy(c->ev_join);
     }
     if (c->w.ymod) cudaFree(c->w.ymod);
-    if (c->w.alpha) cudaFree(c->w.alpha);
-    if (c->w.abar) cudaFree(c->w.abar);
+    if (c->w.itop) cudaFree(c->w.itop);
     if (c->w.estore) cudaFree(c->w.estore);
     prof_resolve(c);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);

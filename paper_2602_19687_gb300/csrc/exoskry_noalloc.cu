@@ -77,17 +77,14 @@ size_t carve(const es::Model &m, int B, bool emission, unsigned char *base, es::
     w.lmat = c.take<float>(B * L * L);
     w.area = c.take<float>(B * L);
     w.dr = c.take<float>(B * L);
-    w.w4 = c.take<float4>(B * L);
     w.it = c.take<int>(B * L);
     w.gt = c.take<float>(B * L);
     w.wtr = c.take<float>(B * L);
-    w.coef = c.take<float>(B * L * S);
     w.itc = c.take<int>(B * L);
     w.wtc = c.take<float>(B * L);
     w.gtc = c.take<float>(B * L);
     w.ccia = c.take<float>(B * L * 2);
     w.ray = c.take<float>(B * L);
-    w.alpha = emission ? c.take<float>((size_t)B * L * N) : nullptr;   // extinction of emission samples
     w.spec = c.take<float>((size_t)B * N);
     w.ymod = c.take<double>((size_t)B * m.nbins);
     w.lnl = c.take<double>(B);
@@ -140,8 +137,7 @@ extern "C" es_status es_loglike_noalloc(es_ctx *c, const double *theta, const in
     launches += es::launch_setup(c->m, w, st, none);
     launches += es::launch_trans_fused_forward(c->m, w, false, 0, st, none);
     if (kind) {
-        launches += es::launch_extinction(c->m, w, ES_KIND_EMISSION, st, none);
-        launches += es::launch_emission(c->m, w, st, none);
+        launches += es::launch_emis_fused_forward(c->m, w, false, st, none);
     }
     launches += es::launch_bins(c->m, w, false, nullptr, nullptr, lnl, st, none);
     c->last_launches = launches;

@@ -244,6 +244,10 @@ struct PairInterp {
     __device__ __forceinline__ float2 cia(const LayerConst &lc) const {
         return ex2x2(fma2(lc.wtc, d, add2(b, lc.cc[h])));
     }
+    // this lane's part of alpha: n 2^-K (its species sum) + its CIA pair (+ Rayleigh on h = 0)
+    __device__ __forceinline__ float2 part(const LayerConst &lc, float2 sum, float2 c) const {
+        return fma2(lc.ray, nu4, fma2(sum, lc.nsc, c));
+    }
 };
 
 __device__ __forceinline__ float2 shfl_xor2(float2 v, int o) {

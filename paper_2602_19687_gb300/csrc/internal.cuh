@@ -93,27 +93,24 @@ struct Work {
     float *lmat;                  // [B][L][L] path lengths L_il = P_il dr_l
     float *area;                  // [B][L] annulus area / R_*^2
     float *dr;                    // [B][L]
-    float4 *w4;                   // [B][L] bilinear weights x log2(10)
     int *it;                      // [B][L] temperature bracket
     float *gt;                    // [B][L] 1/dlog10T of the bracket (0 if clamped)
     float *wtr;                   // [B][L] raw temperature weight
-    float *coef;                  // [B][L][S] log2(X_s n_l) + offsets
     int *itc;                     // [B][L] CIA temperature bracket
     float *wtc, *gtc;             // [B][L] CIA weight, 1/dT (0 if clamped)
     float *ccia;                  // [B][L][2] log2(n^2 X_H2 X_H2), log2(n^2 X_H2 X_He)
     float *ray;                   // [B][L] n (X_H2 s_H2 + X_He s_He)
-    float *alpha;                 // [B][L][N] (emission samples)
     float *spec;                  // [B][N] transmission: depth - base; emission: Fp/F*
     double *ymod;                 // [B][nbins]
     double *lnl;                  // [B]
     // adjoint
     float *dbar;                  // [B][Np] d lnL / d spec (zero beyond N)
     float *estore;                // [B][L][Np] exp(-tau) of the forward (transmission adjoint)
-    float *abar;                  // [B][L][N] d lnL / d alpha (emission samples)
     double *lbar;                 // [B][L][L]
     double *red;                  // [B][L][N_RED]
     double *qtot;                 // [B][S] per-species reductions summed over layers
     double *zbar;                 // [B][L] transmission: sum_nu tau_bar_i(nu) (nu/nu_ref)^4
+    float *itop;                  // [B][Np][4] emission: top-of-atmosphere intensity per angle (for the adjoint)
     double *areabar;              // [B][L]
     double *levbar;               // [B][L+1] d lnL / d T_lev (emission)
     double *drbar;                // [B][L]   d lnL / d dr (emission)
@@ -139,15 +136,14 @@ struct Hook {
 // kernel launchers (each returns the number of kernels launched)
 int launch_build_coef(const Model &m, float4 *coef, cudaStream_t st);
 int launch_setup(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
-int launch_extinction(const Model &m, const Work &w, int only_kind, cudaStream_t st, const Hook &h);
+// fused emission: interpolation + Schwarzschild integration (store_i keeps I_toa for the adjoint)
+int launch_emis_fused_forward(const Model &m, const Work &w, bool store_i, cudaStream_t st, const Hook &h);
+int launch_emis_fused_backward(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
 // chunk: wavenumber tiles per persistent work item (<= 0: built-in heuristic)
 int launch_trans_fused_forward(const Model &m, const Work &w, bool store_e, int chunk, cudaStream_t st, const Hook &h);
 int launch_trans_fused_backward(const Model &m, const Work &w, int chunk, cudaStream_t st, const Hook &h);
-int launch_emission(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
 int launch_bins(const Model &m, const Work &w, bool want_adjoint, float *spectrum_out,
                 double *binned_out, double *lnl_out, cudaStream_t st, const Hook &h);
-int launch_emission_backward(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
-int launch_extinction_backward(const Model &m, const Work &w, int only_kind, cudaStream_t st, const Hook &h);
 int launch_setup_backward(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
 
 }  // namespace es

@@ -109,21 +109,12 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup(Model m, Work w) {
         double wt;
         bool clamped;
         bracket(m.log_t, m.NT, log10(t), it, wt, clamped);
-        const int ip = m.ip[l];
         const double wp = m.wp[l];
-        double w00 = (1 - wt) * (1 - wp), w01 = (1 - wt) * wp, w10 = wt * (1 - wp), w11 = wt * wp;
         w.it[bl] = it;
         w.wtr[bl] = (float)wt;
         w.gt[bl] = clamped ? 0.f : (float)(1.0 / (m.log_t[it + 1] - m.log_t[it]));
-        w.w4[bl] = make_float4((float)(w00 * LOG2_10), (float)(w01 * LOG2_10), (float)(w10 * LOG2_10),
-                               (float)(w11 * LOG2_10));
         double n = m.p_lay[l] / (K_B * t);
         w.n_lay[bl] = bad ? 0.0 : n;
-        for (int s = 0; s < S; ++s) {
-            const float *off = m.row_off + ((size_t)s * m.NT + it) * m.NP + ip;
-            double o = w00 * off[0] + w01 * off[1] + w10 * off[m.NP] + w11 * off[m.NP + 1];
-            w.coef[bl * S + s] = bad ? -1000.f : (float)(log2(xs[s] * n) + LOG2_10 * o);
-        }
         int itc;
         double wtc;
         bool cl2;
