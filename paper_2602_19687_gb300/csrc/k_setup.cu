@@ -109,7 +109,6 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup(Model m, Work w) {
         double wt;
         bool clamped;
         bracket(m.log_t, m.NT, log10(t), it, wt, clamped);
-        const double wp = m.wp[l];
         w.it[bl] = it;
         w.wtr[bl] = (float)wt;
         w.gt[bl] = clamped ? 0.f : (float)(1.0 / (m.log_t[it + 1] - m.log_t[it]));
@@ -155,27 +154,39 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup_bwd(Model m, Work w) {
     const double rc = w.rc[b];
     if (!bad && !emis) {
         // path lengths: L_ii = 2 sqrt(r_i^2 - b_i^2); L_il (l < i) =
-        // 2 [sqrt(r_l^2 - b_i^2) - sqrt(r_{l+1}^2 - b_i^2)], b_i = (r_i + r_{i+1})/2
-        for (int idx = tid; idx < L * L; idx += blockDim.x) {
-            int i = idx / L, l = idx % L;
-            if (l > i) continue;
-            double lb = w.lbar[(size_t)b * L * L + idx];
-            if (lb == 0.0) continue;
-            double bi = 0.5 * (rl[i] + rl[i + 1]);
-            double ru = rl[l];
-            double su = sqrt((ru - bi) * (ru + bi));
-            double dbi;
-            atomicAdd(&rbar[l], lb * 2.0 * ru / su);
-            if (l < i) {
-                double rd = rl[l + 1];
-                double sd = sqrt((rd - bi) * (rd + bi));
-                atomicAdd(&rbar[l + 1], -lb * 2.0 * rd / sd);
-                dbi = lb * 2.0 * bi * (1.0 / sd - 1.0 / su);
-            } else {
-                dbi = -lb * 2.0 * bi / su;
+        // 2 [sqrt(r_l^2 - b_i^2) - sqrt(r_{l+1}^2 - b_i^2)], b_i = (r_i + r_{i+1})/2.
+        // Two contention-free passes over the lower triangle: per row i the
+        // impact-parameter terms (to r_i, r_{i+1}), per column l the terms of
+        // the layer's own radii (to r_l, r_{l+1}); one shared atomic per sum.
+        const double *lbar = w.lbar + (size_t)b * L * L;
+        for (int i = tid; i < L; i += blockDim.x) {
+            const double bi = 0.5 * (rl[i] + rl[i + 1]);
+            double dsum = 0.0;
+            for (int l = 0; l <= i; ++l) {
+                const double lb = lbar[(size_t)i * L + l];
+                if (lb == 0.0) continue;
+                const double su = sqrt((rl[l] - bi) * (rl[l] + bi));
+                if (l < i) {
+                    const double sd = sqrt((rl[l + 1] - bi) * (rl[l + 1] + bi));
+                    dsum += lb * 2.0 * bi * (1.0 / sd - 1.0 / su);
+                } else {
+                    dsum -= lb * 2.0 * bi / su;
+                }
             }
-            atomicAdd(&rbar[i], 0.5 * dbi);
-            atomicAdd(&rbar[i + 1], 0.5 * dbi);
+            atomicAdd(&rbar[i], 0.5 * dsum);
+            atomicAdd(&rbar[i + 1], 0.5 * dsum);
+        }
+        for (int l = tid; l < L; l += blockDim.x) {
+            double up = 0.0, dn = 0.0;
+            for (int i = l; i < L; ++i) {
+                const double lb = lbar[(size_t)i * L + l];
+                if (lb == 0.0) continue;
+                const double bi = 0.5 * (rl[i] + rl[i + 1]);
+                up += lb * 2.0 * rl[l] / sqrt((rl[l] - bi) * (rl[l] + bi));
+                if (l < i) dn += lb * 2.0 * rl[l + 1] / sqrt((rl[l + 1] - bi) * (rl[l + 1] + bi));
+            }
+            atomicAdd(&rbar[l], up);
+            atomicAdd(&rbar[l + 1], -dn);
         }
         // annulus areas A_i = (r_i^2 - max(r_{i+1}, r_c)^2)/R_*^2 and base r_c^2/R_*^2
         for (int i = tid; i < L; i += blockDim.x) {
