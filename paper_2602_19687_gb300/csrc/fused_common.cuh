@@ -125,7 +125,12 @@ struct __align__(16) LayerConst {
 struct SampleConst {
     LayerConst lay[ES_MAX_LAYERS];
     float lx[ES_MAX_SPECIES];   // log2 X_s + KSHIFT
+    int gb[8];                  // layer-group boundaries gb[0] = 0 < ... < gb[4] = L
 };
+
+// Relative cost of starting a run of layers (a coefficient reload from L2)
+// against interpolating one layer, for balancing the layer groups.
+constexpr float RUN_COST = 3.f;
 
 // All threads of the block: per-layer constants of sample b into shared memory.
 __device__ inline void stage_sample(const Model &m, const Work &w, int b, SampleConst &sc) {
@@ -139,9 +144,7 @@ __device__ inline void stage_sample(const Model &m, const Work &w, int b, Sample
         const int it = w.it[bl], itc = w.itc[bl];
         c.cell = it * (m.NP - 1) + m.ip[l];
         c.itc = itc;
-        int r = l + 1;   // runs are a few layers long: a short forward scan
-        while (r < L && w.it[b0 + r] == it && m.ip[r] == m.ip[l] && w.itc[b0 + r] == itc) ++r;
-        c.run_end = r;
+        c.run_end = l + 1;   // set below, once every layer's (cell, itc) is staged
         c.pad = 0;
         c.wp = f2(m.wp[l]);
         c.wt = f2(w.wtr[bl]);
@@ -160,14 +163,31 @@ __device__ inline void stage_sample(const Model &m, const Work &w, int b, Sample
         const double x = (s < m.S) ? w.xs[(size_t)b * (m.S + 2) + s] : 0.0;
         sc.lx[s] = (x > 0.0) ? (float)(log2(x) + KSHIFT) : -1.0e4f;
     }
+    __syncthreads();
+    // end of each layer's run of equal (cell, CIA bracket): a short scan in shared memory
+    for (int l = threadIdx.x; l < L; l += blockDim.x) {
+        const int cell = sc.lay[l].cell, itc = sc.lay[l].itc;
+        int r = l + 1;
+        while (r < L && sc.lay[r].cell == cell && sc.lay[r].itc == itc) ++r;
+        sc.lay[l].run_end = r;
+    }
+    __syncthreads();
+    // four layer groups of equal cost: one per layer plus RUN_COST per run start
+    if (threadIdx.x == 0) {
+        float total = 0.f;
+        for (int l = 0; l < L; ++l) total += 1.f + ((l == 0 || sc.lay[l - 1].run_end == l) ? RUN_COST : 0.f);
+        int g = 1;
+        float acc = 0.f;
+        sc.gb[0] = 0;
+        for (int l = 0; l < L && g < 4; ++l) {
+            acc += 1.f + ((l == 0 || sc.lay[l - 1].run_end == l) ? RUN_COST : 0.f);
+            if (acc >= total * (float)g * 0.25f) sc.gb[g++] = l + 1;
+        }
+        while (g < 4) sc.gb[g++] = L;
+        sc.gb[4] = L;
+    }
 }
 
-// Layers of layer group `g` out of `ng` (contiguous ranges).
-__device__ __forceinline__ void group_layers(int L, int g, int ng, int &lb, int &le) {
-    const int per = (L + ng - 1) / ng;
-    lb = g * per;
-    le = min(L, lb + per);
-}
 
 // ------------------------------------------------------------ interpolation
 // Coefficient table layout (k_tables.cu): per (cell, wavenumber pair) the SP

@@ -123,9 +123,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, in
     // interpolation: 4 layer groups x 4 quarters (32 wavenumbers) of the tile;
     // a wavenumber pair is shared by a lane pair splitting the species. Lane
     // half 0 stores the hi parts of its pair's extinction, half 1 the lo parts.
-    const int half = lane & 1, vq = warp & 3, pair = 16 * vq + (lane >> 1);
-    int lb, le;
-    group_layers(L, warp >> 2, 4, lb, le);
+    const int half = lane & 1, vq = warp & 3, pair = 16 * vq + (lane >> 1), grp = warp >> 2;
     unsigned char *const a_dst = (half ? sm.al : sm.ah) + op_off(0, 2 * pair, SBO_NU);
     // epilogue: TMEM lane quadrant vq (wavenumber 32 vq + lane), impact parameters [28 ck, 28 ck + 28)
     const int ck = warp >> 2;
@@ -196,7 +194,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, in
         const int t1 = min(ntiles, (c + 1) * chunk_tiles);
         for (int t = c * chunk_tiles; t < t1; ++t) {
             const int nt0 = t * FT2;
-            extinction_pair<SPL>(m, sm.sc, lb, le, nt0 + 2 * pair, half, [&](int l, float2 a) {
+            extinction_pair<SPL>(m, sm.sc, sm.sc.gb[grp], sm.sc.gb[grp + 1], nt0 + 2 * pair, half, [&](int l, float2 a) {
                 uint32_t hi, lo;
                 split2(a, hi, lo);
                 *reinterpret_cast<uint32_t *>(a_dst + (l >> 3) * SBO_NU + (l & 7) * 16) = half ? lo : hi;
@@ -207,15 +205,16 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, in
             if (threadIdx.x == 0) {   // 7 k-steps x (hi hi + hi lo + lo hi)
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(buf * 128);
-#pragma unroll 1
+                // descriptors of k-step 0; a k-step advances the start address field
+                // (bits 0-13, 16-byte units) by 2 row groups of alpha / 2 cores of L
+                const uint64_t a_h = desc_mn_major(ah_s, SBO_NU), a_l = desc_mn_major(al_s, SBO_NU);
+                const uint64_t b_h = desc_k_major(lh_s, SBO_LP), b_l = desc_k_major(ll_s, SBO_LP);
+#pragma unroll
                 for (int k = 0; k < LP / 16; ++k) {
-                    const uint64_t a_h = desc_mn_major(ah_s + k * 2 * SBO_NU, SBO_NU);
-                    const uint64_t a_l = desc_mn_major(al_s + k * 2 * SBO_NU, SBO_NU);
-                    const uint64_t b_h = desc_k_major(lh_s + k * 2 * CORE_STRIDE, SBO_LP);
-                    const uint64_t b_l = desc_k_major(ll_s + k * 2 * CORE_STRIDE, SBO_LP);
-                    tc_mma(d, a_h, b_h, idesc, k > 0);
-                    tc_mma(d, a_h, b_l, idesc, true);
-                    tc_mma(d, a_l, b_h, idesc, true);
+                    const uint64_t da = (uint64_t)(k * 2 * SBO_NU / 16), db = (uint64_t)(k * 2 * CORE_STRIDE / 16);
+                    tc_mma(d, a_h + da, b_h + db, idesc, k > 0);
+                    tc_mma(d, a_h + da, b_l + db, idesc, true);
+                    tc_mma(d, a_l + da, b_h + db, idesc, true);
                 }
                 tc_commit(mbar);
             }
@@ -426,9 +425,7 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
     const long long total = (long long)w.B * nchunks;
     const int group = warp >> 1;                        // tau_bar phase: rows i = group + 8 k
     // interpolation: 4 layer groups x 4 quarters (32 wavenumbers); lane pairs split species
-    const int half = lane & 1, vq = warp & 3, pair = 16 * vq + (lane >> 1);
-    int lb, le;
-    group_layers(L, warp >> 2, 4, lb, le);
+    const int half = lane & 1, vq = warp & 3, pair = 16 * vq + (lane >> 1), grp = warp >> 2;
     const int NL = (L + 1 + 15) & ~15;                  // L_bar product N: layers and the weight row
     // padding rows stay zero: tau_bar rows [L, 112), alpha rows [L + 1, 128)
     for (int idx = threadIdx.x; idx < (LP - L) * (BT / 2); idx += BW_THREADS) {
@@ -609,22 +606,22 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
             }
             if (threadIdx.x == 0) {   // alpha_bar: 7 k-steps over impact parameters x 3 split terms
                 tc_fence_after();
-#pragma unroll 1
-                for (int k = 0; k < LP / 16; ++k) {
-                    const uint64_t a_h = desc_mn_major(th_s + k * 2 * SBO_NU, SBO_NU);
-                    const uint64_t a_l = desc_mn_major(tl_s + k * 2 * SBO_NU, SBO_NU);
-                    const uint64_t b_h = desc_mn_major(lh_s + k * 2 * SBO_LP, SBO_LP);
-                    const uint64_t b_l = desc_mn_major(ll_s + k * 2 * SBO_LP, SBO_LP);
-                    tc_mma(tmem, a_h, b_h, idesc_a, k > 0);
-                    tc_mma(tmem, a_h, b_l, idesc_a, true);
-                    tc_mma(tmem, a_l, b_h, idesc_a, true);
+                const uint64_t a_h = desc_mn_major(th_s, SBO_NU), a_l = desc_mn_major(tl_s, SBO_NU);
+                const uint64_t b_h = desc_mn_major(lh_s, SBO_LP), b_l = desc_mn_major(ll_s, SBO_LP);
+#pragma unroll
+                for (int k = 0; k < LP / 16; ++k) {   // start address field advances by 2 row groups
+                    const uint64_t da = (uint64_t)(k * 2 * SBO_NU / 16), db = (uint64_t)(k * 2 * SBO_LP / 16);
+                    tc_mma(tmem, a_h + da, b_h + db, idesc_a, k > 0);
+                    tc_mma(tmem, a_h + da, b_l + db, idesc_a, true);
+                    tc_mma(tmem, a_l + da, b_h + db, idesc_a, true);
                 }
                 tc_commit(mbar_a);
             }
             if (!mbar_wait(mbar_a, pa)) sm.abort = 1;
             pa ^= 1;
             tc_fence_after();
-            interp_backward<SPL>(m, sm.sc, lb, le, nt0 + 2 * pair, half, lane, abar_t, a_dst, sm.red, sm.qtot);
+            interp_backward<SPL>(m, sm.sc, sm.sc.gb[grp], sm.sc.gb[grp + 1], nt0 + 2 * pair, half, lane, abar_t, a_dst,
+                                 sm.red, sm.qtot);
             tc_fence_before();
             fence_async_smem();
             __syncthreads();
@@ -635,15 +632,14 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
             if (threadIdx.x == 0) {   // L_bar: 8 k-steps over the tile's wavenumbers x 3 split terms
                 tc_fence_after();
                 const uint32_t d = tmem + 128u;
-#pragma unroll 1
-                for (int k = 0; k < BT / 16; ++k) {
-                    const uint64_t a_h = desc_k_major(th_s + k * 2 * CORE_STRIDE, SBO_NU);
-                    const uint64_t a_l = desc_k_major(tl_s + k * 2 * CORE_STRIDE, SBO_NU);
-                    const uint64_t b_h = desc_k_major(ah_s + k * 2 * CORE_STRIDE, SBO_NU);
-                    const uint64_t b_l = desc_k_major(al_s + k * 2 * CORE_STRIDE, SBO_NU);
-                    tc_mma(d, a_h, b_h, idesc_l, l_started || k > 0);
-                    tc_mma(d, a_h, b_l, idesc_l, true);
-                    tc_mma(d, a_l, b_h, idesc_l, true);
+                const uint64_t a_h = desc_k_major(th_s, SBO_NU), a_l = desc_k_major(tl_s, SBO_NU);
+                const uint64_t b_h = desc_k_major(ah_s, SBO_NU), b_l = desc_k_major(al_s, SBO_NU);
+#pragma unroll
+                for (int k = 0; k < BT / 16; ++k) {   // start address field advances by 2 cores
+                    const uint64_t dk = (uint64_t)(k * 2 * CORE_STRIDE / 16);
+                    tc_mma(d, a_h + dk, b_h + dk, idesc_l, l_started || k > 0);
+                    tc_mma(d, a_h + dk, b_l + dk, idesc_l, true);
+                    tc_mma(d, a_l + dk, b_h + dk, idesc_l, true);
                 }
                 tc_commit(mbar_l);
             }
