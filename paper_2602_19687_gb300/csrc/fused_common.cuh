@@ -129,11 +129,13 @@ struct SampleConst {
 };
 
 // Relative cost of starting a run of layers (a coefficient reload from L2)
-// against interpolating one layer, for balancing the layer groups.
-constexpr float RUN_COST = 3.f;
+// against interpolating one layer, for balancing the layer groups: measured
+// best at 3 for the forward interpolation and 1 for the adjoint's (whose
+// layers cost more: reductions and the pair exchange of alpha_bar).
+constexpr float RUN_COST_FWD = 3.f, RUN_COST_BWD = 1.f;
 
 // All threads of the block: per-layer constants of sample b into shared memory.
-__device__ inline void stage_sample(const Model &m, const Work &w, int b, SampleConst &sc) {
+__device__ inline void stage_sample(const Model &m, const Work &w, int b, SampleConst &sc, float run_cost) {
     const float ry = (float)(1.0 / ((double)m.ray_nu_ref * m.ray_nu_ref * m.ray_nu_ref * m.ray_nu_ref));
     const float il2 = (float)(1.0 / LOG2_10);
     const int L = m.L;
@@ -172,15 +174,15 @@ __device__ inline void stage_sample(const Model &m, const Work &w, int b, Sample
         sc.lay[l].run_end = r;
     }
     __syncthreads();
-    // four layer groups of equal cost: one per layer plus RUN_COST per run start
+    // four layer groups of equal cost: one per layer plus run_cost per run start
     if (threadIdx.x == 0) {
         float total = 0.f;
-        for (int l = 0; l < L; ++l) total += 1.f + ((l == 0 || sc.lay[l - 1].run_end == l) ? RUN_COST : 0.f);
+        for (int l = 0; l < L; ++l) total += 1.f + ((l == 0 || sc.lay[l - 1].run_end == l) ? run_cost : 0.f);
         int g = 1;
         float acc = 0.f;
         sc.gb[0] = 0;
         for (int l = 0; l < L && g < 4; ++l) {
-            acc += 1.f + ((l == 0 || sc.lay[l - 1].run_end == l) ? RUN_COST : 0.f);
+            acc += 1.f + ((l == 0 || sc.lay[l - 1].run_end == l) ? run_cost : 0.f);
             if (acc >= total * (float)g * 0.25f) sc.gb[g++] = l + 1;
         }
         while (g < 4) sc.gb[g++] = L;

@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_emis_fwd(Model m, Work w, int
         if (w.kind[b] != ES_KIND_EMISSION) continue;
         if (b != cur_b) {
             __syncthreads();
-            stage_sample(m, w, b, sm.sc);
+            stage_sample(m, w, b, sm.sc, RUN_COST_FWD);
             stage_levels(m, w, b, sm);
             cur_b = b;
             __syncthreads();
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_emis_bwd(Model m, Work w, int
         if (b != cur_b) {
             if (cur_b >= 0) flush(cur_b);
             __syncthreads();
-            stage_sample(m, w, b, sm.sc);
+            stage_sample(m, w, b, sm.sc, RUN_COST_FWD);
             stage_levels(m, w, b, sm);
             for (int idx = threadIdx.x; idx < L * N_RED; idx += EM_THREADS) sm.red[idx] = 0.f;
             for (int l = threadIdx.x; l <= L; l += EM_THREADS) {

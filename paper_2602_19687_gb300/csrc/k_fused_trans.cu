@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, in
             }
             tc_fence_before();
             __syncthreads();
-            stage_sample(m, w, b, sm.sc);
+            stage_sample(m, w, b, sm.sc, RUN_COST_FWD);
             stage_lmat_tc(m, w, b, sm.lh, sm.ll, sm.area);
             cur_b = b;
             fence_async_smem();
@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
             }
             tc_fence_before();
             __syncthreads();
-            stage_sample(m, w, b, sm.sc);
+            stage_sample(m, w, b, sm.sc, RUN_COST_BWD);
             stage_lmat_tc(m, w, b, sm.lh, sm.ll, sm.area);
             for (int idx = threadIdx.x; idx < L * N_RED; idx += BW_THREADS) sm.red[idx] = 0.f;
             for (int i = threadIdx.x; i < LP; i += BW_THREADS) sm.area_acc[i] = 0.f;
