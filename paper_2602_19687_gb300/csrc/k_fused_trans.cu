@@ -504,19 +504,15 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
     };
     // L2 prefetch of the exp(-tau) rows and dbar of tile t of sample b (the
     // tau_bar phase reads them straight from HBM otherwise, with every warp
-    // of the block waiting on the same loads)
-    uint64_t evict_first;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(evict_first));
+    // of the block waiting on the same loads): one 128-byte line per thread
+    // (4 lines per row of 128 wavenumbers), issued through the load/store
+    // units rather than as bulk copies, which the TMA unit serialises
     auto prefetch_tile = [&](int pb, int pt) {
-        if (threadIdx.x < L) {   // read once: evict-first, the coefficient table stays resident
-            const float *src = w.estore + ((size_t)pb * L + threadIdx.x) * m.Np + (size_t)pt * BT;
-            asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;" ::"l"(src), "r"(BT * 4),
-                         "l"(evict_first)
-                         : "memory");
-        } else if (threadIdx.x == L) {
-            const float *src = w.dbar + (size_t)pb * m.Np + (size_t)pt * BT;
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(BT * 4) : "memory");
-        }
+        const int row = threadIdx.x >> 2, line = threadIdx.x & 3;
+        const float *src = nullptr;
+        if (row < L) src = w.estore + ((size_t)pb * L + row) * m.Np + (size_t)pt * BT + 32 * line;
+        else if (row == L) src = w.dbar + (size_t)pb * m.Np + (size_t)pt * BT + 32 * line;
+        if (src) asm volatile("prefetch.global.L2 [%0];" ::"l"(src));
     };
     if (blockIdx.x < total) {
         const long long it0 = blockIdx.x;
