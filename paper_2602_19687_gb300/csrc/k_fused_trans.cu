@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, in
             fence_async_smem();
             __syncthreads();
             const int buf = issued & 1;
-            if (threadIdx.x == 0) {   // 7 k-steps x (hi hi + hi lo + lo hi)
+            if (threadIdx.x == 12 * 32) {   // warp 12's epilogue share is the lightest: 7 k-steps x 3 split terms
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(buf * 128);
                 // descriptors of k-step 0; a k-step advances the start address field
@@ -349,9 +349,9 @@ __device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
 // dlog10 T, C_h = sum abar c_h, CT_h = sum abar c_h dlog2 k_h/dT (red slots
 // 0/1, 2/3, 4/5, 6/7 for h = 0/1); per species Q_s = sum_l sum abar n e_s.
 // The Rayleigh sum over wavenumber comes from the L_bar product.
-template <int SPL>
+template <int SPL, class Wait>
 __device__ void interp_backward(const Model &m, const SampleConst &sc, int lb, int le, int n, int half, int lane,
-                                uint32_t abar_t, unsigned char *a_dst, float *red, float *qtot) {
+                                uint32_t abar_t, unsigned char *a_dst, float *red, float *qtot, Wait &&wait_abar) {
     const int S = m.S;
     const int ridx = reduce_index8(lane);
     const bool writer = (lane & 3) == 0;
@@ -363,10 +363,15 @@ __device__ void interp_backward(const Model &m, const SampleConst &sc, int lb, i
     float2 qa[SPL];
 #pragma unroll
     for (int j = 0; j < SPL; ++j) qa[j] = f2(0.f);
+    bool waited = false;
     for (int l = lb; l < le;) {
         const int end = min(sc.lay[l].run_end, le);
         pi.load(sc, sc.lay[l].cell, sc.lay[l].itc);
         if (end < le) pi.prefetch(sc.lay[end].cell, sc.lay[end].itc);
+        if (!waited) {   // the first coefficient loads are in flight while the alpha_bar product completes
+            wait_abar();
+            waited = true;
+        }
         for (; l < end; ++l) {
             const LayerConst &lc = sc.lay[l];
             const float own = tmem_ld1(abar_t + (uint32_t)l);
@@ -400,6 +405,7 @@ __device__ void interp_backward(const Model &m, const SampleConst &sc, int lb, i
             *reinterpret_cast<uint32_t *>(a_dst + (l >> 3) * SBO_NU + (l & 7) * 16) = half ? lo : hi;
         }
     }
+    if (!waited) wait_abar();   // empty layer group
     // per-species totals: slot j of lane half h is species SPL h + j
 #pragma unroll
     for (int c0 = 0; c0 < 2 * SPL; c0 += 8) {
@@ -613,11 +619,12 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
                 }
                 tc_commit(mbar_a);
             }
-            if (!mbar_wait(mbar_a, pa)) sm.abort = 1;
-            pa ^= 1;
-            tc_fence_after();
             interp_backward<SPL>(m, sm.sc, sm.sc.gb[grp], sm.sc.gb[grp + 1], nt0 + 2 * pair, half, lane, abar_t, a_dst,
-                                 sm.red, sm.qtot);
+                                 sm.red, sm.qtot, [&]() {
+                                     if (!mbar_wait(mbar_a, pa)) sm.abort = 1;
+                                     tc_fence_after();
+                                 });
+            pa ^= 1;
             tc_fence_before();
             fence_async_smem();
             __syncthreads();
@@ -625,7 +632,7 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
                 abort = true;
                 break;
             }
-            if (threadIdx.x == 0) {   // L_bar: 8 k-steps over the tile's wavenumbers x 3 split terms
+            if (threadIdx.x == 32) {   // L_bar (from another warp than alpha_bar's issuer): 8 k-steps x 3 terms
                 tc_fence_after();
                 const uint32_t d = tmem + 128u;
                 const uint64_t a_h = desc_k_major(th_s, SBO_NU), a_l = desc_k_major(tl_s, SBO_NU);
