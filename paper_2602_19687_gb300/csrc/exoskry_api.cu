@@ -406,6 +406,11 @@ es_status es_create(es_ctx **out, int device, const es_model_desc *d) {
     m.p_lev = dp;
     if ((s = upload(c, c->model_bufs, &dp, p_lay.data(), p_lay.size())) != ES_OK) { es_destroy(c); return s; }
     m.p_lay = dp;
+    std::vector<double> lnp(m.L + 1);
+    for (int k = 0; k <= m.L; ++k) lnp[k] = std::log(p_lev[k]);
+    if ((s = upload(c, c->model_bufs, &dp, lnp.data(), lnp.size())) != ES_OK) { es_destroy(c); return s; }
+    m.lnp_lev = dp;
+    m.ln_p_ref = std::log(m.p_ref);
     c->ws_bytes = 0;
     *out = c;
     return ES_OK;

@@ -58,6 +58,8 @@ struct Model {
     double mu_gl[N_MU], w_gl[N_MU];
     // device arrays
     const double *p_lev, *p_lay;  // [L+1], [L]
+    const double *lnp_lev;        // [L+1] ln p_lev
+    double ln_p_ref;              // ln p_ref
     const int *ip;                // [L] pressure bracket of each layer
     const float *wp;              // [L] pressure weight of each layer
     const double *log_t;          // [NT] log10 of the temperature grid

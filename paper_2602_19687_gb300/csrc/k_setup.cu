@@ -1,9 +1,18 @@
-// Per-sample setup (FP64): parameter unpack, T-p profile (Sect. 2.4), VMR
-// fill (Sect. 3.1), hydrostatic altitude grid, path-length matrix
+// Per-sample setup: parameter unpack, T-p profile (Sect. 2.4), VMR fill
+// (Sect. 3.1), hydrostatic altitude grid (FP64), path-length matrix
 // (Sect. 4, Eq. P_1D times dr), annulus areas with the grey deck, and the
 // per-layer interpolation coefficients used by the extinction kernels.
 // Also the adjoint of all of that (reverse sweep over the geometry, then
 // forward-mode tangents of the profile/hydrostatics, one lane per parameter).
+//
+// GB300 runs FP64 at a small fraction of its FP32 rate, so FP64 is kept for
+// the profile, the hydrostatic integration and the sums, and the O(L^2)
+// path-length work runs in FP32 on differences that are formed exactly:
+// every radius r (and impact parameter b) is split as hi + lo with hi =
+// fl32(r), so r_l - b_i = (hi_l - hi_b) + (lo_l - lo_b), the first difference
+// exact (Sterbenz) and the second tiny. A chord segment is written without
+// cancellation, sqrt(r_l^2 - b^2) - sqrt(r_{l+1}^2 - b^2) =
+// (r_l - r_{l+1})(r_l + r_{l+1}) / (s_u + s_d).
 #include "physics.cuh"
 
 namespace es {
@@ -11,6 +20,36 @@ namespace es {
 namespace {
 
 constexpr int SETUP_THREADS = 128;
+
+// Level radii and impact parameters as FP32 hi/lo pairs plus the per-layer
+// thickness dr_l = r_l - r_{l+1} and sum r_l + r_{l+1} (all from FP64).
+struct SplitRadii {
+    float rh[ES_MAX_LAYERS + 1], rlo[ES_MAX_LAYERS + 1];
+    float bh[ES_MAX_LAYERS], blo[ES_MAX_LAYERS];
+    float dl[ES_MAX_LAYERS], sl[ES_MAX_LAYERS];
+};
+
+__device__ inline void split_radii(const double *rl, int L, SplitRadii &q) {
+    for (int k = threadIdx.x; k <= L; k += blockDim.x) {
+        const float h = (float)rl[k];
+        q.rh[k] = h;
+        q.rlo[k] = (float)(rl[k] - (double)h);
+        if (k < L) {
+            const double b = 0.5 * (rl[k] + rl[k + 1]);
+            const float bh = (float)b;
+            q.bh[k] = bh;
+            q.blo[k] = (float)(b - (double)bh);
+            q.dl[k] = (float)(rl[k] - rl[k + 1]);
+            q.sl[k] = (float)(rl[k] + rl[k + 1]);
+        }
+    }
+}
+
+// r_k^2 - b_i^2 in FP32 from the exact difference r_k - b_i
+__device__ __forceinline__ float chord_sq(const SplitRadii &q, int k, int i) {
+    const float d = (q.rh[k] - q.bh[i]) + (q.rlo[k] - q.blo[i]);
+    return d * (q.rh[k] + q.bh[i]);
+}
 
 __global__ void __launch_bounds__(SETUP_THREADS) k_setup(Model m, Work w) {
     const int b = blockIdx.x, tid = threadIdx.x;
@@ -20,6 +59,7 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup(Model m, Work w) {
     __shared__ double tl[ES_MAX_LAYERS], tv[ES_MAX_LAYERS + 1], rl[ES_MAX_LAYERS + 1];
     __shared__ double s_mu, s_g, s_rref, s_rc;
     __shared__ int s_bad;
+    __shared__ SplitRadii q;
 
     if (tid < m.nfull) th[tid] = m.theta_fixed[tid];
     if (tid == 0) s_bad = 0;
@@ -78,19 +118,23 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup(Model m, Work w) {
         w.t_lev[(size_t)b * (L + 1) + k] = bad ? 1000.0 : tv[k];
         w.r_lev[(size_t)b * (L + 1) + k] = rl[k];
     }
-    // path-length matrix L_il (row: impact parameter of layer i, column: layer l)
+    // path-length matrix L_il (row: impact parameter of layer i, column: layer l);
+    // b_i lies inside layer i, so only the diagonal chord starts at b_i
+    split_radii(rl, L, q);
+    __syncthreads();
     for (int idx = tid; idx < L * L; idx += blockDim.x) {
-        int i = idx / L, l = idx % L;
-        double v = 0.0;
+        const int i = idx / L, l = idx % L;
+        float v = 0.f;
         if (!bad && l <= i) {
-            double bi = 0.5 * (rl[i] + rl[i + 1]);
-            double ru = rl[l], rd = rl[l + 1];
-            if (ru > bi) {
-                double su = sqrt((ru - bi) * (ru + bi));
-                v = (rd < bi) ? 2.0 * su : 2.0 * (su - sqrt((rd - bi) * (rd + bi)));
+            const float su = sqrtf(chord_sq(q, l, i));
+            if (l == i) {
+                v = 2.f * su;
+            } else {
+                const float sd = sqrtf(chord_sq(q, l + 1, i));
+                v = 2.f * q.dl[l] * q.sl[l] / (su + sd);
             }
         }
-        w.lmat[(size_t)b * L * L + idx] = (float)v;
+        w.lmat[(size_t)b * L * L + idx] = v;
     }
     for (int l = tid; l < L; l += blockDim.x) {
         const size_t bl = (size_t)b * L + l;
@@ -136,7 +180,12 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup_bwd(Model m, Work w) {
     __shared__ double rl[ES_MAX_LAYERS + 1], rbar[ES_MAX_LAYERS + 1], tvbar[ES_MAX_LAYERS + 1];
     __shared__ double tlbar[ES_MAX_LAYERS];
     __shared__ double xbar[ES_MAX_SPECIES + 2], xs[ES_MAX_SPECIES + 2];
+    __shared__ double thv[ES_MAX_PARAMS];
     __shared__ double rcbar;
+    __shared__ float tlf[ES_MAX_LAYERS];
+    // temperature tangents dT/dtheta_p at layers and (emission) levels
+    __shared__ float dtl[ES_MAX_PARAMS][ES_MAX_LAYERS], dtv[ES_MAX_PARAMS][ES_MAX_LAYERS + 1];
+    __shared__ SplitRadii q;
     const bool bad = w.flags[b] != 0;
     const bool emis = w.kind[b] == ES_KIND_EMISSION;
     const double rs2 = m.r_star * m.r_star;
@@ -149,41 +198,49 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup_bwd(Model m, Work w) {
         xbar[tid] = 0.0;
         xs[tid] = w.xs[(size_t)b * (S + 2) + tid];
     }
+    if (tid < m.nfull) thv[tid] = w.theta[(size_t)b * m.nfull + tid];
+    for (int l = tid; l < L; l += blockDim.x) tlf[l] = (float)w.t_lay[(size_t)b * L + l];
     if (tid == 0) rcbar = 0.0;
+    __syncthreads();
+    split_radii(rl, L, q);
     __syncthreads();
     const double rc = w.rc[b];
     if (!bad && !emis) {
-        // path lengths: L_ii = 2 sqrt(r_i^2 - b_i^2); L_il (l < i) =
-        // 2 [sqrt(r_l^2 - b_i^2) - sqrt(r_{l+1}^2 - b_i^2)], b_i = (r_i + r_{i+1})/2.
+        // path lengths: L_ii = 2 s(i, i); L_il (l < i) = 2 [s(l, i) - s(l+1, i)],
+        // s(k, i) = sqrt(r_k^2 - b_i^2), b_i = (r_i + r_{i+1})/2.
         // Two contention-free passes over the lower triangle: per row i the
         // impact-parameter terms (to r_i, r_{i+1}), per column l the terms of
         // the layer's own radii (to r_l, r_{l+1}); one shared atomic per sum.
+        // Terms in FP32 (1/s_d - 1/s_u without cancellation), sums in FP64.
         const double *lbar = w.lbar + (size_t)b * L * L;
         for (int i = tid; i < L; i += blockDim.x) {
-            const double bi = 0.5 * (rl[i] + rl[i + 1]);
+            const float bi = q.bh[i];
             double dsum = 0.0;
             for (int l = 0; l <= i; ++l) {
                 const double lb = lbar[(size_t)i * L + l];
                 if (lb == 0.0) continue;
-                const double su = sqrt((rl[l] - bi) * (rl[l] + bi));
+                const float u = chord_sq(q, l, i), ru = rsqrtf(u);
+                float t;
                 if (l < i) {
-                    const double sd = sqrt((rl[l + 1] - bi) * (rl[l + 1] + bi));
-                    dsum += lb * 2.0 * bi * (1.0 / sd - 1.0 / su);
+                    const float d = chord_sq(q, l + 1, i), rd = rsqrtf(d);
+                    // 1/s_d - 1/s_u = (r_l^2 - r_{l+1}^2) / (s_u s_d (s_u + s_d))
+                    t = 2.f * bi * (q.dl[l] * q.sl[l]) * ru * rd / (u * ru + d * rd);
                 } else {
-                    dsum -= lb * 2.0 * bi / su;
+                    t = -2.f * bi * ru;
                 }
+                dsum += lb * (double)t;
             }
             atomicAdd(&rbar[i], 0.5 * dsum);
             atomicAdd(&rbar[i + 1], 0.5 * dsum);
         }
         for (int l = tid; l < L; l += blockDim.x) {
             double up = 0.0, dn = 0.0;
+            const float r0 = 2.f * q.rh[l], r1 = 2.f * q.rh[l + 1];
             for (int i = l; i < L; ++i) {
                 const double lb = lbar[(size_t)i * L + l];
                 if (lb == 0.0) continue;
-                const double bi = 0.5 * (rl[i] + rl[i + 1]);
-                up += lb * 2.0 * rl[l] / sqrt((rl[l] - bi) * (rl[l] + bi));
-                if (l < i) dn += lb * 2.0 * rl[l + 1] / sqrt((rl[l + 1] - bi) * (rl[l + 1] + bi));
+                up += lb * (double)(r0 * rsqrtf(chord_sq(q, l, i)));
+                if (l < i) dn += lb * (double)(r1 * rsqrtf(chord_sq(q, l + 1, i)));
             }
             atomicAdd(&rbar[l], up);
             atomicAdd(&rbar[l + 1], -dn);
@@ -227,46 +284,78 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup_bwd(Model m, Work w) {
         }
         tlbar[l] = tb;
     }
+    // forward-mode tangents in FP32 (values from the forward's FP64 results).
+    // Temperature tangents, parallel over (parameter, layer or level): only
+    // the profile parameters and log g reach T.
+    const int npts = emis ? 2 * L + 1 : L;
+    if (!bad) {
+        for (int idx = tid; idx < m.nfree * npts; idx += blockDim.x) {
+            const int p = idx / npts, k = idx % npts;
+            const int seed = m.free_idx[p];
+            float dt = 0.f;
+            if (seed >= S && seed - S <= ES_P_LOG_G) {
+                DualF th[ES_MAX_PARAMS];
+                for (int j = 0; j < m.nfull; ++j) th[j] = DualF((float)thv[j], j == seed ? 1.f : 0.f);
+                dt = temperature<DualF>(m, th, k < L ? m.p_lay[k] : m.p_lev[k - L]).d;
+            }
+            if (k < L) dtl[p][k] = dt;
+            else dtv[p][k - L] = dt;
+        }
+    }
     __syncthreads();
-    // forward-mode tangents: lane p differentiates with respect to free slot p
+    // then one lane per free parameter: VMRs, hydrostatics, deck, star scale
     if (tid >= 32) return;
     const int p = tid;
     if (p >= m.nfree) return;
     double *gout = w.grad + (size_t)b * m.nfree;
     if (bad) { gout[p] = 0.0; return; }
     const int seed = m.free_idx[p];
-    Dual th[ES_MAX_PARAMS];
-    for (int k = 0; k < m.nfull; ++k) th[k] = Dual(w.theta[(size_t)b * m.nfull + k], k == seed ? 1.0 : 0.0);
-    Dual x[ES_MAX_SPECIES], xh2, xhe, mu;
-    vmr_fill<Dual>(m, th, x, xh2, xhe, mu);
+    DualF th[ES_MAX_PARAMS];
+    for (int k = 0; k < m.nfull; ++k) th[k] = DualF((float)thv[k], k == seed ? 1.f : 0.f);
+    DualF x[ES_MAX_SPECIES], xh2, xhe, mu;
+    vmr_fill<DualF>(m, th, x, xh2, xhe, mu);
     double acc = 0.0;
-    for (int s = 0; s < S; ++s) acc += xbar[s] * x[s].d;
-    acc += xbar[S] * xh2.d + xbar[S + 1] * xhe.d;
-    Dual tl[ES_MAX_LAYERS];
+    for (int s = 0; s < S; ++s) acc += xbar[s] * (double)x[s].d;
+    acc += xbar[S] * (double)xh2.d + xbar[S + 1] * (double)xhe.d;
+    DualF tl[ES_MAX_LAYERS];
     for (int l = 0; l < L; ++l) {
-        tl[l] = temperature<Dual>(m, th, m.p_lay[l]);
-        acc += tlbar[l] * tl[l].d;
+        tl[l] = DualF(tlf[l], dtl[p][l]);
+        acc += tlbar[l] * (double)dtl[p][l];
     }
     if (emis)
-        for (int k = 0; k <= L; ++k) acc += tvbar[k] * temperature<Dual>(m, th, m.p_lev[k]).d;
-    Dual g = dexp10(th[S + ES_P_LOG_G]);
-    Dual rref = th[S + ES_P_R_P] * R_JUP;
-    Dual inv_r[ES_MAX_LAYERS + 1];
-    hydrostatic<Dual>(m, tl, mu, g, rref, inv_r);
-    Dual r[ES_MAX_LAYERS + 1];
+        for (int k = 0; k <= L; ++k) acc += tvbar[k] * (double)dtv[p][k];
+    DualF g = dexp10(th[S + ES_P_LOG_G]);
+    DualF rref = th[S + ES_P_R_P] * R_JUP;
+    DualF inv_r[ES_MAX_LAYERS + 1];
+    hydrostatic<DualF>(m, tl, mu, g, rref, inv_r);
     for (int k = 0; k <= L; ++k) {
-        r[k] = 1.0 / inv_r[k];
-        acc += rbar[k] * r[k].d;
+        const DualF r = 1.0 / inv_r[k];
+        inv_r[k].d = r.d;   // keep dr_k for the deck
+        acc += rbar[k] * (double)r.d;
     }
     if (!emis) {
-        Dual rcd = (m.cloud_kind == ES_CLOUD_DECK) ? deck_radius<Dual>(m, r, th[S + ES_P_LOG_P_CLOUD]) : r[L];
-        acc += rcbar * rcd.d;
+        // deck radius r_c = r_k + f (r_{k+1} - r_k), f linear in ln p_c; the
+        // radius difference from the FP64 levels
+        float drc;
+        const double p_c = exp10(thv[S + ES_P_LOG_P_CLOUD]) * BAR;
+        const int k = deck_bracket(m, p_c);
+        if (k == -1) {
+            drc = inv_r[L].d;
+        } else if (k == -2) {
+            drc = inv_r[0].d;
+        } else {
+            const double l0 = m.lnp_lev[k], l1 = m.lnp_lev[k + 1];
+            const double f = (thv[S + ES_P_LOG_P_CLOUD] * LN10 + log(BAR) - l0) / (l1 - l0);
+            const double df = LN10 * (double)th[S + ES_P_LOG_P_CLOUD].d / (l1 - l0);
+            drc = (float)((double)inv_r[k].d + f * (double)(inv_r[k + 1].d - inv_r[k].d) + df * (rl[k + 1] - rl[k]));
+        }
+        acc += rcbar * (double)drc;
     } else {
-        Dual rp = th[S + ES_P_R_P] * R_JUP;
-        Dual sc = th[S + ES_P_DILUTION] * rp * rp / rs2;
-        acc += w.misc[(size_t)b * 4 + 1] * sc.d;
+        DualF rp = th[S + ES_P_R_P] * R_JUP;
+        DualF sc = th[S + ES_P_DILUTION] * rp * rp / rs2;
+        acc += w.misc[(size_t)b * 4 + 1] * (double)sc.d;
     }
-    acc += w.misc[(size_t)b * 4 + 2] * th[S + ES_P_C_INFL].d;
+    acc += w.misc[(size_t)b * 4 + 2] * (double)th[S + ES_P_C_INFL].d;
     gout[p] = acc;
 }
 

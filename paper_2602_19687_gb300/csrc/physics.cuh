@@ -1,5 +1,6 @@
 // Per-sample atmosphere physics, templated on the scalar type so the same
-// code gives values (double) and forward-mode tangents (Dual) for the adjoint.
+// code gives values (double) and forward-mode tangents (Dual, DualF) for the
+// adjoint.
 #pragma once
 
 #include "internal.cuh"
@@ -40,6 +41,43 @@ __device__ inline Dual dpow(Dual a, double p) {
     return Dual(s, p * s / a.v * a.d);
 }
 __device__ inline Dual dexp10(Dual a) { double e = exp10(a.v); return Dual(e, e * LN10 * a.d); }
+// Forward-mode dual number in FP32 for the adjoint's tangent sweeps: the
+// tangents only need ~1e-6 relative accuracy (the gradient is checked to
+// 1e-3), and GB300 runs FP32 at many times its FP64 rate.
+struct DualF {
+    float v, d;
+    __host__ __device__ DualF() : v(0.f), d(0.f) {}
+    __host__ __device__ DualF(double x) : v((float)x), d(0.f) {}
+    __host__ __device__ DualF(float x, float dx) : v(x), d(dx) {}
+};
+__device__ inline DualF operator+(DualF a, DualF b) { return DualF(a.v + b.v, a.d + b.d); }
+__device__ inline DualF operator-(DualF a, DualF b) { return DualF(a.v - b.v, a.d - b.d); }
+__device__ inline DualF operator-(DualF a) { return DualF(-a.v, -a.d); }
+__device__ inline DualF operator*(DualF a, DualF b) { return DualF(a.v * b.v, a.d * b.v + a.v * b.d); }
+__device__ inline DualF operator/(DualF a, DualF b) {
+    float q = a.v / b.v;
+    return DualF(q, (a.d - q * b.d) / b.v);
+}
+__device__ inline DualF operator+(DualF a, double b) { return DualF(a.v + (float)b, a.d); }
+__device__ inline DualF operator+(double a, DualF b) { return DualF((float)a + b.v, b.d); }
+__device__ inline DualF operator-(DualF a, double b) { return DualF(a.v - (float)b, a.d); }
+__device__ inline DualF operator-(double a, DualF b) { return DualF((float)a - b.v, -b.d); }
+__device__ inline DualF operator*(DualF a, double b) { return DualF(a.v * (float)b, a.d * (float)b); }
+__device__ inline DualF operator*(double a, DualF b) { return DualF((float)a * b.v, (float)a * b.d); }
+__device__ inline DualF operator/(DualF a, double b) { return DualF(a.v / (float)b, a.d / (float)b); }
+__device__ inline DualF operator/(double a, DualF b) {
+    float q = (float)a / b.v;
+    return DualF(q, -q * b.d / b.v);
+}
+__device__ inline DualF dexp(DualF a) { float e = expf(a.v); return DualF(e, e * a.d); }
+__device__ inline DualF dlog(DualF a) { return DualF(logf(a.v), a.d / a.v); }
+__device__ inline DualF dsqrt(DualF a) { float s = sqrtf(a.v); return DualF(s, 0.5f * a.d / s); }
+__device__ inline DualF dpow(DualF a, double p) {
+    float s = powf(a.v, (float)p);
+    return DualF(s, (float)p * s / a.v * a.d);
+}
+__device__ inline DualF dexp10(DualF a) { float e = exp10f(a.v); return DualF(e, e * (float)LN10 * a.d); }
+__device__ inline double val(DualF a) { return (double)a.v; }
 __device__ inline double dexp(double a) { return exp(a); }
 __device__ inline double dlog(double a) { return log(a); }
 __device__ inline double dsqrt(double a) { return sqrt(a); }
@@ -112,12 +150,13 @@ __device__ void hydrostatic(const Model &m, const R *t_lay, R mu, R g, R r_ref, 
     R coef = K_B / (mu * AMU * g * r_ref * r_ref);
     int j = anchor_layer(m);
     R inv_ref = 1.0 / r_ref;
-    inv_r[j] = inv_ref + coef * t_lay[j] * log(m.p_lev[j] / m.p_ref);
-    inv_r[j + 1] = inv_ref + coef * t_lay[j] * log(m.p_lev[j + 1] / m.p_ref);
+    // ln(p_a / p_b) as differences of the levels' tabulated ln p
+    inv_r[j] = inv_ref + coef * t_lay[j] * (m.lnp_lev[j] - m.ln_p_ref);
+    inv_r[j + 1] = inv_ref + coef * t_lay[j] * (m.lnp_lev[j + 1] - m.ln_p_ref);
     for (int k = j - 1; k >= 0; --k)
-        inv_r[k] = inv_r[k + 1] + coef * t_lay[k] * log(m.p_lev[k] / m.p_lev[k + 1]);
+        inv_r[k] = inv_r[k + 1] + coef * t_lay[k] * (m.lnp_lev[k] - m.lnp_lev[k + 1]);
     for (int k = j + 2; k <= m.L; ++k)
-        inv_r[k] = inv_r[k - 1] + coef * t_lay[k - 1] * log(m.p_lev[k] / m.p_lev[k - 1]);
+        inv_r[k] = inv_r[k - 1] + coef * t_lay[k - 1] * (m.lnp_lev[k] - m.lnp_lev[k - 1]);
 }
 
 // Deck level bracket: returns -1 (no deck / at or below the bottom: r_c = r_bot),
@@ -139,7 +178,7 @@ __device__ R deck_radius(const Model &m, const R *r_lev, R log10_pc) {
     if (k == -1) return r_lev[m.L];
     if (k == -2) return r_lev[0];
     R lnpc = log10_pc * LN10 + log(BAR);
-    double l0 = log(m.p_lev[k]), l1 = log(m.p_lev[k + 1]);
+    double l0 = m.lnp_lev[k], l1 = m.lnp_lev[k + 1];
     R f = (lnpc - l0) / (l1 - l0);
     return r_lev[k] + f * (r_lev[k + 1] - r_lev[k]);
 }
