@@ -1,6 +1,7 @@
-// Building blocks of the fused per-tile kernels: warp-level BF16 tensor-core
-// MMA (split-precision), packed FP32x2 arithmetic, and the register-cached
-// opacity interpolation of one 64-wavenumber tile.
+// Building blocks of the fused per-tile kernels: packed FP32x2 arithmetic,
+// the split of FP32 values into BF16 hi + lo pairs for the tensor-core
+// operands, per-sample layer constants, and the register-cached opacity
+// interpolation of a wavenumber pair.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -9,13 +10,8 @@
 
 namespace es {
 
-constexpr int FT = 64;            // wavenumbers per tile
-constexpr int FWARPS = 8;         // warps per fused block
-constexpr int FTHREADS = FWARPS * 32;
 constexpr int LP = 112;           // layers padded to 7 x 16 (tensor-core K/M blocks)
 constexpr float KSHIFT = 64.f;    // log2 scale folded into the species exponents
-constexpr int L_PITCH = 120;      // bf16 pitch of [112][112] path-matrix rows (240 B: 15 x 16 B)
-constexpr int R_PITCH = 72;       // bf16 pitch of [row][64 nu] operand rows (144 B: 9 x 16 B)
 
 // ------------------------------------------------------------ packed FP32x2
 // Two FP32 lanes per instruction (sm_100+ FFMA2/FADD2/FMUL2 builtins).
@@ -47,7 +43,7 @@ __device__ __forceinline__ float2 ex2x2(float2 x) {
 }
 __device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
 
-// ------------------------------------------------------------ BF16 split and tensor cores
+// ------------------------------------------------------------ BF16 split
 // x = hi + lo with hi, lo BF16 (hi round-to-nearest, lo the rounded residual)
 __device__ __forceinline__ void split2(float2 x, uint32_t &hi, uint32_t &lo) {
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(x.y), "f"(x.x));
@@ -56,56 +52,6 @@ __device__ __forceinline__ void split2(float2 x, uint32_t &hi, uint32_t &lo) {
 }
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void ldsm_x4(uint32_t a, uint32_t (&r)[4]) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
-}
-__device__ __forceinline__ void ldsm_x4_t(uint32_t a, uint32_t (&r)[4]) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
-}
-__device__ __forceinline__ void ldsm_x2(uint32_t a, uint32_t (&r)[2]) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
-}
-__device__ __forceinline__ void ldsm_x2_t(uint32_t a, uint32_t (&r)[2]) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];"
-                 : "=r"(r[0]), "=r"(r[1]) : "r"(a));
-}
-// D += A B, m16n8k16, BF16 inputs, FP32 accumulation
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                 "{%0,%1,%2,%3};"
-                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-// split-precision product: (Ah + Al)(Bh + Bl) ~ Ah Bh + Ah Bl + Al Bh
-__device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4],
-                                     const uint32_t (&bh)[2], const uint32_t (&bl)[2]) {
-    mma16816(d, al, bh);
-    mma16816(d, ah, bl);
-    mma16816(d, ah, bh);
-}
-
-// Address of lane's ldmatrix row for an A fragment (m16 x k16) of a row-major
-// [m][k] BF16 array with `pitch` elements per row.
-__device__ __forceinline__ uint32_t a_addr(uint32_t base, int pitch, int m0, int k0, int lane) {
-    return base + 2u * (uint32_t)((m0 + (lane & 15)) * pitch + k0 + ((lane >> 4) << 3));
-}
-// A fragment (m16 x k16) of A = S^T where S is stored row-major [k][m] (ldmatrix .trans)
-__device__ __forceinline__ uint32_t at_addr(uint32_t base, int pitch, int m0, int k0, int lane) {
-    const int q = lane >> 3, r = lane & 7;   // matrix q: (k half, m half) = (q>>1, q&1)
-    return base + 2u * (uint32_t)((k0 + ((q >> 1) << 3) + r) * pitch + m0 + ((q & 1) << 3));
-}
-// B fragment (k16 x n8) from a row-major [n][k] array (ldmatrix, non-trans)
-__device__ __forceinline__ uint32_t b_addr(uint32_t base, int pitch, int n0, int k0, int lane) {
-    const int l = lane & 15;
-    return base + 2u * (uint32_t)((n0 + (l & 7)) * pitch + k0 + ((l >> 3) << 3));
-}
-// B fragment (k16 x n8) from a row-major [k][n] array (ldmatrix .trans)
-__device__ __forceinline__ uint32_t bt_addr(uint32_t base, int pitch, int n0, int k0, int lane) {
-    const int l = lane & 15;
-    return base + 2u * (uint32_t)((k0 + l) * pitch + n0);
 }
 
 // ------------------------------------------------------------ per-sample constants
@@ -119,7 +65,7 @@ struct __align__(16) LayerConst {
     float gts, gtcs;     // d/dlog10 T of the log2 exponents: gt / log2(10), gtc / log2(10)
     int cell, itc;       // (T, p) table cell = it * (NP - 1) + ip; CIA temperature bracket
     int run_end;         // first layer after l whose (cell, itc) differs (or L)
-    int pad;
+    int aoff;            // byte offset of row l in a core-matrix operand with 8-row stride asbo
 };
 
 struct SampleConst {
@@ -135,7 +81,8 @@ struct SampleConst {
 constexpr float RUN_COST_FWD = 3.f, RUN_COST_BWD = 1.f;
 
 // All threads of the block: per-layer constants of sample b into shared memory.
-__device__ inline void stage_sample(const Model &m, const Work &w, int b, SampleConst &sc, float run_cost) {
+__device__ inline void stage_sample(const Model &m, const Work &w, int b, SampleConst &sc, float run_cost,
+                                    int asbo = 0) {
     const float ry = (float)(1.0 / ((double)m.ray_nu_ref * m.ray_nu_ref * m.ray_nu_ref * m.ray_nu_ref));
     const float il2 = (float)(1.0 / LOG2_10);
     const int L = m.L;
@@ -147,7 +94,7 @@ __device__ inline void stage_sample(const Model &m, const Work &w, int b, Sample
         c.cell = it * (m.NP - 1) + m.ip[l];
         c.itc = itc;
         c.run_end = l + 1;   // set below, once every layer's (cell, itc) is staged
-        c.pad = 0;
+        c.aoff = (l >> 3) * asbo + (l & 7) * 16;
         c.wp = f2(m.wp[l]);
         c.wt = f2(w.wtr[bl]);
         c.wtc = f2(w.wtc[bl]);
@@ -279,7 +226,7 @@ __device__ __forceinline__ float2 shfl_xor2(float2 v, int o) {
 // Extinction alpha_l(nu) at wavenumber pair n, n+1 for layers [lb, le), the
 // lane pair (lane, lane ^ 1) splitting species and CIA pairs:
 //   alpha = n 2^-K sum_s 2^e_s + CIA_H2H2 + CIA_H2He + Rayleigh.
-// Calls out(l, alpha) on both lanes of the pair.
+// Calls out(layer constants, alpha) on both lanes of the pair.
 template <int SPL, class Out>
 __device__ __forceinline__ void extinction_pair(const Model &m, const SampleConst &sc, int lb, int le, int n,
                                                 int half, Out &&out) {
@@ -289,14 +236,31 @@ __device__ __forceinline__ void extinction_pair(const Model &m, const SampleCons
         const int end = min(sc.lay[l].run_end, le);
         pi.load(sc, sc.lay[l].cell, sc.lay[l].itc);
         if (end < le) pi.prefetch(sc.lay[end].cell, sc.lay[end].itc);
-        for (; l < end; ++l) {
-            const LayerConst &lc = sc.lay[l];
+        const LayerConst *lp = &sc.lay[l], *const lend = &sc.lay[end];
+        // two layers per iteration: independent chains for the schedulers
+        for (; lp + 1 < lend; lp += 2) {
+            const LayerConst &c0 = lp[0], &c1 = lp[1];
+            float2 t, s0 = ex2x2(pi.expo(0, c0.wp, c0.wt, t)), s1 = ex2x2(pi.expo(0, c1.wp, c1.wt, t));
+#pragma unroll
+            for (int j = 1; j < SPL; ++j) {
+                s0 = add2(s0, ex2x2(pi.expo(j, c0.wp, c0.wt, t)));
+                s1 = add2(s1, ex2x2(pi.expo(j, c1.wp, c1.wt, t)));
+            }
+            const float2 m0 = fma2(c0.ray, pi.nu4, fma2(s0, c0.nsc, pi.cia(c0)));
+            const float2 m1 = fma2(c1.ray, pi.nu4, fma2(s1, c1.nsc, pi.cia(c1)));
+            const float2 o0 = shfl_xor2(m0, 1), o1 = shfl_xor2(m1, 1);
+            out(c0, add2(m0, o0));
+            out(c1, add2(m1, o1));
+        }
+        if (lp != lend) {
+            const LayerConst &lc = *lp;
             float2 t, sum = ex2x2(pi.expo(0, lc.wp, lc.wt, t));
 #pragma unroll
             for (int j = 1; j < SPL; ++j) sum = add2(sum, ex2x2(pi.expo(j, lc.wp, lc.wt, t)));
             const float2 mine = fma2(lc.ray, pi.nu4, fma2(sum, lc.nsc, pi.cia(lc)));
-            out(l, add2(mine, shfl_xor2(mine, 1)));
+            out(lc, add2(mine, shfl_xor2(mine, 1)));
         }
+        l = end;
     }
 }
 

@@ -1,19 +1,18 @@
 // Fused transmission kernels (Sect. 3 opacities -> Sect. 4 chord optical
 // depth and transit depth), persistent over (sample, wavenumber-chunk) items.
 //
-// Forward, per 64-wavenumber tile: the extinction alpha[l][nu] of every
+// Forward, per 128-wavenumber tile: the extinction alpha[l][nu] of every
 // layer is interpolated into shared memory as a split BF16 pair, the chord
-// optical depth tau[i][nu] = sum_l L_il alpha_l(nu) runs on the tensor cores
-// (mma.sync m16n8k16, hi*hi + hi*lo + lo*hi, FP32 accumulation; only the
-// lower-triangular blocks of L), and the epilogue forms
-// delta(nu) - base = sum_i A_i (1 - exp(-tau_i)); exp(-tau) is optionally
-// stored for the adjoint.
+// optical depth tau[i][nu] = sum_l L_il alpha_l(nu) runs on the tcgen05
+// tensor cores (hi*hi + hi*lo + lo*hi, FP32 accumulation in TMEM), and the
+// epilogue forms delta(nu) - base = sum_i A_i (1 - exp(-tau_i)); exp(-tau) is
+// optionally stored for the adjoint.
 //
 // Backward, per tile: tau_bar = dbar A_i exp(-tau) (split BF16 in shared
-// memory), alpha_bar = L^T tau_bar on the tensor cores, the interpolation is
-// recomputed and reduced against alpha_bar (per-layer sums over wavenumber),
-// and L_bar += tau_bar alpha^T on the tensor cores, accumulated in registers
-// across the item's tiles.
+// memory), alpha_bar = L^T tau_bar on the tensor cores (into TMEM), the
+// interpolation is recomputed and reduced against alpha_bar (per-layer sums
+// over wavenumber), and L_bar += tau_bar alpha^T on the tensor cores,
+// accumulated in TMEM across the sample's tiles.
 #include <algorithm>
 
 #include "fused_common.cuh"
@@ -26,8 +25,10 @@ namespace {
 constexpr float LOG2E_F = 1.4426950408889634f;
 
 // Forward block: 16 warps, 128-wavenumber tiles; the chord product runs on
-// the tcgen05 tensor cores with the accumulator in TMEM (double-buffered so
-// the epilogue of tile t overlaps the product of tile t + 1).
+// the tcgen05 tensor cores with the accumulator in TMEM. The extinction
+// operand and the accumulator are double-buffered: tile t + 1 is
+// interpolated while the product of tile t runs, and the epilogue of tile t
+// follows the issue of tile t + 1's product (one block barrier per tile).
 constexpr int FT2 = 128;                          // wavenumbers per forward tile (the MMA's M)
 constexpr int F2_WARPS = 16;
 constexpr int F2_THREADS = F2_WARPS * 32;
@@ -38,10 +39,12 @@ constexpr int F2_TMEM_COLS = 256;                 // two 112-column accumulators
 struct TransFwdSmem {
     SampleConst sc;
     alignas(128) unsigned char lh[(LP / 8) * SBO_LP], ll[(LP / 8) * SBO_LP];    // L[i][l], split BF16
-    alignas(128) unsigned char ah[(LP / 8) * SBO_NU], al[(LP / 8) * SBO_NU];    // alpha[l][nu], split BF16
+    // alpha[l][nu], split BF16, double-buffered: tile t + 1 is interpolated
+    // while the product of tile t still reads buffer t & 1
+    alignas(128) unsigned char ah[2][(LP / 8) * SBO_NU], al[2][(LP / 8) * SBO_NU];
     float area[LP];
-    float part[4][FT2];                            // per-column-chunk partial transit sums
-    alignas(8) uint64_t mbar;
+    float part[2][4][FT2];                         // per-column-chunk partial transit sums, per buffer
+    alignas(8) uint64_t mbar[2];
     uint32_t tmem_base;
     int abort;
 };
@@ -107,12 +110,16 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, in
     // extinction rows of the padding layers stay zero
     for (int idx = threadIdx.x; idx < (LP - L) * (FT2 / 2); idx += F2_THREADS) {
         const uint32_t o = op_off(L + idx / (FT2 / 2), 2 * (idx % (FT2 / 2)), SBO_NU);
-        *reinterpret_cast<uint32_t *>(sm.ah + o) = 0u;
-        *reinterpret_cast<uint32_t *>(sm.al + o) = 0u;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            *reinterpret_cast<uint32_t *>(sm.ah[k] + o) = 0u;
+            *reinterpret_cast<uint32_t *>(sm.al[k] + o) = 0u;
+        }
     }
-    const uint32_t mbar = smem_u32(&sm.mbar);
+    const uint32_t mbar0 = smem_u32(&sm.mbar[0]);   // mbar[1] is 8 bytes above
     if (threadIdx.x == 0) {
-        mbar_init(mbar, 1);
+        mbar_init(mbar0, 1);
+        mbar_init(mbar0 + 8, 1);
         sm.abort = 0;
     }
     if (warp == 0) tmem_alloc(smem_u32(&sm.tmem_base), F2_TMEM_COLS);
@@ -124,17 +131,25 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, in
     // a wavenumber pair is shared by a lane pair splitting the species. Lane
     // half 0 stores the hi parts of its pair's extinction, half 1 the lo parts.
     const int half = lane & 1, vq = warp & 3, pair = 16 * vq + (lane >> 1), grp = warp >> 2;
-    unsigned char *const a_dst = (half ? sm.al : sm.ah) + op_off(0, 2 * pair, SBO_NU);
+    const uint32_t a_off = op_off(0, 2 * pair, SBO_NU);
     // epilogue: TMEM lane quadrant vq (wavenumber 32 vq + lane), impact parameters [28 ck, 28 ck + 28)
     const int ck = warp >> 2;
     // tau^T[nu][i] = sum_l alpha^T[nu][l] L^T[l][i]: M = 128 wavenumbers, N = 112, K = 112;
     // A = alpha (stored [l][nu]: MN-major), B = L (stored [i][l]: K-major)
     const uint32_t idesc = idesc_bf16(FT2, LP, true, false);
-    const uint32_t ah_s = smem_u32(sm.ah), al_s = smem_u32(sm.al), lh_s = smem_u32(sm.lh), ll_s = smem_u32(sm.ll);
-    uint32_t phase = 0;
+    const uint32_t lh_s = smem_u32(sm.lh), ll_s = smem_u32(sm.ll);
+    uint32_t phases = 0u;   // bit k: parity of the next completion of mbar[k]
     int issued = 0, cur_b = -1;
+    // pend: the last tile issued to the tensor cores (epilogue not yet run);
+    // spec: the tile whose epilogue ran (its spectrum written after the next barrier)
     int pend_b = -1, pend_t = 0, pend_buf = 0;
+    int spec_b = -1, spec_t = 0, spec_buf = 0;
     bool abort = false;
+    auto wait_mma = [&](int buf) {
+        if (!mbar_wait(mbar0 + 8u * (uint32_t)buf, (phases >> buf) & 1u)) sm.abort = 1;
+        phases ^= 1u << buf;
+        tc_fence_after();
+    };
 
     auto epilogue = [&](int pb, int pt, int buf) {
         const int nl = 32 * vq + lane;
@@ -160,15 +175,28 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, in
         for (int k = 0; k < 8; ++k) term(28 * ck + 16 + k, v8[k]);
 #pragma unroll
         for (int k = 0; k < 4; ++k) term(28 * ck + 24 + k, v4[k]);
-        sm.part[ck][nl] = s;
+        sm.part[buf][ck][nl] = s;
     };
-    auto write_spec = [&](int pb, int pt) {
+    auto write_spec = [&](int pb, int pt, int buf) {
         if (threadIdx.x < FT2) {
             const int n = pt * FT2 + threadIdx.x;
+            const float(*pp)[FT2] = sm.part[buf];
             if (n < N)
-                w.spec[(size_t)pb * N + n] = (sm.part[0][threadIdx.x] + sm.part[1][threadIdx.x]) +
-                                             (sm.part[2][threadIdx.x] + sm.part[3][threadIdx.x]);
+                w.spec[(size_t)pb * N + n] = (pp[0][threadIdx.x] + pp[1][threadIdx.x]) +
+                                             (pp[2][threadIdx.x] + pp[3][threadIdx.x]);
         }
+    };
+    // finish every tile in flight: its product, epilogue and spectrum
+    auto drain = [&]() {
+        if (pend_b >= 0) {
+            wait_mma(pend_buf);
+            epilogue(pend_b, pend_t, pend_buf);
+        }
+        tc_fence_before();
+        __syncthreads();
+        if (spec_b >= 0) write_spec(spec_b, spec_t, spec_buf);
+        if (pend_b >= 0) write_spec(pend_b, pend_t, pend_buf);
+        pend_b = spec_b = -1;
     };
 
     for (long long item = blockIdx.x; item < total && !abort; item += gridDim.x) {
@@ -177,15 +205,14 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, in
         const int c = (int)(item / w.B), b = (int)(item % w.B);
         if (w.kind[b] != ES_KIND_TRANSMISSION) continue;
         if (b != cur_b) {
-            if (pend_b >= 0) {   // the previous sample's last tile, before its constants are replaced
-                epilogue(pend_b, pend_t, pend_buf);
-                __syncthreads();
-                write_spec(pend_b, pend_t);
-                pend_b = -1;
+            drain();   // the previous sample's tiles, before its constants are replaced
+            if (sm.abort) {
+                abort = true;
+                break;
             }
             tc_fence_before();
             __syncthreads();
-            stage_sample(m, w, b, sm.sc, RUN_COST_FWD);
+            stage_sample(m, w, b, sm.sc, RUN_COST_FWD, SBO_NU);
             stage_lmat_tc(m, w, b, sm.lh, sm.ll, sm.area);
             cur_b = b;
             fence_async_smem();
@@ -194,20 +221,31 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, in
         const int t1 = min(ntiles, (c + 1) * chunk_tiles);
         for (int t = c * chunk_tiles; t < t1; ++t) {
             const int nt0 = t * FT2;
-            extinction_pair<SPL>(m, sm.sc, sm.sc.gb[grp], sm.sc.gb[grp + 1], nt0 + 2 * pair, half, [&](int l, float2 a) {
+            const int buf = issued & 1;
+            unsigned char *const a_dst = (half ? sm.al[buf] : sm.ah[buf]) + a_off;
+            extinction_pair<SPL>(m, sm.sc, sm.sc.gb[grp], sm.sc.gb[grp + 1], nt0 + 2 * pair, half, [&](const LayerConst &lc, float2 a) {
                 uint32_t hi, lo;
                 split2(a, hi, lo);
-                *reinterpret_cast<uint32_t *>(a_dst + (l >> 3) * SBO_NU + (l & 7) * 16) = half ? lo : hi;
+                *reinterpret_cast<uint32_t *>(a_dst + lc.aoff) = half ? lo : hi;
             });
             fence_async_smem();
+            tc_fence_before();
             __syncthreads();
-            const int buf = issued & 1;
+            if (sm.abort) {
+                abort = true;
+                break;
+            }
+            if (spec_b >= 0) {   // its epilogue ran in every warp before this barrier
+                write_spec(spec_b, spec_t, spec_buf);
+                spec_b = -1;
+            }
             if (threadIdx.x == 12 * 32) {   // warp 12's epilogue share is the lightest: 7 k-steps x 3 split terms
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(buf * 128);
                 // descriptors of k-step 0; a k-step advances the start address field
                 // (bits 0-13, 16-byte units) by 2 row groups of alpha / 2 cores of L
-                const uint64_t a_h = desc_mn_major(ah_s, SBO_NU), a_l = desc_mn_major(al_s, SBO_NU);
+                const uint64_t a_h = desc_mn_major(smem_u32(sm.ah[buf]), SBO_NU);
+                const uint64_t a_l = desc_mn_major(smem_u32(sm.al[buf]), SBO_NU);
                 const uint64_t b_h = desc_k_major(lh_s, SBO_LP), b_l = desc_k_major(ll_s, SBO_LP);
 #pragma unroll
                 for (int k = 0; k < LP / 16; ++k) {
@@ -216,30 +254,26 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, in
                     tc_mma(d, a_h + da, b_l + db, idesc, true);
                     tc_mma(d, a_l + da, b_h + db, idesc, true);
                 }
-                tc_commit(mbar);
+                tc_commit(mbar0 + 8u * (uint32_t)buf);
             }
-            if (pend_b >= 0) epilogue(pend_b, pend_t, pend_buf);   // overlaps the product just issued
-            tc_fence_before();
-            if (!mbar_wait(mbar, phase)) sm.abort = 1;
-            phase ^= 1;
-            tc_fence_after();
-            __syncthreads();
-            if (sm.abort) {
-                abort = true;
-                break;
+            // the previous tile: its product was issued a whole interpolation
+            // ago; its epilogue overlaps the product just issued. The wait also
+            // frees that tile's alpha buffer for the next interpolation.
+            if (pend_b >= 0) {
+                wait_mma(pend_buf);
+                epilogue(pend_b, pend_t, pend_buf);
+                spec_b = pend_b;
+                spec_t = pend_t;
+                spec_buf = pend_buf;
             }
-            if (pend_b >= 0) write_spec(pend_b, pend_t);
             pend_b = b;
             pend_t = t;
             pend_buf = buf;
             ++issued;
         }
     }
-    if (pend_b >= 0 && !abort) {
-        epilogue(pend_b, pend_t, pend_buf);
-        __syncthreads();
-        write_spec(pend_b, pend_t);
-    }
+    if (!abort) drain();
+    if (sm.abort) abort = true;
     if (abort && threadIdx.x == 0) atomicOr(w.err, 1);
     tc_fence_before();
     __syncthreads();
@@ -402,7 +436,7 @@ __device__ void interp_backward(const Model &m, const SampleConst &sc, int lb, i
             const float2 alpha = add2(mine, shfl_xor2(mine, 1));
             uint32_t hi, lo;
             split2(alpha, hi, lo);
-            *reinterpret_cast<uint32_t *>(a_dst + (l >> 3) * SBO_NU + (l & 7) * 16) = half ? lo : hi;
+            *reinterpret_cast<uint32_t *>(a_dst + lc.aoff) = half ? lo : hi;
         }
     }
     if (!waited) wait_abar();   // empty layer group
@@ -535,7 +569,7 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
             }
             tc_fence_before();
             __syncthreads();
-            stage_sample(m, w, b, sm.sc, RUN_COST_BWD);
+            stage_sample(m, w, b, sm.sc, RUN_COST_BWD, SBO_NU);
             stage_lmat_tc(m, w, b, sm.lh, sm.ll, sm.area);
             for (int idx = threadIdx.x; idx < L * N_RED; idx += BW_THREADS) sm.red[idx] = 0.f;
             for (int i = threadIdx.x; i < LP; i += BW_THREADS) sm.area_acc[i] = 0.f;
