@@ -232,8 +232,11 @@ __device__ __forceinline__ void extinction_pair(const Model &m, const SampleCons
                                                 int half, Out &&out) {
     PairInterp<SPL> pi;
     pi.init(m, n, half, threadIdx.x & 31);
+    // loop bounds broadcast from lane 0: provably warp-uniform for the compiler
+    lb = __shfl_sync(0xffffffffu, lb, 0);
+    le = __shfl_sync(0xffffffffu, le, 0);
     for (int l = lb; l < le;) {
-        const int end = min(sc.lay[l].run_end, le);
+        const int end = __shfl_sync(0xffffffffu, min(sc.lay[l].run_end, le), 0);
         pi.load(sc, sc.lay[l].cell, sc.lay[l].itc);
         if (end < le) pi.prefetch(sc.lay[end].cell, sc.lay[end].itc);
         const LayerConst *lp = &sc.lay[l], *const lend = &sc.lay[end];

@@ -398,8 +398,11 @@ __device__ void interp_backward(const Model &m, const SampleConst &sc, int lb, i
 #pragma unroll
     for (int j = 0; j < SPL; ++j) qa[j] = f2(0.f);
     bool waited = false;
+    // loop bounds broadcast from lane 0: provably warp-uniform for the compiler
+    lb = __shfl_sync(0xffffffffu, lb, 0);
+    le = __shfl_sync(0xffffffffu, le, 0);
     for (int l = lb; l < le;) {
-        const int end = min(sc.lay[l].run_end, le);
+        const int end = __shfl_sync(0xffffffffu, min(sc.lay[l].run_end, le), 0);
         pi.load(sc, sc.lay[l].cell, sc.lay[l].itc);
         if (end < le) pi.prefetch(sc.lay[end].cell, sc.lay[end].itc);
         if (!waited) {   // the first coefficient loads are in flight while the alpha_bar product completes
