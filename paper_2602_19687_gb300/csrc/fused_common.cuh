@@ -47,8 +47,9 @@ __device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
 // x = hi + lo with hi, lo BF16 (hi round-to-nearest, lo the rounded residual)
 __device__ __forceinline__ void split2(float2 x, uint32_t &hi, uint32_t &lo) {
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(x.y), "f"(x.x));
-    float hx = __uint_as_float(hi << 16), hy = __uint_as_float(hi & 0xffff0000u);
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(x.y - hy), "f"(x.x - hx));
+    const float2 h = make_float2(__uint_as_float(hi << 16), __uint_as_float(hi & 0xffff0000u));
+    const float2 r = fma2(h, f2(-1.f), x);   // x - hi, exact
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(r.y), "f"(r.x));
 }
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));

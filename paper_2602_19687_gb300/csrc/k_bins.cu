@@ -2,9 +2,10 @@
 // and the Gaussian log-likelihood of Sect. 2.3,
 //   ln L = sum_k [-ln s_k - 1/2 ln 2 pi - 1/2 (r_k/s_k)^2],
 //   r_k = y_obs,k - y_k, s_k^2 = sigma_k^2 + 10^(2c) (Eq. c_error),
-// in FP64, one block per sample and one warp per bin. With the adjoint
-// requested it also writes
-// d lnL / d spectrum (dbar) and the base / error-inflation adjoints.
+// in FP64, one block per sample: bin sums with one warp per bin, the
+// likelihood terms with one thread per bin. With the adjoint requested it
+// also writes d lnL / d spectrum (dbar) and the base / error-inflation
+// adjoints.
 #include "internal.cuh"
 
 namespace es {
@@ -38,25 +39,33 @@ __global__ void __launch_bounds__(BIN_THREADS) k_bins(Model m, Work w, int adjoi
     const double infl = exp10(2.0 * c);
     const float *sp = w.spec + (size_t)b * N;
     const double *yo = m.y_obs + (size_t)kind * m.nbins, *sg = m.sigma + (size_t)kind * m.nbins;
-    // one warp per bin: coalesced reads of its native points, FP64 sums
+    // bin means: one warp per bin, coalesced reads of its native points, FP64 sums
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double lsum = 0.0, cbar = 0.0, bbar = 0.0;
+    double *ym = w.ymod + (size_t)b * m.nbins;
+    // (FP32 partial sums of at most 32 points per lane group, FP64 for the
+    // last two combining stages: GB300's FP64 rate is a small fraction of FP32)
     for (int k = warp; k < m.nbins; k += BIN_THREADS / 32) {
         const int lo = m.bin_lo[k], hi = m.bin_hi[k];
-        double acc = 0.0;
-        for (int n = lo + lane; n < hi; n += 32) acc += (double)sp[n];
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) {
-            const double y = base + acc / (double)(hi - lo);
-            if (!isfinite(y)) s_bad = 1;
-            w.ymod[(size_t)b * m.nbins + k] = y;
-            if (binned_out) binned_out[(size_t)b * m.nbins + k] = y;
-            const double se2 = sg[k] * sg[k] + infl;
-            const double r = yo[k] - y;
-            lsum += -0.5 * log(se2) - 0.5 * log(2.0 * PI) - 0.5 * r * r / se2;
-            cbar += (-0.5 / se2 + 0.5 * r * r / (se2 * se2)) * 2.0 * LN10 * infl;
-            bbar += r / se2;
-        }
+        float acc = 0.f;
+        for (int n = lo + lane; n < hi; n += 32) acc += sp[n];
+        for (int o = 16; o > 2; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        double d = (double)acc;
+        for (int o = 2; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if (lane == 0) ym[k] = d;   // the bin sum; its mean is formed below
+    }
+    __syncthreads();
+    // likelihood terms: one thread per bin
+    double lsum = 0.0, cbar = 0.0, bbar = 0.0;
+    for (int k = threadIdx.x; k < m.nbins; k += BIN_THREADS) {
+        const double y = base + ym[k] / (double)(m.bin_hi[k] - m.bin_lo[k]);
+        ym[k] = y;
+        if (!isfinite(y)) s_bad = 1;
+        if (binned_out) binned_out[(size_t)b * m.nbins + k] = y;
+        const double se2 = sg[k] * sg[k] + infl;
+        const double r = yo[k] - y;
+        lsum += -0.5 * log(se2) - 0.5 * log(2.0 * PI) - 0.5 * r * r / se2;
+        cbar += (-0.5 / se2 + 0.5 * r * r / (se2 * se2)) * 2.0 * LN10 * infl;
+        bbar += r / se2;
     }
     lsum = block_sum_d(lsum, scratch);
     cbar = block_sum_d(cbar, scratch);
@@ -78,8 +87,7 @@ __global__ void __launch_bounds__(BIN_THREADS) k_bins(Model m, Work w, int adjoi
         // d lnL / d spec(n) = (y_obs - y_k) / s_k^2 / n_k for n in bin k
         for (int k = warp; k < m.nbins; k += BIN_THREADS / 32) {
             const int lo = m.bin_lo[k], hi = m.bin_hi[k];
-            const double se2 = sg[k] * sg[k] + infl;
-            const float g = (float)((yo[k] - w.ymod[(size_t)b * m.nbins + k]) / se2 / (double)(hi - lo));
+            const float g = (float)(yo[k] - ym[k]) / (float)(sg[k] * sg[k] + infl) / (float)(hi - lo);
             for (int n = lo + lane; n < hi; n += 32) w.dbar[(size_t)b * m.Np + n] = g;
         }
     }

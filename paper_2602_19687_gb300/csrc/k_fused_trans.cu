@@ -69,7 +69,9 @@ struct TransBwdSmem {
     alignas(128) unsigned char ah[(LB_ROWS / 8) * SBO_NU], al[(LB_ROWS / 8) * SBO_NU];   // alpha[l][nu]
     float area[LP];
     float area_acc[LP];                                 // area_bar of the current sample
-    float red[ES_MAX_LAYERS * N_RED];                   // per-layer reductions of the current sample
+    // per-layer reductions of the current sample: 8 slots (value, lane parity)
+    // x 4 partial sums (one per lane-bit pair b2 b1), summed at the flush
+    float red[ES_MAX_LAYERS * 32];
     float qtot[ES_MAX_SPECIES];                         // per-species totals of the current sample
     alignas(8) uint64_t mbar_a, mbar_l;
     uint32_t tmem_base;
@@ -345,10 +347,11 @@ __device__ __forceinline__ int reduce_index8(int lane) {
     return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
 }
 
-// Warp reduction of 4 values per lane that keeps the two lane parities
-// apart: on return lane holds the sum of v[2 b4 + b3] over the 16 lanes of its
-// parity (bk = bit k of the lane).
-__device__ __forceinline__ float reduce4_parity(const float (&v)[4], int lane) {
+// Two transpose stages of a warp reduction of 4 values per lane: lane holds
+// the sum of v[2 b4 + b3] over the 4 lanes that differ from it in bits 4 and 3
+// (bk = bit k of the lane); the remaining sums over bits 2 and 1 (the lane
+// parity, bit 0, stays apart) are left to the shared-memory accumulation.
+__device__ __forceinline__ float reduce4_partial(const float (&v)[4], int lane) {
     float a[2];
     {
         const bool up = lane & 16;
@@ -357,10 +360,7 @@ __device__ __forceinline__ float reduce4_parity(const float (&v)[4], int lane) {
             a[k] = (up ? v[k + 2] : v[k]) + __shfl_xor_sync(0xffffffffu, up ? v[k] : v[k + 2], 16);
     }
     const bool up = lane & 8;
-    float e = (up ? a[1] : a[0]) + __shfl_xor_sync(0xffffffffu, up ? a[0] : a[1], 8);
-    e += __shfl_xor_sync(0xffffffffu, e, 4);
-    e += __shfl_xor_sync(0xffffffffu, e, 2);
-    return e;
+    return (up ? a[1] : a[0]) + __shfl_xor_sync(0xffffffffu, up ? a[0] : a[1], 8);
 }
 
 // One TMEM column of this warp's lane quadrant: thread i <- lane i. The
@@ -375,23 +375,25 @@ __device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
 // Backward interpolation for one warp: layers [lb, le), wavenumber pair n, n+1
 // shared by the lane pair (lane, lane ^ 1) that splits the species. Reads
 // alpha_bar from TMEM (`abar_t`: column 0 of the warp's lane quadrant, lane =
-// wavenumber), adds per-layer reductions to red[l][*] and per-species totals
-// to qtot[s], and writes the extinction as split BF16 into the alpha operand
-// (`a_dst`: row 0 at this lane's column, hi for half 0, lo for half 1).
-// Per layer, summed over wavenumber, with lane half h's species and CIA pair
-// h: QS_h = sum abar n sum_s e_s, D_h = sum abar n sum_s e_s dlog2(sigma_s)/
-// dlog10 T, C_h = sum abar c_h, CT_h = sum abar c_h dlog2 k_h/dT (red slots
-// 0/1, 2/3, 4/5, 6/7 for h = 0/1); per species Q_s = sum_l sum abar n e_s.
-// The Rayleigh sum over wavenumber comes from the L_bar product.
+// wavenumber), adds per-layer partial reductions to red[l][32] and
+// per-species totals to qtot[s], and writes the extinction as split BF16 into
+// the alpha operand (`a_dst`: row 0 at this lane's column, hi for half 0, lo
+// for half 1). Per layer, summed over wavenumber, with lane half h's species
+// and CIA pair h: QS_h = sum abar n sum_s e_s, D_h = sum abar n sum_s e_s
+// dlog2(sigma_s)/dw_T, C_h = sum abar c_h, CT_h = sum abar c_h dlog2 k_h/dw_Tc
+// (slots 0/1, 2/3, 4/5, 6/7 for h = 0/1, each as 4 partial sums; the flush
+// adds them and applies the per-layer weight slopes gts, gtcs); per species
+// Q_s = sum_l sum abar n e_s. The Rayleigh sum over wavenumber comes from the
+// L_bar product.
 template <int SPL, class Wait>
 __device__ void interp_backward(const Model &m, const SampleConst &sc, int lb, int le, int n, int half, int lane,
                                 uint32_t abar_t, unsigned char *a_dst, float *red, float *qtot, Wait &&wait_abar) {
     const int S = m.S;
     const int ridx = reduce_index8(lane);
     const bool writer = (lane & 3) == 0;
-    // after reduce4_parity: lanes with bits 2, 1 clear write slot 2 (2 b4 + b3) + b0
-    const bool rwriter = (lane & 6) == 0;
-    const int rslot = 2 * (2 * ((lane >> 4) & 1) + ((lane >> 3) & 1)) + (lane & 1);
+    // after the two transpose stages every lane holds a distinct partial sum:
+    // slot 2 (2 b4 + b3) + b0, partial (b2 b1); one atomic per lane, no branch
+    const int rslot = 4 * (2 * (2 * ((lane >> 4) & 1) + ((lane >> 3) & 1)) + (lane & 1)) + ((lane >> 1) & 3);
     PairInterp<SPL> pi;
     pi.init(m, n, half, lane);
     float2 qa[SPL];
@@ -430,11 +432,10 @@ __device__ void interp_backward(const Model &m, const SampleConst &sc, int lb, i
             const float2 act = mul2(ac, pi.d);
             float v[4];
             v[0] = fmaf(abn.x, sum.x, abn.y * sum.y);
-            v[1] = fmaf(abn.x, pt.x, abn.y * pt.y) * lc.gts;
+            v[1] = fmaf(abn.x, pt.x, abn.y * pt.y);   // x gts at the flush
             v[2] = ac.x + ac.y;
-            v[3] = (act.x + act.y) * lc.gtcs;
-            const float tot = reduce4_parity(v, lane);
-            if (rwriter) atomicAdd(red + l * N_RED + rslot, tot);
+            v[3] = act.x + act.y;                     // x gtcs at the flush
+            atomicAdd(red + l * 32 + rslot, reduce4_partial(v, lane));
             const float2 mine = fma2(lc.ray, pi.nu4, fma2(sum, lc.nsc, c));
             const float2 alpha = add2(mine, shfl_xor2(mine, 1));
             uint32_t hi, lo;
@@ -536,9 +537,13 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
         }
         tc_fence_before();
         __syncthreads();
-        for (int idx = threadIdx.x; idx < L * N_RED; idx += BW_THREADS) {
-            const float v = sm.red[idx];
-            if (v != 0.f) atomicAdd(w.red + (size_t)b * L * N_RED + idx, (double)v);
+        for (int idx = threadIdx.x; idx < L * 8; idx += BW_THREADS) {
+            const int l = idx >> 3, s = idx & 7;
+            const float *q = sm.red + l * 32 + 4 * s;
+            float v = (q[0] + q[1]) + (q[2] + q[3]);
+            if (s == 2 || s == 3) v *= sm.sc.lay[l].gts;   // D: d/dlog10 T of the species exponents
+            if (s >= 6) v *= sm.sc.lay[l].gtcs;            // CT: of the CIA exponents
+            if (v != 0.f) atomicAdd(w.red + ((size_t)b * L + l) * N_RED + s, (double)v);
         }
         for (int i = threadIdx.x; i < L; i += BW_THREADS)
             if (sm.area_acc[i] != 0.f) atomicAdd(w.areabar + (size_t)b * L + i, (double)sm.area_acc[i]);
@@ -574,7 +579,7 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
             __syncthreads();
             stage_sample(m, w, b, sm.sc, RUN_COST_BWD, SBO_NU);
             stage_lmat_tc(m, w, b, sm.lh, sm.ll, sm.area);
-            for (int idx = threadIdx.x; idx < L * N_RED; idx += BW_THREADS) sm.red[idx] = 0.f;
+            for (int idx = threadIdx.x; idx < L * 32; idx += BW_THREADS) sm.red[idx] = 0.f;
             for (int i = threadIdx.x; i < LP; i += BW_THREADS) sm.area_acc[i] = 0.f;
             for (int s2 = threadIdx.x; s2 < ES_MAX_SPECIES; s2 += BW_THREADS) sm.qtot[s2] = 0.f;
             cur_b = b;
