@@ -371,13 +371,12 @@ def run_gpu(args):
                                     "derived from unit counts x median SM clock %.0f MHz" % sm_mhz),
                     "nominal_peak": alu_peak(unit_kind, sm_mhz) / scale if alu_peak(unit_kind, sm_mhz) else None}
 
-    # ---- plain per-sample path (batched vs plain)
-    plain = None
-    if not args.no_plain and rank == 0:
-        wp = synth.workload("jwst_plain")
+    # ---- plain per-sample path (batched vs plain): the plain JWST-shaped
+    # workload, and the batched workload itself one vector per call
+    def plain_ms(wp, theta_row, kind_row):
         cp = binding.context_for(wp, device=local)
-        thp = torch.tensor(wp.theta, dtype=torch.float64, device=dev)
-        cp.es_set_batch(thp)
+        thp = torch.tensor(theta_row, dtype=torch.float64, device=dev)
+        cp.es_set_batch(thp, torch.tensor(kind_row, dtype=torch.int32, device=dev))
         lp = torch.empty(1, dtype=torch.float64, device=dev)
         gp = torch.empty_like(thp)
         for _ in range(3):
@@ -390,10 +389,19 @@ def run_gpu(args):
             cp.es_forward_backward(lp, gp)
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        pms = e0.elapsed_time(e1) / reps
+        cp.es_destroy()
+        return e0.elapsed_time(e1) / reps
+
+    plain = plain_same = None
+    if not args.no_plain and rank == 0:
+        wp = synth.workload("jwst_plain")
+        pms = plain_ms(wp, wp.theta, wp.kind)
         plain = {"value": 1e3 / pms, "unit": UNIT, "ms_per_spectrum": pms,
                  "workload": "jwst_plain: " + wp.description + " (one vector per call, forward+gradient)"}
-        cp.es_destroy()
+        pms = plain_ms(w, w.theta[:1], w.kind[:1])
+        plain_same = {"value": 1e3 / pms, "unit": UNIT, "ms_per_spectrum": pms,
+                      "workload": args.workload + ": " + w.description +
+                      " (one vector per call, forward+gradient)"}
 
     extra = None
     if rank == 0 and not args.no_extra:
@@ -419,6 +427,8 @@ def run_gpu(args):
             "kernels": per_kernel,
             "plain": plain,
             "batched_over_plain": (value / world / plain["value"]) if plain else None,
+            "plain_same_workload": plain_same,
+            "batched_over_plain_same_workload": (value / world / plain_same["value"]) if plain_same else None,
             "cpu_baseline": cpu,
             "other_workloads": extra,
             "clocks": clk,

@@ -161,22 +161,28 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, in
         tmem_ld8(taddr + 16, v8);
         tmem_ld4(taddr + 24, v4);
         tmem_wait_ld();
-        float *eb = w.estore + (size_t)pb * L * m.Np + (size_t)pt * FT2 + nl;
-        float s = 0.f;
-        auto term = [&](int i, float tau) {
-            if (i < L) {
-                const float e = ex2f(-tau * LOG2E_F);
-                s = fmaf(sm.area[i], 1.f - e, s);
-                // streaming store: keep the opacity coefficients, not these, in L2
-                if (STORE_E) __stcs(eb + (size_t)i * m.Np, e);
+        // exp(-tau) store, tile-contiguous: [vector][tile][impact parameter][128 nu]
+        float *eb = w.estore + (((size_t)pb * ntiles + pt) * L + 28 * ck) * FT2 + nl;
+        float2 s2 = f2(0.f);
+        // terms i0 = 28 ck + k and i0 + 1 in packed pairs; area[i] = 0 beyond L
+        auto term2 = [&](int k, float t0, float t1) {
+            const int i0 = 28 * ck + k;
+            const float2 e = ex2x2(mul2(make_float2(t0, t1), f2(-LOG2E_F)));
+            const float2 a = *reinterpret_cast<const float2 *>(&sm.area[i0]);
+            s2 = fma2(a, fma2(e, f2(-1.f), f2(1.f)), s2);
+            // streaming stores: keep the opacity coefficients, not these, in L2
+            if (STORE_E) {
+                if (i0 < L) __stcs(eb + k * FT2, e.x);
+                if (i0 + 1 < L) __stcs(eb + (k + 1) * FT2, e.y);
             }
         };
 #pragma unroll
-        for (int k = 0; k < 16; ++k) term(28 * ck + k, v16[k]);
+        for (int k = 0; k < 16; k += 2) term2(k, v16[k], v16[k + 1]);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) term(28 * ck + 16 + k, v8[k]);
+        for (int k = 0; k < 8; k += 2) term2(16 + k, v8[k], v8[k + 1]);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) term(28 * ck + 24 + k, v4[k]);
+        for (int k = 0; k < 4; k += 2) term2(24 + k, v4[k], v4[k + 1]);
+        const float s = s2.x + s2.y;
         sm.part[buf][ck][nl] = s;
     };
     auto write_spec = [&](int pb, int pt, int buf) {
@@ -558,7 +564,7 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
     auto prefetch_tile = [&](int pb, int pt) {
         const int row = threadIdx.x >> 2, line = threadIdx.x & 3;
         const float *src = nullptr;
-        if (row < L) src = w.estore + ((size_t)pb * L + row) * m.Np + (size_t)pt * BT + 32 * line;
+        if (row < L) src = w.estore + (((size_t)pb * ntiles + pt) * L + row) * BT + 32 * line;
         else if (row == L) src = w.dbar + (size_t)pb * m.Np + (size_t)pt * BT + 32 * line;
         if (src) asm volatile("prefetch.global.L2 [%0];" ::"l"(src));
     };
@@ -602,12 +608,12 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
             const int col = 2 * (lane + 32 * (warp & 1));
             const int nl = nt0 + col;
             const float2 db = *reinterpret_cast<const float2 *>(w.dbar + (size_t)b * m.Np + nl);
-            const float *eb = w.estore + (size_t)b * L * m.Np + nl;
+            const float *eb = w.estore + ((size_t)b * ntiles + t) * L * BT + col;
             float2 ev[14];
 #pragma unroll
             for (int k = 0; k < 14; ++k) {
                 const int i = group + 8 * k;
-                ev[k] = (i < L) ? *reinterpret_cast<const float2 *>(eb + (size_t)i * m.Np) : make_float2(1.f, 1.f);
+                ev[k] = (i < L) ? *reinterpret_cast<const float2 *>(eb + i * BT) : make_float2(1.f, 1.f);
             }
             wait_lbar();
             // Rayleigh weight row w(nu) of the alpha operand
