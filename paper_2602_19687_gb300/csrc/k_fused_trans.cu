@@ -378,6 +378,15 @@ __device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
     return __uint_as_float(r);
 }
 
+// Split TMEM load of one column of this warp's lane quadrant: the issue, and
+// the wait that binds the value (no use may be scheduled before it).
+__device__ __forceinline__ void tmem_issue1(uint32_t taddr, uint32_t &r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr) : "memory");
+}
+__device__ __forceinline__ void tmem_wait1(uint32_t &r) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r)::"memory");
+}
+
 // Backward interpolation for one warp: layers [lb, le), wavenumber pair n, n+1
 // shared by the lane pair (lane, lane ^ 1) that splits the species. Reads
 // alpha_bar from TMEM (`abar_t`: column 0 of the warp's lane quadrant, lane =
@@ -406,6 +415,7 @@ __device__ void interp_backward(const Model &m, const SampleConst &sc, int lb, i
 #pragma unroll
     for (int j = 0; j < SPL; ++j) qa[j] = f2(0.f);
     bool waited = false;
+    uint32_t nxt = 0u;   // alpha_bar of the next layer: its TMEM load runs during the current layer
     // loop bounds broadcast from lane 0: provably warp-uniform for the compiler
     lb = __shfl_sync(0xffffffffu, lb, 0);
     le = __shfl_sync(0xffffffffu, le, 0);
@@ -416,10 +426,18 @@ __device__ void interp_backward(const Model &m, const SampleConst &sc, int lb, i
         if (!waited) {   // the first coefficient loads are in flight while the alpha_bar product completes
             wait_abar();
             waited = true;
+            tmem_issue1(abar_t + (uint32_t)l, nxt);
         }
-        for (; l < end; ++l) {
-            const LayerConst &lc = sc.lay[l];
-            const float own = tmem_ld1(abar_t + (uint32_t)l);
+        const LayerConst *lp = &sc.lay[l], *const lend = &sc.lay[end];
+        float *rp = red + l * 32 + rslot;
+        uint32_t ta = abar_t + (uint32_t)l;
+        for (; lp != lend; ++lp, rp += 32, ++ta) {
+            const LayerConst &lc = *lp;
+            tmem_wait1(nxt);
+            const float own = __uint_as_float(nxt);
+            // the next column, unconditionally (column le is inside the
+            // allocation; its value is never used)
+            tmem_issue1(ta + 1u, nxt);
             const float other = __shfl_xor_sync(0xffffffffu, own, 1);
             const float2 ab = half ? make_float2(other, own) : make_float2(own, other);
             const float2 abn = mul2(ab, lc.nsc);
@@ -441,15 +459,17 @@ __device__ void interp_backward(const Model &m, const SampleConst &sc, int lb, i
             v[1] = fmaf(abn.x, pt.x, abn.y * pt.y);   // x gts at the flush
             v[2] = ac.x + ac.y;
             v[3] = act.x + act.y;                     // x gtcs at the flush
-            atomicAdd(red + l * 32 + rslot, reduce4_partial(v, lane));
+            atomicAdd(rp, reduce4_partial(v, lane));
             const float2 mine = fma2(lc.ray, pi.nu4, fma2(sum, lc.nsc, c));
             const float2 alpha = add2(mine, shfl_xor2(mine, 1));
             uint32_t hi, lo;
             split2(alpha, hi, lo);
             *reinterpret_cast<uint32_t *>(a_dst + lc.aoff) = half ? lo : hi;
         }
+        l = end;
     }
     if (!waited) wait_abar();   // empty layer group
+    else tmem_wait1(nxt);       // the load issued past the last layer
     // per-species totals: slot j of lane half h is species SPL h + j
 #pragma unroll
     for (int c0 = 0; c0 < 2 * SPL; c0 += 8) {
