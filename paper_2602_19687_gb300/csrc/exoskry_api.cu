@@ -756,7 +756,7 @@ es_status enqueue_forward_backward(es_ctx *c, cudaStream_t st) {
     cudaMemsetAsync(w.areabar, 0, sizeof(double) * B * L, st);
     cudaMemsetAsync(w.levbar, 0, sizeof(double) * B * (L + 1), st);
     cudaMemsetAsync(w.drbar, 0, sizeof(double) * B * L, st);
-    cudaMemsetAsync(w.lbar, 0, sizeof(double) * B * L * L, st);
+    cudaMemsetAsync(w.lbar, 0, sizeof(float) * B * L * L, st);
     es_status s = run_forward(c, true, nullptr, nullptr, c->d_lnl, st);
     if (s != ES_OK) return s;
     int launches = (int)c->last_launches;

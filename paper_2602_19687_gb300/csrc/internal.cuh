@@ -108,7 +108,7 @@ struct Work {
     // adjoint
     float *dbar;                  // [B][Np] d lnL / d spec (zero beyond N)
     float *estore;                // [B][L][Np] exp(-tau) of the forward (transmission adjoint)
-    double *lbar;                 // [B][L][L]
+    float *lbar;                  // [B][L][L] (FP32 atomics: one partial per work item)
     double *red;                  // [B][L][N_RED]
     double *qtot;                 // [B][S] per-species reductions summed over layers
     double *zbar;                 // [B][L] transmission: sum_nu tau_bar_i(nu) (nu/nu_ref)^4

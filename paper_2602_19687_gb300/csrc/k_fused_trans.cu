@@ -542,9 +542,10 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
         }
     };
     auto flush = [&](int b) {
-        // L_bar (TMEM: lane i, column 128 + l) and z, the reductions, per-species
+        // L_bar (TMEM: lane i, column 128 + l; FP32 atomics) and z, the reductions, per-species
         // totals and area_bar of sample b, by FP64 atomics
-        double *lbar = w.lbar + (size_t)b * L * L, *zbar = w.zbar + (size_t)b * L;
+        float *lbar = w.lbar + (size_t)b * L * L;
+        double *zbar = w.zbar + (size_t)b * L;
         const int ck = warp >> 2, ii = 32 * vq + lane;
         float v0[16], v1[16];
         const uint32_t ta = tmem + (uint32_t)(128 + 32 * ck) + ((uint32_t)(32 * vq) << 16);
@@ -558,7 +559,7 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
                 const float v = j < 16 ? v0[j] : v1[j - 16];
                 if (v == 0.f) continue;
                 if (ll == L) atomicAdd(zbar + ii, (double)v);
-                else if (ll <= ii) atomicAdd(lbar + (size_t)ii * L + ll, (double)v);
+                else if (ll <= ii) atomicAdd(lbar + (size_t)ii * L + ll, v);
             }
         }
         tc_fence_before();

@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup_bwd(Model m, Work w) {
     __shared__ double xbar[ES_MAX_SPECIES + 2], xs[ES_MAX_SPECIES + 2];
     __shared__ double thv[ES_MAX_PARAMS];
     __shared__ double rcbar;
-    __shared__ float tlf[ES_MAX_LAYERS];
+    __shared__ float tlf[ES_MAX_LAYERS], zf[ES_MAX_LAYERS];
     // temperature tangents dT/dtheta_p at layers and (emission) levels
     __shared__ float dtl[ES_MAX_PARAMS][ES_MAX_LAYERS], dtv[ES_MAX_PARAMS][ES_MAX_LAYERS + 1];
     __shared__ SplitRadii q;
@@ -212,13 +212,13 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup_bwd(Model m, Work w) {
         // impact-parameter terms (to r_i, r_{i+1}), per column l the terms of
         // the layer's own radii (to r_l, r_{l+1}); one shared atomic per sum.
         // Terms in FP32 (1/s_d - 1/s_u without cancellation), sums in FP64.
-        const double *lbar = w.lbar + (size_t)b * L * L;
+        const float *lbar = w.lbar + (size_t)b * L * L;
         for (int i = tid; i < L; i += blockDim.x) {
             const float bi = q.bh[i];
             double dsum = 0.0;
             for (int l = 0; l <= i; ++l) {
-                const double lb = lbar[(size_t)i * L + l];
-                if (lb == 0.0) continue;
+                const float lb = lbar[(size_t)i * L + l];
+                if (lb == 0.f) continue;
                 const float u = chord_sq(q, l, i), ru = rsqrtf(u);
                 float t;
                 if (l < i) {
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup_bwd(Model m, Work w) {
                 } else {
                     t = -2.f * bi * ru;
                 }
-                dsum += lb * (double)t;
+                dsum += (double)(lb * t);
             }
             atomicAdd(&rbar[i], 0.5 * dsum);
             atomicAdd(&rbar[i + 1], 0.5 * dsum);
@@ -237,10 +237,10 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup_bwd(Model m, Work w) {
             double up = 0.0, dn = 0.0;
             const float r0 = 2.f * q.rh[l], r1 = 2.f * q.rh[l + 1];
             for (int i = l; i < L; ++i) {
-                const double lb = lbar[(size_t)i * L + l];
-                if (lb == 0.0) continue;
-                up += lb * (double)(r0 * rsqrtf(chord_sq(q, l, i)));
-                if (l < i) dn += lb * (double)(r1 * rsqrtf(chord_sq(q, l + 1, i)));
+                const float lb = lbar[(size_t)i * L + l];
+                if (lb == 0.f) continue;
+                up += (double)(lb * r0 * rsqrtf(chord_sq(q, l, i)));
+                if (l < i) dn += (double)(lb * r1 * rsqrtf(chord_sq(q, l + 1, i)));
             }
             atomicAdd(&rbar[l], up);
             atomicAdd(&rbar[l + 1], -dn);
@@ -265,24 +265,37 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup_bwd(Model m, Work w) {
     }
     // extinction reductions -> layer temperature and VMR adjoints
     if (!bad && tid < S) atomicAdd(&xbar[tid], w.qtot[(size_t)b * S + tid] / xs[tid]);
+    if (!emis && !bad)
+        for (int i = tid; i < L; i += blockDim.x) zf[i] = (float)w.zbar[(size_t)b * L + i];
+    __syncthreads();
+    double xh = 0.0, xe = 0.0;   // this thread's part of xbar[S], xbar[S + 1]
     for (int l = tid; l < L; l += blockDim.x) {
         const double *rd = w.red + ((size_t)b * L + l) * N_RED;
         double n = w.n_lay[(size_t)b * L + l], t = w.t_lay[(size_t)b * L + l];
         const double qsum = rd[0] + rd[1];
         double dd = rd[2] + rd[3], c1 = rd[4], c2 = rd[5], c1t = rd[6], c2t = rd[7], w4 = rd[8];
-        if (!emis && !bad) {   // W4_l = sum_nu alpha_bar_l w = sum_i L_il z_i
+        if (!emis && !bad) {   // W4_l = sum_nu alpha_bar_l w = sum_i L_il z_i (FP32 products)
             const float *lm = w.lmat + (size_t)b * L * L + l;
-            const double *z = w.zbar + (size_t)b * L;
-            for (int i = 0; i < L; ++i) w4 += (double)lm[(size_t)i * L] * z[i];
+            float a = 0.f;
+            for (int i = l; i < L; ++i) a = fmaf(lm[(size_t)i * L], zf[i], a);
+            w4 += (double)a;
         }
         double nbar = 0.0, tb = 0.0;
         if (!bad) {
             nbar = (qsum + 2.0 * (c1 + c2)) / n + (xs[S] * m.ray_h2 + xs[S + 1] * m.ray_he) * w4;
             tb = dd / t + LN10 * (c1t + c2t) - nbar * n / t;
-            atomicAdd(&xbar[S], (2.0 * c1 + c2) / xs[S] + n * m.ray_h2 * w4);
-            atomicAdd(&xbar[S + 1], c2 / xs[S + 1] + n * m.ray_he * w4);
+            xh += (2.0 * c1 + c2) / xs[S] + n * m.ray_h2 * w4;
+            xe += c2 / xs[S + 1] + n * m.ray_he * w4;
         }
         tlbar[l] = tb;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        xh += __shfl_xor_sync(0xffffffffu, xh, o);
+        xe += __shfl_xor_sync(0xffffffffu, xe, o);
+    }
+    if ((tid & 31) == 0) {
+        atomicAdd(&xbar[S], xh);
+        atomicAdd(&xbar[S + 1], xe);
     }
     // forward-mode tangents in FP32 (values from the forward's FP64 results).
     // Temperature tangents, parallel over (parameter, layer or level): only
