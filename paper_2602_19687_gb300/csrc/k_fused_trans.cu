@@ -369,15 +369,6 @@ __device__ __forceinline__ float reduce4_partial(const float (&v)[4], int lane) 
     return (up ? a[1] : a[0]) + __shfl_xor_sync(0xffffffffu, up ? a[0] : a[1], 8);
 }
 
-// One TMEM column of this warp's lane quadrant: thread i <- lane i. The
-// value is bound to the wait so that no use is scheduled before it.
-__device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
-    uint32_t r;
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r)::"memory");
-    return __uint_as_float(r);
-}
-
 // Split TMEM load of one column of this warp's lane quadrant: the issue, and
 // the wait that binds the value (no use may be scheduled before it).
 __device__ __forceinline__ void tmem_issue1(uint32_t taddr, uint32_t &r) {
