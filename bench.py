@@ -154,8 +154,11 @@ def kernel_work(name, w, n_valid):
     tri = L * (L + 1) // 2
     n_t = int(np.sum((w.kind == 0)[:B])) if B else 0
     n_e = B - n_t
-    if name in ("k_extinction", "k_extinction_bwd"):
-        return n_e * L * (S + 2) * N, "ex2", "alu"
+    if name in ("k_emis_fwd", "k_emis_bwd"):
+        # per (emission vector, layer, wavenumber): the interpolation's S + 2
+        # exponentials, one attenuation per Gauss-Legendre angle (4) and the
+        # Planck function at the level (1); the adjoint recomputes all of them
+        return n_e * L * (S + 7) * N, "ex2", "alu"
     if name == "k_trans_fwd":
         # one ex2 per (vector, layer, species or CIA pair, wavenumber) of the
         # interpolation, plus exp(-tau_i) per (vector, impact parameter, wavenumber)
@@ -163,8 +166,6 @@ def kernel_work(name, w, n_valid):
     if name == "k_trans_bwd":
         # the adjoint recomputes the interpolation's exponentials
         return n_t * L * (S + 2) * N, "ex2", "alu"
-    if name in ("k_emission", "k_emission_bwd"):
-        return B * N * L * 4, "layer-angle steps", "alu"
     return None
 
 

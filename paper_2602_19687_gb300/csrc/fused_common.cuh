@@ -51,6 +51,12 @@ __device__ __forceinline__ void split2(float2 x, uint32_t &hi, uint32_t &lo) {
     const float2 r = fma2(h, f2(-1.f), x);   // x - hi, exact
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(r.y), "f"(r.x));
 }
+// round-to-nearest BF16 pair (x.x in the low half)
+__device__ __forceinline__ uint32_t bf16x2(float2 x) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(x.y), "f"(x.x));
+    return r;
+}
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
