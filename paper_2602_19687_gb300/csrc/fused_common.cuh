@@ -60,6 +60,23 @@ __device__ __forceinline__ uint32_t bf16x2(float2 x) {
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+// 16-byte asynchronous global -> shared copies (bypassing L1), their group
+// commit and the wait for all of this thread's groups
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ float4 lds128(uint32_t saddr) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(saddr)
+                 : "memory");
+    return v;
+}
+// Per-warp staging of a run's coefficients: [2 SPL + 1 blocks][32 lanes] float4
+// (species blocks (j, c), then the CIA pair), for SPL <= 4.
+constexpr int STAGE_BLOCKS = 9;
+constexpr int STAGE_BYTES_PER_WARP = STAGE_BLOCKS * 32 * 16;
 
 // ------------------------------------------------------------ per-sample constants
 // Per-layer constants, with the operands of packed FP32x2 instructions stored
@@ -202,6 +219,30 @@ struct PairInterp {
         b = make_float2(k.x, k.y);
         d = make_float2(k.z, k.w);
     }
+    // asynchronous copy of a run's coefficients (shift: float4 offset of the
+    // tile, 0 or the next tile's 128) into this lane's staging slots `stg`
+    __device__ __forceinline__ void stage(uint32_t stg, int cell, int itc, int shift) const {
+        const float4 *p = cp + (size_t)cell * cstride + shift;
+#pragma unroll
+        for (int k = 0; k < 2 * SPL; ++k) cp_async16(stg + k * 512, p + (size_t)k * jstride);
+        cp_async16(stg + 2 * SPL * 512, ciap + (size_t)itc * cia_stride + shift);
+        cp_async_commit();
+    }
+    // the staged run: wait for this lane's copies, then read its own slots
+    __device__ __forceinline__ void load_staged(const SampleConst &sc, uint32_t stg) {
+        cp_async_wait_all();
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) {
+            const float4 c0 = lds128(stg + (2 * j) * 512), c1 = lds128(stg + (2 * j + 1) * 512);
+            a0[j] = add2(make_float2(c0.x, c0.y), f2(sc.lx[SPL * h + j]));
+            a1[j] = make_float2(c0.z, c0.w);
+            a2[j] = make_float2(c1.x, c1.y);
+            a3[j] = make_float2(c1.z, c1.w);
+        }
+        const float4 k = lds128(stg + 2 * SPL * 512);
+        b = make_float2(k.x, k.y);
+        d = make_float2(k.z, k.w);
+    }
     // L1 prefetch of the next run's coefficients: the warp's 2 SPL x 512 B,
     // one 128-B line per lane (two for SPL = 8), and the lane's CIA entry
     __device__ __forceinline__ void prefetch(int cell, int itc) const {
@@ -234,18 +275,31 @@ __device__ __forceinline__ float2 shfl_xor2(float2 v, int o) {
 // lane pair (lane, lane ^ 1) splitting species and CIA pairs:
 //   alpha = n 2^-K sum_s 2^e_s + CIA_H2H2 + CIA_H2He + Rayleigh.
 // Calls out(layer constants, alpha) on both lanes of the pair.
-template <int SPL, class Out>
+// With STAGE, coefficients come through the per-warp staging slots (`stg`:
+// this lane's slot 0): each run's copy is issued one run ahead, and the last
+// run of a tile stages the first run of the next tile (`next_shift` 128, or 0
+// at the last tile of an item); `prestaged` says the first run was staged
+// that way. Without it, direct loads with an L1 prefetch of the next run.
+template <int SPL, bool STAGE, class Out>
 __device__ __forceinline__ void extinction_pair(const Model &m, const SampleConst &sc, int lb, int le, int n,
-                                                int half, Out &&out) {
+                                                int half, uint32_t stg, bool prestaged, int next_shift, Out &&out) {
     PairInterp<SPL> pi;
     pi.init(m, n, half, threadIdx.x & 31);
     // loop bounds broadcast from lane 0: provably warp-uniform for the compiler
     lb = __shfl_sync(0xffffffffu, lb, 0);
     le = __shfl_sync(0xffffffffu, le, 0);
+    constexpr bool STAGED = STAGE && 2 * SPL + 1 <= STAGE_BLOCKS;
+    if (STAGED && lb < le && !prestaged) pi.stage(stg, sc.lay[lb].cell, sc.lay[lb].itc, 0);
     for (int l = lb; l < le;) {
         const int end = __shfl_sync(0xffffffffu, min(sc.lay[l].run_end, le), 0);
-        pi.load(sc, sc.lay[l].cell, sc.lay[l].itc);
-        if (end < le) pi.prefetch(sc.lay[end].cell, sc.lay[end].itc);
+        if constexpr (STAGED) {
+            pi.load_staged(sc, stg);
+            if (end < le) pi.stage(stg, sc.lay[end].cell, sc.lay[end].itc, 0);
+            else if (next_shift) pi.stage(stg, sc.lay[lb].cell, sc.lay[lb].itc, next_shift);
+        } else {
+            pi.load(sc, sc.lay[l].cell, sc.lay[l].itc);
+            if (end < le) pi.prefetch(sc.lay[end].cell, sc.lay[end].itc);
+        }
         const LayerConst *lp = &sc.lay[l], *const lend = &sc.lay[end];
         // two layers per iteration: independent chains for the schedulers
         for (; lp + 1 < lend; lp += 2) {

@@ -28,10 +28,11 @@ namespace {
 constexpr float LOG2E_F = 1.4426950408889634f;
 
 // Forward block: 16 warps, 128-wavenumber tiles; the chord product runs on
-// the tcgen05 tensor cores with the accumulator in TMEM. The extinction
-// operand and the accumulator are double-buffered: tile t + 1 is
-// interpolated while the product of tile t runs, and the epilogue of tile t
-// follows the issue of tile t + 1's product (one block barrier per tile).
+// the tcgen05 tensor cores with the accumulator in TMEM, double-buffered: the
+// epilogue of tile t - 1 overlaps the product of tile t, whose completion
+// then frees the (single) extinction operand for tile t + 1 (one block
+// barrier per tile). A second extinction buffer measured slower: the shared
+// memory it takes comes out of L1.
 constexpr int FT2 = 128;                          // wavenumbers per forward tile (the MMA's M)
 constexpr int F2_WARPS = 16;
 constexpr int F2_THREADS = F2_WARPS * 32;
@@ -42,9 +43,7 @@ constexpr int F2_TMEM_COLS = 256;                 // two 112-column accumulators
 struct TransFwdSmem {
     SampleConst sc;
     alignas(128) unsigned char lh[(LP / 8) * SBO_LP], ll[(LP / 8) * SBO_LP];    // L[i][l], split BF16
-    // alpha[l][nu], split BF16, double-buffered: tile t + 1 is interpolated
-    // while the product of tile t still reads buffer t & 1
-    alignas(128) unsigned char ah[2][(LP / 8) * SBO_NU], al[2][(LP / 8) * SBO_NU];
+    alignas(128) unsigned char ah[1][(LP / 8) * SBO_NU], al[1][(LP / 8) * SBO_NU];   // alpha[l][nu], split BF16
     float area[LP];
     float part[2][4][FT2];                         // per-column-chunk partial transit sums, per buffer
     alignas(8) uint64_t mbar[2];
@@ -78,6 +77,7 @@ struct TransBwdSmem {
     // x 4 partial sums (one per lane-bit pair b2 b1), summed at the flush
     float red[ES_MAX_LAYERS * 32];
     float qtot[ES_MAX_SPECIES];                         // per-species totals of the current sample
+    alignas(16) unsigned char stage[BW_WARPS][STAGE_BYTES_PER_WARP];   // per-warp coefficient staging
     alignas(8) uint64_t mbar_a, mbar_l;
     uint32_t tmem_base;
     int abort;
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, in
     for (int idx = threadIdx.x; idx < (LP - L) * (FT2 / 2); idx += F2_THREADS) {
         const uint32_t o = op_off(L + idx / (FT2 / 2), 2 * (idx % (FT2 / 2)), SBO_NU);
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < 1; ++k) {
             *reinterpret_cast<uint32_t *>(sm.ah[k] + o) = 0u;
             *reinterpret_cast<uint32_t *>(sm.al[k] + o) = 0u;
         }
@@ -201,10 +201,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, in
     };
     // finish every tile in flight: its product, epilogue and spectrum
     auto drain = [&]() {
-        if (pend_b >= 0) {
-            wait_mma(pend_buf);
-            epilogue(pend_b, pend_t, pend_buf);
-        }
+        if (pend_b >= 0) epilogue(pend_b, pend_t, pend_buf);
         tc_fence_before();
         __syncthreads();
         if (spec_b >= 0) write_spec(spec_b, spec_t, spec_buf);
@@ -235,8 +232,11 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, in
         for (int t = c * chunk_tiles; t < t1; ++t) {
             const int nt0 = t * FT2;
             const int buf = issued & 1;
-            unsigned char *const a_dst = (half ? sm.al[buf] : sm.ah[buf]) + a_off;
-            extinction_pair<SPL>(m, sm.sc, sm.sc.gb[grp], sm.sc.gb[grp + 1], nt0 + 2 * pair, half, [&](const LayerConst &lc, float2 a) {
+            unsigned char *const a_dst = (half ? sm.al[0] : sm.ah[0]) + a_off;
+            // direct coefficient loads: staging them through shared memory costs
+            // the forward more in queue throttling and L1 than it saves here
+            extinction_pair<SPL, false>(m, sm.sc, sm.sc.gb[grp], sm.sc.gb[grp + 1], nt0 + 2 * pair, half, 0u,
+                                        false, 0, [&](const LayerConst &lc, float2 a) {
                 uint32_t hi, lo;
                 split2(a, hi, lo);
                 *reinterpret_cast<uint32_t *>(a_dst + lc.aoff) = half ? lo : hi;
@@ -257,8 +257,8 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, in
                 const uint32_t d = tmem + (uint32_t)(buf * 128);
                 // descriptors of k-step 0; a k-step advances the start address field
                 // (bits 0-13, 16-byte units) by 2 row groups of alpha / 2 cores of L
-                const uint64_t a_h = desc_mn_major(smem_u32(sm.ah[buf]), SBO_NU);
-                const uint64_t a_l = desc_mn_major(smem_u32(sm.al[buf]), SBO_NU);
+                const uint64_t a_h = desc_mn_major(smem_u32(sm.ah[0]), SBO_NU);
+                const uint64_t a_l = desc_mn_major(smem_u32(sm.al[0]), SBO_NU);
                 const uint64_t b_h = desc_k_major(lh_s, SBO_LP), b_l = desc_k_major(ll_s, SBO_LP);
 #pragma unroll
                 for (int k = 0; k < LP / 16; ++k) {
@@ -269,16 +269,15 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, in
                 }
                 tc_commit(mbar0 + 8u * (uint32_t)buf);
             }
-            // the previous tile: its product was issued a whole interpolation
-            // ago; its epilogue overlaps the product just issued. The wait also
-            // frees that tile's alpha buffer for the next interpolation.
+            // the previous tile's epilogue (its product completed in the
+            // previous iteration) overlaps the product just issued
             if (pend_b >= 0) {
-                wait_mma(pend_buf);
                 epilogue(pend_b, pend_t, pend_buf);
                 spec_b = pend_b;
                 spec_t = pend_t;
                 spec_buf = pend_buf;
             }
+            wait_mma(buf);   // this tile's product: frees the single alpha buffer
             pend_b = b;
             pend_t = t;
             pend_buf = buf;
@@ -398,7 +397,8 @@ __device__ __forceinline__ void tmem_wait1(uint32_t &r) {
 // L_bar product.
 template <int SPL, class Wait>
 __device__ void interp_backward(const Model &m, const SampleConst &sc, int lb, int le, int n, int half, int lane,
-                                uint32_t abar_t, unsigned char *a_dst, float *red, float *qtot, Wait &&wait_abar) {
+                                uint32_t abar_t, unsigned char *a_dst, float *red, float *qtot, uint32_t stg,
+                                bool prestaged, int next_shift, Wait &&wait_abar) {
     const int S = m.S;
     const int ridx = reduce_index8(lane);
     const bool writer = (lane & 3) == 0;
@@ -415,10 +415,18 @@ __device__ void interp_backward(const Model &m, const SampleConst &sc, int lb, i
     // loop bounds broadcast from lane 0: provably warp-uniform for the compiler
     lb = __shfl_sync(0xffffffffu, lb, 0);
     le = __shfl_sync(0xffffffffu, le, 0);
+    constexpr bool STAGED = 2 * SPL + 1 <= STAGE_BLOCKS;   // else direct loads with an L1 prefetch
+    if (STAGED && lb < le && !prestaged) pi.stage(stg, sc.lay[lb].cell, sc.lay[lb].itc, 0);
     for (int l = lb; l < le;) {
         const int end = __shfl_sync(0xffffffffu, min(sc.lay[l].run_end, le), 0);
-        pi.load(sc, sc.lay[l].cell, sc.lay[l].itc);
-        if (end < le) pi.prefetch(sc.lay[end].cell, sc.lay[end].itc);
+        if constexpr (STAGED) {
+            pi.load_staged(sc, stg);
+            if (end < le) pi.stage(stg, sc.lay[end].cell, sc.lay[end].itc, 0);
+            else if (next_shift) pi.stage(stg, sc.lay[lb].cell, sc.lay[lb].itc, next_shift);
+        } else {
+            pi.load(sc, sc.lay[l].cell, sc.lay[l].itc);
+            if (end < le) pi.prefetch(sc.lay[end].cell, sc.lay[end].itc);
+        }
         if (!waited) {   // the first coefficient loads are in flight while the alpha_bar product completes
             wait_abar();
             waited = true;
@@ -521,6 +529,7 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
     const uint32_t ah_s = smem_u32(sm.ah);
     const uint32_t abar_t = tmem + ((uint32_t)(32 * vq) << 16);
     unsigned char *const a_dst = sm.ah + op_off(0, 2 * pair, SBO_NU);
+    const uint32_t stg = smem_u32(sm.stage[warp]) + 16u * (uint32_t)lane;
     uint32_t pa = 0, pl = 0;
     bool l_pending = false, l_started = false, abort = false;
     int cur_b = -1;
@@ -674,7 +683,7 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
                 tc_commit(mbar_a);
             }
             interp_backward<SPL>(m, sm.sc, sm.sc.gb[grp], sm.sc.gb[grp + 1], nt0 + 2 * pair, half, lane, abar_t, a_dst,
-                                 sm.red, sm.qtot, [&]() {
+                                 sm.red, sm.qtot, stg, t > c * chunk_tiles, t + 1 < t1 ? BT : 0, [&]() {
                                      if (!mbar_wait(mbar_a, pa)) sm.abort = 1;
                                      tc_fence_after();
                                  });
