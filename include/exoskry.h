@@ -47,7 +47,10 @@ typedef enum {
     ES_ETIMEOUT = 5   /* a bounded device-side wait gave up              */
 } es_status;
 
-enum { ES_TP_ISOTHERMAL = 0, ES_TP_GUILLOT = 1, ES_TP_GUILLOT_MOD = 2 };
+enum { ES_TP_ISOTHERMAL = 0, ES_TP_GUILLOT = 1, ES_TP_GUILLOT_MOD = 2, ES_TP_MILNE = 3 };
+/* Emission output: planet-to-star flux ratio (Sect. 5, Fp/F*) or the
+ * absolute flux of an isolated brown dwarf at distance D (Sect. 5, F_bd). */
+enum { ES_FLUX_PLANET_STAR = 0, ES_FLUX_BROWN_DWARF = 1 };
 enum { ES_CLOUD_NONE = 0, ES_CLOUD_DECK = 1 };
 enum { ES_KIND_TRANSMISSION = 0, ES_KIND_EMISSION = 1 };
 enum { ES_TABLE_F32 = 0, ES_TABLE_BF16 = 1 };
@@ -62,17 +65,23 @@ enum { ES_FLAG_INVALID = 1 };
  *   LOG_KAPPA_IR log10 infrared opacity [cm^2 g^-1]          (Sect. 2.4.3)
  *   LOG_GAMMA_V  log10 visible-to-infrared opacity ratio     (Sect. 2.4.4)
  *   Q_IRR0, LOG_P_T, BETA  stretched-exponential Hopf function
- *                of the irradiation term, Eq. (q); p_t in bar (GUILLOT_MOD)
+ *                of the irradiation term, Eq. (q); p_t in bar (GUILLOT_MOD);
+ *                LOG_P_T and BETA also parameterise the MILNE Hopf function
  *   LOG_G        log10 reference gravity [cm s^-2]
  *   R_P          planet radius at p_ref [Jupiter radii, 7.1492e9 cm]
+ *                (unused with ES_FLUX_BROWN_DWARF: the radius is derived)
  *   LOG_P_CLOUD  log10 grey cloud-deck pressure [bar]        (ES_CLOUD_DECK)
  *   C_INFL       error inflation c of Eq. c_error (-99: none)
  *   DILUTION     dilution factor s of Sect. 5 (emission)
+ *   T_RATIO      skin-to-internal temperature ratio T_skin/T_int of the
+ *                modified Milne profile, q0 = 4/3 T_RATIO^4 (Sect. 2.4.3)
+ *   M_BD         brown-dwarf mass [Jupiter masses, 1.89813e30 g]; the radius
+ *                is R_bd = sqrt(G M_bd / g) (Sect. 5, ES_FLUX_BROWN_DWARF)
  */
 enum {
     ES_P_T_ISO = 0, ES_P_T_INT, ES_P_T_EQ, ES_P_LOG_KAPPA_IR, ES_P_LOG_GAMMA_V,
     ES_P_Q_IRR0, ES_P_LOG_P_T, ES_P_BETA, ES_P_LOG_G, ES_P_R_P, ES_P_LOG_P_CLOUD,
-    ES_P_C_INFL, ES_P_DILUTION, ES_P_N_EXTRA
+    ES_P_C_INFL, ES_P_DILUTION, ES_P_T_RATIO, ES_P_M_BD, ES_P_N_EXTRA
 };
 
 #define ES_MAX_SPECIES 16
@@ -84,10 +93,13 @@ enum {
  * Sect. 4-5 geometry and star). Layers: n_layers (2..ES_MAX_LAYERS) with
  * n_layers+1 levels log-spaced from p_top (top) to p_bot (bottom); a
  * layer's pressure is the geometric mean of its levels. Hydrostatic
- * balance with g(r) = g_ref (R_p/r)^2 is anchored at r(p_ref) = R_p.
+ * balance with g(r) = g_ref (R_p/r)^2 is anchored at r(p_ref) = R_p (the
+ * derived R_bd with ES_FLUX_BROWN_DWARF).
  * theta_fixed holds every canonical slot's value; the user's parameter
  * vectors fill the n_free slots listed in free_idx (in that order).
  * Rayleigh cross-sections are sigma(nu) = ray_*_cm2 (nu / ray_nu_ref)^4.
+ * emission_flux selects the emission output (ES_FLUX_*); distance_cm is
+ * the brown dwarf's distance D (> 0 with ES_FLUX_BROWN_DWARF).
  */
 typedef struct {
     int n_layers;
@@ -101,6 +113,8 @@ typedef struct {
     double theta_fixed[ES_MAX_PARAMS];
     int n_free;
     int free_idx[ES_MAX_PARAMS];
+    int emission_flux;           /* ES_FLUX_*        */
+    double distance_cm;
 } es_model_desc;
 
 /*

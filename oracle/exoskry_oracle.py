@@ -32,6 +32,8 @@ Readings where the paper is silent (documented in DESIGN.md, "Readings"):
    and r_c the radius of an opaque grey deck (r_bot without a deck);
  - emission: absorption-only linear-in-tau RT with 4 Gauss-Legendre angles on
    [0, 1], bottom boundary I = B(T_bottom level), F_* = pi B(T_*);
+ - modified Milne profile: q_inf fixed at the Hopf function's deep limit;
+   a brown dwarf's hydrostatic reference radius is its R_bd = sqrt(G M_bd/g);
  - binning: equal-weight mean over native points with lambda in [lo, hi).
 
 Parity status: every stage is pinned by tests/test_oracle_pins.py (closed forms,
@@ -65,8 +67,17 @@ INVALID_LNL = -1.0e300      # Sect. 2.3: invalid forward-model output
 
 # canonical slots after the S log-VMR slots
 (P_T_ISO, P_T_INT, P_T_EQ, P_LOG_KAPPA, P_LOG_GAMMA, P_Q_IRR0, P_LOG_PT, P_BETA,
- P_LOG_G, P_R_P, P_LOG_PCLOUD, P_C_INFL, P_DILUTION) = range(13)
-TP_ISOTHERMAL, TP_GUILLOT, TP_GUILLOT_MOD = 0, 1, 2
+ P_LOG_G, P_R_P, P_LOG_PCLOUD, P_C_INFL, P_DILUTION, P_T_RATIO, P_M_BD) = range(15)
+TP_ISOTHERMAL, TP_GUILLOT, TP_GUILLOT_MOD, TP_MILNE = 0, 1, 2, 3
+FLUX_PLANET_STAR, FLUX_BROWN_DWARF = 0, 1
+
+# Sect. 2.4.3 (modified Milne): q_inf is not a retrieved parameter; the paper
+# quotes the grey solution's deep value as ~0.71. Reading: the Hopf function's
+# deep limit q(infinity) = 0.7104460895.
+Q_MILNE_INF = 0.7104460895
+# Sect. 5 (brown dwarfs): R_bd = sqrt(G M_bd / g); CODATA 2018 G, nominal Jupiter mass
+G_GRAV = 6.67430e-8         # cm^3 g^-1 s^-2
+M_JUP = 1.89813e30          # g
 CLOUD_NONE, CLOUD_DECK = 0, 1
 
 
@@ -122,6 +133,21 @@ def temperature_guillot(p, t_int, t_eq, kappa_ir, gamma_v, g, q_irr=None):
                                            + (gamma_v / s3 - 1.0 / (gamma_v * s3))
                                            * np.exp(-gamma_v * tau * s3))
     return t4 ** 0.25
+
+
+def temperature_milne(p, t_int, kappa_ir, g, t_ratio, p_t, beta):
+    """Sect. 2.4.3, modified Milne: T^4 = 3/4 T_int^4 [tau + q(p)] with
+    tau = kappa_ir p / g and the stretched-exponential Hopf function of
+    Eq. (q), q0 = 4/3 T_ratio^4 (so T -> T_ratio T_int as p -> 0), q_inf fixed."""
+    tau = kappa_ir * p / g
+    q0 = 4.0 / 3.0 * t_ratio ** 4
+    q = stretched_hopf(p, q0, Q_MILNE_INF, p_t, beta)
+    return (0.75 * t_int ** 4 * (tau + q)) ** 0.25
+
+
+def brown_dwarf_radius(m_bd_jup, g):
+    """Sect. 5: R_bd = sqrt(G M_bd / g) [cm], M_bd in Jupiter masses."""
+    return np.sqrt(G_GRAV * M_JUP * m_bd_jup / g)
 
 
 # --------------------------------------------------------------------------
@@ -350,6 +376,11 @@ def atmosphere(model, theta):
     if model.tp_kind == TP_ISOTHERMAL:
         t_lay = temperature_isothermal(th[s + P_T_ISO], p_lay)
         t_lev = temperature_isothermal(th[s + P_T_ISO], p_lev)
+    elif model.tp_kind == TP_MILNE:
+        kappa = 10.0 ** th[s + P_LOG_KAPPA]
+        p_t = 10.0 ** th[s + P_LOG_PT] * BAR
+        t_lay, t_lev = (temperature_milne(p, th[s + P_T_INT], kappa, g, th[s + P_T_RATIO], p_t, th[s + P_BETA])
+                        for p in (p_lay, p_lev))
     else:
         kappa = 10.0 ** th[s + P_LOG_KAPPA]
         gamma = 10.0 ** th[s + P_LOG_GAMMA]
@@ -364,7 +395,12 @@ def atmosphere(model, theta):
     mu = mean_molecular_mass(x_trace, model.masses_amu, x_h2, x_he)
     valid = bool(np.all(np.isfinite(_re(t_lay))) and np.all(_re(t_lay) > 0)
                  and np.all(_re(t_lev) > 0) and _re(np.sum(x_trace)) < 1.0)
-    r_ref = th[s + P_R_P] * R_JUP
+    brown_dwarf = getattr(model, "emission_flux", FLUX_PLANET_STAR) == FLUX_BROWN_DWARF
+    if brown_dwarf:
+        valid = valid and _re(th[s + P_M_BD]) > 0
+        r_ref = brown_dwarf_radius(th[s + P_M_BD], g) if valid else 0.0
+    else:
+        r_ref = th[s + P_R_P] * R_JUP
     out = dict(x_trace=x_trace, x_h2=x_h2, x_he=x_he, mu=mu, g=g, p_lev=p_lev, p_lay=p_lay,
                t_lay=t_lay, t_lev=t_lev, r_ref=r_ref, valid=valid)
     if not valid:
@@ -399,9 +435,13 @@ def forward(model, tabs, theta, kind, members):
         dtau = alpha * dr[:, None]
         b_lev = planck_wavenumber(atm["t_lev"][:, None], tabs.nu[None, :])
         f_toa = emergent_flux(b_lev, dtau)
-        f_star = np.pi * planck_wavenumber(model.t_star_k, tabs.nu)
-        # Sect. 5: Fp/F* = s F_toa / F_* (R_p / R_*)^2
-        spec = theta[s + P_DILUTION] * f_toa / f_star * (atm["r_ref"] / model.r_star_cm) ** 2
+        if getattr(model, "emission_flux", FLUX_PLANET_STAR) == FLUX_BROWN_DWARF:
+            # Sect. 5: F_bd = s F_toa (R_bd / D)^2
+            spec = theta[s + P_DILUTION] * f_toa * (atm["r_ref"] / model.distance_cm) ** 2
+        else:
+            f_star = np.pi * planck_wavenumber(model.t_star_k, tabs.nu)
+            # Sect. 5: Fp/F* = s F_toa / F_* (R_p / R_*)^2
+            spec = theta[s + P_DILUTION] * f_toa / f_star * (atm["r_ref"] / model.r_star_cm) ** 2
     if not np.all(np.isfinite(_re(spec))):
         return None
     return spec, bin_spectrum(spec, members)

@@ -19,7 +19,7 @@ ES_OK, ES_EINVAL, ES_ENOMEM, ES_ECUDA, ES_ESTATE, ES_ETIMEOUT = range(6)
 ES_MEM_HOST, ES_MEM_DEVICE = 0, 1
 ES_TABLE_F32, ES_TABLE_BF16 = 0, 1
 ES_MAX_SPECIES = 16
-ES_P_N_EXTRA = 13
+ES_P_N_EXTRA = 15
 ES_MAX_PARAMS = ES_MAX_SPECIES + ES_P_N_EXTRA
 ES_MAX_LAYERS = 112
 STATUS_NAMES = {0: "ES_OK", 1: "ES_EINVAL", 2: "ES_ENOMEM", 3: "ES_ECUDA", 4: "ES_ESTATE", 5: "ES_ETIMEOUT"}
@@ -38,7 +38,8 @@ class es_model_desc(ctypes.Structure):
                 ("r_star_cm", ctypes.c_double), ("t_star_k", ctypes.c_double),
                 ("ray_h2_cm2", ctypes.c_double), ("ray_he_cm2", ctypes.c_double), ("ray_nu_ref", ctypes.c_double),
                 ("theta_fixed", ctypes.c_double * ES_MAX_PARAMS),
-                ("n_free", ctypes.c_int), ("free_idx", ctypes.c_int * ES_MAX_PARAMS)]
+                ("n_free", ctypes.c_int), ("free_idx", ctypes.c_int * ES_MAX_PARAMS),
+                ("emission_flux", ctypes.c_int), ("distance_cm", ctypes.c_double)]
 
 
 class es_tables_desc(ctypes.Structure):
@@ -134,6 +135,8 @@ def model_desc(model) -> es_model_desc:
     d.n_free = len(model.free_idx)
     for k, v in enumerate(model.free_idx):
         d.free_idx[k] = int(v)
+    d.emission_flux = int(getattr(model, "emission_flux", 0))
+    d.distance_cm = float(getattr(model, "distance_cm", 0.0))
     return d
 
 

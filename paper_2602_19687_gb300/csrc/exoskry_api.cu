@@ -349,7 +349,9 @@ es_status es_create(es_ctx **out, int device, const es_model_desc *d) {
     if (d->n_layers < 2 || d->n_layers > ES_MAX_LAYERS) return ES_EINVAL;
     if (d->n_species < 1 || d->n_species > ES_MAX_SPECIES) return ES_EINVAL;
     if (!(d->p_top_bar > 0) || !(d->p_bot_bar > d->p_top_bar) || !(d->p_ref_bar > 0)) return ES_EINVAL;
-    if (d->tp_kind < 0 || d->tp_kind > 2 || d->cloud_kind < 0 || d->cloud_kind > 1) return ES_EINVAL;
+    if (d->tp_kind < 0 || d->tp_kind > ES_TP_MILNE || d->cloud_kind < 0 || d->cloud_kind > 1) return ES_EINVAL;
+    if (d->emission_flux != ES_FLUX_PLANET_STAR && d->emission_flux != ES_FLUX_BROWN_DWARF) return ES_EINVAL;
+    if (d->emission_flux == ES_FLUX_BROWN_DWARF && !(d->distance_cm > 0)) return ES_EINVAL;
     if (!(d->r_star_cm > 0) || !(d->t_star_k > 0)) return ES_EINVAL;
     const int nfull = d->n_species + ES_P_N_EXTRA;
     if (d->n_free < 1 || d->n_free > 32 || d->n_free > nfull) return ES_EINVAL;
@@ -376,6 +378,8 @@ es_status es_create(es_ctx **out, int device, const es_model_desc *d) {
     m.nfull = nfull;
     m.tp_kind = d->tp_kind;
     m.cloud_kind = d->cloud_kind;
+    m.emis_flux = d->emission_flux;
+    m.distance = d->distance_cm;
     m.p_ref = d->p_ref_bar * BAR;
     m.r_star = d->r_star_cm;
     m.t_star = d->t_star_k;
@@ -507,7 +511,8 @@ es_status es_load_tables(es_ctx *c, const es_tables_desc *t) {
     for (size_t n = 0; n < Np; ++n) {
         const double nv = t->nu[n < N ? n : N - 1];
         nuf[n] = (float)nv;
-        ifs[n] = (float)(1.0 / (PI * planck_host(nv, m.t_star)));
+        // Fp/F* divides by the stellar flux; a brown dwarf's flux is absolute
+        ifs[n] = (m.emis_flux == ES_FLUX_BROWN_DWARF) ? 1.f : (float)(1.0 / (PI * planck_host(nv, m.t_star)));
     }
     if ((s = upload(c, c->table_bufs, &df, nuf.data(), Np)) != ES_OK) return s;
     m.nu = df;

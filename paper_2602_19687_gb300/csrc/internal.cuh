@@ -25,6 +25,12 @@ constexpr double M_HE = 4.002602;
 constexpr double F_HEM = 0.25;
 constexpr double Q_INT = 2.0 / 3.0;
 constexpr double Q_IRR_INF = 2.0 / 3.0;
+// Sect. 2.4.3 modified Milne: q_inf fixed at the grey Hopf function's deep
+// limit q(infinity) (the paper quotes it as ~0.71)
+constexpr double Q_MILNE_INF = 0.7104460895;
+// Sect. 5 brown dwarfs: R_bd = sqrt(G M_bd / g); CODATA 2018 G, nominal Jupiter mass
+constexpr double G_GRAV = 6.67430e-8;
+constexpr double M_JUP = 1.89813e30;
 // Sect. 2.3: invalid forward-model output
 constexpr double INVALID_LNL = -1.0e300;
 // second radiation constant h c / k_B [cm K] and 2 h c^2 [erg cm^2 s^-1]
@@ -49,6 +55,8 @@ struct Model {
     int Np;                       // padded row stride of tables and per-wavenumber arrays (N rounded up to 128)
     int SP;                       // species slots per coefficient-table entry (2 spl_for(S) >= S)
     int tp_kind, cloud_kind, bf16;
+    int emis_flux;                // ES_FLUX_*
+    double distance;              // cm (brown-dwarf flux)
     double p_ref;                 // dyn cm^-2
     double r_star, t_star;
     double ray_h2, ray_he, ray_nu_ref;

@@ -76,8 +76,8 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup(Model m, Work w) {
         xs[S + 1] = xhe;
         s_mu = mu;
         s_g = exp10(th[S + ES_P_LOG_G]);
-        s_rref = th[S + ES_P_R_P] * R_JUP;
-        if (!(sum < 1.0)) s_bad = 1;
+        s_rref = reference_radius<double>(m, th, s_g);
+        if (!(sum < 1.0) || !(s_rref > 0.0)) s_bad = 1;
     }
     for (int l = tid; l < L; l += blockDim.x) tl[l] = temperature<double>(m, th, m.p_lay[l]);
     for (int k = tid; k <= L; k += blockDim.x) tv[k] = temperature<double>(m, th, m.p_lev[k]);
@@ -110,8 +110,7 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup(Model m, Work w) {
         w.flags[b] = bad ? ES_FLAG_INVALID : 0;
         w.rc[b] = bad ? 0.0 : s_rc;
         w.base[b] = bad ? 0.0 : s_rc * s_rc / rs2;
-        double rp = th[S + ES_P_R_P] * R_JUP;
-        w.scale[b] = bad ? 0.0 : th[S + ES_P_DILUTION] * rp * rp / rs2;
+        w.scale[b] = bad ? 0.0 : emission_scale<double>(m, th, s_rref);
     }
     if (tid < S + 2) w.xs[(size_t)b * (S + 2) + tid] = xs[tid];
     for (int k = tid; k <= L; k += blockDim.x) {
@@ -338,7 +337,7 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup_bwd(Model m, Work w) {
     if (emis)
         for (int k = 0; k <= L; ++k) acc += tvbar[k] * (double)dtv[p][k];
     DualF g = dexp10(th[S + ES_P_LOG_G]);
-    DualF rref = th[S + ES_P_R_P] * R_JUP;
+    DualF rref = reference_radius<DualF>(m, th, g);
     DualF inv_r[ES_MAX_LAYERS + 1];
     hydrostatic<DualF>(m, tl, mu, g, rref, inv_r);
     for (int k = 0; k <= L; ++k) {
@@ -364,8 +363,7 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup_bwd(Model m, Work w) {
         }
         acc += rcbar * (double)drc;
     } else {
-        DualF rp = th[S + ES_P_R_P] * R_JUP;
-        DualF sc = th[S + ES_P_DILUTION] * rp * rp / rs2;
+        DualF sc = emission_scale<DualF>(m, th, rref);
         acc += w.misc[(size_t)b * 4 + 1] * (double)sc.d;
     }
     acc += w.misc[(size_t)b * 4 + 2] * (double)th[S + ES_P_C_INFL].d;

@@ -114,6 +114,21 @@ template <class R>
 __device__ R temperature(const Model &m, const R *th, double p) {
     Params<R> P{th, m.S};
     if (m.tp_kind == ES_TP_ISOTHERMAL) return P.slot(ES_P_T_ISO);
+    if (m.tp_kind == ES_TP_MILNE) {
+        // Sect. 2.4.3: T^4 = 3/4 T_int^4 [tau + q(p)], tau = kappa_ir p / g,
+        // q(p) = q_inf + (q0 - q_inf) exp[-(p/p_t)^beta], q0 = 4/3 T_ratio^4
+        R g = dexp10(P.slot(ES_P_LOG_G));
+        R kappa = dexp10(P.slot(ES_P_LOG_KAPPA_IR));
+        R tint = P.slot(ES_P_T_INT), tr = P.slot(ES_P_T_RATIO);
+        R tau = kappa * p / g;
+        R tr2 = tr * tr;
+        R q0 = (4.0 / 3.0) * (tr2 * tr2);
+        R p_t = dexp10(P.slot(ES_P_LOG_P_T)) * BAR;
+        R z = dexp(P.slot(ES_P_BETA) * dlog(p / p_t));   // (p/p_t)^beta
+        R q = Q_MILNE_INF + (q0 - Q_MILNE_INF) * dexp(-z);
+        R tint2 = tint * tint;
+        return dsqrt(dsqrt(0.75 * (tint2 * tint2) * (tau + q)));
+    }
     R g = dexp10(P.slot(ES_P_LOG_G));
     R kappa = dexp10(P.slot(ES_P_LOG_KAPPA_IR));
     R gamma = dexp10(P.slot(ES_P_LOG_GAMMA_V));
@@ -132,6 +147,21 @@ __device__ R temperature(const Model &m, const R *th, double p) {
          + 0.75 * (teq2 * teq2) * (4.0 * F_HEM)
                * (q_irr + 1.0 / (gamma * s3) + (gamma / s3 - 1.0 / (gamma * s3)) * dexp(-(gamma * tau * s3)));
     return dsqrt(dsqrt(t4));
+}
+
+// Reference radius of the hydrostatic grid: R_p, or for a brown dwarf the
+// radius from its mass and gravity, R_bd = sqrt(G M_bd / g) (Sect. 5).
+template <class R>
+__device__ R reference_radius(const Model &m, const R *th, R g) {
+    if (m.emis_flux == ES_FLUX_BROWN_DWARF) return dsqrt((G_GRAV * M_JUP) * th[m.S + ES_P_M_BD] / g);
+    return th[m.S + ES_P_R_P] * R_JUP;
+}
+// Emission output scale: s (R_p/R_*)^2 for Fp/F*, s (R_bd/D)^2 for a brown
+// dwarf's flux at distance D (Sect. 5); the ratio is formed before squaring.
+template <class R>
+__device__ R emission_scale(const Model &m, const R *th, R r_ref) {
+    R ratio = (m.emis_flux == ES_FLUX_BROWN_DWARF) ? r_ref / m.distance : r_ref / m.r_star;
+    return th[m.S + ES_P_DILUTION] * ratio * ratio;
 }
 
 // Index of the layer whose levels bracket p_ref (clamped to the grid).

@@ -24,10 +24,12 @@ R_SUN_CM = 6.957e10
 # Canonical parameter slots that follow the S log-VMR slots (same documented
 # order as include/exoskry.h and the oracle).
 P_T_ISO, P_T_INT, P_T_EQ, P_LOG_KAPPA, P_LOG_GAMMA, P_Q_IRR0, P_LOG_PT, P_BETA, \
-    P_LOG_G, P_R_P, P_LOG_PCLOUD, P_C_INFL, P_DILUTION = range(13)
-N_EXTRA = 13
+    P_LOG_G, P_R_P, P_LOG_PCLOUD, P_C_INFL, P_DILUTION, P_T_RATIO, P_M_BD = range(15)
+N_EXTRA = 15
 
-TP_ISOTHERMAL, TP_GUILLOT, TP_GUILLOT_MOD = 0, 1, 2
+TP_ISOTHERMAL, TP_GUILLOT, TP_GUILLOT_MOD, TP_MILNE = 0, 1, 2, 3
+FLUX_PLANET_STAR, FLUX_BROWN_DWARF = 0, 1
+PARSEC_CM = 3.0856775814913673e18
 CLOUD_NONE, CLOUD_DECK = 0, 1
 KIND_TRANSMISSION, KIND_EMISSION = 0, 1
 
@@ -55,6 +57,8 @@ class Model:
     ray_nu_ref: float
     theta_fixed: np.ndarray       # full canonical vector of defaults
     free_idx: np.ndarray          # canonical slots that the user vector fills
+    emission_flux: int = FLUX_PLANET_STAR
+    distance_cm: float = 0.0
 
     @property
     def n_species(self):
@@ -174,9 +178,10 @@ def make_bins(nu, n_bins):
     return edges[:-1].copy(), edges[1:].copy()
 
 
-def make_data(n_bins, kind, level, seed=7):
+def make_data(n_bins, kind, level, seed=7, rel_sigma=None):
     """Synthetic observed spectrum: a smooth seeded curve around `level`
-    with Gaussian noise (30 ppm transmission, 50 ppm of Fp/F* emission)."""
+    with Gaussian noise (30 ppm transmission, 50 ppm of Fp/F* emission, or
+    rel_sigma x level for an absolute flux)."""
     rng = np.random.default_rng(seed + kind)
     x = np.linspace(0.0, 1.0, n_bins)
     smooth = sum(rng.uniform(-1, 1) * np.sin((k + 1) * np.pi * x + rng.uniform(0, 6.28))
@@ -185,13 +190,13 @@ def make_data(n_bins, kind, level, seed=7):
         sigma = np.full(n_bins, 30e-6)
         y = level * (1.0 + 0.004 * smooth)
     else:
-        sigma = np.full(n_bins, 50e-6)
+        sigma = np.full(n_bins, 50e-6 if rel_sigma is None else rel_sigma * level)
         y = level * (1.0 + 0.3 * smooth / 4.0)
     return y + sigma * rng.standard_normal(n_bins), sigma
 
 
 def _model(n_species, n_layers, p_top, p_bot, tp_kind, cloud_kind, free, fixed=None,
-           species=None, r_star_rsun=1.0, t_star=5000.0):
+           species=None, r_star_rsun=1.0, t_star=5000.0, emission_flux=FLUX_PLANET_STAR, distance_pc=0.0):
     names = species or list(SPECIES)[:n_species]
     theta = np.zeros(n_species + N_EXTRA)
     theta[:n_species] = -8.0
@@ -209,6 +214,8 @@ def _model(n_species, n_layers, p_top, p_bot, tp_kind, cloud_kind, free, fixed=N
     theta[s + P_LOG_PCLOUD] = 3.0          # below the model bottom: no deck
     theta[s + P_C_INFL] = -99.0
     theta[s + P_DILUTION] = 1.0
+    theta[s + P_T_RATIO] = 0.5
+    theta[s + P_M_BD] = 70.0
     for k, v in (fixed or {}).items():
         theta[k] = v
     return Model(n_layers=n_layers, p_top_bar=p_top, p_bot_bar=p_bot, p_ref_bar=10.0,
@@ -216,7 +223,8 @@ def _model(n_species, n_layers, p_top, p_bot, tp_kind, cloud_kind, free, fixed=N
                  masses_amu=np.array([SPECIES[n] for n in names]),
                  r_star_cm=r_star_rsun * R_SUN_CM, t_star_k=t_star,
                  ray_h2_cm2=1.36e-27, ray_he_cm2=9.0e-29, ray_nu_ref=2.0e4,
-                 theta_fixed=theta, free_idx=np.asarray(free, dtype=np.int64))
+                 theta_fixed=theta, free_idx=np.asarray(free, dtype=np.int64),
+                 emission_flux=emission_flux, distance_cm=distance_pc * PARSEC_CM)
 
 
 def _prior_batch(model, batch, seed, ranges):
@@ -235,7 +243,8 @@ def prior_ranges(model):
               s + P_LOG_PT: (-7.0, 1.0), s + P_BETA: (0.0, 1.0),
               s + P_LOG_G: (2.7, 3.3), s + P_R_P: (0.9, 1.5),
               s + P_LOG_PCLOUD: (-6.0, 2.0), s + P_C_INFL: (-9.0, -4.0),
-              s + P_DILUTION: (0.5, 1.0)})
+              s + P_DILUTION: (0.5, 1.0), s + P_T_RATIO: (0.2, 0.9),
+              s + P_M_BD: (65.0, 78.0)})
     return r
 
 
@@ -258,9 +267,16 @@ def workload(name: str, batch: int | None = None, seed: int = 42,
                 deck, radius), L=60, 4 absorbers on 12 x 10 x 440000 nu
                 (0.9-5.3 um, R~250k), ~4400 bins of 100 points, BF16,
                 mixed transmission/emission batch.
+    browndwarf  256 brown-dwarf emission vectors shaped like the paper's
+                Gliese 229 B setup: 15 free parameters (6 log-VMR, T_int,
+                log kappa_ir, T_ratio, log p_t, beta of the modified Milne
+                profile, log g, M_bd, s, c), L=100 (1e-8..1000 bar), 6
+                absorbers on 20 T (300-3500 K) x 16 P x 54240 nu (1.0-5.1 um),
+                absolute flux at D = 10 pc, 500 bins, BF16.
     `n_nu` shrinks the spectral grid (same physics) for fast tests.
     """
-    S = {"tiny": 3, "jwst_plain": 6, "batched_trans": 8, "batched_emis": 8, "highres": 4}[name]
+    S = {"tiny": 3, "jwst_plain": 6, "batched_trans": 8, "batched_emis": 8, "highres": 4,
+         "browndwarf": 6}[name]
     s = S
     if name == "tiny":
         n = n_nu or 2000
@@ -332,13 +348,36 @@ def workload(name: str, batch: int | None = None, seed: int = 42,
         dtype, desc = "bf16", ("high-resolution mixed batch with adjoint, B=64, L=60, 4 absorbers, "
                                "12x10x440000 BF16 (0.9-5.3 um), ~4400 bins")
         level = (1.2 * R_JUP_CM / model.r_star_cm) ** 2
+    elif name == "browndwarf":
+        n = n_nu or 54240
+        free = list(range(6)) + [s + P_T_INT, s + P_LOG_KAPPA, s + P_T_RATIO, s + P_LOG_PT, s + P_BETA,
+                                 s + P_LOG_G, s + P_M_BD, s + P_DILUTION, s + P_C_INFL]
+        model = _model(6, 100, 1e-8, 1000.0, TP_MILNE, CLOUD_NONE, free=free,
+                       species=["H2O", "CO", "CH4", "NH3", "H2S", "K"],
+                       emission_flux=FLUX_BROWN_DWARF, distance_pc=10.0)
+        nu = nu_grid_constant_r(1.0, 5.1, n)
+        tabs = make_tables(nu, 6, np.geomspace(300.0, 3500.0, 20), np.geomspace(1e-8, 1000.0, 16))
+        lo, hi = make_bins(nu, min(500, n // 10))
+        rows = batch or 256
+        ranges = prior_ranges(model)
+        ranges.update({s + P_T_INT: (800.0, 1400.0), s + P_LOG_KAPPA: (-3.0, -1.0),
+                       s + P_LOG_PT: (-2.0, 2.0), s + P_BETA: (0.3, 1.0), s + P_LOG_G: (4.8, 5.4),
+                       s + P_C_INFL: (-16.0, -15.0)})
+        theta = _prior_batch(model, rows, seed, ranges)
+        kind = np.ones(rows, np.int32)
+        dtype, desc = "bf16", ("brown-dwarf emission with adjoint, B=256, L=100, 6 absorbers, "
+                               "20x16x54240 BF16 (1.0-5.1 um), modified Milne, flux at 10 pc, 500 bins")
+        level = 2.0e-15
     else:
         raise KeyError(name)
     y_obs, sigma = {}, {}
     nb = lo.size
     y_obs[KIND_TRANSMISSION], sigma[KIND_TRANSMISSION] = make_data(nb, KIND_TRANSMISSION,
                                                                    level if name != "batched_emis" else 0.014)
-    y_obs[KIND_EMISSION], sigma[KIND_EMISSION] = make_data(nb, KIND_EMISSION, 2.0e-3)
+    if name == "browndwarf":
+        y_obs[KIND_EMISSION], sigma[KIND_EMISSION] = make_data(nb, KIND_EMISSION, level, rel_sigma=0.05)
+    else:
+        y_obs[KIND_EMISSION], sigma[KIND_EMISSION] = make_data(nb, KIND_EMISSION, 2.0e-3)
     return Workload(name=name, model=model, tables=tabs, bin_lo_um=lo, bin_hi_um=hi,
                     y_obs=y_obs, sigma=sigma, theta=theta, kind=kind, table_dtype=dtype,
                     description=desc)

@@ -145,6 +145,21 @@ def test_batched_emission_bf16_small():
         check_sample(out, b, ref, 1, grad=(b < 2))
 
 
+def test_brown_dwarf_milne_emission():
+    """Modified Milne profile (Sect. 2.4.3) and the absolute brown-dwarf flux
+    at distance D with R_bd = sqrt(G M_bd / g) (Sect. 5): spectra, ln L and the
+    gradient with respect to all 15 free parameters of the Gliese 229 B-shaped
+    setup."""
+    w = synth.workload("browndwarf", batch=4, n_nu=2000)
+    tabs = oracle_tables(w)
+    ctx = binding.context_for(w)
+    out = gpu_eval(ctx, w, w.theta, np.ones(4, np.int32))
+    for b in range(4):
+        ref = oracle_eval(w, tabs, w.theta[b], 1, grad=(b < 2))
+        assert ref["valid"]
+        check_sample(out, b, ref, 1, grad=(b < 2))
+
+
 def test_mixed_batch_highres_shape():
     w = synth.workload("highres", batch=4, n_nu=6000)
     tabs = oracle_tables(w)

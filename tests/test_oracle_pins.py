@@ -80,6 +80,56 @@ def test_guillot_deep_limit_and_hopf_limits():
     assert q[0] == pytest.approx(0.2, abs=1e-6) and q[1] == pytest.approx(2.0 / 3.0, abs=1e-12)
 
 
+def test_milne_skin_eddington_deep_and_transition():
+    """Modified Milne (Sect. 2.4.3): T -> T_ratio T_int at the top (q -> q0 =
+    4/3 T_ratio^4, tau -> 0); with q0 = q_inf it is the Eddington-like Milne
+    solution 3/4 T_int^4 (tau + q_inf) at every pressure; deep, T^4 -> 3/4
+    T_int^4 tau; at p = p_t the Hopf function is q_inf + (q0 - q_inf)/e."""
+    t_int, kappa, g, p_t, beta = 1150.0, 10 ** -1.9, 10 ** 5.2, 8.0 * O.BAR, 0.9
+    t_ratio = 0.43
+    top = O.temperature_milne(np.array([1e-12 * O.BAR]), t_int, kappa, g, t_ratio, p_t, beta)
+    assert top[0] == pytest.approx(t_ratio * t_int, rel=1e-8)
+    p = np.geomspace(1e-8, 1e3, 50) * O.BAR
+    tau = kappa * p / g
+    t_edd = (0.75 * O.Q_MILNE_INF) ** 0.25
+    t = O.temperature_milne(p, t_int, kappa, g, t_edd, p_t, beta)
+    assert np.allclose(t, (0.75 * t_int ** 4 * (tau + O.Q_MILNE_INF)) ** 0.25, rtol=1e-13)
+    deep = np.array([1e12, 1e13]) * O.BAR
+    t = O.temperature_milne(deep, t_int, kappa, g, t_ratio, p_t, beta)
+    assert np.allclose(t ** 4 / (kappa * deep / g), 0.75 * t_int ** 4, rtol=1e-5)
+    t = O.temperature_milne(np.array([p_t]), t_int, kappa, g, t_ratio, p_t, beta)
+    q = O.Q_MILNE_INF + (4.0 / 3.0 * t_ratio ** 4 - O.Q_MILNE_INF) / np.e
+    assert t[0] ** 4 == pytest.approx(0.75 * t_int ** 4 * (kappa * p_t / g + q), rel=1e-13)
+
+
+def test_brown_dwarf_isothermal_flux():
+    """Sect. 5 brown-dwarf flux: an isothermal atmosphere emits pi B(T) at every
+    wavenumber, so F_bd = s pi B(T) (R_bd / D)^2 with R_bd = sqrt(G M_bd / g),
+    which also anchors the hydrostatic grid."""
+    m = _model(L=25)
+    m.emission_flux = O.FLUX_BROWN_DWARF
+    m.distance_cm = 10.0 * synth.PARSEC_CM
+    nu = synth.nu_grid_constant_r(1.0, 5.1, 40)
+    rng = np.random.default_rng(9)
+    tabs = _flat_tables(nu, -22.0)
+    tabs.log10_sigma = rng.uniform(-28, -19, tabs.log10_sigma.shape)
+    s = m.n_species
+    th = m.theta_fixed.copy()
+    th[0], th[s + O.P_LOG_G], th[s + O.P_M_BD], th[s + O.P_DILUTION] = -3.0, 5.1, 68.0, 0.8
+    mem = O.bin_members(nu, np.array([0.9]), np.array([6.0]))
+    spec, _ = O.forward(m, tabs, th, 1, mem)
+    r_bd = np.sqrt(6.67430e-8 * 1.89813e30 * 68.0 / 10 ** 5.1)
+    expect = 0.8 * np.pi * O.planck_wavenumber(th[s + O.P_T_ISO], nu) * (r_bd / m.distance_cm) ** 2
+    assert np.allclose(spec, expect, rtol=1e-12)
+    atm = O.atmosphere(m, th)
+    assert atm["r_ref"] == pytest.approx(r_bd, rel=1e-15)
+    # isothermal hydrostatics anchored at R_bd (closed form, as for planets)
+    g = 10 ** th[s + O.P_LOG_G]
+    inv = 1.0 / r_bd + O.K_B * th[s + O.P_T_ISO] * np.log(atm["p_lev"] / (m.p_ref_bar * O.BAR)) \
+        / (atm["mu"] * O.AMU * g * r_bd ** 2)
+    assert np.allclose(atm["r_lev"], 1.0 / inv, rtol=1e-13)
+
+
 # ---------------------------------------------------------------- hydrostatics
 def test_hydrostatic_isothermal_closed_form():
     """Isothermal, constant mu, g ~ 1/r^2: 1/r(p) = 1/R + k T ln(p/p_ref)/(mu m_u g R^2)
@@ -469,4 +519,25 @@ def test_complex_step_gradient_matches_central_differences(kind):
         b[slot] -= h
         fd = (O.loglike(m, w.tables, a, kind, mem, y_obs, sig)
               - O.loglike(m, w.tables, b, kind, mem, y_obs, sig)) / (2 * h)
+        assert g[k] == pytest.approx(fd, rel=2e-5, abs=1e-6 * np.max(np.abs(g))), slot
+
+
+def test_complex_step_gradient_brown_dwarf_milne():
+    """Complex-step gradient of the brown-dwarf emission likelihood (modified
+    Milne profile, mass and gravity through R_bd, dilution, inflation) against
+    central differences."""
+    w = synth.workload("browndwarf", n_nu=300, batch=2)
+    m = w.model
+    slots = list(m.free_idx)
+    th = m.full_theta(w.theta)[0]
+    mem = O.bin_members(w.tables.nu, w.bin_lo_um, w.bin_hi_um)
+    y_obs, sig = w.y_obs[1], w.sigma[1]
+    g = O.loglike_gradient(m, w.tables, th, 1, mem, y_obs, sig, slots)
+    for k, slot in enumerate(slots):
+        h = 1e-5 * max(1.0, abs(th[slot]))
+        a, b = th.copy(), th.copy()
+        a[slot] += h
+        b[slot] -= h
+        fd = (O.loglike(m, w.tables, a, 1, mem, y_obs, sig)
+              - O.loglike(m, w.tables, b, 1, mem, y_obs, sig)) / (2 * h)
         assert g[k] == pytest.approx(fd, rel=2e-5, abs=1e-6 * np.max(np.abs(g))), slot
