@@ -298,14 +298,14 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup_bwd(Model m, Work w) {
     }
     // forward-mode tangents in FP32 (values from the forward's FP64 results).
     // Temperature tangents, parallel over (parameter, layer or level): only
-    // the profile parameters and log g reach T.
+    // the profile parameters (slots up to log g, and T_ratio) reach T.
     const int npts = emis ? 2 * L + 1 : L;
     if (!bad) {
         for (int idx = tid; idx < m.nfree * npts; idx += blockDim.x) {
             const int p = idx / npts, k = idx % npts;
             const int seed = m.free_idx[p];
             float dt = 0.f;
-            if (seed >= S && seed - S <= ES_P_LOG_G) {
+            if (seed >= S && (seed - S <= ES_P_LOG_G || seed - S == ES_P_T_RATIO)) {
                 DualF th[ES_MAX_PARAMS];
                 for (int j = 0; j < m.nfull; ++j) th[j] = DualF((float)thv[j], j == seed ? 1.f : 0.f);
                 dt = temperature<DualF>(m, th, k < L ? m.p_lay[k] : m.p_lev[k - L]).d;
