@@ -51,7 +51,7 @@ enum { ES_TP_ISOTHERMAL = 0, ES_TP_GUILLOT = 1, ES_TP_GUILLOT_MOD = 2, ES_TP_MIL
 /* Emission output: planet-to-star flux ratio (Sect. 5, Fp/F*) or the
  * absolute flux of an isolated brown dwarf at distance D (Sect. 5, F_bd). */
 enum { ES_FLUX_PLANET_STAR = 0, ES_FLUX_BROWN_DWARF = 1 };
-enum { ES_CLOUD_NONE = 0, ES_CLOUD_DECK = 1 };
+enum { ES_CLOUD_NONE = 0, ES_CLOUD_DECK = 1, ES_CLOUD_KH18 = 2 };
 enum { ES_KIND_TRANSMISSION = 0, ES_KIND_EMISSION = 1 };
 enum { ES_TABLE_F32 = 0, ES_TABLE_BF16 = 1 };
 enum { ES_MEM_HOST = 0, ES_MEM_DEVICE = 1 };
@@ -77,11 +77,24 @@ enum { ES_FLAG_INVALID = 1 };
  *                modified Milne profile, q0 = 4/3 T_RATIO^4 (Sect. 2.4.3)
  *   M_BD         brown-dwarf mass [Jupiter masses, 1.89813e30 g]; the radius
  *                is R_bd = sqrt(G M_bd / g) (Sect. 5, ES_FLUX_BROWN_DWARF)
+ * Non-grey cloud (ES_CLOUD_KH18, Sect. 2.5): extinction rho_a kappa_ext with
+ * kappa_ext = 3 q_c^eff Q_ext(x) / (4 r_eff), Q_ext = 1/(Q0 x^-a + x^0.2),
+ * x = 2 pi r_eff nu, q_c^eff(p) = q_base (p/p_base)^alpha_c above the base
+ * (0 below), and the cloud fraction f_cld mixing cloudy and clear spectra:
+ *   LOG_QC       log10 q_base (effective mass mixing ratio at the base)
+ *   LOG_PC_BASE  log10 cloud-base pressure [bar]
+ *   ALPHA_C      power-law index alpha_c of q_c^eff above the base
+ *   LOG_R_EFF    log10 effective particle radius [micron]
+ *   A_KH         spectral slope index a of Q_ext
+ *   LOG_Q0       log10 Q0 of Q_ext
+ *   F_CLD        cloud fraction f_cld in [0, 1]
  */
 enum {
     ES_P_T_ISO = 0, ES_P_T_INT, ES_P_T_EQ, ES_P_LOG_KAPPA_IR, ES_P_LOG_GAMMA_V,
     ES_P_Q_IRR0, ES_P_LOG_P_T, ES_P_BETA, ES_P_LOG_G, ES_P_R_P, ES_P_LOG_P_CLOUD,
-    ES_P_C_INFL, ES_P_DILUTION, ES_P_T_RATIO, ES_P_M_BD, ES_P_N_EXTRA
+    ES_P_C_INFL, ES_P_DILUTION, ES_P_T_RATIO, ES_P_M_BD,
+    ES_P_LOG_QC, ES_P_LOG_PC_BASE, ES_P_ALPHA_C, ES_P_LOG_R_EFF, ES_P_A_KH, ES_P_LOG_Q0, ES_P_F_CLD,
+    ES_P_N_EXTRA
 };
 
 #define ES_MAX_SPECIES 16

@@ -33,6 +33,8 @@ Readings where the paper is silent (documented in DESIGN.md, "Readings"):
  - emission: absorption-only linear-in-tau RT with 4 Gauss-Legendre angles on
    [0, 1], bottom boundary I = B(T_bottom level), F_* = pi B(T_*);
  - modified Milne profile: q_inf fixed at the Hopf function's deep limit;
+ - non-grey cloud: r_eff in micron, the mass-mixing-ratio profile of the cloud
+   base with a power law above it, no grey deck in the same model;
    a brown dwarf's hydrostatic reference radius is its R_bd = sqrt(G M_bd/g);
  - binning: equal-weight mean over native points with lambda in [lo, hi).
 
@@ -67,7 +69,8 @@ INVALID_LNL = -1.0e300      # Sect. 2.3: invalid forward-model output
 
 # canonical slots after the S log-VMR slots
 (P_T_ISO, P_T_INT, P_T_EQ, P_LOG_KAPPA, P_LOG_GAMMA, P_Q_IRR0, P_LOG_PT, P_BETA,
- P_LOG_G, P_R_P, P_LOG_PCLOUD, P_C_INFL, P_DILUTION, P_T_RATIO, P_M_BD) = range(15)
+ P_LOG_G, P_R_P, P_LOG_PCLOUD, P_C_INFL, P_DILUTION, P_T_RATIO, P_M_BD,
+ P_LOG_QC, P_LOG_PC_BASE, P_ALPHA_C, P_LOG_R_EFF, P_A_KH, P_LOG_Q0, P_F_CLD) = range(22)
 TP_ISOTHERMAL, TP_GUILLOT, TP_GUILLOT_MOD, TP_MILNE = 0, 1, 2, 3
 FLUX_PLANET_STAR, FLUX_BROWN_DWARF = 0, 1
 
@@ -78,7 +81,7 @@ Q_MILNE_INF = 0.7104460895
 # Sect. 5 (brown dwarfs): R_bd = sqrt(G M_bd / g); CODATA 2018 G, nominal Jupiter mass
 G_GRAV = 6.67430e-8         # cm^3 g^-1 s^-2
 M_JUP = 1.89813e30          # g
-CLOUD_NONE, CLOUD_DECK = 0, 1
+CLOUD_NONE, CLOUD_DECK, CLOUD_KH18 = 0, 1, 2
 
 
 def _re(x):
@@ -284,6 +287,30 @@ def extinction(tabs, model, x_trace, x_h2, x_he, t_lay, p_lay):
 
 
 # --------------------------------------------------------------------------
+# Sect. 2.5: non-grey aerosol opacity
+# --------------------------------------------------------------------------
+def cloud_mass_mixing_ratio(p, q_base, p_base, alpha_c):
+    """Sect. 2.5.1 (third profile): q_c(p) = q_base (p / p_base)^alpha above
+    the cloud base (p <= p_base) and 0 below it."""
+    return np.where(_re(p) <= _re(p_base), q_base * (p / p_base) ** alpha_c, 0.0)
+
+
+def q_ext_kh18(x, q0, a):
+    """Eq. Q_ext_KH with Q_1 subsumed into the effective mass mixing ratio:
+    Q_ext / Q_1 = 1 / (Q_0 x^-a + x^0.2)."""
+    return 1.0 / (q0 * x ** (-a) + x ** 0.2)
+
+
+def cloud_extinction(nu, rho_a, q_c_eff, r_eff, q0, a):
+    """Sect. 2.5.2 (modified Fisher & Heng 2018): kappa_ext = 3 q_c^eff Q_ext(x)
+    / (4 r_eff) [cm^2 g^-1] with the size parameter x = 2 pi r_eff / lambda =
+    2 pi r_eff nu, and the layer extinction alpha_c(l, nu) = rho_a(l) kappa_ext
+    [cm^-1]; rho_a is the background gas mass density."""
+    x = 2.0 * np.pi * r_eff * nu
+    return (3.0 * rho_a * q_c_eff / (4.0 * r_eff))[:, None] * q_ext_kh18(x, q0, a)[None, :]
+
+
+# --------------------------------------------------------------------------
 # transmission (Sect. 4)
 # --------------------------------------------------------------------------
 def transit_depth(tau, r_lev, r_c, r_star):
@@ -421,6 +448,17 @@ def forward(model, tabs, theta, kind, members):
     alpha = extinction(tabs, model, atm["x_trace"], atm["x_h2"], atm["x_he"],
                        atm["t_lay"], atm["p_lay"])
     r_lev = atm["r_lev"]
+    # Sect. 2.5.2: cloudy and cloud-free spectra mixed by the cloud fraction,
+    # Phi = f Phi_cld + (1 - f) Phi_cf
+    cloudy = model.cloud_kind == CLOUD_KH18
+    if cloudy:
+        p_lay, t_lay = atm["p_lay"], atm["t_lay"]
+        q_c = cloud_mass_mixing_ratio(p_lay, 10.0 ** theta[s + P_LOG_QC],
+                                      10.0 ** theta[s + P_LOG_PC_BASE] * BAR, theta[s + P_ALPHA_C])
+        rho_a = atm["mu"] * AMU * p_lay / (K_B * t_lay)
+        alpha_cld = alpha + cloud_extinction(tabs.nu, rho_a, q_c, 10.0 ** theta[s + P_LOG_R_EFF] * 1.0e-4,
+                                             10.0 ** theta[s + P_LOG_Q0], theta[s + P_A_KH])
+        f_cld = theta[s + P_F_CLD]
     if kind == 0:
         P, dr, _ = path_matrix(r_lev)
         dtau_vert = alpha * dr[:, None]
@@ -430,11 +468,16 @@ def forward(model, tabs, theta, kind, members):
         else:
             r_c = r_lev[-1]
         spec = transit_depth(tau, r_lev, r_c, model.r_star_cm)
+        if cloudy:
+            spec_cld = transit_depth(P @ (alpha_cld * dr[:, None]), r_lev, r_c, model.r_star_cm)
+            spec = f_cld * spec_cld + (1.0 - f_cld) * spec
     else:
         dr = r_lev[:-1] - r_lev[1:]
         dtau = alpha * dr[:, None]
         b_lev = planck_wavenumber(atm["t_lev"][:, None], tabs.nu[None, :])
         f_toa = emergent_flux(b_lev, dtau)
+        if cloudy:
+            f_toa = f_cld * emergent_flux(b_lev, alpha_cld * dr[:, None]) + (1.0 - f_cld) * f_toa
         if getattr(model, "emission_flux", FLUX_PLANET_STAR) == FLUX_BROWN_DWARF:
             # Sect. 5: F_bd = s F_toa (R_bd / D)^2
             spec = theta[s + P_DILUTION] * f_toa * (atm["r_ref"] / model.distance_cm) ** 2

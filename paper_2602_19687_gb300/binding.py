@@ -19,7 +19,7 @@ ES_OK, ES_EINVAL, ES_ENOMEM, ES_ECUDA, ES_ESTATE, ES_ETIMEOUT = range(6)
 ES_MEM_HOST, ES_MEM_DEVICE = 0, 1
 ES_TABLE_F32, ES_TABLE_BF16 = 0, 1
 ES_MAX_SPECIES = 16
-ES_P_N_EXTRA = 15
+ES_P_N_EXTRA = 22
 ES_MAX_PARAMS = ES_MAX_SPECIES + ES_P_N_EXTRA
 ES_MAX_LAYERS = 112
 STATUS_NAMES = {0: "ES_OK", 1: "ES_EINVAL", 2: "ES_ENOMEM", 3: "ES_ECUDA", 4: "ES_ESTATE", 5: "ES_ETIMEOUT"}

@@ -24,13 +24,14 @@ R_SUN_CM = 6.957e10
 # Canonical parameter slots that follow the S log-VMR slots (same documented
 # order as include/exoskry.h and the oracle).
 P_T_ISO, P_T_INT, P_T_EQ, P_LOG_KAPPA, P_LOG_GAMMA, P_Q_IRR0, P_LOG_PT, P_BETA, \
-    P_LOG_G, P_R_P, P_LOG_PCLOUD, P_C_INFL, P_DILUTION, P_T_RATIO, P_M_BD = range(15)
-N_EXTRA = 15
+    P_LOG_G, P_R_P, P_LOG_PCLOUD, P_C_INFL, P_DILUTION, P_T_RATIO, P_M_BD, \
+    P_LOG_QC, P_LOG_PC_BASE, P_ALPHA_C, P_LOG_R_EFF, P_A_KH, P_LOG_Q0, P_F_CLD = range(22)
+N_EXTRA = 22
 
 TP_ISOTHERMAL, TP_GUILLOT, TP_GUILLOT_MOD, TP_MILNE = 0, 1, 2, 3
 FLUX_PLANET_STAR, FLUX_BROWN_DWARF = 0, 1
 PARSEC_CM = 3.0856775814913673e18
-CLOUD_NONE, CLOUD_DECK = 0, 1
+CLOUD_NONE, CLOUD_DECK, CLOUD_KH18 = 0, 1, 2
 KIND_TRANSMISSION, KIND_EMISSION = 0, 1
 
 SPECIES = {  # name: mass in amu
@@ -216,6 +217,13 @@ def _model(n_species, n_layers, p_top, p_bot, tp_kind, cloud_kind, free, fixed=N
     theta[s + P_DILUTION] = 1.0
     theta[s + P_T_RATIO] = 0.5
     theta[s + P_M_BD] = 70.0
+    theta[s + P_LOG_QC] = -5.0
+    theta[s + P_LOG_PC_BASE] = 0.0
+    theta[s + P_ALPHA_C] = 1.0
+    theta[s + P_LOG_R_EFF] = -0.5
+    theta[s + P_A_KH] = 4.0
+    theta[s + P_LOG_Q0] = 1.0
+    theta[s + P_F_CLD] = 0.5
     for k, v in (fixed or {}).items():
         theta[k] = v
     return Model(n_layers=n_layers, p_top_bar=p_top, p_bot_bar=p_bot, p_ref_bar=10.0,
@@ -244,7 +252,9 @@ def prior_ranges(model):
               s + P_LOG_G: (2.7, 3.3), s + P_R_P: (0.9, 1.5),
               s + P_LOG_PCLOUD: (-6.0, 2.0), s + P_C_INFL: (-9.0, -4.0),
               s + P_DILUTION: (0.5, 1.0), s + P_T_RATIO: (0.2, 0.9),
-              s + P_M_BD: (65.0, 78.0)})
+              s + P_M_BD: (65.0, 78.0), s + P_LOG_QC: (-8.0, -3.0), s + P_LOG_PC_BASE: (-3.0, 1.0),
+              s + P_ALPHA_C: (0.0, 2.0), s + P_LOG_R_EFF: (-2.0, 0.5), s + P_A_KH: (2.0, 6.0),
+              s + P_LOG_Q0: (0.0, 2.0), s + P_F_CLD: (0.2, 1.0)})
     return r
 
 
@@ -267,6 +277,11 @@ def workload(name: str, batch: int | None = None, seed: int = 42,
                 deck, radius), L=60, 4 absorbers on 12 x 10 x 440000 nu
                 (0.9-5.3 um, R~250k), ~4400 bins of 100 points, BF16,
                 mixed transmission/emission batch.
+    cloudy_trans 1024 transmission vectors as batched_trans with the non-grey
+                cloud (modified Fisher & Heng / Kitzmann & Heng Q_ext, base
+                + power-law q_c profile) and a cloud fraction instead of the
+                grey deck: 18 free parameters (6 log-VMR, 4 Guillot, radius,
+                7 cloud).
     browndwarf  256 brown-dwarf emission vectors shaped like the paper's
                 Gliese 229 B setup: 15 free parameters (6 log-VMR, T_int,
                 log kappa_ir, T_ratio, log p_t, beta of the modified Milne
@@ -276,7 +291,7 @@ def workload(name: str, batch: int | None = None, seed: int = 42,
     `n_nu` shrinks the spectral grid (same physics) for fast tests.
     """
     S = {"tiny": 3, "jwst_plain": 6, "batched_trans": 8, "batched_emis": 8, "highres": 4,
-         "browndwarf": 6}[name]
+         "browndwarf": 6, "cloudy_trans": 8}[name]
     s = S
     if name == "tiny":
         n = n_nu or 2000
@@ -347,6 +362,21 @@ def workload(name: str, batch: int | None = None, seed: int = 42,
         kind = (np.arange(rows) % 2).astype(np.int32)     # mixed batch
         dtype, desc = "bf16", ("high-resolution mixed batch with adjoint, B=64, L=60, 4 absorbers, "
                                "12x10x440000 BF16 (0.9-5.3 um), ~4400 bins")
+        level = (1.2 * R_JUP_CM / model.r_star_cm) ** 2
+    elif name == "cloudy_trans":
+        n = n_nu or 30000
+        free = list(range(6)) + [s + P_T_INT, s + P_T_EQ, s + P_LOG_KAPPA, s + P_LOG_GAMMA, s + P_R_P,
+                                 s + P_LOG_QC, s + P_LOG_PC_BASE, s + P_ALPHA_C, s + P_LOG_R_EFF,
+                                 s + P_A_KH, s + P_LOG_Q0, s + P_F_CLD]
+        model = _model(8, 100, 1e-8, 100.0, TP_GUILLOT, CLOUD_KH18, free=free)
+        nu = nu_grid_constant_r(0.5, 5.5, n)
+        tabs = make_tables(nu, 8, np.geomspace(400.0, 3000.0, 20), np.geomspace(1e-8, 100.0, 15))
+        lo, hi = make_bins(nu, min(300, n // 10))
+        rows = batch or 1024
+        theta = _prior_batch(model, rows, seed, prior_ranges(model))
+        kind = np.zeros(rows, np.int32)
+        dtype, desc = "bf16", ("batched transmission with a non-grey cloud and cloud fraction, B=1024, L=100, "
+                               "8 absorbers, 20x15x30000 BF16, Guillot-4, 300 bins")
         level = (1.2 * R_JUP_CM / model.r_star_cm) ** 2
     elif name == "browndwarf":
         n = n_nu or 54240

@@ -130,6 +130,81 @@ def test_brown_dwarf_isothermal_flux():
     assert np.allclose(atm["r_lev"], 1.0 / inv, rtol=1e-13)
 
 
+def test_cloud_profile_qext_and_number_density_form():
+    """Sect. 2.5: the base + power-law mass mixing ratio (zero below the base);
+    the KH18 fitting form; and kappa_ext = 3 q_eff Q_ext / (4 r) equal to
+    N0 Q_ext pi r^2 / rho_a with N0 = 3 rho_a q_c / (4 pi rho_d r^3) and
+    q_eff = Q1 q_c / rho_d, for any rho_d and Q1 (monodisperse spheres)."""
+    p = np.array([1e-3, 0.5, 1.0, 2.0]) * O.BAR
+    q = O.cloud_mass_mixing_ratio(p, 1e-4, 1.0 * O.BAR, 1.5)
+    assert np.allclose(q, [1e-4 * 1e-3 ** 1.5, 1e-4 * 0.5 ** 1.5, 1e-4, 0.0], rtol=1e-15, atol=0)
+    x = np.array([0.01, 0.3, 1.0, 7.0, 90.0])
+    assert np.allclose(O.q_ext_kh18(x, 12.0, 4.5), 1.0 / (12.0 * x ** -4.5 + x ** 0.2), rtol=1e-15)
+    rho_a, q_c, r, rho_d, q1 = 3.7e-6, 2.3e-5, 0.8e-4, 3.3, 2.1
+    nu = np.array([2000.0, 11000.0])
+    n0 = 3.0 * rho_a * q_c / (4.0 * np.pi * rho_d * r ** 3)
+    qext = q1 * O.q_ext_kh18(2.0 * np.pi * r * nu, 12.0, 4.5)
+    alpha = O.cloud_extinction(nu, np.array([rho_a]), np.array([q1 * q_c / rho_d]), r, 12.0, 4.5)
+    assert np.allclose(alpha[0], n0 * qext * np.pi * r ** 2, rtol=1e-13)
+
+
+def _cloud_setup(kind):
+    w = synth.workload("cloudy_trans", n_nu=300, batch=2)
+    m = w.model
+    th = m.full_theta(w.theta)[0]
+    s = m.n_species
+    th[s + O.P_LOG_QC], th[s + O.P_LOG_PC_BASE], th[s + O.P_LOG_R_EFF] = -4.0, 0.5, -0.7
+    mem = O.bin_members(w.tables.nu, w.bin_lo_um, w.bin_hi_um)
+    return w, m, th, s, mem
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_cloud_fraction_limits_and_linearity(kind):
+    """f_cld = 0 gives the cloud-free model exactly, the spectrum is linear in
+    f_cld, and a vanishing cloud mass has no effect; the cloud changes it."""
+    w, m, th, s, mem = _cloud_setup(kind)
+    clear = dataclasses.replace(m, cloud_kind=O.CLOUD_NONE)
+    ref, _ = O.forward(clear, w.tables, th, kind, mem)
+    spec = {}
+    for f in (0.0, 0.37, 1.0):
+        t = th.copy()
+        t[s + O.P_F_CLD] = f
+        spec[f], _ = O.forward(m, w.tables, t, kind, mem)
+    assert np.allclose(spec[0.0], ref, rtol=1e-14, atol=0)
+    assert np.allclose(spec[0.37], 0.37 * spec[1.0] + 0.63 * spec[0.0], rtol=1e-12, atol=0)
+    assert np.max(np.abs(spec[1.0] / ref - 1.0)) > 1e-3
+    t = th.copy()
+    t[s + O.P_LOG_QC], t[s + O.P_F_CLD] = -99.0, 1.0
+    assert np.allclose(O.forward(m, w.tables, t, kind, mem)[0], ref, rtol=1e-14, atol=0)
+
+
+def test_uniform_cloud_equals_constant_absorber():
+    """A cloud of uniform q_c (base below the model, alpha_c = 0) with no gas
+    opacity gives the transit depth of an absorber whose cross-section times
+    VMR is mu m_u kappa_ext(nu): pins rho_a = mu m_u n and the cloud's entry
+    into the chord optical depth."""
+    m = _model(L=40, tp=O.TP_ISOTHERMAL, cloud=O.CLOUD_KH18)
+    m.ray_h2_cm2 = m.ray_he_cm2 = 0.0
+    s = m.n_species
+    nu = synth.nu_grid_constant_r(0.6, 5.0, 30)
+    th = m.theta_fixed.copy()
+    th[0] = -4.0
+    th[s + O.P_LOG_QC], th[s + O.P_LOG_PC_BASE], th[s + O.P_ALPHA_C] = -5.5, 5.0, 0.0
+    th[s + O.P_LOG_R_EFF], th[s + O.P_A_KH], th[s + O.P_LOG_Q0], th[s + O.P_F_CLD] = -0.4, 4.0, 1.2, 1.0
+    mem = O.bin_members(nu, np.array([0.55]), np.array([5.5]))
+    cloud_tabs = _flat_tables(nu, -99.0)
+    spec_cloud, _ = O.forward(m, cloud_tabs, th, 0, mem)
+    atm = O.atmosphere(m, th)
+    r = 10 ** th[s + O.P_LOG_R_EFF] * 1e-4
+    kappa = 3.0 * 10 ** th[s + O.P_LOG_QC] / (4.0 * r) * O.q_ext_kh18(2 * np.pi * r * nu, 10 ** 1.2, 4.0)
+    sigma = atm["mu"] * O.AMU * kappa / 10 ** th[0]
+    gas_tabs = _flat_tables(nu, -99.0)
+    gas_tabs.log10_sigma = np.broadcast_to(np.log10(sigma), gas_tabs.log10_sigma.shape).copy()
+    clear = dataclasses.replace(m, cloud_kind=O.CLOUD_NONE)
+    spec_gas, _ = O.forward(clear, gas_tabs, th, 0, mem)
+    assert np.allclose(spec_cloud, spec_gas, rtol=1e-12)
+
+
 # ---------------------------------------------------------------- hydrostatics
 def test_hydrostatic_isothermal_closed_form():
     """Isothermal, constant mu, g ~ 1/r^2: 1/r(p) = 1/R + k T ln(p/p_ref)/(mu m_u g R^2)
@@ -540,4 +615,23 @@ def test_complex_step_gradient_brown_dwarf_milne():
         b[slot] -= h
         fd = (O.loglike(m, w.tables, a, 1, mem, y_obs, sig)
               - O.loglike(m, w.tables, b, 1, mem, y_obs, sig)) / (2 * h)
+        assert g[k] == pytest.approx(fd, rel=2e-5, abs=1e-6 * np.max(np.abs(g))), slot
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_complex_step_gradient_cloud(kind):
+    """Complex-step gradient of the non-grey cloud and cloud fraction (all 7
+    cloud slots, radius, a VMR, a profile slot) against central differences."""
+    w, m, th, s, mem = _cloud_setup(kind)
+    slots = [0, s + O.P_T_EQ, s + O.P_R_P] + [s + k for k in (O.P_LOG_QC, O.P_LOG_PC_BASE, O.P_ALPHA_C,
+                                                              O.P_LOG_R_EFF, O.P_A_KH, O.P_LOG_Q0, O.P_F_CLD)]
+    y_obs, sig = w.y_obs[kind], w.sigma[kind]
+    g = O.loglike_gradient(m, w.tables, th, kind, mem, y_obs, sig, slots)
+    for k, slot in enumerate(slots):
+        h = 1e-5 * max(1.0, abs(th[slot]))
+        a, b = th.copy(), th.copy()
+        a[slot] += h
+        b[slot] -= h
+        fd = (O.loglike(m, w.tables, a, kind, mem, y_obs, sig)
+              - O.loglike(m, w.tables, b, kind, mem, y_obs, sig)) / (2 * h)
         assert g[k] == pytest.approx(fd, rel=2e-5, abs=1e-6 * np.max(np.abs(g))), slot
