@@ -222,6 +222,9 @@ es_status alloc_forward(es_ctx *c, int B) {
     ALLOC(w.gtc, B * L);
     ALLOC(w.ccia, B * L * 2);
     ALLOC(w.ray, B * L);
+    ALLOC(w.cloud_c, B * L);
+    ALLOC(w.cloud_d, B * L);
+    ALLOC(w.cloud_g, B * 4);
     ALLOC(w.spec, (size_t)B * N);
     ALLOC(w.lnl, B);
     ALLOC(w.misc, (size_t)B * 4);
@@ -349,7 +352,7 @@ es_status es_create(es_ctx **out, int device, const es_model_desc *d) {
     if (d->n_layers < 2 || d->n_layers > ES_MAX_LAYERS) return ES_EINVAL;
     if (d->n_species < 1 || d->n_species > ES_MAX_SPECIES) return ES_EINVAL;
     if (!(d->p_top_bar > 0) || !(d->p_bot_bar > d->p_top_bar) || !(d->p_ref_bar > 0)) return ES_EINVAL;
-    if (d->tp_kind < 0 || d->tp_kind > ES_TP_MILNE || d->cloud_kind < 0 || d->cloud_kind > 1) return ES_EINVAL;
+    if (d->tp_kind < 0 || d->tp_kind > ES_TP_MILNE || d->cloud_kind < 0 || d->cloud_kind > ES_CLOUD_KH18) return ES_EINVAL;
     if (d->emission_flux != ES_FLUX_PLANET_STAR && d->emission_flux != ES_FLUX_BROWN_DWARF) return ES_EINVAL;
     if (d->emission_flux == ES_FLUX_BROWN_DWARF && !(d->distance_cm > 0)) return ES_EINVAL;
     if (!(d->r_star_cm > 0) || !(d->t_star_k > 0)) return ES_EINVAL;
@@ -669,6 +672,8 @@ es_status es_set_batch(es_ctx *c, const double *theta, const int32_t *kind, int 
             return fail(c, ES_EINVAL, "kind must be 0 (transmission) or 1 (emission)");
         nk[kh[b]]++;
     }
+    if (c->m.cloud_kind == ES_CLOUD_KH18 && nk[ES_KIND_EMISSION] > 0)
+        return fail(c, ES_EINVAL, "the non-grey cloud is implemented for transmission samples only");
     e = cudaMemcpyAsync(c->w.kind, kh.data(), sizeof(int32_t) * batch, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && mem == ES_MEM_HOST) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess && kind && mem == ES_MEM_DEVICE) e = cudaStreamSynchronize(st);
@@ -777,6 +782,8 @@ es_status enqueue_forward_backward(es_ctx *c, cudaStream_t st) {
 
 es_status es_forward_backward(es_ctx *c, double *lnl, double *grad, int mem, es_stream_t stream) {
     if (!c) return ES_EINVAL;
+    if (c->m.cloud_kind == ES_CLOUD_KH18)
+        return fail(c, ES_EINVAL, "the adjoint of the non-grey cloud is not implemented yet");
     if (mem != ES_MEM_HOST && mem != ES_MEM_DEVICE) return fail(c, ES_EINVAL, "bad mem");
     es_status s = ready(c);
     if (s != ES_OK) return s;

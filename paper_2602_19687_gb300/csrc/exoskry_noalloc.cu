@@ -103,6 +103,8 @@ extern "C" es_status es_loglike_noalloc(es_ctx *c, const double *theta, const in
                                         double *lnl, es_stream_t stream) {
     if (!c) return ES_EINVAL;
     if (!theta || !lnl || batch < 1) return fail(c, ES_EINVAL, "es_loglike_noalloc: NULL theta/lnL or batch < 1");
+    if (c->m.cloud_kind == ES_CLOUD_KH18)
+        return fail(c, ES_EINVAL, "es_loglike_noalloc: the non-grey cloud needs the allocating entry points");
     if (!c->have_tables) return fail(c, ES_ESTATE, "tables not loaded");
     if (!c->have_grid) return fail(c, ES_ESTATE, "instrument grid not set");
     if (!c->have_data[ES_KIND_TRANSMISSION] || (kind && !c->have_data[ES_KIND_EMISSION]))

@@ -110,6 +110,10 @@ struct Work {
     float *wtc, *gtc;             // [B][L] CIA weight, 1/dT (0 if clamped)
     float *ccia;                  // [B][L][2] log2(n^2 X_H2 X_H2), log2(n^2 X_H2 X_He)
     float *ray;                   // [B][L] n (X_H2 s_H2 + X_He s_He)
+    // non-grey cloud (ES_CLOUD_KH18): extinction C_l g(nu), g = 1/(Q0 x^-a + x^0.2)
+    float *cloud_c;               // [B][L] C_l = 3 rho_a q_c^eff / (4 r_eff)
+    float *cloud_d;               // [B][L] D_i = sum_l L_il C_l: cloudy chord depth = tau_i + g(nu) D_i
+    float *cloud_g;               // [B][4] 2 pi r_eff [cm], a, Q0, f_cld
     float *spec;                  // [B][N] transmission: depth - base; emission: Fp/F*
     double *ymod;                 // [B][nbins]
     double *lnl;                  // [B]

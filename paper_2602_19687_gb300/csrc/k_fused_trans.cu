@@ -45,6 +45,8 @@ struct TransFwdSmem {
     alignas(128) unsigned char lh[(LP / 8) * SBO_LP], ll[(LP / 8) * SBO_LP];    // L[i][l], split BF16
     alignas(128) unsigned char ah[1][(LP / 8) * SBO_NU], al[1][(LP / 8) * SBO_NU];   // alpha[l][nu], split BF16
     float area[LP];
+    float cd[LP];                                  // non-grey cloud: D_i (0 beyond L)
+    float cg[4];                                   // non-grey cloud: 2 pi r_eff, a, Q0, f_cld
     float part[2][4][FT2];                         // per-column-chunk partial transit sums, per buffer
     alignas(8) uint64_t mbar[2];
     uint32_t tmem_base;
@@ -181,13 +183,44 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, in
                 if (i0 + 1 < L) __stcs(eb + (k + 1) * FT2, e.y);
             }
         };
+        float s;
+        if (m.cloud_kind != ES_CLOUD_KH18) {
 #pragma unroll
-        for (int k = 0; k < 16; k += 2) term2(k, v16[k], v16[k + 1]);
+            for (int k = 0; k < 16; k += 2) term2(k, v16[k], v16[k + 1]);
 #pragma unroll
-        for (int k = 0; k < 8; k += 2) term2(16 + k, v8[k], v8[k + 1]);
+            for (int k = 0; k < 8; k += 2) term2(16 + k, v8[k], v8[k + 1]);
 #pragma unroll
-        for (int k = 0; k < 4; k += 2) term2(24 + k, v4[k], v4[k + 1]);
-        const float s = s2.x + s2.y;
+            for (int k = 0; k < 4; k += 2) term2(24 + k, v4[k], v4[k + 1]);
+            s = s2.x + s2.y;
+        } else {
+            // non-grey cloud (Sect. 2.5): the cloudy chord depth is tau_i + g(nu) D_i,
+            // g = 1/(Q0 x^-a + x^0.2), x = 2 pi r_eff nu; the two transit depths
+            // mix by the cloud fraction, f delta_cld + (1 - f) delta_cf
+            const float lx = log2f(sm.cg[0] * m.nu[(size_t)pt * FT2 + nl]);
+            const float g = 1.f / (sm.cg[2] * exp2f(-sm.cg[1] * lx) + exp2f(0.2f * lx));
+            const float2 gl = f2(-g * LOG2E_F);
+            float2 s2c = f2(0.f);
+            auto term2c = [&](int k, float t0, float t1) {
+                const int i0 = 28 * ck + k;
+                const float2 e = ex2x2(mul2(make_float2(t0, t1), f2(-LOG2E_F)));
+                const float2 a = *reinterpret_cast<const float2 *>(&sm.area[i0]);
+                const float2 d = *reinterpret_cast<const float2 *>(&sm.cd[i0]);
+                const float2 ec = mul2(e, ex2x2(mul2(gl, d)));
+                s2 = fma2(a, fma2(e, f2(-1.f), f2(1.f)), s2);
+                s2c = fma2(a, fma2(ec, f2(-1.f), f2(1.f)), s2c);
+                if (STORE_E) {   // the cloud-free exp(-tau); the adjoint rebuilds the cloudy one
+                    if (i0 < L) __stcs(eb + k * FT2, e.x);
+                    if (i0 + 1 < L) __stcs(eb + (k + 1) * FT2, e.y);
+                }
+            };
+#pragma unroll
+            for (int k = 0; k < 16; k += 2) term2c(k, v16[k], v16[k + 1]);
+#pragma unroll
+            for (int k = 0; k < 8; k += 2) term2c(16 + k, v8[k], v8[k + 1]);
+#pragma unroll
+            for (int k = 0; k < 4; k += 2) term2c(24 + k, v4[k], v4[k + 1]);
+            s = sm.cg[3] * (s2c.x + s2c.y) + (1.f - sm.cg[3]) * (s2.x + s2.y);
+        }
         sm.part[buf][ck][nl] = s;
     };
     auto write_spec = [&](int pb, int pt, int buf) {
@@ -224,6 +257,10 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, in
             __syncthreads();
             stage_sample(m, w, b, sm.sc, RUN_COST_FWD, SBO_NU);
             stage_lmat_tc(m, w, b, sm.lh, sm.ll, sm.area);
+            if (m.cloud_kind == ES_CLOUD_KH18) {
+                for (int i = threadIdx.x; i < LP; i += F2_THREADS) sm.cd[i] = (i < L) ? w.cloud_d[(size_t)b * L + i] : 0.f;
+                if (threadIdx.x < 4) sm.cg[threadIdx.x] = w.cloud_g[(size_t)b * 4 + threadIdx.x];
+            }
             cur_b = b;
             fence_async_smem();
             __syncthreads();

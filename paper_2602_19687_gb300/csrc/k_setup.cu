@@ -135,6 +135,34 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup(Model m, Work w) {
         }
         w.lmat[(size_t)b * L * L + idx] = v;
     }
+    if (m.cloud_kind == ES_CLOUD_KH18) {
+        // Sect. 2.5: C_l = 3 rho_a q_c^eff(p_l) / (4 r_eff) with the base +
+        // power-law profile, and D_i = sum_l L_il C_l (the cloud's chord depth
+        // per unit g(nu)); the block's lmat rows are read back after the barrier
+        const double r_eff = exp10(th[S + ES_P_LOG_R_EFF]) * 1.0e-4;
+        const double q_base = exp10(th[S + ES_P_LOG_QC]), p_base = exp10(th[S + ES_P_LOG_PC_BASE]) * BAR;
+        for (int l = tid; l < L; l += blockDim.x) {
+            const double p = m.p_lay[l];
+            const double q = (p <= p_base) ? q_base * pow(p / p_base, th[S + ES_P_ALPHA_C]) : 0.0;
+            const double rho = s_mu * AMU * p / (K_B * tl[l]);
+            w.cloud_c[(size_t)b * L + l] = bad ? 0.f : (float)(3.0 * rho * q / (4.0 * r_eff));
+        }
+        __syncthreads();
+        const float *cl = w.cloud_c + (size_t)b * L;
+        for (int i = tid; i < L; i += blockDim.x) {
+            const float *li = w.lmat + (size_t)b * L * L + (size_t)i * L;
+            double d = 0.0;
+            for (int l = 0; l <= i; ++l) d += (double)li[l] * (double)cl[l];
+            w.cloud_d[(size_t)b * L + i] = (float)d;
+        }
+        if (tid == 0) {
+            float *cg = w.cloud_g + (size_t)b * 4;
+            cg[0] = (float)(2.0 * PI * r_eff);
+            cg[1] = (float)th[S + ES_P_A_KH];
+            cg[2] = (float)exp10(th[S + ES_P_LOG_Q0]);
+            cg[3] = (float)th[S + ES_P_F_CLD];
+        }
+    }
     for (int l = tid; l < L; l += blockDim.x) {
         const size_t bl = (size_t)b * L + l;
         double ru = rl[l], rd = rl[l + 1];

@@ -160,6 +160,21 @@ def test_brown_dwarf_milne_emission():
         check_sample(out, b, ref, 1, grad=(b < 2))
 
 
+def test_cloudy_transmission_forward():
+    """Non-grey cloud (Sect. 2.5, base + power-law q_c, KH18 Q_ext) and cloud
+    fraction: transit depth element by element, binned model and ln L."""
+    w = synth.workload("cloudy_trans", batch=6, n_nu=3000)
+    tabs = oracle_tables(w)
+    ctx = binding.context_for(w)
+    out = gpu_eval(ctx, w, w.theta, np.zeros(6, np.int32), backward=False)
+    for b in range(6):
+        ref = oracle_eval(w, tabs, w.theta[b], 0)
+        assert ref["valid"] and out["flags"][b] == 0
+        assert_spec(out["spec"][b], ref["spec"], 0)
+        np.testing.assert_allclose(out["binned"][b], ref["binned"], rtol=1e-6)
+        np.testing.assert_allclose(out["lnl"][b], ref["lnl"], rtol=1e-5, atol=1e-3)
+
+
 def test_mixed_batch_highres_shape():
     w = synth.workload("highres", batch=4, n_nu=6000)
     tabs = oracle_tables(w)
