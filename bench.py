@@ -406,7 +406,7 @@ def run_gpu(args):
 
     extra = None
     if rank == 0 and not args.no_extra:
-        extra = [measure_workload(n, local) for n in ("batched_emis", "highres", "browndwarf")]
+        extra = [measure_workload(n, local) for n in ("batched_emis", "highres", "browndwarf", "cloudy_trans")]
     cpu = cpu_baseline(args.workload) if (rank == 0 and not args.no_cpu) else None
     if rank == 0:
         line = {

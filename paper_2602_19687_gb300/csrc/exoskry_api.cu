@@ -254,6 +254,8 @@ es_status alloc_backward(es_ctx *c) {
     ALLOC(w.levbar, (size_t)B * (L + 1));
     ALLOC(w.drbar, (size_t)B * L);
     ALLOC(w.grad, (size_t)B * c->m.nfree);
+    ALLOC(w.cloud_dbar, (size_t)B * L);
+    ALLOC(w.cloud_pbar, (size_t)B * 4);
 #undef ALLOC
     c->cap_b_bwd = B;
     return ES_OK;
@@ -767,6 +769,8 @@ es_status enqueue_forward_backward(es_ctx *c, cudaStream_t st) {
     cudaMemsetAsync(w.levbar, 0, sizeof(double) * B * (L + 1), st);
     cudaMemsetAsync(w.drbar, 0, sizeof(double) * B * L, st);
     cudaMemsetAsync(w.lbar, 0, sizeof(float) * B * L * L, st);
+    cudaMemsetAsync(w.cloud_dbar, 0, sizeof(double) * B * L, st);
+    cudaMemsetAsync(w.cloud_pbar, 0, sizeof(double) * B * 4, st);
     es_status s = run_forward(c, true, nullptr, nullptr, c->d_lnl, st);
     if (s != ES_OK) return s;
     int launches = (int)c->last_launches;
@@ -782,8 +786,6 @@ es_status enqueue_forward_backward(es_ctx *c, cudaStream_t st) {
 
 es_status es_forward_backward(es_ctx *c, double *lnl, double *grad, int mem, es_stream_t stream) {
     if (!c) return ES_EINVAL;
-    if (c->m.cloud_kind == ES_CLOUD_KH18)
-        return fail(c, ES_EINVAL, "the adjoint of the non-grey cloud is not implemented yet");
     if (mem != ES_MEM_HOST && mem != ES_MEM_DEVICE) return fail(c, ES_EINVAL, "bad mem");
     es_status s = ready(c);
     if (s != ES_OK) return s;

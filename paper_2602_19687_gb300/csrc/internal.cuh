@@ -129,6 +129,8 @@ struct Work {
     double *levbar;               // [B][L+1] d lnL / d T_lev (emission)
     double *drbar;                // [B][L]   d lnL / d dr (emission)
     double *misc;                 // [B][4] base_bar, scale_bar, c_bar, -
+    double *cloud_dbar;           // [B][L] non-grey cloud: d lnL / d D_i
+    double *cloud_pbar;           // [B][4] d lnL / d (ln r_eff via g, a, ln Q0, f_cld)
     double *grad;                 // [B][nfree]
 };
 

@@ -79,6 +79,9 @@ struct TransBwdSmem {
     // x 4 partial sums (one per lane-bit pair b2 b1), summed at the flush
     float red[ES_MAX_LAYERS * 32];
     float qtot[ES_MAX_SPECIES];                         // per-species totals of the current sample
+    // non-grey cloud: D_i, its adjoint, d lnL / d g(nu) of the tile, the
+    // constants (2 pi r_eff, a, Q0, f) and the parameter adjoints of the sample
+    float cd[LP], cdbar[LP], gbar[BT], cg[4], cpbar[4];
     alignas(16) unsigned char stage[BW_WARPS][STAGE_BYTES_PER_WARP];   // per-warp coefficient staging
     alignas(8) uint64_t mbar_a, mbar_l;
     uint32_t tmem_base;
@@ -536,6 +539,8 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
     // interpolation: 4 layer groups x 4 quarters (32 wavenumbers); lane pairs split species
     const int half = lane & 1, vq = warp & 3, pair = 16 * vq + (lane >> 1), grp = warp >> 2;
     const int NL = (L + 1 + 15) & ~15;                  // L_bar product N: layers and the weight row
+    const bool cloudy = m.cloud_kind == ES_CLOUD_KH18;
+    for (int i = threadIdx.x; i < BT; i += BW_THREADS) sm.gbar[i] = 0.f;
     // padding rows stay zero: tau_bar rows [L, 112), alpha rows [L + 1, 128)
     for (int idx = threadIdx.x; idx < (LP - L) * (BT / 2); idx += BW_THREADS) {
         const uint32_t o = op_off(L + idx / (BT / 2), 2 * (idx % (BT / 2)), SBO_NU);
@@ -614,6 +619,12 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
             if (sm.area_acc[i] != 0.f) atomicAdd(w.areabar + (size_t)b * L + i, (double)sm.area_acc[i]);
         for (int s2 = threadIdx.x; s2 < S; s2 += BW_THREADS)
             if (sm.qtot[s2] != 0.f) atomicAdd(w.qtot + (size_t)b * S + s2, (double)sm.qtot[s2]);
+        if (cloudy) {
+            for (int i = threadIdx.x; i < L; i += BW_THREADS)
+                if (sm.cdbar[i] != 0.f) atomicAdd(w.cloud_dbar + (size_t)b * L + i, (double)sm.cdbar[i]);
+            if (threadIdx.x < 4 && sm.cpbar[threadIdx.x] != 0.f)
+                atomicAdd(w.cloud_pbar + (size_t)b * 4 + threadIdx.x, (double)sm.cpbar[threadIdx.x]);
+        }
     };
     // L2 prefetch of the exp(-tau) rows and dbar of tile t of sample b (the
     // tau_bar phase reads them straight from HBM otherwise, with every warp
@@ -647,6 +658,16 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
             for (int idx = threadIdx.x; idx < L * 32; idx += BW_THREADS) sm.red[idx] = 0.f;
             for (int i = threadIdx.x; i < LP; i += BW_THREADS) sm.area_acc[i] = 0.f;
             for (int s2 = threadIdx.x; s2 < ES_MAX_SPECIES; s2 += BW_THREADS) sm.qtot[s2] = 0.f;
+            if (cloudy) {
+                for (int i = threadIdx.x; i < LP; i += BW_THREADS) {
+                    sm.cd[i] = (i < L) ? w.cloud_d[(size_t)b * L + i] : 0.f;
+                    sm.cdbar[i] = 0.f;
+                }
+                if (threadIdx.x < 4) {
+                    sm.cg[threadIdx.x] = w.cloud_g[(size_t)b * 4 + threadIdx.x];
+                    sm.cpbar[threadIdx.x] = 0.f;
+                }
+            }
             cur_b = b;
             l_started = false;
             fence_async_smem();
@@ -683,7 +704,7 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
                 const uint32_t o = op_off(L, 2 * t2, SBO_NU);
                 *reinterpret_cast<uint32_t *>(sm.ah + o) = bf16x2(mul2(mul2(nu2, nu2), f2(ray_ref)));
             }
-            {
+            if (!cloudy) {
                 float av[16];
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
@@ -700,6 +721,47 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
                 const float tot = transpose_reduce16(av, lane);
                 const int k = reduce_index(lane), i = group + 8 * k;
                 if ((lane & 1) == 0 && k < 14 && i < L && tot != 0.f) atomicAdd(sm.area_acc + i, tot);
+            } else {
+                // non-grey cloud: E_i = f e_cld + (1 - f) e with e_cld = e 2^(-g D_i log2 e);
+                // tau_bar = dbar A_i E_i, area_bar += dbar (1 - E_i), and the
+                // adjoints of D_i, of g(nu) and of f
+                const float2 nu = *reinterpret_cast<const float2 *>(m.nu + nl);
+                const float lx0 = log2f(sm.cg[0] * nu.x), lx1 = log2f(sm.cg[0] * nu.y);
+                const float2 g = make_float2(1.f / (sm.cg[2] * exp2f(-sm.cg[1] * lx0) + exp2f(0.2f * lx0)),
+                                             1.f / (sm.cg[2] * exp2f(-sm.cg[1] * lx1) + exp2f(0.2f * lx1)));
+                const float2 gl = mul2(g, f2(-LOG2E_F));
+                const float fc = sm.cg[3];
+                float av[16], dv[16], fs = 0.f;
+                float2 gs = f2(0.f);
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    av[k] = dv[k] = 0.f;
+                    const int i = group + 8 * k;
+                    if (k < 14 && i < L) {
+                        const float2 e = ev[k];
+                        const float a = sm.area[i], d = sm.cd[i];
+                        const float2 ec = mul2(e, ex2x2(mul2(gl, f2(d))));
+                        const float2 E = fma2(f2(fc), add2(ec, mul2(e, f2(-1.f))), e);
+                        const uint32_t o = op_off(i, col, SBO_NU);
+                        *reinterpret_cast<uint32_t *>(sm.th + o) = bf16x2(make_float2(db.x * a * E.x, db.y * a * E.y));
+                        av[k] = db.x * (1.f - E.x) + db.y * (1.f - E.y);
+                        const float2 wc = mul2(db, ec);
+                        dv[k] = fc * a * (wc.x * g.x + wc.y * g.y);
+                        gs = fma2(f2(fc * a * d), wc, gs);
+                        fs = fmaf(a, db.x * (e.x - ec.x) + db.y * (e.y - ec.y), fs);
+                    }
+                }
+                const float tot = transpose_reduce16(av, lane);
+                const float totd = transpose_reduce16(dv, lane);
+                const int k = reduce_index(lane), i = group + 8 * k;
+                if ((lane & 1) == 0 && k < 14 && i < L) {
+                    if (tot != 0.f) atomicAdd(sm.area_acc + i, tot);
+                    if (totd != 0.f) atomicAdd(sm.cdbar + i, totd);
+                }
+                atomicAdd(sm.gbar + col, gs.x);
+                atomicAdd(sm.gbar + col + 1, gs.y);
+                fs = warp_sum(fs);
+                if (lane == 0 && fs != 0.f) atomicAdd(sm.cpbar + 3, fs);
             }
             fence_async_smem();
             __syncthreads();
@@ -718,6 +780,29 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
                     tc_mma(tmem, a_h + da, b_l + db, idesc_a, true);
                 }
                 tc_commit(mbar_a);
+            }
+            if (cloudy && threadIdx.x < BT) {
+                // d lnL / d g(nu) -> ln r_eff, a, ln Q0 at this tile's wavenumbers:
+                // g = 1/u, u = Q0 x^-a + x^0.2, x = 2 pi r_eff nu
+                const float gb = sm.gbar[threadIdx.x];
+                sm.gbar[threadIdx.x] = 0.f;
+                float g_r = 0.f, g_a = 0.f, g_q = 0.f;
+                if (gb != 0.f) {
+                    const float x = sm.cg[0] * m.nu[nt0 + threadIdx.x];
+                    const float lx = log2f(x), xa = sm.cg[2] * exp2f(-sm.cg[1] * lx), x2 = exp2f(0.2f * lx);
+                    const float g = 1.f / (xa + x2), gg = gb * g * g;
+                    g_r = -gg * (0.2f * x2 - sm.cg[1] * xa);   // dg/dln x = dg/dln r_eff
+                    g_a = gg * xa * lx * 0.6931471805599453f;   // dg/da
+                    g_q = -gg * xa;                             // dg/dln Q0
+                }
+                g_r = warp_sum(g_r);
+                g_a = warp_sum(g_a);
+                g_q = warp_sum(g_q);
+                if (lane == 0) {
+                    atomicAdd(sm.cpbar + 0, g_r);
+                    atomicAdd(sm.cpbar + 1, g_a);
+                    atomicAdd(sm.cpbar + 2, g_q);
+                }
             }
             interp_backward<SPL>(m, sm.sc, sm.sc.gb[grp], sm.sc.gb[grp + 1], nt0 + 2 * pair, half, lane, abar_t, a_dst,
                                  sm.red, sm.qtot, stg, t > c * chunk_tiles, t + 1 < t1 ? BT : 0, [&]() {

@@ -210,6 +210,9 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup_bwd(Model m, Work w) {
     __shared__ double thv[ES_MAX_PARAMS];
     __shared__ double rcbar;
     __shared__ float tlf[ES_MAX_LAYERS], zf[ES_MAX_LAYERS];
+    // non-grey cloud: d lnL / d D_i, C_l and d lnL / d C_l = sum_i L_il Dbar_i
+    __shared__ float cdb[ES_MAX_LAYERS], ccl[ES_MAX_LAYERS];
+    __shared__ double cbar[ES_MAX_LAYERS];
     // temperature tangents dT/dtheta_p at layers and (emission) levels
     __shared__ float dtl[ES_MAX_PARAMS][ES_MAX_LAYERS], dtv[ES_MAX_PARAMS][ES_MAX_LAYERS + 1];
     __shared__ SplitRadii q;
@@ -228,8 +231,20 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup_bwd(Model m, Work w) {
     if (tid < m.nfull) thv[tid] = w.theta[(size_t)b * m.nfull + tid];
     for (int l = tid; l < L; l += blockDim.x) tlf[l] = (float)w.t_lay[(size_t)b * L + l];
     if (tid == 0) rcbar = 0.0;
+    const bool cloudy = m.cloud_kind == ES_CLOUD_KH18 && !emis;
+    for (int l = tid; l < L; l += blockDim.x) {
+        cdb[l] = cloudy ? (float)w.cloud_dbar[(size_t)b * L + l] : 0.f;
+        ccl[l] = cloudy ? w.cloud_c[(size_t)b * L + l] : 0.f;
+    }
     __syncthreads();
     split_radii(rl, L, q);
+    if (cloudy && !bad) {   // D_i = sum_l L_il C_l: Cbar_l = sum_i L_il Dbar_i
+        for (int l = tid; l < L; l += blockDim.x) {
+            double a = 0.0;
+            for (int i = l; i < L; ++i) a += (double)w.lmat[((size_t)b * L + i) * L + l] * (double)cdb[i];
+            cbar[l] = a;
+        }
+    }
     __syncthreads();
     const double rc = w.rc[b];
     if (!bad && !emis) {
@@ -244,7 +259,7 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup_bwd(Model m, Work w) {
             const float bi = q.bh[i];
             double dsum = 0.0;
             for (int l = 0; l <= i; ++l) {
-                const float lb = lbar[(size_t)i * L + l];
+                const float lb = lbar[(size_t)i * L + l] + cdb[i] * ccl[l];   // + the cloud's D_i = sum L_il C_l
                 if (lb == 0.f) continue;
                 const float u = chord_sq(q, l, i), ru = rsqrtf(u);
                 float t;
@@ -264,7 +279,7 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup_bwd(Model m, Work w) {
             double up = 0.0, dn = 0.0;
             const float r0 = 2.f * q.rh[l], r1 = 2.f * q.rh[l + 1];
             for (int i = l; i < L; ++i) {
-                const float lb = lbar[(size_t)i * L + l];
+                const float lb = lbar[(size_t)i * L + l] + cdb[i] * ccl[l];
                 if (lb == 0.f) continue;
                 up += (double)(lb * r0 * rsqrtf(chord_sq(q, l, i)));
                 if (l < i) dn += (double)(lb * r1 * rsqrtf(chord_sq(q, l + 1, i)));
@@ -393,6 +408,24 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup_bwd(Model m, Work w) {
     } else {
         DualF sc = emission_scale<DualF>(m, th, rref);
         acc += w.misc[(size_t)b * 4 + 1] * (double)sc.d;
+    }
+    if (cloudy) {
+        // C_l = 3 rho_a q_c^eff(p_l) / (4 r_eff), rho_a = mu m_u p / (k_B T_l); the
+        // base + power-law profile's branch is taken on the value (p <= p_base)
+        const DualF q_base = dexp10(th[S + ES_P_LOG_QC]), p_base = dexp10(th[S + ES_P_LOG_PC_BASE]) * BAR;
+        const DualF r_eff = dexp10(th[S + ES_P_LOG_R_EFF]) * 1.0e-4;
+        for (int l = 0; l < L; ++l) {
+            const double pl = m.p_lay[l];
+            if (!((float)pl <= p_base.v) || cbar[l] == 0.0) continue;
+            const DualF qc = q_base * dexp(th[S + ES_P_ALPHA_C] * dlog(pl / p_base));
+            const DualF rho = mu * (AMU * pl / K_B) / tl[l];
+            const DualF c = 3.0 * rho * qc / (4.0 * r_eff);
+            acc += cbar[l] * (double)c.d;
+        }
+        // g(nu): the kernel's sums over wavenumber of dbar-weighted dg/d(ln r_eff, a, ln Q0); f_cld
+        const double *cp = w.cloud_pbar + (size_t)b * 4;
+        acc += cp[0] * LN10 * (double)th[S + ES_P_LOG_R_EFF].d + cp[1] * (double)th[S + ES_P_A_KH].d +
+               cp[2] * LN10 * (double)th[S + ES_P_LOG_Q0].d + cp[3] * (double)th[S + ES_P_F_CLD].d;
     }
     acc += w.misc[(size_t)b * 4 + 2] * (double)th[S + ES_P_C_INFL].d;
     gout[p] = acc;

@@ -160,19 +160,26 @@ def test_brown_dwarf_milne_emission():
         check_sample(out, b, ref, 1, grad=(b < 2))
 
 
-def test_cloudy_transmission_forward():
+def test_cloudy_transmission():
     """Non-grey cloud (Sect. 2.5, base + power-law q_c, KH18 Q_ext) and cloud
-    fraction: transit depth element by element, binned model and ln L."""
+    fraction: transit depth element by element, binned model, ln L, and the
+    gradient with respect to all 18 free parameters (7 of them the cloud's)."""
     w = synth.workload("cloudy_trans", batch=6, n_nu=3000)
     tabs = oracle_tables(w)
     ctx = binding.context_for(w)
-    out = gpu_eval(ctx, w, w.theta, np.zeros(6, np.int32), backward=False)
+    out = gpu_eval(ctx, w, w.theta, np.zeros(6, np.int32))
     for b in range(6):
-        ref = oracle_eval(w, tabs, w.theta[b], 0)
-        assert ref["valid"] and out["flags"][b] == 0
-        assert_spec(out["spec"][b], ref["spec"], 0)
-        np.testing.assert_allclose(out["binned"][b], ref["binned"], rtol=1e-6)
-        np.testing.assert_allclose(out["lnl"][b], ref["lnl"], rtol=1e-5, atol=1e-3)
+        ref = oracle_eval(w, tabs, w.theta[b], 0, grad=(b < 3))
+        assert ref["valid"]
+        check_sample(out, b, ref, 0, grad=(b < 3))
+
+
+def test_cloudy_rejects_emission_samples():
+    w = synth.workload("cloudy_trans", batch=2, n_nu=600)
+    ctx = binding.context_for(w)
+    th = torch.tensor(w.theta, dtype=torch.float64, device=DEV)
+    with pytest.raises(binding.ExoskryError):
+        ctx.es_set_batch(th, torch.tensor([0, 1], dtype=torch.int32, device=DEV))
 
 
 def test_mixed_batch_highres_shape():
