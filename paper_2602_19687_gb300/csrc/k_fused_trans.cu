@@ -110,7 +110,9 @@ __device__ void stage_lmat_tc(const Model &m, const Work &w, int b, unsigned cha
     for (int i = threadIdx.x; i < LP; i += blockDim.x) area[i] = (i < L) ? w.area[(size_t)b * L + i] : 0.f;
 }
 
-template <int SPL, bool STORE_E>
+// CLOUD: the non-grey cloud and cloud fraction (ES_CLOUD_KH18) as a separate
+// instantiation, so that the cloud-free kernels carry none of its code.
+template <int SPL, bool STORE_E, bool CLOUD>
 __global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, int chunk_tiles) {
     extern __shared__ float4 smem4[];
     TransFwdSmem &sm = *reinterpret_cast<TransFwdSmem *>(smem4);
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, in
             }
         };
         float s;
-        if (m.cloud_kind != ES_CLOUD_KH18) {
+        if (!CLOUD) {
 #pragma unroll
             for (int k = 0; k < 16; k += 2) term2(k, v16[k], v16[k + 1]);
 #pragma unroll
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, in
             __syncthreads();
             stage_sample(m, w, b, sm.sc, RUN_COST_FWD, SBO_NU);
             stage_lmat_tc(m, w, b, sm.lh, sm.ll, sm.area);
-            if (m.cloud_kind == ES_CLOUD_KH18) {
+            if (CLOUD) {
                 for (int i = threadIdx.x; i < LP; i += F2_THREADS) sm.cd[i] = (i < L) ? w.cloud_d[(size_t)b * L + i] : 0.f;
                 if (threadIdx.x < 4) sm.cg[threadIdx.x] = w.cloud_g[(size_t)b * 4 + threadIdx.x];
             }
@@ -526,7 +528,7 @@ __device__ void interp_backward(const Model &m, const SampleConst &sc, int lb, i
     }
 }
 
-template <int SPL>
+template <int SPL, bool CLOUD>
 __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, int chunk_tiles) {
     extern __shared__ float4 smem4[];
     TransBwdSmem &sm = *reinterpret_cast<TransBwdSmem *>(smem4);
@@ -539,8 +541,9 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
     // interpolation: 4 layer groups x 4 quarters (32 wavenumbers); lane pairs split species
     const int half = lane & 1, vq = warp & 3, pair = 16 * vq + (lane >> 1), grp = warp >> 2;
     const int NL = (L + 1 + 15) & ~15;                  // L_bar product N: layers and the weight row
-    const bool cloudy = m.cloud_kind == ES_CLOUD_KH18;
-    for (int i = threadIdx.x; i < BT; i += BW_THREADS) sm.gbar[i] = 0.f;
+    constexpr bool cloudy = CLOUD;
+    if (cloudy)
+        for (int i = threadIdx.x; i < BT; i += BW_THREADS) sm.gbar[i] = 0.f;
     // padding rows stay zero: tau_bar rows [L, 112), alpha rows [L + 1, 128)
     for (int idx = threadIdx.x; idx < (LP - L) * (BT / 2); idx += BW_THREADS) {
         const uint32_t o = op_off(L + idx / (BT / 2), 2 * (idx % (BT / 2)), SBO_NU);
@@ -869,15 +872,19 @@ int launch_trans_fused_forward(const Model &m, const Work &w, bool store_e, int 
     const long long items = (long long)w.B * ((ntiles + chunk - 1) / chunk);
     const int grid = (int)std::min<long long>(items, (long long)sm_count());
     const size_t sm = fwd_smem();
-#define ES_FWD(SPL, SE)                                                                         \
+#define ES_FWD1(SPL, SE, CL)                                                                    \
     do {                                                                                        \
-        cudaFuncSetAttribute(k_trans_fwd<SPL, SE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-        ES_LAUNCH(h, "k_trans_fwd", st, k_trans_fwd<SPL, SE><<<grid, F2_THREADS, sm, st>>>(m, w, chunk)); \
+        cudaFuncSetAttribute(k_trans_fwd<SPL, SE, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+        ES_LAUNCH(h, "k_trans_fwd", st, k_trans_fwd<SPL, SE, CL><<<grid, F2_THREADS, sm, st>>>(m, w, chunk)); \
     } while (0)
+#define ES_FWD(SPL, SE) \
+    do { if (cloud) ES_FWD1(SPL, SE, true); else ES_FWD1(SPL, SE, false); } while (0)
+    const bool cloud = m.cloud_kind == ES_CLOUD_KH18;
     const int spl = spl_for(m.S);
     if (spl == 2) { if (store_e) ES_FWD(2, true); else ES_FWD(2, false); }
     else if (spl == 4) { if (store_e) ES_FWD(4, true); else ES_FWD(4, false); }
     else { if (store_e) ES_FWD(8, true); else ES_FWD(8, false); }
+#undef ES_FWD1
 #undef ES_FWD
     return 1;
 }
@@ -888,16 +895,20 @@ int launch_trans_fused_backward(const Model &m, const Work &w, int chunk_req, cu
     const long long items = (long long)w.B * ((ntiles + chunk - 1) / chunk);
     const int grid = (int)std::min<long long>(items, (long long)sm_count());
     const size_t sm = bwd_smem();
-#define ES_BWD(SPL)                                                                             \
+#define ES_BWD1(SPL, CL)                                                                        \
     do {                                                                                        \
-        cudaFuncSetAttribute(k_trans_bwd<SPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-        ES_LAUNCH(h, "k_trans_bwd", st, k_trans_bwd<SPL><<<grid, BW_THREADS, sm, st>>>(m, w, chunk)); \
+        cudaFuncSetAttribute(k_trans_bwd<SPL, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+        ES_LAUNCH(h, "k_trans_bwd", st, k_trans_bwd<SPL, CL><<<grid, BW_THREADS, sm, st>>>(m, w, chunk)); \
     } while (0)
+#define ES_BWD(SPL) \
+    do { if (cloud) ES_BWD1(SPL, true); else ES_BWD1(SPL, false); } while (0)
+    const bool cloud = m.cloud_kind == ES_CLOUD_KH18;
     const int spl = spl_for(m.S);
     if (spl == 2) ES_BWD(2);
     else if (spl == 4) ES_BWD(4);
     else ES_BWD(8);
 #undef ES_BWD
+#undef ES_BWD1
     return 1;
 }
 
