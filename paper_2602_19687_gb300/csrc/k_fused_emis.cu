@@ -37,8 +37,10 @@ struct EmisSmem {
     SampleConst sc;
     float inv_t[ES_MAX_LAYERS + 1];    // 1 / T at the levels
     float dr[ES_MAX_LAYERS];           // layer thickness
-    // adjoint accumulators of the current sample
-    float red[ES_MAX_LAYERS * N_RED];
+    // adjoint accumulators of the current sample: per layer 32 partial sums
+    // [value 0..7][lane parity][lane bit 1] (values: QS, D, C, CT, W4, dr_bar,
+    // T_bar of the level; 7 unused), combined at the flush
+    float red[ES_MAX_LAYERS * 32];
     float drb[ES_MAX_LAYERS];
     float levb[ES_MAX_LAYERS + 1];
     float qtot[ES_MAX_SPECIES];
@@ -159,7 +161,8 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_emis_fwd(Model m, Work w, int
             float bt = pl.value(sm.inv_t[0]);
             float2 tr[2] = {f2(1.f), f2(1.f)}, in[2] = {f2(0.f), f2(0.f)};
             for (int l = 0; l < L;) {
-                const int end = sm.sc.lay[l].run_end;
+                // broadcast from lane 0: provably warp-uniform for the compiler
+                const int end = __shfl_sync(0xffffffffu, sm.sc.lay[l].run_end, 0);
                 pi.load(sm.sc, sm.sc.lay[l].cell, sm.sc.lay[l].itc);
                 if (end < L) pi.prefetch(sm.sc.lay[end].cell, sm.sc.lay[end].itc);
                 for (; l < end; ++l) {
@@ -219,6 +222,26 @@ __device__ __forceinline__ float reduce8_parity(const float (&v)[8], int lane) {
     return e;
 }
 
+// The three transpose stages of reduce8_parity: lane holds the sum of
+// v[4 b4 + 2 b3 + b2] over the 8 lanes that differ from it in bits 4, 3, 2.
+__device__ __forceinline__ float reduce8_partial(const float (&v)[8], int lane) {
+    float a[4], c[2];
+    {
+        const bool up = lane & 16;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            a[k] = (up ? v[k + 4] : v[k]) + __shfl_xor_sync(0xffffffffu, up ? v[k] : v[k + 4], 16);
+    }
+    {
+        const bool up = lane & 8;
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+            c[k] = (up ? a[k + 2] : a[k]) + __shfl_xor_sync(0xffffffffu, up ? a[k] : a[k + 2], 8);
+    }
+    const bool up = lane & 4;
+    return (up ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, up ? c[0] : c[1], 4);
+}
+
 // Warp transpose-reduction of 8 values: on return lane holds the warp-wide
 // sum of v[4 b4 + 2 b3 + b2].
 __device__ __forceinline__ float transpose_reduce8_e(const float (&v)[8], int lane) {
@@ -242,9 +265,10 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_emis_bwd(Model m, Work w, int
     const int nchunks = (ntiles + chunk_tiles - 1) / chunk_tiles;
     const long long total = (long long)w.B * nchunks;
     const float ray_ref = (float)(1.0 / ((double)m.ray_nu_ref * m.ray_nu_ref * m.ray_nu_ref * m.ray_nu_ref));
-    // after reduce8_parity: lanes with bit 1 clear hold slot 4 b4 + 2 b3 + b2 of parity b0
-    const int rs = 4 * ((lane >> 4) & 1) + 2 * ((lane >> 3) & 1) + ((lane >> 2) & 1);
-    const bool rwriter = (lane & 2) == 0;
+    // after three transpose stages every lane holds a distinct partial sum:
+    // value 4 b4 + 2 b3 + b2, parity b0, partial b1; one atomic per lane, no branch
+    const int rslot = 4 * (4 * ((lane >> 4) & 1) + 2 * ((lane >> 3) & 1) + ((lane >> 2) & 1)) + 2 * (lane & 1) +
+                      ((lane >> 1) & 1);
     const int ridx = 4 * ((lane >> 4) & 1) + 2 * ((lane >> 3) & 1) + ((lane >> 2) & 1);   // transpose_reduce8 slot
     const bool qwriter = (lane & 3) == 0;
     Angles ang;
@@ -252,14 +276,28 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_emis_bwd(Model m, Work w, int
     int cur_b = -1;
     auto flush = [&](int b) {
         __syncthreads();
-        for (int idx = threadIdx.x; idx < L * N_RED; idx += EM_THREADS) {
-            const float v = sm.red[idx];
-            if (v != 0.f) atomicAdd(w.red + (size_t)b * L * N_RED + idx, (double)v);
+        for (int l = threadIdx.x; l < L; l += EM_THREADS) {
+            const float *q = sm.red + l * 32;
+            const LayerConst &lc = sm.sc.lay[l];
+            // value v, parity h: q[4 v + 2 h] + q[4 v + 2 h + 1]
+            float r[N_RED];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                r[0 + h] = q[0 + 2 * h] + q[1 + 2 * h];                    // QS
+                r[2 + h] = (q[4 + 2 * h] + q[5 + 2 * h]) * lc.gts;         // D
+                r[4 + h] = q[8 + 2 * h] + q[9 + 2 * h];                    // C
+                r[6 + h] = (q[12 + 2 * h] + q[13 + 2 * h]) * lc.gtcs;      // CT
+            }
+            r[8] = ((q[16] + q[17]) + (q[18] + q[19])) * ray_ref;          // W4
+            const float drb = (q[20] + q[21]) + (q[22] + q[23]);
+            const float lvb = (q[24] + q[25]) + (q[26] + q[27]);
+#pragma unroll
+            for (int k = 0; k < N_RED; ++k)
+                if (r[k] != 0.f) atomicAdd(w.red + ((size_t)b * L + l) * N_RED + k, (double)r[k]);
+            if (drb != 0.f) atomicAdd(w.drbar + (size_t)b * L + l, (double)drb);
+            if (lvb != 0.f) atomicAdd(w.levbar + (size_t)b * (L + 1) + l, (double)lvb);
         }
-        for (int l = threadIdx.x; l < L; l += EM_THREADS)
-            if (sm.drb[l] != 0.f) atomicAdd(w.drbar + (size_t)b * L + l, (double)sm.drb[l]);
-        for (int k = threadIdx.x; k <= L; k += EM_THREADS)
-            if (sm.levb[k] != 0.f) atomicAdd(w.levbar + (size_t)b * (L + 1) + k, (double)sm.levb[k]);
+        if (threadIdx.x == 0 && sm.levb[L] != 0.f) atomicAdd(w.levbar + (size_t)b * (L + 1) + L, (double)sm.levb[L]);
         for (int s2 = threadIdx.x; s2 < S; s2 += EM_THREADS)
             if (sm.qtot[s2] != 0.f) atomicAdd(w.qtot + (size_t)b * S + s2, (double)sm.qtot[s2]);
         if (threadIdx.x == 0 && sm.sbar != 0.f) atomicAdd(w.misc + (size_t)b * 4 + 1, (double)sm.sbar);
@@ -272,7 +310,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_emis_bwd(Model m, Work w, int
             __syncthreads();
             stage_sample(m, w, b, sm.sc, RUN_COST_FWD);
             stage_levels(m, w, b, sm);
-            for (int idx = threadIdx.x; idx < L * N_RED; idx += EM_THREADS) sm.red[idx] = 0.f;
+            for (int idx = threadIdx.x; idx < L * 32; idx += EM_THREADS) sm.red[idx] = 0.f;
             for (int l = threadIdx.x; l <= L; l += EM_THREADS) {
                 if (l < L) sm.drb[l] = 0.f;
                 sm.levb[l] = 0.f;
@@ -306,7 +344,8 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_emis_bwd(Model m, Work w, int
 #pragma unroll
             for (int j = 0; j < SPL; ++j) qa[j] = f2(0.f);
             for (int l = 0; l < L;) {
-                const int end = sm.sc.lay[l].run_end;
+                // broadcast from lane 0: provably warp-uniform for the compiler
+                const int end = __shfl_sync(0xffffffffu, sm.sc.lay[l].run_end, 0);
                 pi.load(sm.sc, sm.sc.lay[l].cell, sm.sc.lay[l].itc);
                 if (end < L) pi.prefetch(sm.sc.lay[end].cell, sm.sc.lay[end].itc);
                 for (; l < end; ++l) {
@@ -361,20 +400,14 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_emis_bwd(Model m, Work w, int
                     const float2 act = mul2(ac, pi.d);
                     float v[8];
                     v[0] = fmaf(abn.x, sum.x, abn.y * sum.y);
-                    v[1] = fmaf(abn.x, pt.x, abn.y * pt.y) * lc.gts;
+                    v[1] = fmaf(abn.x, pt.x, abn.y * pt.y);                   // x gts at the flush
                     v[2] = ac.x + ac.y;
-                    v[3] = (act.x + act.y) * lc.gtcs;
-                    v[4] = fmaf(ab.x, pi.nu4.x, ab.y * pi.nu4.y) * ray_ref;   // zero on the odd lane
+                    v[3] = act.x + act.y;                                     // x gtcs at the flush
+                    v[4] = fmaf(ab.x, pi.nu4.x, ab.y * pi.nu4.y);             // zero on the odd lane; x ray_ref
                     v[5] = dtb * alpha;                                        // dr_bar
                     v[6] = btb * dbdt;                                         // T_bar of level l
                     v[7] = 0.f;
-                    const float tot = reduce8_parity(v, lane);
-                    if (rwriter) {
-                        if (rs < 4) atomicAdd(sm.red + l * N_RED + 2 * rs + (lane & 1), tot);
-                        else if (rs == 4) atomicAdd(sm.red + l * N_RED + 8, tot);
-                        else if (rs == 5) atomicAdd(sm.drb + l, tot);
-                        else if (rs == 6) atomicAdd(sm.levb + l, tot);
-                    }
+                    atomicAdd(sm.red + l * 32 + rslot, reduce8_partial(v, lane));
                     bprev = bbb;
                     bt = bb;
                     dbdt = dbdt_b;
