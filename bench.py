@@ -148,24 +148,29 @@ def measured_peaks():
 
 def kernel_work(name, w, n_valid):
     """Algorithmic work of one launch of each kernel at this workload:
-    (amount, unit, bound). Counts as stated in DESIGN.md."""
+    (amount, unit, bound), counted per kernel below."""
+    from paper_2602_19687_gb300 import synth
     m = w.model
     B, L, S, N = n_valid, m.n_layers, m.n_species, w.tables.nu.size
     tri = L * (L + 1) // 2
     n_t = int(np.sum((w.kind == 0)[:B])) if B else 0
     n_e = B - n_t
+    cloud = 1 if m.cloud_kind == synth.CLOUD_KH18 else 0
     if name in ("k_emis_fwd", "k_emis_bwd"):
         # per (emission vector, layer, wavenumber): the interpolation's S + 2
         # exponentials, one attenuation per Gauss-Legendre angle (4) and the
-        # Planck function at the level (1); the adjoint recomputes all of them
-        return n_e * L * (S + 7) * N, "ex2", "alu"
+        # Planck function at the level (1); the adjoint recomputes all of them.
+        # The non-grey cloud's second column adds 4 attenuations.
+        return n_e * L * (S + 7 + 4 * cloud) * N, "ex2", "alu"
     if name == "k_trans_fwd":
         # one ex2 per (vector, layer, species or CIA pair, wavenumber) of the
-        # interpolation, plus exp(-tau_i) per (vector, impact parameter, wavenumber)
-        return n_t * L * (S + 3) * N, "ex2", "alu"
+        # interpolation, plus exp(-tau_i) per (vector, impact parameter,
+        # wavenumber), twice with the non-grey cloud (clear and cloudy chords)
+        return n_t * L * (S + 3 + cloud) * N, "ex2", "alu"
     if name == "k_trans_bwd":
-        # the adjoint recomputes the interpolation's exponentials
-        return n_t * L * (S + 2) * N, "ex2", "alu"
+        # the adjoint recomputes the interpolation's exponentials (and the
+        # cloudy chord's transmission)
+        return n_t * L * (S + 2 + cloud) * N, "ex2", "alu"
     return None
 
 
@@ -406,7 +411,7 @@ def run_gpu(args):
 
     extra = None
     if rank == 0 and not args.no_extra:
-        extra = [measure_workload(n, local) for n in ("batched_emis", "highres", "browndwarf", "cloudy_trans")]
+        extra = [measure_workload(n, local) for n in ("batched_emis", "highres", "browndwarf", "cloudy_trans", "cloudy_emis")]
     cpu = cpu_baseline(args.workload) if (rank == 0 and not args.no_cpu) else None
     if rank == 0:
         line = {

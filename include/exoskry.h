@@ -52,6 +52,12 @@ enum { ES_TP_ISOTHERMAL = 0, ES_TP_GUILLOT = 1, ES_TP_GUILLOT_MOD = 2, ES_TP_MIL
  * absolute flux of an isolated brown dwarf at distance D (Sect. 5, F_bd). */
 enum { ES_FLUX_PLANET_STAR = 0, ES_FLUX_BROWN_DWARF = 1 };
 enum { ES_CLOUD_NONE = 0, ES_CLOUD_DECK = 1, ES_CLOUD_KH18 = 2 };
+/* Vertical profile of the non-grey cloud's mass mixing ratio (Sect. 2.5.1),
+ * evaluated at each layer's pressure p:
+ *   ES_QC_POWER_LAW  q_base (p / p_base)^alpha_c for p <= p_base, 0 below
+ *   ES_QC_SLAB       q_slab at every pressure
+ *   ES_QC_SLAB_BAND  q_slab for p_top <= p <= p_top + dp, 0 elsewhere */
+enum { ES_QC_POWER_LAW = 0, ES_QC_SLAB = 1, ES_QC_SLAB_BAND = 2 };
 enum { ES_KIND_TRANSMISSION = 0, ES_KIND_EMISSION = 1 };
 enum { ES_TABLE_F32 = 0, ES_TABLE_BF16 = 1 };
 enum { ES_MEM_HOST = 0, ES_MEM_DEVICE = 1 };
@@ -80,20 +86,27 @@ enum { ES_FLAG_INVALID = 1 };
  * Non-grey cloud (ES_CLOUD_KH18, Sect. 2.5): extinction rho_a kappa_ext with
  * kappa_ext = 3 q_c^eff Q_ext(x) / (4 r_eff), Q_ext = 1/(Q0 x^-a + x^0.2),
  * x = 2 pi r_eff nu, q_c^eff(p) = q_base (p/p_base)^alpha_c above the base
- * (0 below), and the cloud fraction f_cld mixing cloudy and clear spectra:
- *   LOG_QC       log10 q_base (effective mass mixing ratio at the base)
+ * (0 below; or one of the slab profiles of cloud_profile), and the cloud
+ * fraction f_cld mixing cloudy and clear spectra:
+ *   LOG_QC       log10 q_base (effective mass mixing ratio at the base), or
+ *                log10 q_slab of the slab profiles
  *   LOG_PC_BASE  log10 cloud-base pressure [bar]
  *   ALPHA_C      power-law index alpha_c of q_c^eff above the base
  *   LOG_R_EFF    log10 effective particle radius [micron]
  *   A_KH         spectral slope index a of Q_ext
  *   LOG_Q0       log10 Q0 of Q_ext
  *   F_CLD        cloud fraction f_cld in [0, 1]
+ *   LOG_PC_TOP   log10 p_top of the slab band [bar]            (ES_QC_SLAB_BAND)
+ *   LOG_DPC      log10 of the band's pressure extent dp [bar]  (ES_QC_SLAB_BAND)
+ * The band's edges decide which layers hold cloud, so lnL is piecewise
+ * constant in LOG_PC_TOP and LOG_DPC: their gradient is zero.
  */
 enum {
     ES_P_T_ISO = 0, ES_P_T_INT, ES_P_T_EQ, ES_P_LOG_KAPPA_IR, ES_P_LOG_GAMMA_V,
     ES_P_Q_IRR0, ES_P_LOG_P_T, ES_P_BETA, ES_P_LOG_G, ES_P_R_P, ES_P_LOG_P_CLOUD,
     ES_P_C_INFL, ES_P_DILUTION, ES_P_T_RATIO, ES_P_M_BD,
     ES_P_LOG_QC, ES_P_LOG_PC_BASE, ES_P_ALPHA_C, ES_P_LOG_R_EFF, ES_P_A_KH, ES_P_LOG_Q0, ES_P_F_CLD,
+    ES_P_LOG_PC_TOP, ES_P_LOG_DPC,
     ES_P_N_EXTRA
 };
 
@@ -113,6 +126,7 @@ enum {
  * Rayleigh cross-sections are sigma(nu) = ray_*_cm2 (nu / ray_nu_ref)^4.
  * emission_flux selects the emission output (ES_FLUX_*); distance_cm is
  * the brown dwarf's distance D (> 0 with ES_FLUX_BROWN_DWARF).
+ * cloud_profile selects the non-grey cloud's q_c profile (ES_QC_*).
  */
 typedef struct {
     int n_layers;
@@ -128,6 +142,7 @@ typedef struct {
     int free_idx[ES_MAX_PARAMS];
     int emission_flux;           /* ES_FLUX_*        */
     double distance_cm;
+    int cloud_profile;           /* ES_QC_*          */
 } es_model_desc;
 
 /*

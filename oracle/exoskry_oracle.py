@@ -19,7 +19,7 @@ Every function accepts complex input so that the complex-step method
 (Squire & Trapp 1998) gives the oracle's own gradient: all branch decisions
 (bracket indices, clamps, deck annulus, Taylor switch) are taken on real parts.
 
-Readings where the paper is silent (documented in DESIGN.md, "Readings"):
+Readings taken where the paper is silent:
  - levels log-spaced p_top..p_bot, layer pressure = geometric mean of its levels;
  - hydrostatics with g(r) = g_ref (R_ref/r)^2, each layer isothermal at its
    layer temperature, anchored r(p_ref) = R_p,ref;
@@ -33,8 +33,10 @@ Readings where the paper is silent (documented in DESIGN.md, "Readings"):
  - emission: absorption-only linear-in-tau RT with 4 Gauss-Legendre angles on
    [0, 1], bottom boundary I = B(T_bottom level), F_* = pi B(T_*);
  - modified Milne profile: q_inf fixed at the Hopf function's deep limit;
- - non-grey cloud: r_eff in micron, the mass-mixing-ratio profile of the cloud
-   base with a power law above it, no grey deck in the same model;
+ - non-grey cloud: r_eff in micron; each of the three mass-mixing-ratio
+   profiles (power law above a base, whole-column slab, slab band with closed
+   edges) evaluated at the layer pressures; no grey deck in the same model;
+   in emission a clear and a cloudy column mixed by the cloud fraction;
    a brown dwarf's hydrostatic reference radius is its R_bd = sqrt(G M_bd/g);
  - binning: equal-weight mean over native points with lambda in [lo, hi).
 
@@ -70,7 +72,10 @@ INVALID_LNL = -1.0e300      # Sect. 2.3: invalid forward-model output
 # canonical slots after the S log-VMR slots
 (P_T_ISO, P_T_INT, P_T_EQ, P_LOG_KAPPA, P_LOG_GAMMA, P_Q_IRR0, P_LOG_PT, P_BETA,
  P_LOG_G, P_R_P, P_LOG_PCLOUD, P_C_INFL, P_DILUTION, P_T_RATIO, P_M_BD,
- P_LOG_QC, P_LOG_PC_BASE, P_ALPHA_C, P_LOG_R_EFF, P_A_KH, P_LOG_Q0, P_F_CLD) = range(22)
+ P_LOG_QC, P_LOG_PC_BASE, P_ALPHA_C, P_LOG_R_EFF, P_A_KH, P_LOG_Q0, P_F_CLD,
+ P_LOG_PC_TOP, P_LOG_DPC) = range(24)
+# Sect. 2.5.1 vertical profiles of the cloud mass mixing ratio
+QC_POWER_LAW, QC_SLAB, QC_SLAB_BAND = 0, 1, 2
 TP_ISOTHERMAL, TP_GUILLOT, TP_GUILLOT_MOD, TP_MILNE = 0, 1, 2, 3
 FLUX_PLANET_STAR, FLUX_BROWN_DWARF = 0, 1
 
@@ -295,6 +300,32 @@ def cloud_mass_mixing_ratio(p, q_base, p_base, alpha_c):
     return np.where(_re(p) <= _re(p_base), q_base * (p / p_base) ** alpha_c, 0.0)
 
 
+def cloud_mmr_slab(p, q_slab):
+    """Sect. 2.5.1 (first profile): q_c(p) = q_slab over the whole column."""
+    return q_slab * np.ones_like(p)
+
+
+def cloud_mmr_slab_band(p, q_slab, p_top, dp):
+    """Sect. 2.5.1 (second profile): q_c = q_slab for p_top <= p <= p_top + dp,
+    0 above and below the band."""
+    inside = (_re(p) >= _re(p_top)) & (_re(p) <= _re(p_top) + _re(dp))
+    return np.where(inside, q_slab, 0.0)
+
+
+def cloud_profile(model, theta, p_lay):
+    """q_c^eff at the layer pressures for the model's profile choice; pressures
+    in the parameter vector are log10 bar."""
+    s = model.n_species
+    q = 10.0 ** theta[s + P_LOG_QC]
+    kind = getattr(model, "cloud_profile", QC_POWER_LAW)
+    if kind == QC_SLAB:
+        return cloud_mmr_slab(p_lay, q)
+    if kind == QC_SLAB_BAND:
+        return cloud_mmr_slab_band(p_lay, q, 10.0 ** theta[s + P_LOG_PC_TOP] * BAR,
+                                   10.0 ** theta[s + P_LOG_DPC] * BAR)
+    return cloud_mass_mixing_ratio(p_lay, q, 10.0 ** theta[s + P_LOG_PC_BASE] * BAR, theta[s + P_ALPHA_C])
+
+
 def q_ext_kh18(x, q0, a):
     """Eq. Q_ext_KH with Q_1 subsumed into the effective mass mixing ratio:
     Q_ext / Q_1 = 1 / (Q_0 x^-a + x^0.2)."""
@@ -453,8 +484,7 @@ def forward(model, tabs, theta, kind, members):
     cloudy = model.cloud_kind == CLOUD_KH18
     if cloudy:
         p_lay, t_lay = atm["p_lay"], atm["t_lay"]
-        q_c = cloud_mass_mixing_ratio(p_lay, 10.0 ** theta[s + P_LOG_QC],
-                                      10.0 ** theta[s + P_LOG_PC_BASE] * BAR, theta[s + P_ALPHA_C])
+        q_c = cloud_profile(model, theta, p_lay)
         rho_a = atm["mu"] * AMU * p_lay / (K_B * t_lay)
         alpha_cld = alpha + cloud_extinction(tabs.nu, rho_a, q_c, 10.0 ** theta[s + P_LOG_R_EFF] * 1.0e-4,
                                              10.0 ** theta[s + P_LOG_Q0], theta[s + P_A_KH])

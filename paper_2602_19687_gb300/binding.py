@@ -19,7 +19,7 @@ ES_OK, ES_EINVAL, ES_ENOMEM, ES_ECUDA, ES_ESTATE, ES_ETIMEOUT = range(6)
 ES_MEM_HOST, ES_MEM_DEVICE = 0, 1
 ES_TABLE_F32, ES_TABLE_BF16 = 0, 1
 ES_MAX_SPECIES = 16
-ES_P_N_EXTRA = 22
+ES_P_N_EXTRA = 24
 ES_MAX_PARAMS = ES_MAX_SPECIES + ES_P_N_EXTRA
 ES_MAX_LAYERS = 112
 STATUS_NAMES = {0: "ES_OK", 1: "ES_EINVAL", 2: "ES_ENOMEM", 3: "ES_ECUDA", 4: "ES_ESTATE", 5: "ES_ETIMEOUT"}
@@ -39,7 +39,8 @@ class es_model_desc(ctypes.Structure):
                 ("ray_h2_cm2", ctypes.c_double), ("ray_he_cm2", ctypes.c_double), ("ray_nu_ref", ctypes.c_double),
                 ("theta_fixed", ctypes.c_double * ES_MAX_PARAMS),
                 ("n_free", ctypes.c_int), ("free_idx", ctypes.c_int * ES_MAX_PARAMS),
-                ("emission_flux", ctypes.c_int), ("distance_cm", ctypes.c_double)]
+                ("emission_flux", ctypes.c_int), ("distance_cm", ctypes.c_double),
+                ("cloud_profile", ctypes.c_int)]
 
 
 class es_tables_desc(ctypes.Structure):
@@ -137,6 +138,7 @@ def model_desc(model) -> es_model_desc:
         d.free_idx[k] = int(v)
     d.emission_flux = int(getattr(model, "emission_flux", 0))
     d.distance_cm = float(getattr(model, "distance_cm", 0.0))
+    d.cloud_profile = int(getattr(model, "cloud_profile", 0))
     return d
 
 
@@ -278,6 +280,25 @@ def context_for(workload, device: int = 0) -> Context:
     for kind in (0, 1):
         ctx.es_set_data(kind, workload.y_obs[kind], workload.sigma[kind])
     return ctx
+
+
+class LogLikeBatch:
+    """ln L of host parameter vectors through one es_set_batch + es_loglike per
+    call (host in, host out): the batched likelihood a sampler consumes
+    (e.g. nested.run). theta: float64 [B, n_free]; returns float64 [B]."""
+
+    def __init__(self, context, kind=0, stream=None):
+        self.context, self.kind, self.stream = context, int(kind), stream
+        self.calls = 0
+
+    def __call__(self, theta):
+        theta = np.ascontiguousarray(theta, np.float64)
+        B = theta.shape[0]
+        self.context.es_set_batch(theta, np.full(B, self.kind, np.int32), self.stream)
+        lnl = np.empty(B, np.float64)
+        self.context.es_loglike(lnl, self.stream)
+        self.calls += 1
+        return lnl
 
 
 def _autograd_function():

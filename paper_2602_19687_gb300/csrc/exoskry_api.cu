@@ -318,8 +318,10 @@ es_status prepare(es_ctx *c, bool adjoint) {
         if (c->n_kind[0] &&
             (s = ensure_big(c, &c->w.estore, c->estore_cap, (size_t)c->batch * c->m.L * c->m.Np)) != ES_OK)
             return s;
+        // emission: I_toa per angle, a second (cloudy) column with the non-grey cloud
+        const size_t cols = c->m.cloud_kind == ES_CLOUD_KH18 ? 2 : 1;
         if (c->n_kind[1] &&
-            (s = ensure_big(c, &c->w.itop, c->alpha_cap, (size_t)c->batch * c->m.Np * N_MU)) != ES_OK)
+            (s = ensure_big(c, &c->w.itop, c->alpha_cap, (size_t)c->batch * c->m.Np * N_MU * cols)) != ES_OK)
             return s;
     }
     return ES_OK;
@@ -357,6 +359,7 @@ es_status es_create(es_ctx **out, int device, const es_model_desc *d) {
     if (d->tp_kind < 0 || d->tp_kind > ES_TP_MILNE || d->cloud_kind < 0 || d->cloud_kind > ES_CLOUD_KH18) return ES_EINVAL;
     if (d->emission_flux != ES_FLUX_PLANET_STAR && d->emission_flux != ES_FLUX_BROWN_DWARF) return ES_EINVAL;
     if (d->emission_flux == ES_FLUX_BROWN_DWARF && !(d->distance_cm > 0)) return ES_EINVAL;
+    if (d->cloud_profile < ES_QC_POWER_LAW || d->cloud_profile > ES_QC_SLAB_BAND) return ES_EINVAL;
     if (!(d->r_star_cm > 0) || !(d->t_star_k > 0)) return ES_EINVAL;
     const int nfull = d->n_species + ES_P_N_EXTRA;
     if (d->n_free < 1 || d->n_free > 32 || d->n_free > nfull) return ES_EINVAL;
@@ -385,6 +388,7 @@ es_status es_create(es_ctx **out, int device, const es_model_desc *d) {
     m.cloud_kind = d->cloud_kind;
     m.emis_flux = d->emission_flux;
     m.distance = d->distance_cm;
+    m.cloud_profile = d->cloud_profile;
     m.p_ref = d->p_ref_bar * BAR;
     m.r_star = d->r_star_cm;
     m.t_star = d->t_star_k;
@@ -674,8 +678,6 @@ es_status es_set_batch(es_ctx *c, const double *theta, const int32_t *kind, int 
             return fail(c, ES_EINVAL, "kind must be 0 (transmission) or 1 (emission)");
         nk[kh[b]]++;
     }
-    if (c->m.cloud_kind == ES_CLOUD_KH18 && nk[ES_KIND_EMISSION] > 0)
-        return fail(c, ES_EINVAL, "the non-grey cloud is implemented for transmission samples only");
     e = cudaMemcpyAsync(c->w.kind, kh.data(), sizeof(int32_t) * batch, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && mem == ES_MEM_HOST) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess && kind && mem == ES_MEM_DEVICE) e = cudaStreamSynchronize(st);

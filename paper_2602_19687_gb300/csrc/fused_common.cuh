@@ -328,14 +328,31 @@ __device__ __forceinline__ void extinction_pair(const Model &m, const SampleCons
     }
 }
 
-// Adjoint reductions of one layer for the lane's pair, with abar = d lnL / d alpha:
-// Q_s = sum abar e_s (species), D = sum abar sum_s e_s dlog10(sigma_s)/dlog10 T,
-// C1, C2, C1T, C2T (CIA and their temperature slopes), W4 = sum abar (nu/nu_ref)^4.
-// Values are reduced over the warp and added to red[l][*] (shared, one warp per layer).
+// Sum over the warp, on every lane.
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// ------------------------------------------------------------ non-grey cloud
+// Sect. 2.5 extinction efficiency with Q_1 folded into q_c^eff:
+// g(nu) = 1/u, u = Q0 x^-a + x^0.2, x = 2 pi r_eff nu; cg = (2 pi r_eff, a, Q0, f_cld).
+__device__ __forceinline__ float kh18_g(const float *cg, float nu) {
+    const float lx = log2f(cg[0] * nu);
+    return 1.f / (cg[2] * exp2f(-cg[1] * lx) + exp2f(0.2f * lx));
+}
+
+// Given gb = d lnL / d g(nu), the derivatives along ln r_eff (= ln x), a and
+// ln Q0: dg/dln x = -g^2 (0.2 x^0.2 - a Q0 x^-a), dg/da = g^2 Q0 x^-a ln x,
+// dg/dln Q0 = -g^2 Q0 x^-a.
+__device__ __forceinline__ void kh18_g_adjoint(const float *cg, float nu, float gb, float &g_r, float &g_a,
+                                               float &g_q) {
+    const float lx = log2f(cg[0] * nu), xa = cg[2] * exp2f(-cg[1] * lx), x2 = exp2f(0.2f * lx);
+    const float g = 1.f / (xa + x2), gg = gb * g * g;
+    g_r = -gg * (0.2f * x2 - cg[1] * xa);
+    g_a = gg * xa * lx * 0.6931471805599453f;
+    g_q = -gg * xa;
 }
 
 }  // namespace es

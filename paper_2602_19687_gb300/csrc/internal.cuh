@@ -55,6 +55,7 @@ struct Model {
     int Np;                       // padded row stride of tables and per-wavenumber arrays (N rounded up to 128)
     int SP;                       // species slots per coefficient-table entry (2 spl_for(S) >= S)
     int tp_kind, cloud_kind, bf16;
+    int cloud_profile;            // ES_QC_* (non-grey cloud)
     int emis_flux;                // ES_FLUX_*
     double distance;              // cm (brown-dwarf flux)
     double p_ref;                 // dyn cm^-2
@@ -124,12 +125,13 @@ struct Work {
     double *red;                  // [B][L][N_RED]
     double *qtot;                 // [B][S] per-species reductions summed over layers
     double *zbar;                 // [B][L] transmission: sum_nu tau_bar_i(nu) (nu/nu_ref)^4
-    float *itop;                  // [B][Np][4] emission: top-of-atmosphere intensity per angle (for the adjoint)
+    float *itop;                  // [B][Np][1 or 2][4] emission: top-of-atmosphere intensity per angle of the
+                                  // clear (and, with the non-grey cloud, the cloudy) column, for the adjoint
     double *areabar;              // [B][L]
     double *levbar;               // [B][L+1] d lnL / d T_lev (emission)
     double *drbar;                // [B][L]   d lnL / d dr (emission)
     double *misc;                 // [B][4] base_bar, scale_bar, c_bar, -
-    double *cloud_dbar;           // [B][L] non-grey cloud: d lnL / d D_i
+    double *cloud_dbar;           // [B][L] non-grey cloud: d lnL / d D_i (transmission), d lnL / d C_l (emission)
     double *cloud_pbar;           // [B][4] d lnL / d (ln r_eff via g, a, ln Q0, f_cld)
     double *grad;                 // [B][nfree]
 };

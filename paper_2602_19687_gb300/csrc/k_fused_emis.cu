@@ -21,6 +21,11 @@
 //   dI/dB_top = T_l (1 - E - f),  dI/dB_bot = T_l f,  dI/dB_surface = T_L,
 // and the interpolation is recomputed and reduced against
 // alpha_bar = dtau_bar dr.
+//
+// With the non-grey cloud (Sect. 2.5) each lane also integrates a cloudy
+// column, dtau_l + C_l g(nu) dr_l, and the emergent fluxes are mixed by the
+// cloud fraction; its adjoint adds the cloudy column's dtau_bar to alpha_bar
+// and returns d lnL / d C_l, d lnL / d g(nu) and d lnL / d f_cld.
 #include <algorithm>
 
 #include "fused_common.cuh"
@@ -37,20 +42,27 @@ struct EmisSmem {
     SampleConst sc;
     float inv_t[ES_MAX_LAYERS + 1];    // 1 / T at the levels
     float dr[ES_MAX_LAYERS];           // layer thickness
+    float ccl[ES_MAX_LAYERS];          // non-grey cloud: C_l (extinction per unit g(nu))
+    float cg[4];                       // non-grey cloud: 2 pi r_eff, a, Q0, f_cld
     // adjoint accumulators of the current sample: per layer 32 partial sums
     // [value 0..7][lane parity][lane bit 1] (values: QS, D, C, CT, W4, dr_bar,
-    // T_bar of the level; 7 unused), combined at the flush
+    // T_bar of the level, C_l bar of the cloud), combined at the flush
     float red[ES_MAX_LAYERS * 32];
-    float drb[ES_MAX_LAYERS];
-    float levb[ES_MAX_LAYERS + 1];
+    float levb_bot;                    // T_bar of the bottom level
     float qtot[ES_MAX_SPECIES];
     float sbar;
+    float cpbar[4];                    // d lnL / d (ln r_eff via g, a, ln Q0, f_cld)
 };
 
+template <bool CLOUD>
 __device__ void stage_levels(const Model &m, const Work &w, int b, EmisSmem &sm) {
     const int L = m.L;
     for (int k = threadIdx.x; k <= L; k += blockDim.x) sm.inv_t[k] = (float)(1.0 / w.t_lev[(size_t)b * (L + 1) + k]);
     for (int l = threadIdx.x; l < L; l += blockDim.x) sm.dr[l] = w.dr[(size_t)b * L + l];
+    if (CLOUD) {
+        for (int l = threadIdx.x; l < L; l += blockDim.x) sm.ccl[l] = w.cloud_c[(size_t)b * L + l];
+        if (threadIdx.x < 4) sm.cg[threadIdx.x] = w.cloud_g[(size_t)b * 4 + threadIdx.x];
+    }
 }
 
 // Planck function per unit wavenumber at a level: B = nu3c / (2^a - 1) with
@@ -126,7 +138,62 @@ __device__ __forceinline__ float2 lin_fp(float2 x, float2 e, float2 ome, float2 
 // Lane's alpha at its own wavenumber from the pair sum.
 __device__ __forceinline__ float own(float2 a, int half) { return half ? a.y : a.x; }
 
-template <int SPL, bool STORE_I>
+// One layer of the top-down sum for the lane's wavenumber at both angle
+// pairs: I += T Src, T *= E (see the header comment).
+__device__ __forceinline__ void rt_layer(const Angles &ang, float dtau, float bt, float bb, float2 (&tr)[2],
+                                         float2 (&in)[2]) {
+    const float rdt = __frcp_rn(dtau);
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const float2 x = mul2(f2(dtau), ang.imu[p]);
+        const float2 e = ex2x2(mul2(f2(-dtau), ang.c[p]));
+        float2 ome, f;
+        lin_factors(x, e, mul2(ang.mu[p], f2(rdt)), ome, f);
+        const float2 src = fma2(f2(bt), ome, mul2(f2(bb - bt), f));
+        in[p] = fma2(tr[p], src, in[p]);
+        tr[p] = mul2(tr[p], e);
+    }
+}
+
+// Adjoint of rt_layer for one column with the stored I_toa: returns
+// d lnL / d dtau_l and adds the adjoints of the layer's top and bottom Planck
+// values to btb and bbb; ib = d lnL / d I_toa per angle.
+__device__ __forceinline__ float rt_layer_bwd(const Angles &ang, float dtau, float bt, float bb,
+                                              const float2 (&itoa)[2], const float2 (&ib)[2], float2 (&tr)[2],
+                                              float2 (&pre)[2], float &btb, float &bbb) {
+    const float rdt = __frcp_rn(dtau);
+    float dtb = 0.f;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const float2 x = mul2(f2(dtau), ang.imu[q]);
+        const float2 e = ex2x2(mul2(f2(-dtau), ang.c[q]));
+        const float2 ix = mul2(ang.mu[q], f2(rdt));
+        float2 ome, f;
+        lin_factors(x, e, ix, ome, f);
+        const float2 fp = lin_fp(x, e, fma2(e, f2(-1.f), f2(1.f)), ix);
+        const float2 src = fma2(f2(bt), ome, mul2(f2(bb - bt), f));
+        pre[q] = fma2(tr[q], src, pre[q]);
+        const float2 below = add2(itoa[q], mul2(pre[q], f2(-1.f)));
+        // dI/d dtau = (1/mu) [T (B_top E + dB f') - below]
+        const float2 g = mul2(ang.imu[q], fma2(tr[q], fma2(f2(bt), e, mul2(f2(bb - bt), fp)), mul2(below, f2(-1.f))));
+        const float2 it = mul2(ib[q], tr[q]);
+        dtb = fmaf(ib[q].x, g.x, fmaf(ib[q].y, g.y, dtb));
+        const float2 omf = add2(ome, mul2(f, f2(-1.f)));
+        btb = fmaf(it.x, omf.x, fmaf(it.y, omf.y, btb));
+        bbb = fmaf(it.x, f.x, fmaf(it.y, f.y, bbb));
+        tr[q] = mul2(tr[q], e);
+    }
+    return dtb;
+}
+
+__device__ __forceinline__ float flux_of(const Angles &ang, const float2 (&in)[2]) {
+    return fmaf(ang.wt[0].x, in[0].x, fmaf(ang.wt[0].y, in[0].y, fmaf(ang.wt[1].x, in[1].x, ang.wt[1].y * in[1].y)));
+}
+
+// CLOUD: the non-grey cloud and cloud fraction (ES_CLOUD_KH18). A second
+// column with dtau_l + C_l g(nu) dr_l is integrated beside the clear one and
+// the fluxes are mixed, F = f F_cld + (1 - f) F_cf (Sect. 2.5).
+template <int SPL, bool STORE_I, bool CLOUD>
 __global__ void __launch_bounds__(EM_THREADS, 1) k_emis_fwd(Model m, Work w, int chunk_tiles) {
     extern __shared__ float4 smem4[];
     EmisSmem &sm = *reinterpret_cast<EmisSmem *>(smem4);
@@ -144,7 +211,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_emis_fwd(Model m, Work w, int
         if (b != cur_b) {
             __syncthreads();
             stage_sample(m, w, b, sm.sc, RUN_COST_FWD);
-            stage_levels(m, w, b, sm);
+            stage_levels<CLOUD>(m, w, b, sm);
             cur_b = b;
             __syncthreads();
         }
@@ -158,8 +225,10 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_emis_fwd(Model m, Work w, int
             pi.init(m, n, half, lane);
             Planck pl;
             pl.init(m.nu[nme]);
+            const float gc = CLOUD ? kh18_g(sm.cg, m.nu[nme]) : 0.f;
             float bt = pl.value(sm.inv_t[0]);
             float2 tr[2] = {f2(1.f), f2(1.f)}, in[2] = {f2(0.f), f2(0.f)};
+            float2 trc[2] = {f2(1.f), f2(1.f)}, inc[2] = {f2(0.f), f2(0.f)};   // cloudy column
             for (int l = 0; l < L;) {
                 // broadcast from lane 0: provably warp-uniform for the compiler
                 const int end = __shfl_sync(0xffffffffu, sm.sc.lay[l].run_end, 0);
@@ -173,28 +242,25 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_emis_fwd(Model m, Work w, int
                     const float2 mine = pi.part(lc, sum, pi.cia(lc));
                     const float dtau = own(add2(mine, shfl_xor2(mine, 1)), half) * sm.dr[l];
                     const float bb = pl.value(sm.inv_t[l + 1]);
-                    const float rdt = __frcp_rn(dtau);
-#pragma unroll
-                    for (int p = 0; p < 2; ++p) {
-                        const float2 x = mul2(f2(dtau), ang.imu[p]);
-                        const float2 e = ex2x2(mul2(f2(-dtau), ang.c[p]));
-                        float2 ome, f;
-                        lin_factors(x, e, mul2(ang.mu[p], f2(rdt)), ome, f);
-                        const float2 src = fma2(f2(bt), ome, mul2(f2(bb - bt), f));
-                        in[p] = fma2(tr[p], src, in[p]);
-                        tr[p] = mul2(tr[p], e);
-                    }
+                    rt_layer(ang, dtau, bt, bb, tr, in);
+                    if (CLOUD) rt_layer(ang, fmaf(sm.ccl[l] * gc, sm.dr[l], dtau), bt, bb, trc, inc);
                     bt = bb;
                 }
             }
             // surface: I = B(bottom level) below the last layer
 #pragma unroll
-            for (int p = 0; p < 2; ++p) in[p] = fma2(tr[p], f2(bt), in[p]);
-            const float flux = fmaf(ang.wt[0].x, in[0].x, fmaf(ang.wt[0].y, in[0].y,
-                                    fmaf(ang.wt[1].x, in[1].x, ang.wt[1].y * in[1].y)));
+            for (int p = 0; p < 2; ++p) {
+                in[p] = fma2(tr[p], f2(bt), in[p]);
+                if (CLOUD) inc[p] = fma2(trc[p], f2(bt), inc[p]);
+            }
+            float flux = flux_of(ang, in);
+            if (CLOUD) flux = sm.cg[3] * flux_of(ang, inc) + (1.f - sm.cg[3]) * flux;
             if (nme < N) w.spec[(size_t)b * N + nme] = scale * flux * m.inv_fstar[nme];
-            if (STORE_I)
-                reinterpret_cast<float4 *>(w.itop)[(size_t)b * m.Np + nme] = make_float4(in[0].x, in[0].y, in[1].x, in[1].y);
+            if (STORE_I) {   // [B][Np][column][4 angles], the cloudy column second
+                float4 *it4 = reinterpret_cast<float4 *>(w.itop) + ((size_t)b * m.Np + nme) * (CLOUD ? 2 : 1);
+                it4[0] = make_float4(in[0].x, in[0].y, in[1].x, in[1].y);
+                if (CLOUD) it4[1] = make_float4(inc[0].x, inc[0].y, inc[1].x, inc[1].y);
+            }
         }
     }
 }
@@ -255,7 +321,7 @@ __device__ __forceinline__ float warp_total(float v) {
     return v;
 }
 
-template <int SPL>
+template <int SPL, bool CLOUD>
 __global__ void __launch_bounds__(EM_THREADS, 1) k_emis_bwd(Model m, Work w, int chunk_tiles) {
     extern __shared__ float4 smem4[];
     EmisSmem &sm = *reinterpret_cast<EmisSmem *>(smem4);
@@ -296,8 +362,14 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_emis_bwd(Model m, Work w, int
                 if (r[k] != 0.f) atomicAdd(w.red + ((size_t)b * L + l) * N_RED + k, (double)r[k]);
             if (drb != 0.f) atomicAdd(w.drbar + (size_t)b * L + l, (double)drb);
             if (lvb != 0.f) atomicAdd(w.levbar + (size_t)b * (L + 1) + l, (double)lvb);
+            if (CLOUD) {   // d lnL / d C_l
+                const float ccb = (q[28] + q[29]) + (q[30] + q[31]);
+                if (ccb != 0.f) atomicAdd(w.cloud_dbar + (size_t)b * L + l, (double)ccb);
+            }
         }
-        if (threadIdx.x == 0 && sm.levb[L] != 0.f) atomicAdd(w.levbar + (size_t)b * (L + 1) + L, (double)sm.levb[L]);
+        if (threadIdx.x == 0 && sm.levb_bot != 0.f) atomicAdd(w.levbar + (size_t)b * (L + 1) + L, (double)sm.levb_bot);
+        if (CLOUD && threadIdx.x < 4 && sm.cpbar[threadIdx.x] != 0.f)
+            atomicAdd(w.cloud_pbar + (size_t)b * 4 + threadIdx.x, (double)sm.cpbar[threadIdx.x]);
         for (int s2 = threadIdx.x; s2 < S; s2 += EM_THREADS)
             if (sm.qtot[s2] != 0.f) atomicAdd(w.qtot + (size_t)b * S + s2, (double)sm.qtot[s2]);
         if (threadIdx.x == 0 && sm.sbar != 0.f) atomicAdd(w.misc + (size_t)b * 4 + 1, (double)sm.sbar);
@@ -309,14 +381,14 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_emis_bwd(Model m, Work w, int
             if (cur_b >= 0) flush(cur_b);
             __syncthreads();
             stage_sample(m, w, b, sm.sc, RUN_COST_FWD);
-            stage_levels(m, w, b, sm);
+            stage_levels<CLOUD>(m, w, b, sm);
             for (int idx = threadIdx.x; idx < L * 32; idx += EM_THREADS) sm.red[idx] = 0.f;
-            for (int l = threadIdx.x; l <= L; l += EM_THREADS) {
-                if (l < L) sm.drb[l] = 0.f;
-                sm.levb[l] = 0.f;
-            }
             for (int s2 = threadIdx.x; s2 < ES_MAX_SPECIES; s2 += EM_THREADS) sm.qtot[s2] = 0.f;
-            if (threadIdx.x == 0) sm.sbar = 0.f;
+            if (threadIdx.x < 4) sm.cpbar[threadIdx.x] = 0.f;
+            if (threadIdx.x == 0) {
+                sm.sbar = 0.f;
+                sm.levb_bot = 0.f;
+            }
             cur_b = b;
             __syncthreads();
         }
@@ -330,16 +402,29 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_emis_bwd(Model m, Work w, int
             pi.init(m, n, half, lane);
             Planck pl;
             pl.init(m.nu[nme]);
-            const float4 i4 = reinterpret_cast<const float4 *>(w.itop)[(size_t)b * m.Np + nme];
+            const float4 *it4 = reinterpret_cast<const float4 *>(w.itop) + ((size_t)b * m.Np + nme) * (CLOUD ? 2 : 1);
+            const float4 i4 = it4[0];
             const float2 itoa[2] = {make_float2(i4.x, i4.y), make_float2(i4.z, i4.w)};
             const float db = w.dbar[(size_t)b * m.Np + nme];   // zero beyond N
             const float fsc = m.inv_fstar[nme];
             const float fbar = db * scale * fsc;
-            const float2 ib[2] = {mul2(f2(fbar), ang.wt[0]), mul2(f2(fbar), ang.wt[1])};
+            // d lnL / d I_toa per angle: the clear column weighted 1 - f_cld, the cloudy one f_cld
+            const float wcf = CLOUD ? 1.f - sm.cg[3] : 1.f, wcl = CLOUD ? sm.cg[3] : 0.f;
+            const float2 ib[2] = {mul2(f2(fbar * wcf), ang.wt[0]), mul2(f2(fbar * wcf), ang.wt[1])};
+            const float2 ibc[2] = {mul2(f2(fbar * wcl), ang.wt[0]), mul2(f2(fbar * wcl), ang.wt[1])};
+            float2 itc[2] = {f2(0.f), f2(0.f)};
+            if (CLOUD) {
+                const float4 c4 = it4[1];
+                itc[0] = make_float2(c4.x, c4.y);
+                itc[1] = make_float2(c4.z, c4.w);
+            }
+            const float gc = CLOUD ? kh18_g(sm.cg, m.nu[nme]) : 0.f;
+            float gacc = 0.f;                          // d lnL / d g(nu) of the lane's wavenumber
             float dbdt;
             float bt = pl.value_dt(sm.inv_t[0], dbdt);
             float bprev = 0.f;                         // B_bar of the current top level from the layer above
             float2 tr[2] = {f2(1.f), f2(1.f)}, pre[2] = {f2(0.f), f2(0.f)};
+            float2 trc[2] = {f2(1.f), f2(1.f)}, prec[2] = {f2(0.f), f2(0.f)};   // cloudy column
             float2 qa[SPL];
 #pragma unroll
             for (int j = 0; j < SPL; ++j) qa[j] = f2(0.f);
@@ -366,31 +451,17 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_emis_bwd(Model m, Work w, int
                     const float dtau = alpha * sm.dr[l];
                     float dbdt_b;
                     const float bb = pl.value_dt(sm.inv_t[l + 1], dbdt_b);
-                    const float rdt = __frcp_rn(dtau);
-                    float dtb = 0.f, btb = bprev, bbb = 0.f;
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const float2 x = mul2(f2(dtau), ang.imu[q]);
-                        const float2 e = ex2x2(mul2(f2(-dtau), ang.c[q]));
-                        const float2 ix = mul2(ang.mu[q], f2(rdt));
-                        float2 ome, f;
-                        lin_factors(x, e, ix, ome, f);
-                        const float2 fp = lin_fp(x, e, fma2(e, f2(-1.f), f2(1.f)), ix);
-                        const float2 src = fma2(f2(bt), ome, mul2(f2(bb - bt), f));
-                        pre[q] = fma2(tr[q], src, pre[q]);
-                        const float2 below = add2(itoa[q], mul2(pre[q], f2(-1.f)));
-                        // dI/d dtau = (1/mu) [T (B_top E + dB f') - below]
-                        const float2 g = mul2(ang.imu[q], fma2(tr[q], fma2(f2(bt), e, mul2(f2(bb - bt), fp)),
-                                                                mul2(below, f2(-1.f))));
-                        const float2 it = mul2(ib[q], tr[q]);
-                        dtb = fmaf(ib[q].x, g.x, fmaf(ib[q].y, g.y, dtb));
-                        const float2 omf = add2(ome, mul2(f, f2(-1.f)));
-                        btb = fmaf(it.x, omf.x, fmaf(it.y, omf.y, btb));
-                        bbb = fmaf(it.x, f.x, fmaf(it.y, f.y, bbb));
-                        tr[q] = mul2(tr[q], e);
+                    float btb = bprev, bbb = 0.f;
+                    const float dtb = rt_layer_bwd(ang, dtau, bt, bb, itoa, ib, tr, pre, btb, bbb);
+                    // cloudy column: dtau + C_l g dr (alpha_bar as the clear one's; C_l bar, g bar)
+                    const float acl = CLOUD ? sm.ccl[l] * gc : 0.f;
+                    float dtbc = 0.f;
+                    if (CLOUD) {
+                        dtbc = rt_layer_bwd(ang, fmaf(acl, sm.dr[l], dtau), bt, bb, itc, ibc, trc, prec, btb, bbb);
+                        gacc = fmaf(dtbc * sm.dr[l], sm.ccl[l], gacc);
                     }
                     // alpha_bar of both wavenumbers of the pair
-                    const float abar_me = dtb * sm.dr[l];
+                    const float abar_me = (dtb + dtbc) * sm.dr[l];
                     const float abar_ot = __shfl_xor_sync(0xffffffffu, abar_me, 1);
                     const float2 ab = half ? make_float2(abar_ot, abar_me) : make_float2(abar_me, abar_ot);
                     const float2 abn = mul2(ab, lc.nsc);
@@ -404,9 +475,9 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_emis_bwd(Model m, Work w, int
                     v[2] = ac.x + ac.y;
                     v[3] = act.x + act.y;                                     // x gtcs at the flush
                     v[4] = fmaf(ab.x, pi.nu4.x, ab.y * pi.nu4.y);             // zero on the odd lane; x ray_ref
-                    v[5] = dtb * alpha;                                        // dr_bar
+                    v[5] = fmaf(dtbc, acl, (dtb + dtbc) * alpha);              // dr_bar
                     v[6] = btb * dbdt;                                         // T_bar of level l
-                    v[7] = 0.f;
+                    v[7] = CLOUD ? dtbc * sm.dr[l] * gc : 0.f;                 // C_l bar
                     atomicAdd(sm.red + l * 32 + rslot, reduce8_partial(v, lane));
                     bprev = bbb;
                     bt = bb;
@@ -416,13 +487,32 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_emis_bwd(Model m, Work w, int
             // bottom level: from the last layer and the surface term I = B_bottom below it
             float bl = bprev;
 #pragma unroll
-            for (int q = 0; q < 2; ++q) bl = fmaf(ib[q].x, tr[q].x, fmaf(ib[q].y, tr[q].y, bl));
+            for (int q = 0; q < 2; ++q) {
+                bl = fmaf(ib[q].x, tr[q].x, fmaf(ib[q].y, tr[q].y, bl));
+                if (CLOUD) bl = fmaf(ibc[q].x, trc[q].x, fmaf(ibc[q].y, trc[q].y, bl));
+            }
             const float lev_last = warp_total(bl * dbdt);
-            const float flux = fmaf(ang.wt[0].x, itoa[0].x, fmaf(ang.wt[0].y, itoa[0].y,
-                                    fmaf(ang.wt[1].x, itoa[1].x, ang.wt[1].y * itoa[1].y)));
+            float flux = flux_of(ang, itoa);
+            if (CLOUD) {
+                // f_cld and g(nu) -> ln r_eff, a, ln Q0 of the lane's wavenumber
+                const float fcl = flux_of(ang, itc);
+                const float fb = warp_total(db * scale * fsc * (fcl - flux));
+                float g_r = 0.f, g_a = 0.f, g_q = 0.f;
+                if (gacc != 0.f) kh18_g_adjoint(sm.cg, m.nu[nme], gacc, g_r, g_a, g_q);
+                g_r = warp_total(g_r);
+                g_a = warp_total(g_a);
+                g_q = warp_total(g_q);
+                if (lane == 0) {
+                    atomicAdd(sm.cpbar + 0, g_r);
+                    atomicAdd(sm.cpbar + 1, g_a);
+                    atomicAdd(sm.cpbar + 2, g_q);
+                    atomicAdd(sm.cpbar + 3, fb);
+                }
+                flux = wcl * fcl + wcf * flux;
+            }
             const float sb = warp_total(db * flux * fsc);
             if (lane == 0) {
-                atomicAdd(sm.levb + L, lev_last);
+                atomicAdd(&sm.levb_bot, lev_last);
                 atomicAdd(&sm.sbar, sb);
             }
             // per-species totals: slot j of lane half h is species SPL h + j
@@ -465,16 +555,20 @@ int launch_emis_fused_forward(const Model &m, const Work &w, bool store_i, cudaS
     const long long items = (long long)w.B * ((ntiles + chunk - 1) / chunk);
     const int grid = (int)std::min<long long>(items, (long long)sm_count_e());
     const size_t sm = emis_smem();
-#define ES_EF(SPL, SI)                                                                          \
+#define ES_EF1(SPL, SI, CL)                                                                     \
     do {                                                                                        \
-        cudaFuncSetAttribute(k_emis_fwd<SPL, SI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-        ES_LAUNCH(h, "k_emis_fwd", st, k_emis_fwd<SPL, SI><<<grid, EM_THREADS, sm, st>>>(m, w, chunk)); \
+        cudaFuncSetAttribute(k_emis_fwd<SPL, SI, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+        ES_LAUNCH(h, "k_emis_fwd", st, k_emis_fwd<SPL, SI, CL><<<grid, EM_THREADS, sm, st>>>(m, w, chunk)); \
     } while (0)
+#define ES_EF(SPL, SI) \
+    do { if (cloud) ES_EF1(SPL, SI, true); else ES_EF1(SPL, SI, false); } while (0)
+    const bool cloud = m.cloud_kind == ES_CLOUD_KH18;
     const int spl = spl_for(m.S);
     if (spl == 2) { if (store_i) ES_EF(2, true); else ES_EF(2, false); }
     else if (spl == 4) { if (store_i) ES_EF(4, true); else ES_EF(4, false); }
     else { if (store_i) ES_EF(8, true); else ES_EF(8, false); }
 #undef ES_EF
+#undef ES_EF1
     return 1;
 }
 
@@ -484,16 +578,20 @@ int launch_emis_fused_backward(const Model &m, const Work &w, cudaStream_t st, c
     const long long items = (long long)w.B * ((ntiles + chunk - 1) / chunk);
     const int grid = (int)std::min<long long>(items, (long long)sm_count_e());
     const size_t sm = emis_smem();
-#define ES_EB(SPL)                                                                              \
+#define ES_EB1(SPL, CL)                                                                         \
     do {                                                                                        \
-        cudaFuncSetAttribute(k_emis_bwd<SPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-        ES_LAUNCH(h, "k_emis_bwd", st, k_emis_bwd<SPL><<<grid, EM_THREADS, sm, st>>>(m, w, chunk)); \
+        cudaFuncSetAttribute(k_emis_bwd<SPL, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+        ES_LAUNCH(h, "k_emis_bwd", st, k_emis_bwd<SPL, CL><<<grid, EM_THREADS, sm, st>>>(m, w, chunk)); \
     } while (0)
+#define ES_EB(SPL) \
+    do { if (cloud) ES_EB1(SPL, true); else ES_EB1(SPL, false); } while (0)
+    const bool cloud = m.cloud_kind == ES_CLOUD_KH18;
     const int spl = spl_for(m.S);
     if (spl == 2) ES_EB(2);
     else if (spl == 4) ES_EB(4);
     else ES_EB(8);
 #undef ES_EB
+#undef ES_EB1
     return 1;
 }
 

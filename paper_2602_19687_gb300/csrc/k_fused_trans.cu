@@ -201,8 +201,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, in
             // non-grey cloud (Sect. 2.5): the cloudy chord depth is tau_i + g(nu) D_i,
             // g = 1/(Q0 x^-a + x^0.2), x = 2 pi r_eff nu; the two transit depths
             // mix by the cloud fraction, f delta_cld + (1 - f) delta_cf
-            const float lx = log2f(sm.cg[0] * m.nu[(size_t)pt * FT2 + nl]);
-            const float g = 1.f / (sm.cg[2] * exp2f(-sm.cg[1] * lx) + exp2f(0.2f * lx));
+            const float g = kh18_g(sm.cg, m.nu[(size_t)pt * FT2 + nl]);
             const float2 gl = f2(-g * LOG2E_F);
             float2 s2c = f2(0.f);
             auto term2c = [&](int k, float t0, float t1) {
@@ -729,9 +728,7 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
                 // tau_bar = dbar A_i E_i, area_bar += dbar (1 - E_i), and the
                 // adjoints of D_i, of g(nu) and of f
                 const float2 nu = *reinterpret_cast<const float2 *>(m.nu + nl);
-                const float lx0 = log2f(sm.cg[0] * nu.x), lx1 = log2f(sm.cg[0] * nu.y);
-                const float2 g = make_float2(1.f / (sm.cg[2] * exp2f(-sm.cg[1] * lx0) + exp2f(0.2f * lx0)),
-                                             1.f / (sm.cg[2] * exp2f(-sm.cg[1] * lx1) + exp2f(0.2f * lx1)));
+                const float2 g = make_float2(kh18_g(sm.cg, nu.x), kh18_g(sm.cg, nu.y));
                 const float2 gl = mul2(g, f2(-LOG2E_F));
                 const float fc = sm.cg[3];
                 float av[16], dv[16], fs = 0.f;
@@ -785,19 +782,11 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
                 tc_commit(mbar_a);
             }
             if (cloudy && threadIdx.x < BT) {
-                // d lnL / d g(nu) -> ln r_eff, a, ln Q0 at this tile's wavenumbers:
-                // g = 1/u, u = Q0 x^-a + x^0.2, x = 2 pi r_eff nu
+                // d lnL / d g(nu) -> ln r_eff, a, ln Q0 at this tile's wavenumbers
                 const float gb = sm.gbar[threadIdx.x];
                 sm.gbar[threadIdx.x] = 0.f;
                 float g_r = 0.f, g_a = 0.f, g_q = 0.f;
-                if (gb != 0.f) {
-                    const float x = sm.cg[0] * m.nu[nt0 + threadIdx.x];
-                    const float lx = log2f(x), xa = sm.cg[2] * exp2f(-sm.cg[1] * lx), x2 = exp2f(0.2f * lx);
-                    const float g = 1.f / (xa + x2), gg = gb * g * g;
-                    g_r = -gg * (0.2f * x2 - sm.cg[1] * xa);   // dg/dln x = dg/dln r_eff
-                    g_a = gg * xa * lx * 0.6931471805599453f;   // dg/da
-                    g_q = -gg * xa;                             // dg/dln Q0
-                }
+                if (gb != 0.f) kh18_g_adjoint(sm.cg, m.nu[nt0 + threadIdx.x], gb, g_r, g_a, g_q);
                 g_r = warp_sum(g_r);
                 g_a = warp_sum(g_a);
                 g_q = warp_sum(g_q);

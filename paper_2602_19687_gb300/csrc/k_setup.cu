@@ -136,14 +136,14 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup(Model m, Work w) {
         w.lmat[(size_t)b * L * L + idx] = v;
     }
     if (m.cloud_kind == ES_CLOUD_KH18) {
-        // Sect. 2.5: C_l = 3 rho_a q_c^eff(p_l) / (4 r_eff) with the base +
-        // power-law profile, and D_i = sum_l L_il C_l (the cloud's chord depth
-        // per unit g(nu)); the block's lmat rows are read back after the barrier
+        // Sect. 2.5: C_l = 3 rho_a q_c^eff(p_l) / (4 r_eff) with the model's
+        // q_c profile, and D_i = sum_l L_il C_l (the cloud's chord depth per
+        // unit g(nu)); the block's lmat rows are read back after the barrier
         const double r_eff = exp10(th[S + ES_P_LOG_R_EFF]) * 1.0e-4;
-        const double q_base = exp10(th[S + ES_P_LOG_QC]), p_base = exp10(th[S + ES_P_LOG_PC_BASE]) * BAR;
         for (int l = tid; l < L; l += blockDim.x) {
             const double p = m.p_lay[l];
-            const double q = (p <= p_base) ? q_base * pow(p / p_base, th[S + ES_P_ALPHA_C]) : 0.0;
+            double q = 0.0;   // stays 0 outside the cloud
+            cloud_mmr<double>(m, th, th, p, q);
             const double rho = s_mu * AMU * p / (K_B * tl[l]);
             w.cloud_c[(size_t)b * L + l] = bad ? 0.f : (float)(3.0 * rho * q / (4.0 * r_eff));
         }
@@ -210,7 +210,8 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup_bwd(Model m, Work w) {
     __shared__ double thv[ES_MAX_PARAMS];
     __shared__ double rcbar;
     __shared__ float tlf[ES_MAX_LAYERS], zf[ES_MAX_LAYERS];
-    // non-grey cloud: d lnL / d D_i, C_l and d lnL / d C_l = sum_i L_il Dbar_i
+    // non-grey cloud: d lnL / d D_i, C_l and d lnL / d C_l (transmission:
+    // sum_i L_il Dbar_i; emission: written directly by the emission adjoint)
     __shared__ float cdb[ES_MAX_LAYERS], ccl[ES_MAX_LAYERS];
     __shared__ double cbar[ES_MAX_LAYERS];
     // temperature tangents dT/dtheta_p at layers and (emission) levels
@@ -231,10 +232,12 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup_bwd(Model m, Work w) {
     if (tid < m.nfull) thv[tid] = w.theta[(size_t)b * m.nfull + tid];
     for (int l = tid; l < L; l += blockDim.x) tlf[l] = (float)w.t_lay[(size_t)b * L + l];
     if (tid == 0) rcbar = 0.0;
-    const bool cloudy = m.cloud_kind == ES_CLOUD_KH18 && !emis;
+    const bool cloud_any = m.cloud_kind == ES_CLOUD_KH18;
+    const bool cloudy = cloud_any && !emis;   // the chord depths D_i of transmission
     for (int l = tid; l < L; l += blockDim.x) {
         cdb[l] = cloudy ? (float)w.cloud_dbar[(size_t)b * L + l] : 0.f;
         ccl[l] = cloudy ? w.cloud_c[(size_t)b * L + l] : 0.f;
+        if (cloud_any && emis) cbar[l] = bad ? 0.0 : w.cloud_dbar[(size_t)b * L + l];
     }
     __syncthreads();
     split_radii(rl, L, q);
@@ -409,15 +412,14 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup_bwd(Model m, Work w) {
         DualF sc = emission_scale<DualF>(m, th, rref);
         acc += w.misc[(size_t)b * 4 + 1] * (double)sc.d;
     }
-    if (cloudy) {
+    if (cloud_any) {
         // C_l = 3 rho_a q_c^eff(p_l) / (4 r_eff), rho_a = mu m_u p / (k_B T_l); the
-        // base + power-law profile's branch is taken on the value (p <= p_base)
-        const DualF q_base = dexp10(th[S + ES_P_LOG_QC]), p_base = dexp10(th[S + ES_P_LOG_PC_BASE]) * BAR;
+        // profile's branches are taken on the FP64 values, as in the forward
         const DualF r_eff = dexp10(th[S + ES_P_LOG_R_EFF]) * 1.0e-4;
         for (int l = 0; l < L; ++l) {
             const double pl = m.p_lay[l];
-            if (!((float)pl <= p_base.v) || cbar[l] == 0.0) continue;
-            const DualF qc = q_base * dexp(th[S + ES_P_ALPHA_C] * dlog(pl / p_base));
+            DualF qc;
+            if (cbar[l] == 0.0 || !cloud_mmr<DualF>(m, th, thv, pl, qc)) continue;
             const DualF rho = mu * (AMU * pl / K_B) / tl[l];
             const DualF c = 3.0 * rho * qc / (4.0 * r_eff);
             acc += cbar[l] * (double)c.d;

@@ -164,6 +164,25 @@ __device__ R emission_scale(const Model &m, const R *th, R r_ref) {
     return th[m.S + ES_P_DILUTION] * ratio * ratio;
 }
 
+// Non-grey cloud: q_c^eff at pressure p (dyne cm^-2) for the model's profile
+// (Sect. 2.5.1). Returns false where the profile is zero; whether p lies in
+// the cloud is decided on the FP64 parameter values thv, so that the forward
+// and its tangents take the same branch.
+template <class R>
+__device__ bool cloud_mmr(const Model &m, const R *th, const double *thv, double p, R &q) {
+    const int S = m.S;
+    if (m.cloud_profile == ES_QC_SLAB_BAND) {
+        const double pt = exp10(thv[S + ES_P_LOG_PC_TOP]) * BAR, dp = exp10(thv[S + ES_P_LOG_DPC]) * BAR;
+        if (!(p >= pt && p <= pt + dp)) return false;
+    } else if (m.cloud_profile == ES_QC_POWER_LAW) {
+        if (!(p <= exp10(thv[S + ES_P_LOG_PC_BASE]) * BAR)) return false;
+    }
+    q = dexp10(th[S + ES_P_LOG_QC]);
+    if (m.cloud_profile == ES_QC_POWER_LAW)   // q_base (p / p_base)^alpha_c
+        q = q * dexp(th[S + ES_P_ALPHA_C] * dlog(p / (dexp10(th[S + ES_P_LOG_PC_BASE]) * BAR)));
+    return true;
+}
+
 // Index of the layer whose levels bracket p_ref (clamped to the grid).
 __device__ inline int anchor_layer(const Model &m) {
     int j = 0;

@@ -25,13 +25,15 @@ R_SUN_CM = 6.957e10
 # order as include/exoskry.h and the oracle).
 P_T_ISO, P_T_INT, P_T_EQ, P_LOG_KAPPA, P_LOG_GAMMA, P_Q_IRR0, P_LOG_PT, P_BETA, \
     P_LOG_G, P_R_P, P_LOG_PCLOUD, P_C_INFL, P_DILUTION, P_T_RATIO, P_M_BD, \
-    P_LOG_QC, P_LOG_PC_BASE, P_ALPHA_C, P_LOG_R_EFF, P_A_KH, P_LOG_Q0, P_F_CLD = range(22)
-N_EXTRA = 22
+    P_LOG_QC, P_LOG_PC_BASE, P_ALPHA_C, P_LOG_R_EFF, P_A_KH, P_LOG_Q0, P_F_CLD, \
+    P_LOG_PC_TOP, P_LOG_DPC = range(24)
+N_EXTRA = 24
 
 TP_ISOTHERMAL, TP_GUILLOT, TP_GUILLOT_MOD, TP_MILNE = 0, 1, 2, 3
 FLUX_PLANET_STAR, FLUX_BROWN_DWARF = 0, 1
 PARSEC_CM = 3.0856775814913673e18
 CLOUD_NONE, CLOUD_DECK, CLOUD_KH18 = 0, 1, 2
+QC_POWER_LAW, QC_SLAB, QC_SLAB_BAND = 0, 1, 2
 KIND_TRANSMISSION, KIND_EMISSION = 0, 1
 
 SPECIES = {  # name: mass in amu
@@ -60,6 +62,7 @@ class Model:
     free_idx: np.ndarray          # canonical slots that the user vector fills
     emission_flux: int = FLUX_PLANET_STAR
     distance_cm: float = 0.0
+    cloud_profile: int = QC_POWER_LAW
 
     @property
     def n_species(self):
@@ -224,6 +227,8 @@ def _model(n_species, n_layers, p_top, p_bot, tp_kind, cloud_kind, free, fixed=N
     theta[s + P_A_KH] = 4.0
     theta[s + P_LOG_Q0] = 1.0
     theta[s + P_F_CLD] = 0.5
+    theta[s + P_LOG_PC_TOP] = -3.0
+    theta[s + P_LOG_DPC] = -1.0
     for k, v in (fixed or {}).items():
         theta[k] = v
     return Model(n_layers=n_layers, p_top_bar=p_top, p_bot_bar=p_bot, p_ref_bar=10.0,
@@ -254,7 +259,8 @@ def prior_ranges(model):
               s + P_DILUTION: (0.5, 1.0), s + P_T_RATIO: (0.2, 0.9),
               s + P_M_BD: (65.0, 78.0), s + P_LOG_QC: (-8.0, -3.0), s + P_LOG_PC_BASE: (-3.0, 1.0),
               s + P_ALPHA_C: (0.0, 2.0), s + P_LOG_R_EFF: (-2.0, 0.5), s + P_A_KH: (2.0, 6.0),
-              s + P_LOG_Q0: (0.0, 2.0), s + P_F_CLD: (0.2, 1.0)})
+              s + P_LOG_Q0: (0.0, 2.0), s + P_F_CLD: (0.2, 1.0),
+              s + P_LOG_PC_TOP: (-5.0, -1.0), s + P_LOG_DPC: (-3.0, 0.0)})
     return r
 
 
@@ -282,6 +288,9 @@ def workload(name: str, batch: int | None = None, seed: int = 42,
                 + power-law q_c profile) and a cloud fraction instead of the
                 grey deck: 18 free parameters (6 log-VMR, 4 Guillot, radius,
                 7 cloud).
+    cloudy_emis 512 emission vectors as batched_emis with the non-grey cloud
+                and cloud fraction: 20 free parameters (8 log-VMR, 4 Guillot,
+                log g, 7 cloud); a clear and a cloudy column per wavenumber.
     browndwarf  256 brown-dwarf emission vectors shaped like the paper's
                 Gliese 229 B setup: 15 free parameters (6 log-VMR, T_int,
                 log kappa_ir, T_ratio, log p_t, beta of the modified Milne
@@ -291,7 +300,7 @@ def workload(name: str, batch: int | None = None, seed: int = 42,
     `n_nu` shrinks the spectral grid (same physics) for fast tests.
     """
     S = {"tiny": 3, "jwst_plain": 6, "batched_trans": 8, "batched_emis": 8, "highres": 4,
-         "browndwarf": 6, "cloudy_trans": 8}[name]
+         "browndwarf": 6, "cloudy_trans": 8, "cloudy_emis": 8}[name]
     s = S
     if name == "tiny":
         n = n_nu or 2000
@@ -346,6 +355,21 @@ def workload(name: str, batch: int | None = None, seed: int = 42,
         kind = np.ones(rows, np.int32)
         dtype, desc = "bf16", ("batched emission with adjoint, B=512, L=100, 8 absorbers, "
                                "20x15x20000 BF16 (1-12 um), 4 GL angles, 400 bins")
+        level = 2.0e-3
+    elif name == "cloudy_emis":
+        n = n_nu or 20000
+        free = list(range(8)) + [s + P_T_INT, s + P_T_EQ, s + P_LOG_KAPPA, s + P_LOG_GAMMA, s + P_LOG_G,
+                                 s + P_LOG_QC, s + P_LOG_PC_BASE, s + P_ALPHA_C, s + P_LOG_R_EFF,
+                                 s + P_A_KH, s + P_LOG_Q0, s + P_F_CLD]
+        model = _model(8, 100, 1e-8, 100.0, TP_GUILLOT, CLOUD_KH18, free=free, r_star_rsun=0.765)
+        nu = nu_grid_constant_r(1.0, 12.0, n)
+        tabs = make_tables(nu, 8, np.geomspace(400.0, 3000.0, 20), np.geomspace(1e-8, 100.0, 15))
+        lo, hi = make_bins(nu, min(400, n // 10))
+        rows = batch or 512
+        theta = _prior_batch(model, rows, seed, prior_ranges(model))
+        kind = np.ones(rows, np.int32)
+        dtype, desc = "bf16", ("batched emission with a non-grey cloud and cloud fraction, with adjoint, B=512, "
+                               "L=100, 8 absorbers, 20x15x20000 BF16 (1-12 um), 4 GL angles, 400 bins")
         level = 2.0e-3
     elif name == "highres":
         n = n_nu or 440000
@@ -403,7 +427,8 @@ def workload(name: str, batch: int | None = None, seed: int = 42,
     y_obs, sigma = {}, {}
     nb = lo.size
     y_obs[KIND_TRANSMISSION], sigma[KIND_TRANSMISSION] = make_data(nb, KIND_TRANSMISSION,
-                                                                   level if name != "batched_emis" else 0.014)
+                                                                   0.014 if name in ("batched_emis", "cloudy_emis")
+                                                                   else level)
     if name == "browndwarf":
         y_obs[KIND_EMISSION], sigma[KIND_EMISSION] = make_data(nb, KIND_EMISSION, level, rel_sigma=0.05)
     else:

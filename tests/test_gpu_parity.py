@@ -9,6 +9,7 @@ over ~1e4 wavenumbers). BF16-table workloads are compared with the oracle run
 on the same dequantized table values.
 """
 import copy
+import dataclasses
 
 import numpy as np
 import pytest
@@ -174,12 +175,42 @@ def test_cloudy_transmission():
         check_sample(out, b, ref, 0, grad=(b < 3))
 
 
-def test_cloudy_rejects_emission_samples():
-    w = synth.workload("cloudy_trans", batch=2, n_nu=600)
+def test_cloudy_emission():
+    """Non-grey cloud and cloud fraction in emission (Sect. 2.5 with Sect. 5):
+    a clear and a cloudy column per wavenumber, mixed by f_cld; Fp/F* element
+    by element, binned model, ln L and the gradient with respect to all 20
+    free parameters (7 of them the cloud's)."""
+    w = synth.workload("cloudy_emis", batch=4, n_nu=2000)
+    tabs = oracle_tables(w)
     ctx = binding.context_for(w)
-    th = torch.tensor(w.theta, dtype=torch.float64, device=DEV)
-    with pytest.raises(binding.ExoskryError):
-        ctx.es_set_batch(th, torch.tensor([0, 1], dtype=torch.int32, device=DEV))
+    out = gpu_eval(ctx, w, w.theta, np.ones(4, np.int32))
+    for b in range(4):
+        ref = oracle_eval(w, tabs, w.theta[b], 1, grad=(b < 2))
+        if not ref["valid"]:
+            assert out["lnl"][b] == O.INVALID_LNL
+            continue
+        check_sample(out, b, ref, 1, grad=(b < 2))
+
+
+@pytest.mark.parametrize("profile", [synth.QC_SLAB, synth.QC_SLAB_BAND])
+def test_cloud_slab_profiles_mixed_batch(profile):
+    """The whole-column slab and the slab band of Sect. 2.5.1 on a mixed
+    transmission / emission batch with the non-grey cloud: spectra, ln L and
+    gradients (zero along the power law's slots, which these profiles do not
+    use)."""
+    w = synth.workload("cloudy_trans", batch=4, n_nu=2000)
+    s = w.model.n_species
+    fixed = w.model.theta_fixed.copy()
+    fixed[s + synth.P_LOG_PC_TOP], fixed[s + synth.P_LOG_DPC] = -4.13, -0.61
+    w.model = dataclasses.replace(w.model, cloud_profile=profile, theta_fixed=fixed)
+    tabs = oracle_tables(w)
+    ctx = binding.context_for(w)
+    kind = np.array([0, 1, 0, 1], np.int32)
+    out = gpu_eval(ctx, w, w.theta, kind)
+    for b in range(4):
+        ref = oracle_eval(w, tabs, w.theta[b], int(kind[b]), grad=True)
+        assert ref["valid"]
+        check_sample(out, b, ref, int(kind[b]))
 
 
 def test_mixed_batch_highres_shape():

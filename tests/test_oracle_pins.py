@@ -205,6 +205,47 @@ def test_uniform_cloud_equals_constant_absorber():
     assert np.allclose(spec_cloud, spec_gas, rtol=1e-12)
 
 
+@pytest.mark.parametrize("kind", [0, 1])
+def test_slab_profiles_against_power_law_and_clear(kind):
+    """Sect. 2.5.1's three q_c profiles checked against each other: the
+    whole-column slab is the power law with alpha_c = 0 and its base below the
+    model; a band that spans the column is the whole-column slab; a band that
+    holds no layer pressure leaves the clear spectrum; and a band from above
+    the model down to a pressure between two layers is the power law with
+    alpha_c = 0 based at that pressure."""
+    w, m, th, s, mem = _cloud_setup(kind)
+    th[s + O.P_F_CLD] = 1.0
+    slab = dataclasses.replace(m, cloud_profile=O.QC_SLAB)
+    band = dataclasses.replace(m, cloud_profile=O.QC_SLAB_BAND)
+    clear = dataclasses.replace(m, cloud_kind=O.CLOUD_NONE)
+    t = th.copy()
+    t[s + O.P_LOG_PC_BASE], t[s + O.P_ALPHA_C] = 5.0, 0.0
+    ref_pl, _ = O.forward(m, w.tables, t, kind, mem)
+    ref_slab, _ = O.forward(slab, w.tables, th, kind, mem)
+    assert np.allclose(ref_slab, ref_pl, rtol=1e-14, atol=0)
+    t = th.copy()
+    t[s + O.P_LOG_PC_TOP], t[s + O.P_LOG_DPC] = -12.0, 5.0
+    assert np.allclose(O.forward(band, w.tables, t, kind, mem)[0], ref_slab, rtol=1e-14, atol=0)
+    p_lay = O.pressure_grid(m.n_layers, m.p_top_bar, m.p_bot_bar)[1]
+    t = th.copy()   # a band strictly between two layer pressures
+    lo, hi = np.log10(p_lay[40] / O.BAR), np.log10(p_lay[41] / O.BAR)
+    t[s + O.P_LOG_PC_TOP] = lo + 0.2 * (hi - lo)
+    t[s + O.P_LOG_DPC] = np.log10(0.5 * (p_lay[41] - p_lay[40]) / O.BAR)
+    ref_clear, _ = O.forward(clear, w.tables, th, kind, mem)
+    assert np.allclose(O.forward(band, w.tables, t, kind, mem)[0], ref_clear, rtol=1e-14, atol=0)
+    # band from above the model down to a pressure between layers 60 and 61
+    p_edge = np.sqrt(p_lay[60] * p_lay[61]) / O.BAR
+    t = th.copy()
+    t[s + O.P_LOG_PC_TOP] = -12.0
+    t[s + O.P_LOG_DPC] = np.log10(p_edge - 1e-12)
+    u = th.copy()
+    u[s + O.P_LOG_PC_BASE], u[s + O.P_ALPHA_C] = np.log10(p_edge), 0.0
+    got, _ = O.forward(band, w.tables, t, kind, mem)
+    want, _ = O.forward(m, w.tables, u, kind, mem)
+    assert np.allclose(got, want, rtol=1e-14, atol=0)
+    assert np.max(np.abs(got / ref_slab - 1.0)) > 1e-6 and np.max(np.abs(got / ref_clear - 1.0)) > 1e-6
+
+
 # ---------------------------------------------------------------- hydrostatics
 def test_hydrostatic_isothermal_closed_form():
     """Isothermal, constant mu, g ~ 1/r^2: 1/r(p) = 1/R + k T ln(p/p_ref)/(mu m_u g R^2)
@@ -618,13 +659,19 @@ def test_complex_step_gradient_brown_dwarf_milne():
         assert g[k] == pytest.approx(fd, rel=2e-5, abs=1e-6 * np.max(np.abs(g))), slot
 
 
-@pytest.mark.parametrize("kind", [0, 1])
-def test_complex_step_gradient_cloud(kind):
-    """Complex-step gradient of the non-grey cloud and cloud fraction (all 7
-    cloud slots, radius, a VMR, a profile slot) against central differences."""
+@pytest.mark.parametrize("kind,profile", [(0, O.QC_POWER_LAW), (1, O.QC_POWER_LAW), (0, O.QC_SLAB),
+                                          (1, O.QC_SLAB_BAND)])
+def test_complex_step_gradient_cloud(kind, profile):
+    """Complex-step gradient of the non-grey cloud and cloud fraction (the
+    cloud slots, radius, a VMR, a profile slot) against central differences,
+    for the power-law and slab q_c profiles (the band's edges off the layer
+    pressures, where lnL is flat in them)."""
     w, m, th, s, mem = _cloud_setup(kind)
+    m = dataclasses.replace(m, cloud_profile=profile)
+    th[s + O.P_LOG_PC_TOP], th[s + O.P_LOG_DPC] = -4.13, -0.61
     slots = [0, s + O.P_T_EQ, s + O.P_R_P] + [s + k for k in (O.P_LOG_QC, O.P_LOG_PC_BASE, O.P_ALPHA_C,
-                                                              O.P_LOG_R_EFF, O.P_A_KH, O.P_LOG_Q0, O.P_F_CLD)]
+                                                              O.P_LOG_R_EFF, O.P_A_KH, O.P_LOG_Q0, O.P_F_CLD,
+                                                              O.P_LOG_PC_TOP, O.P_LOG_DPC)]
     y_obs, sig = w.y_obs[kind], w.sigma[kind]
     g = O.loglike_gradient(m, w.tables, th, kind, mem, y_obs, sig, slots)
     for k, slot in enumerate(slots):
