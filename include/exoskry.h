@@ -100,13 +100,21 @@ enum { ES_FLAG_INVALID = 1 };
  *   LOG_DPC      log10 of the band's pressure extent dp [bar]  (ES_QC_SLAB_BAND)
  * The band's edges decide which layers hold cloud, so lnL is piecewise
  * constant in LOG_PC_TOP and LOG_DPC: their gradient is zero.
+ * Mid-infrared feature (cloud_feature = 1, Sect. 2.5.3): Q_ext = min(Q_cont +
+ * W(x) Q_feat, 2) with W = exp(-x / 0.5), Q_feat = 2 A exp(-z^2/2) Phi(xi z),
+ * z = (lambda - lambda_0) / omega, Phi the standard normal CDF, lambda in
+ * micron, the cap applied to Q_ext / Q_1 (Q_1 folded into q_c^eff):
+ *   FEAT_A       peak amplitude A
+ *   FEAT_LAM0    central wavelength lambda_0 [micron]
+ *   FEAT_W       width omega [micron]
+ *   FEAT_XI      skewness xi
  */
 enum {
     ES_P_T_ISO = 0, ES_P_T_INT, ES_P_T_EQ, ES_P_LOG_KAPPA_IR, ES_P_LOG_GAMMA_V,
     ES_P_Q_IRR0, ES_P_LOG_P_T, ES_P_BETA, ES_P_LOG_G, ES_P_R_P, ES_P_LOG_P_CLOUD,
     ES_P_C_INFL, ES_P_DILUTION, ES_P_T_RATIO, ES_P_M_BD,
     ES_P_LOG_QC, ES_P_LOG_PC_BASE, ES_P_ALPHA_C, ES_P_LOG_R_EFF, ES_P_A_KH, ES_P_LOG_Q0, ES_P_F_CLD,
-    ES_P_LOG_PC_TOP, ES_P_LOG_DPC,
+    ES_P_LOG_PC_TOP, ES_P_LOG_DPC, ES_P_FEAT_A, ES_P_FEAT_LAM0, ES_P_FEAT_W, ES_P_FEAT_XI,
     ES_P_N_EXTRA
 };
 
@@ -126,7 +134,8 @@ enum {
  * Rayleigh cross-sections are sigma(nu) = ray_*_cm2 (nu / ray_nu_ref)^4.
  * emission_flux selects the emission output (ES_FLUX_*); distance_cm is
  * the brown dwarf's distance D (> 0 with ES_FLUX_BROWN_DWARF).
- * cloud_profile selects the non-grey cloud's q_c profile (ES_QC_*).
+ * cloud_profile selects the non-grey cloud's q_c profile (ES_QC_*);
+ * cloud_feature = 1 adds the mid-infrared feature to its Q_ext.
  */
 typedef struct {
     int n_layers;
@@ -143,6 +152,7 @@ typedef struct {
     int emission_flux;           /* ES_FLUX_*        */
     double distance_cm;
     int cloud_profile;           /* ES_QC_*          */
+    int cloud_feature;           /* 0 or 1           */
 } es_model_desc;
 
 /*

@@ -33,6 +33,8 @@ Readings taken where the paper is silent:
  - emission: absorption-only linear-in-tau RT with 4 Gauss-Legendre angles on
    [0, 1], bottom boundary I = B(T_bottom level), F_* = pi B(T_*);
  - modified Milne profile: q_inf fixed at the Hopf function's deep limit;
+ - mid-infrared cloud feature: the Q_max = 2 cap applies to Q_ext / Q_1 (Q_1
+   folded into q_c^eff); lambda_0 and omega in micron;
  - non-grey cloud: r_eff in micron; each of the three mass-mixing-ratio
    profiles (power law above a base, whole-column slab, slab band with closed
    edges) evaluated at the layer pressures; no grey deck in the same model;
@@ -47,6 +49,7 @@ binning together) has no published worked example and rests on those pins.
 from __future__ import annotations
 
 import numpy as np
+from scipy.special import erf
 
 # CODATA 2018 (cgs) and nominal radii
 K_B = 1.380649e-16          # erg K^-1
@@ -73,7 +76,7 @@ INVALID_LNL = -1.0e300      # Sect. 2.3: invalid forward-model output
 (P_T_ISO, P_T_INT, P_T_EQ, P_LOG_KAPPA, P_LOG_GAMMA, P_Q_IRR0, P_LOG_PT, P_BETA,
  P_LOG_G, P_R_P, P_LOG_PCLOUD, P_C_INFL, P_DILUTION, P_T_RATIO, P_M_BD,
  P_LOG_QC, P_LOG_PC_BASE, P_ALPHA_C, P_LOG_R_EFF, P_A_KH, P_LOG_Q0, P_F_CLD,
- P_LOG_PC_TOP, P_LOG_DPC) = range(24)
+ P_LOG_PC_TOP, P_LOG_DPC, P_FEAT_A, P_FEAT_LAM0, P_FEAT_W, P_FEAT_XI) = range(28)
 # Sect. 2.5.1 vertical profiles of the cloud mass mixing ratio
 QC_POWER_LAW, QC_SLAB, QC_SLAB_BAND = 0, 1, 2
 TP_ISOTHERMAL, TP_GUILLOT, TP_GUILLOT_MOD, TP_MILNE = 0, 1, 2, 3
@@ -332,13 +335,39 @@ def q_ext_kh18(x, q0, a):
     return 1.0 / (q0 * x ** (-a) + x ** 0.2)
 
 
-def cloud_extinction(nu, rho_a, q_c_eff, r_eff, q0, a):
+# Sect. 2.5.3: the feature window's transition size parameter and the cap of
+# the total extinction efficiency
+FEAT_X0 = 0.5
+Q_MAX = 2.0
+
+
+def q_feat_skew_normal(lam_um, amp, lam0, width, skew):
+    """Eq. Q_ext_feat: Q_feat = 2 A exp(-z^2/2) Phi(xi z), z = (lambda -
+    lambda_0)/omega, Phi(t) = [1 + erf(t/sqrt 2)]/2; wavelengths in micron."""
+    z = (lam_um - lam0) / width
+    return 2.0 * amp * np.exp(-0.5 * z * z) * 0.5 * (1.0 + erf(skew * z / np.sqrt(2.0)))
+
+
+def q_ext_with_feature(x, lam_um, q0, a, amp, lam0, width, skew):
+    """Sect. 2.5.3: Q_ext = min(Q_cont + W(x) Q_feat, Q_max), W = exp(-x/x0),
+    Q_cont the KH18 form of q_ext_kh18 (Q_1 folded into q_c^eff, so the cap
+    applies to Q_ext / Q_1); the cap's branch on the real part."""
+    q = q_ext_kh18(x, q0, a) + np.exp(-x / FEAT_X0) * q_feat_skew_normal(lam_um, amp, lam0, width, skew)
+    return np.where(_re(q) > Q_MAX, Q_MAX, q)
+
+
+def cloud_extinction(nu, rho_a, q_c_eff, r_eff, q0, a, feature=None):
     """Sect. 2.5.2 (modified Fisher & Heng 2018): kappa_ext = 3 q_c^eff Q_ext(x)
     / (4 r_eff) [cm^2 g^-1] with the size parameter x = 2 pi r_eff / lambda =
     2 pi r_eff nu, and the layer extinction alpha_c(l, nu) = rho_a(l) kappa_ext
-    [cm^-1]; rho_a is the background gas mass density."""
+    [cm^-1]; rho_a is the background gas mass density. feature = (A, lambda_0,
+    omega, xi) adds the mid-infrared feature of Sect. 2.5.3."""
     x = 2.0 * np.pi * r_eff * nu
-    return (3.0 * rho_a * q_c_eff / (4.0 * r_eff))[:, None] * q_ext_kh18(x, q0, a)[None, :]
+    if feature is None:
+        q = q_ext_kh18(x, q0, a)
+    else:
+        q = q_ext_with_feature(x, 1.0e4 / nu, q0, a, *feature)
+    return (3.0 * rho_a * q_c_eff / (4.0 * r_eff))[:, None] * q[None, :]
 
 
 # --------------------------------------------------------------------------
@@ -486,8 +515,11 @@ def forward(model, tabs, theta, kind, members):
         p_lay, t_lay = atm["p_lay"], atm["t_lay"]
         q_c = cloud_profile(model, theta, p_lay)
         rho_a = atm["mu"] * AMU * p_lay / (K_B * t_lay)
+        feature = None
+        if getattr(model, "cloud_feature", 0):
+            feature = (theta[s + P_FEAT_A], theta[s + P_FEAT_LAM0], theta[s + P_FEAT_W], theta[s + P_FEAT_XI])
         alpha_cld = alpha + cloud_extinction(tabs.nu, rho_a, q_c, 10.0 ** theta[s + P_LOG_R_EFF] * 1.0e-4,
-                                             10.0 ** theta[s + P_LOG_Q0], theta[s + P_A_KH])
+                                             10.0 ** theta[s + P_LOG_Q0], theta[s + P_A_KH], feature)
         f_cld = theta[s + P_F_CLD]
     if kind == 0:
         P, dr, _ = path_matrix(r_lev)

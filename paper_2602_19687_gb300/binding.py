@@ -19,7 +19,7 @@ ES_OK, ES_EINVAL, ES_ENOMEM, ES_ECUDA, ES_ESTATE, ES_ETIMEOUT = range(6)
 ES_MEM_HOST, ES_MEM_DEVICE = 0, 1
 ES_TABLE_F32, ES_TABLE_BF16 = 0, 1
 ES_MAX_SPECIES = 16
-ES_P_N_EXTRA = 24
+ES_P_N_EXTRA = 28
 ES_MAX_PARAMS = ES_MAX_SPECIES + ES_P_N_EXTRA
 ES_MAX_LAYERS = 112
 STATUS_NAMES = {0: "ES_OK", 1: "ES_EINVAL", 2: "ES_ENOMEM", 3: "ES_ECUDA", 4: "ES_ESTATE", 5: "ES_ETIMEOUT"}
@@ -40,7 +40,7 @@ class es_model_desc(ctypes.Structure):
                 ("theta_fixed", ctypes.c_double * ES_MAX_PARAMS),
                 ("n_free", ctypes.c_int), ("free_idx", ctypes.c_int * ES_MAX_PARAMS),
                 ("emission_flux", ctypes.c_int), ("distance_cm", ctypes.c_double),
-                ("cloud_profile", ctypes.c_int)]
+                ("cloud_profile", ctypes.c_int), ("cloud_feature", ctypes.c_int)]
 
 
 class es_tables_desc(ctypes.Structure):
@@ -139,6 +139,7 @@ def model_desc(model) -> es_model_desc:
     d.emission_flux = int(getattr(model, "emission_flux", 0))
     d.distance_cm = float(getattr(model, "distance_cm", 0.0))
     d.cloud_profile = int(getattr(model, "cloud_profile", 0))
+    d.cloud_feature = int(getattr(model, "cloud_feature", 0))
     return d
 
 

@@ -224,7 +224,7 @@ es_status alloc_forward(es_ctx *c, int B) {
     ALLOC(w.ray, B * L);
     ALLOC(w.cloud_c, B * L);
     ALLOC(w.cloud_d, B * L);
-    ALLOC(w.cloud_g, B * 4);
+    ALLOC(w.cloud_g, B * N_CG);
     ALLOC(w.spec, (size_t)B * N);
     ALLOC(w.lnl, B);
     ALLOC(w.misc, (size_t)B * 4);
@@ -255,7 +255,7 @@ es_status alloc_backward(es_ctx *c) {
     ALLOC(w.drbar, (size_t)B * L);
     ALLOC(w.grad, (size_t)B * c->m.nfree);
     ALLOC(w.cloud_dbar, (size_t)B * L);
-    ALLOC(w.cloud_pbar, (size_t)B * 4);
+    ALLOC(w.cloud_pbar, (size_t)B * N_CG);
 #undef ALLOC
     c->cap_b_bwd = B;
     return ES_OK;
@@ -360,6 +360,7 @@ es_status es_create(es_ctx **out, int device, const es_model_desc *d) {
     if (d->emission_flux != ES_FLUX_PLANET_STAR && d->emission_flux != ES_FLUX_BROWN_DWARF) return ES_EINVAL;
     if (d->emission_flux == ES_FLUX_BROWN_DWARF && !(d->distance_cm > 0)) return ES_EINVAL;
     if (d->cloud_profile < ES_QC_POWER_LAW || d->cloud_profile > ES_QC_SLAB_BAND) return ES_EINVAL;
+    if (d->cloud_feature != 0 && d->cloud_feature != 1) return ES_EINVAL;
     if (!(d->r_star_cm > 0) || !(d->t_star_k > 0)) return ES_EINVAL;
     const int nfull = d->n_species + ES_P_N_EXTRA;
     if (d->n_free < 1 || d->n_free > 32 || d->n_free > nfull) return ES_EINVAL;
@@ -389,6 +390,7 @@ es_status es_create(es_ctx **out, int device, const es_model_desc *d) {
     m.emis_flux = d->emission_flux;
     m.distance = d->distance_cm;
     m.cloud_profile = d->cloud_profile;
+    m.cloud_feature = d->cloud_feature;
     m.p_ref = d->p_ref_bar * BAR;
     m.r_star = d->r_star_cm;
     m.t_star = d->t_star_k;
@@ -772,7 +774,7 @@ es_status enqueue_forward_backward(es_ctx *c, cudaStream_t st) {
     cudaMemsetAsync(w.drbar, 0, sizeof(double) * B * L, st);
     cudaMemsetAsync(w.lbar, 0, sizeof(float) * B * L * L, st);
     cudaMemsetAsync(w.cloud_dbar, 0, sizeof(double) * B * L, st);
-    cudaMemsetAsync(w.cloud_pbar, 0, sizeof(double) * B * 4, st);
+    cudaMemsetAsync(w.cloud_pbar, 0, sizeof(double) * B * N_CG, st);
     es_status s = run_forward(c, true, nullptr, nullptr, c->d_lnl, st);
     if (s != ES_OK) return s;
     int launches = (int)c->last_launches;

@@ -336,23 +336,81 @@ __device__ __forceinline__ float warp_sum(float v) {
 }
 
 // ------------------------------------------------------------ non-grey cloud
-// Sect. 2.5 extinction efficiency with Q_1 folded into q_c^eff:
-// g(nu) = 1/u, u = Q0 x^-a + x^0.2, x = 2 pi r_eff nu; cg = (2 pi r_eff, a, Q0, f_cld).
+// Sect. 2.5 extinction efficiency with Q_1 folded into q_c^eff, g(nu) = Q_ext/Q_1:
+// the continuum 1/u, u = Q0 x^-a + x^0.2, x = 2 pi r_eff nu, and with the
+// mid-infrared feature (Sect. 2.5.3; on when A = cg[4] != 0)
+//   g = min(1/u + W(x) Q_feat, Q_max),  W = exp(-x / x0),
+//   Q_feat = 2 A exp(-z^2/2) Phi(xi z),  z = (lambda - lambda_0) / omega,
+// lambda in micron. cg = (2 pi r_eff, a, Q0, f_cld, A, lambda_0, omega, xi).
+constexpr float FEAT_INV_X0 = 2.f;   // 1 / x0, x0 = 0.5
+constexpr float Q_EXT_MAX = 2.f;
+
+struct CloudFeature {
+    float z, e, cdf, win, qf;   // z, exp(-z^2/2), Phi(xi z), W(x), Q_feat
+    __device__ __forceinline__ CloudFeature(const float *cg, float nu, float x) {
+        z = (1.0e4f / nu - cg[5]) / cg[6];
+        e = expf(-0.5f * z * z);
+        cdf = normcdff(cg[7] * z);
+        win = expf(-x * FEAT_INV_X0);
+        qf = 2.f * cg[4] * e * cdf;
+    }
+};
+
 __device__ __forceinline__ float kh18_g(const float *cg, float nu) {
-    const float lx = log2f(cg[0] * nu);
-    return 1.f / (cg[2] * exp2f(-cg[1] * lx) + exp2f(0.2f * lx));
+    const float x = cg[0] * nu, lx = log2f(x);
+    float g = 1.f / (cg[2] * exp2f(-cg[1] * lx) + exp2f(0.2f * lx));
+    if (cg[4] != 0.f) {
+        const CloudFeature f(cg, nu, x);
+        g = fminf(fmaf(f.win, f.qf, g), Q_EXT_MAX);
+    }
+    return g;
 }
 
-// Given gb = d lnL / d g(nu), the derivatives along ln r_eff (= ln x), a and
-// ln Q0: dg/dln x = -g^2 (0.2 x^0.2 - a Q0 x^-a), dg/da = g^2 Q0 x^-a ln x,
-// dg/dln Q0 = -g^2 Q0 x^-a.
-__device__ __forceinline__ void kh18_g_adjoint(const float *cg, float nu, float gb, float &g_r, float &g_a,
-                                               float &g_q) {
-    const float lx = log2f(cg[0] * nu), xa = cg[2] * exp2f(-cg[1] * lx), x2 = exp2f(0.2f * lx);
-    const float g = 1.f / (xa + x2), gg = gb * g * g;
-    g_r = -gg * (0.2f * x2 - cg[1] * xa);
-    g_a = gg * xa * lx * 0.6931471805599453f;
-    g_q = -gg * xa;
+// Given gb = d lnL / d g(nu), the derivatives o = d lnL / d (ln r_eff, a,
+// ln Q0, A, lambda_0, omega, xi) at this wavenumber. Continuum (u as above,
+// g_c = 1/u): dg/dln x = -g_c^2 (0.2 x^0.2 - a Q0 x^-a), dg/da = g_c^2 Q0
+// x^-a ln x, dg/dln Q0 = -g_c^2 Q0 x^-a. Feature: dW/dln x = -(x/x0) W,
+// dQ_feat/dA = Q_feat/A, dQ_feat/dz = 2A exp(-z^2/2) (xi phi(xi z) - z Phi(xi z)),
+// dz/dlambda_0 = -1/omega, dz/domega = -z/omega, dQ_feat/dxi = 2A exp(-z^2/2)
+// phi(xi z) z, phi the normal density. At the cap g is flat: all zero.
+__device__ __forceinline__ void kh18_g_adjoint(const float *cg, float nu, float gb, float (&o)[7]) {
+    const float x = cg[0] * nu, lx = log2f(x), xa = cg[2] * exp2f(-cg[1] * lx), x2 = exp2f(0.2f * lx);
+    const float gc = 1.f / (xa + x2), gg = gb * gc * gc;
+    o[0] = -gg * (0.2f * x2 - cg[1] * xa);
+    o[1] = gg * xa * lx * 0.6931471805599453f;
+    o[2] = -gg * xa;
+    o[3] = o[4] = o[5] = o[6] = 0.f;
+    if (cg[4] != 0.f) {
+        const CloudFeature f(cg, nu, x);
+        if (fmaf(f.win, f.qf, gc) < Q_EXT_MAX) {
+            const float gw = gb * f.win;
+            const float pdf = 0.3989422804014327f * expf(-0.5f * cg[7] * cg[7] * f.z * f.z);
+            const float dqdz = 2.f * cg[4] * f.e * (cg[7] * pdf - f.z * f.cdf);
+            o[0] -= gw * f.qf * x * FEAT_INV_X0;
+            o[3] = gw * 2.f * f.e * f.cdf;
+            o[4] = -gw * dqdz / cg[6];
+            o[5] = -gw * dqdz * f.z / cg[6];
+            o[6] = gw * 2.f * cg[4] * f.e * pdf * f.z;
+        } else {
+            o[0] = o[1] = o[2] = 0.f;
+        }
+    }
+}
+
+// Sums a warp's g-parameter adjoints (kh18_g_adjoint) and adds them to the
+// sample's accumulators: cpbar = (ln r_eff, a, ln Q0, f_cld, A, lambda_0,
+// omega, xi); the feature's four only when it is on (cg[4] != 0).
+__device__ __forceinline__ void cloud_pbar_add(const float *cg, float (&o)[7], float *cpbar, int lane) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) o[k] = warp_sum(o[k]);
+    if (lane == 0)
+        for (int k = 0; k < 3; ++k) atomicAdd(cpbar + k, o[k]);
+    if (cg[4] != 0.f) {
+#pragma unroll
+        for (int k = 3; k < 7; ++k) o[k] = warp_sum(o[k]);
+        if (lane == 0)
+            for (int k = 3; k < 7; ++k) atomicAdd(cpbar + k + 1, o[k]);
+    }
 }
 
 }  // namespace es

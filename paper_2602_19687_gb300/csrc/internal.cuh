@@ -40,6 +40,10 @@ constexpr double TWO_HC2 = 2.0 * H_PLANCK * C_LIGHT * C_LIGHT;
 // wavenumber pair and split the species between them).
 __host__ __device__ constexpr int spl_for(int S) { return S <= 4 ? 2 : (S <= 8 ? 4 : 8); }
 // number of Gauss-Legendre angles for the emission flux integral
+// per-sample constants of the non-grey cloud's g(nu) = Q_ext / Q_1 and the
+// slots of their adjoints: (2 pi r_eff | ln r_eff, a, Q0 | ln Q0, f_cld, A,
+// lambda_0, omega, xi)
+constexpr int N_CG = 8;
 constexpr int N_MU = 4;
 // reductions per (sample, layer) in the extinction adjoint, each a sum over
 // wavenumber of alpha_bar times a part of d alpha: 0/1 QS (species sum; two
@@ -56,6 +60,7 @@ struct Model {
     int SP;                       // species slots per coefficient-table entry (2 spl_for(S) >= S)
     int tp_kind, cloud_kind, bf16;
     int cloud_profile;            // ES_QC_* (non-grey cloud)
+    int cloud_feature;            // 1: the mid-infrared feature in Q_ext
     int emis_flux;                // ES_FLUX_*
     double distance;              // cm (brown-dwarf flux)
     double p_ref;                 // dyn cm^-2
@@ -114,7 +119,7 @@ struct Work {
     // non-grey cloud (ES_CLOUD_KH18): extinction C_l g(nu), g = 1/(Q0 x^-a + x^0.2)
     float *cloud_c;               // [B][L] C_l = 3 rho_a q_c^eff / (4 r_eff)
     float *cloud_d;               // [B][L] D_i = sum_l L_il C_l: cloudy chord depth = tau_i + g(nu) D_i
-    float *cloud_g;               // [B][4] 2 pi r_eff [cm], a, Q0, f_cld
+    float *cloud_g;               // [B][N_CG] 2 pi r_eff [cm], a, Q0, f_cld, A (0: no feature), lambda_0, omega, xi
     float *spec;                  // [B][N] transmission: depth - base; emission: Fp/F*
     double *ymod;                 // [B][nbins]
     double *lnl;                  // [B]
@@ -132,7 +137,7 @@ struct Work {
     double *drbar;                // [B][L]   d lnL / d dr (emission)
     double *misc;                 // [B][4] base_bar, scale_bar, c_bar, -
     double *cloud_dbar;           // [B][L] non-grey cloud: d lnL / d D_i (transmission), d lnL / d C_l (emission)
-    double *cloud_pbar;           // [B][4] d lnL / d (ln r_eff via g, a, ln Q0, f_cld)
+    double *cloud_pbar;           // [B][N_CG] d lnL / d (ln r_eff via g, a, ln Q0, f_cld, A, lambda_0, omega, xi)
     double *grad;                 // [B][nfree]
 };
 

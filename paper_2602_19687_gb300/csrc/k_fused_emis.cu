@@ -43,7 +43,7 @@ struct EmisSmem {
     float inv_t[ES_MAX_LAYERS + 1];    // 1 / T at the levels
     float dr[ES_MAX_LAYERS];           // layer thickness
     float ccl[ES_MAX_LAYERS];          // non-grey cloud: C_l (extinction per unit g(nu))
-    float cg[4];                       // non-grey cloud: 2 pi r_eff, a, Q0, f_cld
+    float cg[N_CG];                    // non-grey cloud: g(nu) constants (kh18_g)
     // adjoint accumulators of the current sample: per layer 32 partial sums
     // [value 0..7][lane parity][lane bit 1] (values: QS, D, C, CT, W4, dr_bar,
     // T_bar of the level, C_l bar of the cloud), combined at the flush
@@ -51,7 +51,7 @@ struct EmisSmem {
     float levb_bot;                    // T_bar of the bottom level
     float qtot[ES_MAX_SPECIES];
     float sbar;
-    float cpbar[4];                    // d lnL / d (ln r_eff via g, a, ln Q0, f_cld)
+    float cpbar[N_CG];                 // d lnL / d (ln r_eff via g, a, ln Q0, f_cld, A, lambda_0, omega, xi)
 };
 
 template <bool CLOUD>
@@ -61,7 +61,7 @@ __device__ void stage_levels(const Model &m, const Work &w, int b, EmisSmem &sm)
     for (int l = threadIdx.x; l < L; l += blockDim.x) sm.dr[l] = w.dr[(size_t)b * L + l];
     if (CLOUD) {
         for (int l = threadIdx.x; l < L; l += blockDim.x) sm.ccl[l] = w.cloud_c[(size_t)b * L + l];
-        if (threadIdx.x < 4) sm.cg[threadIdx.x] = w.cloud_g[(size_t)b * 4 + threadIdx.x];
+        if (threadIdx.x < N_CG) sm.cg[threadIdx.x] = w.cloud_g[(size_t)b * N_CG + threadIdx.x];
     }
 }
 
@@ -368,8 +368,8 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_emis_bwd(Model m, Work w, int
             }
         }
         if (threadIdx.x == 0 && sm.levb_bot != 0.f) atomicAdd(w.levbar + (size_t)b * (L + 1) + L, (double)sm.levb_bot);
-        if (CLOUD && threadIdx.x < 4 && sm.cpbar[threadIdx.x] != 0.f)
-            atomicAdd(w.cloud_pbar + (size_t)b * 4 + threadIdx.x, (double)sm.cpbar[threadIdx.x]);
+        if (CLOUD && threadIdx.x < N_CG && sm.cpbar[threadIdx.x] != 0.f)
+            atomicAdd(w.cloud_pbar + (size_t)b * N_CG + threadIdx.x, (double)sm.cpbar[threadIdx.x]);
         for (int s2 = threadIdx.x; s2 < S; s2 += EM_THREADS)
             if (sm.qtot[s2] != 0.f) atomicAdd(w.qtot + (size_t)b * S + s2, (double)sm.qtot[s2]);
         if (threadIdx.x == 0 && sm.sbar != 0.f) atomicAdd(w.misc + (size_t)b * 4 + 1, (double)sm.sbar);
@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_emis_bwd(Model m, Work w, int
             stage_levels<CLOUD>(m, w, b, sm);
             for (int idx = threadIdx.x; idx < L * 32; idx += EM_THREADS) sm.red[idx] = 0.f;
             for (int s2 = threadIdx.x; s2 < ES_MAX_SPECIES; s2 += EM_THREADS) sm.qtot[s2] = 0.f;
-            if (threadIdx.x < 4) sm.cpbar[threadIdx.x] = 0.f;
+            if (threadIdx.x < N_CG) sm.cpbar[threadIdx.x] = 0.f;
             if (threadIdx.x == 0) {
                 sm.sbar = 0.f;
                 sm.levb_bot = 0.f;
@@ -494,20 +494,13 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_emis_bwd(Model m, Work w, int
             const float lev_last = warp_total(bl * dbdt);
             float flux = flux_of(ang, itoa);
             if (CLOUD) {
-                // f_cld and g(nu) -> ln r_eff, a, ln Q0 of the lane's wavenumber
+                // f_cld and g(nu) -> the g(nu) parameters at the lane's wavenumber
                 const float fcl = flux_of(ang, itc);
                 const float fb = warp_total(db * scale * fsc * (fcl - flux));
-                float g_r = 0.f, g_a = 0.f, g_q = 0.f;
-                if (gacc != 0.f) kh18_g_adjoint(sm.cg, m.nu[nme], gacc, g_r, g_a, g_q);
-                g_r = warp_total(g_r);
-                g_a = warp_total(g_a);
-                g_q = warp_total(g_q);
-                if (lane == 0) {
-                    atomicAdd(sm.cpbar + 0, g_r);
-                    atomicAdd(sm.cpbar + 1, g_a);
-                    atomicAdd(sm.cpbar + 2, g_q);
-                    atomicAdd(sm.cpbar + 3, fb);
-                }
+                float o[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if (gacc != 0.f) kh18_g_adjoint(sm.cg, m.nu[nme], gacc, o);
+                cloud_pbar_add(sm.cg, o, sm.cpbar, lane);
+                if (lane == 0) atomicAdd(sm.cpbar + 3, fb);
                 flux = wcl * fcl + wcf * flux;
             }
             const float sb = warp_total(db * flux * fsc);

@@ -46,7 +46,7 @@ struct TransFwdSmem {
     alignas(128) unsigned char ah[1][(LP / 8) * SBO_NU], al[1][(LP / 8) * SBO_NU];   // alpha[l][nu], split BF16
     float area[LP];
     float cd[LP];                                  // non-grey cloud: D_i (0 beyond L)
-    float cg[4];                                   // non-grey cloud: 2 pi r_eff, a, Q0, f_cld
+    float cg[N_CG];                                // non-grey cloud: g(nu) constants (kh18_g)
     float part[2][4][FT2];                         // per-column-chunk partial transit sums, per buffer
     alignas(8) uint64_t mbar[2];
     uint32_t tmem_base;
@@ -80,8 +80,8 @@ struct TransBwdSmem {
     float red[ES_MAX_LAYERS * 32];
     float qtot[ES_MAX_SPECIES];                         // per-species totals of the current sample
     // non-grey cloud: D_i, its adjoint, d lnL / d g(nu) of the tile, the
-    // constants (2 pi r_eff, a, Q0, f) and the parameter adjoints of the sample
-    float cd[LP], cdbar[LP], gbar[BT], cg[4], cpbar[4];
+    // g(nu) constants and the parameter adjoints of the sample
+    float cd[LP], cdbar[LP], gbar[BT], cg[N_CG], cpbar[N_CG];
     alignas(16) unsigned char stage[BW_WARPS][STAGE_BYTES_PER_WARP];   // per-warp coefficient staging
     alignas(8) uint64_t mbar_a, mbar_l;
     uint32_t tmem_base;
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, in
             stage_lmat_tc(m, w, b, sm.lh, sm.ll, sm.area);
             if (CLOUD) {
                 for (int i = threadIdx.x; i < LP; i += F2_THREADS) sm.cd[i] = (i < L) ? w.cloud_d[(size_t)b * L + i] : 0.f;
-                if (threadIdx.x < 4) sm.cg[threadIdx.x] = w.cloud_g[(size_t)b * 4 + threadIdx.x];
+                if (threadIdx.x < N_CG) sm.cg[threadIdx.x] = w.cloud_g[(size_t)b * N_CG + threadIdx.x];
             }
             cur_b = b;
             fence_async_smem();
@@ -624,8 +624,8 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
         if (cloudy) {
             for (int i = threadIdx.x; i < L; i += BW_THREADS)
                 if (sm.cdbar[i] != 0.f) atomicAdd(w.cloud_dbar + (size_t)b * L + i, (double)sm.cdbar[i]);
-            if (threadIdx.x < 4 && sm.cpbar[threadIdx.x] != 0.f)
-                atomicAdd(w.cloud_pbar + (size_t)b * 4 + threadIdx.x, (double)sm.cpbar[threadIdx.x]);
+            if (threadIdx.x < N_CG && sm.cpbar[threadIdx.x] != 0.f)
+                atomicAdd(w.cloud_pbar + (size_t)b * N_CG + threadIdx.x, (double)sm.cpbar[threadIdx.x]);
         }
     };
     // L2 prefetch of the exp(-tau) rows and dbar of tile t of sample b (the
@@ -665,8 +665,8 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
                     sm.cd[i] = (i < L) ? w.cloud_d[(size_t)b * L + i] : 0.f;
                     sm.cdbar[i] = 0.f;
                 }
-                if (threadIdx.x < 4) {
-                    sm.cg[threadIdx.x] = w.cloud_g[(size_t)b * 4 + threadIdx.x];
+                if (threadIdx.x < N_CG) {
+                    sm.cg[threadIdx.x] = w.cloud_g[(size_t)b * N_CG + threadIdx.x];
                     sm.cpbar[threadIdx.x] = 0.f;
                 }
             }
@@ -782,19 +782,12 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
                 tc_commit(mbar_a);
             }
             if (cloudy && threadIdx.x < BT) {
-                // d lnL / d g(nu) -> ln r_eff, a, ln Q0 at this tile's wavenumbers
+                // d lnL / d g(nu) -> the g(nu) parameters at this tile's wavenumbers
                 const float gb = sm.gbar[threadIdx.x];
                 sm.gbar[threadIdx.x] = 0.f;
-                float g_r = 0.f, g_a = 0.f, g_q = 0.f;
-                if (gb != 0.f) kh18_g_adjoint(sm.cg, m.nu[nt0 + threadIdx.x], gb, g_r, g_a, g_q);
-                g_r = warp_sum(g_r);
-                g_a = warp_sum(g_a);
-                g_q = warp_sum(g_q);
-                if (lane == 0) {
-                    atomicAdd(sm.cpbar + 0, g_r);
-                    atomicAdd(sm.cpbar + 1, g_a);
-                    atomicAdd(sm.cpbar + 2, g_q);
-                }
+                float o[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if (gb != 0.f) kh18_g_adjoint(sm.cg, m.nu[nt0 + threadIdx.x], gb, o);
+                cloud_pbar_add(sm.cg, o, sm.cpbar, lane);
             }
             interp_backward<SPL>(m, sm.sc, sm.sc.gb[grp], sm.sc.gb[grp + 1], nt0 + 2 * pair, half, lane, abar_t, a_dst,
                                  sm.red, sm.qtot, stg, t > c * chunk_tiles, t + 1 < t1 ? BT : 0, [&]() {

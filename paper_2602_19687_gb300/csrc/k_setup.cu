@@ -156,11 +156,16 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup(Model m, Work w) {
             w.cloud_d[(size_t)b * L + i] = (float)d;
         }
         if (tid == 0) {
-            float *cg = w.cloud_g + (size_t)b * 4;
+            float *cg = w.cloud_g + (size_t)b * N_CG;
             cg[0] = (float)(2.0 * PI * r_eff);
             cg[1] = (float)th[S + ES_P_A_KH];
             cg[2] = (float)exp10(th[S + ES_P_LOG_Q0]);
             cg[3] = (float)th[S + ES_P_F_CLD];
+            // mid-infrared feature (A = 0 switches it off in the kernels)
+            cg[4] = m.cloud_feature ? (float)th[S + ES_P_FEAT_A] : 0.f;
+            cg[5] = (float)th[S + ES_P_FEAT_LAM0];
+            cg[6] = (float)th[S + ES_P_FEAT_W];
+            cg[7] = (float)th[S + ES_P_FEAT_XI];
         }
     }
     for (int l = tid; l < L; l += blockDim.x) {
@@ -424,10 +429,14 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup_bwd(Model m, Work w) {
             const DualF c = 3.0 * rho * qc / (4.0 * r_eff);
             acc += cbar[l] * (double)c.d;
         }
-        // g(nu): the kernel's sums over wavenumber of dbar-weighted dg/d(ln r_eff, a, ln Q0); f_cld
-        const double *cp = w.cloud_pbar + (size_t)b * 4;
+        // g(nu): the kernel's sums over wavenumber of dbar-weighted dg/d(ln r_eff, a, ln Q0); f_cld;
+        // the mid-infrared feature's A, lambda_0, omega, xi
+        const double *cp = w.cloud_pbar + (size_t)b * N_CG;
         acc += cp[0] * LN10 * (double)th[S + ES_P_LOG_R_EFF].d + cp[1] * (double)th[S + ES_P_A_KH].d +
                cp[2] * LN10 * (double)th[S + ES_P_LOG_Q0].d + cp[3] * (double)th[S + ES_P_F_CLD].d;
+        if (m.cloud_feature)
+            acc += cp[4] * (double)th[S + ES_P_FEAT_A].d + cp[5] * (double)th[S + ES_P_FEAT_LAM0].d +
+                   cp[6] * (double)th[S + ES_P_FEAT_W].d + cp[7] * (double)th[S + ES_P_FEAT_XI].d;
     }
     acc += w.misc[(size_t)b * 4 + 2] * (double)th[S + ES_P_C_INFL].d;
     gout[p] = acc;

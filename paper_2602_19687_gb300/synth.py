@@ -26,8 +26,8 @@ R_SUN_CM = 6.957e10
 P_T_ISO, P_T_INT, P_T_EQ, P_LOG_KAPPA, P_LOG_GAMMA, P_Q_IRR0, P_LOG_PT, P_BETA, \
     P_LOG_G, P_R_P, P_LOG_PCLOUD, P_C_INFL, P_DILUTION, P_T_RATIO, P_M_BD, \
     P_LOG_QC, P_LOG_PC_BASE, P_ALPHA_C, P_LOG_R_EFF, P_A_KH, P_LOG_Q0, P_F_CLD, \
-    P_LOG_PC_TOP, P_LOG_DPC = range(24)
-N_EXTRA = 24
+    P_LOG_PC_TOP, P_LOG_DPC, P_FEAT_A, P_FEAT_LAM0, P_FEAT_W, P_FEAT_XI = range(28)
+N_EXTRA = 28
 
 TP_ISOTHERMAL, TP_GUILLOT, TP_GUILLOT_MOD, TP_MILNE = 0, 1, 2, 3
 FLUX_PLANET_STAR, FLUX_BROWN_DWARF = 0, 1
@@ -63,6 +63,7 @@ class Model:
     emission_flux: int = FLUX_PLANET_STAR
     distance_cm: float = 0.0
     cloud_profile: int = QC_POWER_LAW
+    cloud_feature: int = 0        # 1: the mid-infrared feature of the non-grey cloud
 
     @property
     def n_species(self):
@@ -229,6 +230,10 @@ def _model(n_species, n_layers, p_top, p_bot, tp_kind, cloud_kind, free, fixed=N
     theta[s + P_F_CLD] = 0.5
     theta[s + P_LOG_PC_TOP] = -3.0
     theta[s + P_LOG_DPC] = -1.0
+    theta[s + P_FEAT_A] = 0.5
+    theta[s + P_FEAT_LAM0] = 9.5
+    theta[s + P_FEAT_W] = 1.5
+    theta[s + P_FEAT_XI] = 2.0
     for k, v in (fixed or {}).items():
         theta[k] = v
     return Model(n_layers=n_layers, p_top_bar=p_top, p_bot_bar=p_bot, p_ref_bar=10.0,
@@ -260,7 +265,9 @@ def prior_ranges(model):
               s + P_M_BD: (65.0, 78.0), s + P_LOG_QC: (-8.0, -3.0), s + P_LOG_PC_BASE: (-3.0, 1.0),
               s + P_ALPHA_C: (0.0, 2.0), s + P_LOG_R_EFF: (-2.0, 0.5), s + P_A_KH: (2.0, 6.0),
               s + P_LOG_Q0: (0.0, 2.0), s + P_F_CLD: (0.2, 1.0),
-              s + P_LOG_PC_TOP: (-5.0, -1.0), s + P_LOG_DPC: (-3.0, 0.0)})
+              s + P_LOG_PC_TOP: (-5.0, -1.0), s + P_LOG_DPC: (-3.0, 0.0),
+              s + P_FEAT_A: (0.0, 1.5), s + P_FEAT_LAM0: (8.0, 11.0), s + P_FEAT_W: (0.5, 3.0),
+              s + P_FEAT_XI: (-5.0, 5.0)})
     return r
 
 

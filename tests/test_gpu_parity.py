@@ -192,6 +192,28 @@ def test_cloudy_emission():
         check_sample(out, b, ref, 1, grad=(b < 2))
 
 
+@pytest.mark.parametrize("kind", [0, 1])
+def test_cloud_mid_infrared_feature(kind):
+    """The non-grey cloud with the mid-infrared feature of Sect. 2.5.3 (skew-
+    normal Q_feat, size window, Q_max cap) placed inside the band: spectra,
+    ln L and the gradient with respect to 22 free parameters, the feature's
+    four among them."""
+    w = synth.workload("cloudy_trans", batch=3, n_nu=2000)
+    s = w.model.n_species
+    feat = [s + synth.P_FEAT_A, s + synth.P_FEAT_LAM0, s + synth.P_FEAT_W, s + synth.P_FEAT_XI]
+    w.model = dataclasses.replace(w.model, cloud_feature=1, free_idx=np.concatenate([w.model.free_idx, feat]))
+    rng = np.random.default_rng(5)
+    w.theta = np.hstack([w.theta, np.column_stack([rng.uniform(0.2, 1.0, 3), rng.uniform(1.5, 4.5, 3),
+                                                   rng.uniform(0.4, 1.2, 3), rng.uniform(-4.0, 4.0, 3)])])
+    tabs = oracle_tables(w)
+    ctx = binding.context_for(w)
+    out = gpu_eval(ctx, w, w.theta, np.full(3, kind, np.int32))
+    for b in range(3):
+        ref = oracle_eval(w, tabs, w.theta[b], kind, grad=True)
+        assert ref["valid"]
+        check_sample(out, b, ref, kind)
+
+
 @pytest.mark.parametrize("profile", [synth.QC_SLAB, synth.QC_SLAB_BAND])
 def test_cloud_slab_profiles_mixed_batch(profile):
     """The whole-column slab and the slab band of Sect. 2.5.1 on a mixed

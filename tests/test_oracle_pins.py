@@ -205,6 +205,35 @@ def test_uniform_cloud_equals_constant_absorber():
     assert np.allclose(spec_cloud, spec_gas, rtol=1e-12)
 
 
+def test_cloud_feature_skew_normal_area_mean_window_and_cap():
+    """Sect. 2.5.3: 2 phi(z) Phi(xi z) / omega is the skew-normal density, so
+    the feature integrates to A omega sqrt(2 pi) over wavelength for any xi
+    and its centroid is lambda_0 + omega delta sqrt(2/pi), delta =
+    xi/sqrt(1 + xi^2); xi = 0 is a Gaussian of peak A at lambda_0; the window
+    keeps the whole feature for x << x0 and removes it for x >> x0; the total
+    efficiency is capped at Q_max = 2."""
+    lam = np.linspace(-30.0, 50.0, 400001)
+    amp, lam0, om = 0.7, 9.5, 1.5
+    for xi in (0.0, 3.0, -2.0):
+        q = O.q_feat_skew_normal(lam, amp, lam0, om, xi)
+        area = np.trapezoid(q, lam)
+        assert area == pytest.approx(amp * om * np.sqrt(2.0 * np.pi), rel=1e-9)
+        delta = xi / np.sqrt(1.0 + xi * xi)
+        assert np.trapezoid(q * lam, lam) / area == pytest.approx(lam0 + om * delta * np.sqrt(2.0 / np.pi),
+                                                                    rel=1e-9)
+    assert O.q_feat_skew_normal(lam0, amp, lam0, om, 0.0) == pytest.approx(amp, rel=1e-15)
+    lam_pt = np.array([8.0, 9.5, 11.0])
+    feat = O.q_feat_skew_normal(lam_pt, amp, lam0, om, 1.0)
+    x = np.full(3, 1e-9)
+    q_small = O.q_ext_with_feature(x, lam_pt, 10.0, 4.0, amp, lam0, om, 1.0)
+    assert np.allclose(q_small, O.q_ext_kh18(x, 10.0, 4.0) + feat, rtol=1e-8)
+    x = np.full(3, 60.0)
+    assert np.allclose(O.q_ext_with_feature(x, lam_pt, 10.0, 4.0, amp, lam0, om, 1.0),
+                       O.q_ext_kh18(x, 10.0, 4.0), rtol=1e-15)
+    capped = O.q_ext_with_feature(np.full(3, 1e-3), lam_pt, 10.0, 4.0, 5.0, lam0, om, 0.0)
+    assert capped[1] == 2.0 and np.all(capped <= 2.0)
+
+
 @pytest.mark.parametrize("kind", [0, 1])
 def test_slab_profiles_against_power_law_and_clear(kind):
     """Sect. 2.5.1's three q_c profiles checked against each other: the
@@ -659,19 +688,23 @@ def test_complex_step_gradient_brown_dwarf_milne():
         assert g[k] == pytest.approx(fd, rel=2e-5, abs=1e-6 * np.max(np.abs(g))), slot
 
 
-@pytest.mark.parametrize("kind,profile", [(0, O.QC_POWER_LAW), (1, O.QC_POWER_LAW), (0, O.QC_SLAB),
-                                          (1, O.QC_SLAB_BAND)])
-def test_complex_step_gradient_cloud(kind, profile):
+@pytest.mark.parametrize("kind,profile,feature", [(0, O.QC_POWER_LAW, 0), (1, O.QC_POWER_LAW, 0),
+                                                  (0, O.QC_SLAB, 0), (1, O.QC_SLAB_BAND, 0),
+                                                  (0, O.QC_POWER_LAW, 1), (1, O.QC_POWER_LAW, 1)])
+def test_complex_step_gradient_cloud(kind, profile, feature):
     """Complex-step gradient of the non-grey cloud and cloud fraction (the
     cloud slots, radius, a VMR, a profile slot) against central differences,
     for the power-law and slab q_c profiles (the band's edges off the layer
-    pressures, where lnL is flat in them)."""
+    pressures, where lnL is flat in them) and with the mid-infrared feature
+    (its four slots; the feature inside the band, below the Q_max cap)."""
     w, m, th, s, mem = _cloud_setup(kind)
-    m = dataclasses.replace(m, cloud_profile=profile)
+    m = dataclasses.replace(m, cloud_profile=profile, cloud_feature=feature)
     th[s + O.P_LOG_PC_TOP], th[s + O.P_LOG_DPC] = -4.13, -0.61
+    th[s + O.P_FEAT_A], th[s + O.P_FEAT_LAM0], th[s + O.P_FEAT_W], th[s + O.P_FEAT_XI] = 0.6, 3.0, 0.8, 2.5
     slots = [0, s + O.P_T_EQ, s + O.P_R_P] + [s + k for k in (O.P_LOG_QC, O.P_LOG_PC_BASE, O.P_ALPHA_C,
                                                               O.P_LOG_R_EFF, O.P_A_KH, O.P_LOG_Q0, O.P_F_CLD,
-                                                              O.P_LOG_PC_TOP, O.P_LOG_DPC)]
+                                                              O.P_LOG_PC_TOP, O.P_LOG_DPC, O.P_FEAT_A,
+                                                              O.P_FEAT_LAM0, O.P_FEAT_W, O.P_FEAT_XI)]
     y_obs, sig = w.y_obs[kind], w.sigma[kind]
     g = O.loglike_gradient(m, w.tables, th, kind, mem, y_obs, sig, slots)
     for k, slot in enumerate(slots):
