@@ -54,6 +54,10 @@ struct EmisSmem {
     float cpbar[N_CG];                 // d lnL / d (ln r_eff via g, a, ln Q0, f_cld, A, lambda_0, omega, xi)
 };
 
+// The adjoint's per-warp coefficient staging follows EmisSmem in dynamic
+// shared memory (the forward has none: its loads go through L1).
+constexpr size_t EM_STAGE_OFFSET = (sizeof(EmisSmem) + 127) / 128 * 128;
+
 template <bool CLOUD>
 __device__ void stage_levels(const Model &m, const Work &w, int b, EmisSmem &sm) {
     const int L = m.L;
@@ -337,6 +341,11 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_emis_bwd(Model m, Work w, int
                       ((lane >> 1) & 1);
     const int ridx = 4 * ((lane >> 4) & 1) + 2 * ((lane >> 3) & 1) + ((lane >> 2) & 1);   // transpose_reduce8 slot
     const bool qwriter = (lane & 3) == 0;
+    // coefficients of each run are staged through shared memory one run ahead
+    // (the last run of a tile stages the first run of the warp's next tile)
+    constexpr bool STAGED = 2 * SPL + 1 <= STAGE_BLOCKS;
+    const uint32_t stg = smem_u32(reinterpret_cast<unsigned char *>(smem4) + EM_STAGE_OFFSET +
+                                  (size_t)warp * STAGE_BYTES_PER_WARP) + 16u * (uint32_t)lane;
     Angles ang;
     ang.init(m);
     int cur_b = -1;
@@ -394,12 +403,15 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_emis_bwd(Model m, Work w, int
         }
         const float scale = (float)w.scale[b];
         const int t1 = min(ntiles, (c + 1) * chunk_tiles);
+        bool prestaged = false;
         for (int t = c * chunk_tiles; t < t1; ++t) {
             const int nw = t * ET + 32 * warp;
             if (nw >= m.Np) continue;
             const int n = nw + 2 * (lane >> 1), nme = n + half;
+            const bool next_ok = t + 1 < t1 && nw + ET < m.Np;   // the warp's next tile of this item
             PairInterp<SPL> pi;
             pi.init(m, n, half, lane);
+            if (STAGED && !prestaged) pi.stage(stg, sm.sc.lay[0].cell, sm.sc.lay[0].itc, 0);
             Planck pl;
             pl.init(m.nu[nme]);
             const float4 *it4 = reinterpret_cast<const float4 *>(w.itop) + ((size_t)b * m.Np + nme) * (CLOUD ? 2 : 1);
@@ -431,8 +443,14 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_emis_bwd(Model m, Work w, int
             for (int l = 0; l < L;) {
                 // broadcast from lane 0: provably warp-uniform for the compiler
                 const int end = __shfl_sync(0xffffffffu, sm.sc.lay[l].run_end, 0);
-                pi.load(sm.sc, sm.sc.lay[l].cell, sm.sc.lay[l].itc);
-                if (end < L) pi.prefetch(sm.sc.lay[end].cell, sm.sc.lay[end].itc);
+                if constexpr (STAGED) {
+                    pi.load_staged(sm.sc, stg);
+                    if (end < L) pi.stage(stg, sm.sc.lay[end].cell, sm.sc.lay[end].itc, 0);
+                    else if (next_ok) pi.stage(stg, sm.sc.lay[0].cell, sm.sc.lay[0].itc, ET);
+                } else {
+                    pi.load(sm.sc, sm.sc.lay[l].cell, sm.sc.lay[l].itc);
+                    if (end < L) pi.prefetch(sm.sc.lay[end].cell, sm.sc.lay[end].itc);
+                }
                 for (; l < end; ++l) {
                     const LayerConst &lc = sm.sc.lay[l];
                     // extinction, keeping this lane's species terms
@@ -520,6 +538,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_emis_bwd(Model m, Work w, int
                 const float tq = transpose_reduce8_e(vq, lane);
                 if (qwriter && c0 + ridx < S && tq != 0.f) atomicAdd(sm.qtot + c0 + ridx, tq);
             }
+            prestaged = STAGED && next_ok;
         }
     }
     if (cur_b >= 0) flush(cur_b);
@@ -570,7 +589,7 @@ int launch_emis_fused_backward(const Model &m, const Work &w, cudaStream_t st, c
     const int chunk = emis_chunk(m, w.B);
     const long long items = (long long)w.B * ((ntiles + chunk - 1) / chunk);
     const int grid = (int)std::min<long long>(items, (long long)sm_count_e());
-    const size_t sm = emis_smem();
+    const size_t sm = EM_STAGE_OFFSET + (size_t)EM_WARPS * STAGE_BYTES_PER_WARP;
 #define ES_EB1(SPL, CL)                                                                         \
     do {                                                                                        \
         cudaFuncSetAttribute(k_emis_bwd<SPL, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
