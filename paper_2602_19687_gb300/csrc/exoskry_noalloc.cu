@@ -85,6 +85,11 @@ size_t carve(const es::Model &m, int B, bool emission, unsigned char *base, es::
     w.gtc = c.take<float>(B * L);
     w.ccia = c.take<float>(B * L * 2);
     w.ray = c.take<float>(B * L);
+    if (m.cloud_kind == ES_CLOUD_KH18) {   // non-grey cloud: C_l, D_i and the g(nu) constants
+        w.cloud_c = c.take<float>(B * L);
+        w.cloud_d = c.take<float>(B * L);
+        w.cloud_g = c.take<float>((size_t)B * es::N_CG);
+    }
     w.spec = c.take<float>((size_t)B * N);
     w.ymod = c.take<double>((size_t)B * m.nbins);
     w.lnl = c.take<double>(B);
@@ -103,8 +108,6 @@ extern "C" es_status es_loglike_noalloc(es_ctx *c, const double *theta, const in
                                         double *lnl, es_stream_t stream) {
     if (!c) return ES_EINVAL;
     if (!theta || !lnl || batch < 1) return fail(c, ES_EINVAL, "es_loglike_noalloc: NULL theta/lnL or batch < 1");
-    if (c->m.cloud_kind == ES_CLOUD_KH18)
-        return fail(c, ES_EINVAL, "es_loglike_noalloc: the non-grey cloud needs the allocating entry points");
     if (!c->have_tables) return fail(c, ES_ESTATE, "tables not loaded");
     if (!c->have_grid) return fail(c, ES_ESTATE, "instrument grid not set");
     if (!c->have_data[ES_KIND_TRANSMISSION] || (kind && !c->have_data[ES_KIND_EMISSION]))

@@ -55,6 +55,23 @@ def test_no_alloc_mixed_kinds_twice():
         np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-5, atol=1e-3)
 
 
+def test_no_alloc_non_grey_cloud_mixed_kinds_twice():
+    """The non-grey cloud with the mid-infrared feature, in transmission and
+    emission: its per-vector cloud constants also come from the fixed array."""
+    import dataclasses
+    w = synth.workload("cloudy_trans", batch=4, n_nu=2000)
+    w.model = dataclasses.replace(w.model, cloud_feature=1)
+    ctx = binding.context_for(w)
+    theta = torch.tensor(w.theta, dtype=torch.float64, device=DEV)
+    kind = torch.tensor([0, 1, 1, 0], dtype=torch.int32, device=DEV)
+    ref = _reference(ctx, theta, kind)
+    for _ in range(2):
+        out = torch.full((4,), float("nan"), dtype=torch.float64, device=DEV)
+        ctx.es_loglike_noalloc(theta, kind, out)
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-5, atol=1e-3)
+
+
 def test_no_alloc_rejects_a_batch_beyond_the_fixed_workspace():
     w = synth.workload("jwst_plain", batch=400, n_nu=20000)    # ~130 kB per vector: 52 MB > 32 MiB
     ctx = binding.context_for(w)
