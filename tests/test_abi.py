@@ -46,8 +46,10 @@ def test_struct_layout_matches_c_header():
 #include <stddef.h>
 #include "exoskry.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(es_model_desc), offsetof(es_model_desc, theta_fixed),
-         offsetof(es_model_desc, free_idx), sizeof(es_tables_desc), offsetof(es_tables_desc, cia_h2he),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(es_model_desc), offsetof(es_model_desc, theta_fixed),
+         offsetof(es_model_desc, free_idx), offsetof(es_model_desc, emission_flux),
+         offsetof(es_model_desc, distance_cm), offsetof(es_model_desc, cloud_profile),
+         offsetof(es_model_desc, cloud_feature), sizeof(es_tables_desc), offsetof(es_tables_desc, cia_h2he),
          offsetof(es_tables_desc, storage));
   return 0;
 }
@@ -59,7 +61,8 @@ int main(void) {
         subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
         vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     M, T = binding.es_model_desc, binding.es_tables_desc
-    assert vals == [ctypes.sizeof(M), M.theta_fixed.offset, M.free_idx.offset, ctypes.sizeof(T),
+    assert vals == [ctypes.sizeof(M), M.theta_fixed.offset, M.free_idx.offset, M.emission_flux.offset,
+                    M.distance_cm.offset, M.cloud_profile.offset, M.cloud_feature.offset, ctypes.sizeof(T),
                     T.cia_h2he.offset, T.storage.offset]
 
 
@@ -76,7 +79,9 @@ def test_null_context_calls(lib):
 
 @pytest.mark.parametrize("field,value", [("n_layers", 1), ("n_layers", 113), ("n_species", 0),
                                          ("n_species", 17), ("p_top_bar", -1.0), ("tp_kind", 7),
-                                         ("cloud_kind", 3), ("n_free", 0), ("r_star_cm", 0.0)])
+                                         ("cloud_kind", 3), ("n_free", 0), ("r_star_cm", 0.0),
+                                         ("emission_flux", 2), ("cloud_profile", 3), ("cloud_profile", -1),
+                                         ("cloud_feature", 2)])
 def test_create_rejects_bad_descriptions_before_touching_cuda(lib, field, value):
     w = synth.workload("tiny", n_nu=64)
     d = binding.model_desc(w.model)
