@@ -178,12 +178,14 @@ def test_cloud_fraction_limits_and_linearity(kind):
     assert np.allclose(O.forward(m, w.tables, t, kind, mem)[0], ref, rtol=1e-14, atol=0)
 
 
-def test_uniform_cloud_equals_constant_absorber():
+@pytest.mark.parametrize("kind", [0, 1])
+def test_uniform_cloud_equals_constant_absorber(kind):
     """A cloud of uniform q_c (base below the model, alpha_c = 0) with no gas
-    opacity gives the transit depth of an absorber whose cross-section times
-    VMR is mu m_u kappa_ext(nu): pins rho_a = mu m_u n and the cloud's entry
-    into the chord optical depth."""
-    m = _model(L=40, tp=O.TP_ISOTHERMAL, cloud=O.CLOUD_KH18)
+    opacity gives the transit depth (emergent flux) of an absorber whose
+    cross-section times VMR is mu m_u kappa_ext(nu): pins rho_a = mu m_u n and
+    the cloud's entry into the chord optical depth and the emission column."""
+    # an isothermal column emits B(T) whatever its opacity: emission needs a gradient
+    m = _model(L=40, tp=O.TP_ISOTHERMAL if kind == 0 else O.TP_GUILLOT, cloud=O.CLOUD_KH18)
     m.ray_h2_cm2 = m.ray_he_cm2 = 0.0
     s = m.n_species
     nu = synth.nu_grid_constant_r(0.6, 5.0, 30)
@@ -193,7 +195,7 @@ def test_uniform_cloud_equals_constant_absorber():
     th[s + O.P_LOG_R_EFF], th[s + O.P_A_KH], th[s + O.P_LOG_Q0], th[s + O.P_F_CLD] = -0.4, 4.0, 1.2, 1.0
     mem = O.bin_members(nu, np.array([0.55]), np.array([5.5]))
     cloud_tabs = _flat_tables(nu, -99.0)
-    spec_cloud, _ = O.forward(m, cloud_tabs, th, 0, mem)
+    spec_cloud, _ = O.forward(m, cloud_tabs, th, kind, mem)
     atm = O.atmosphere(m, th)
     r = 10 ** th[s + O.P_LOG_R_EFF] * 1e-4
     kappa = 3.0 * 10 ** th[s + O.P_LOG_QC] / (4.0 * r) * O.q_ext_kh18(2 * np.pi * r * nu, 10 ** 1.2, 4.0)
@@ -201,8 +203,10 @@ def test_uniform_cloud_equals_constant_absorber():
     gas_tabs = _flat_tables(nu, -99.0)
     gas_tabs.log10_sigma = np.broadcast_to(np.log10(sigma), gas_tabs.log10_sigma.shape).copy()
     clear = dataclasses.replace(m, cloud_kind=O.CLOUD_NONE)
-    spec_gas, _ = O.forward(clear, gas_tabs, th, 0, mem)
+    spec_gas, _ = O.forward(clear, gas_tabs, th, kind, mem)
     assert np.allclose(spec_cloud, spec_gas, rtol=1e-12)
+    spec_none, _ = O.forward(clear, cloud_tabs, th, kind, mem)   # neither cloud nor absorber
+    assert np.max(np.abs(spec_cloud / spec_none - 1.0)) > 1e-3
 
 
 def test_cloud_feature_skew_normal_area_mean_window_and_cap():
