@@ -58,6 +58,11 @@ enum { ES_CLOUD_NONE = 0, ES_CLOUD_DECK = 1, ES_CLOUD_KH18 = 2 };
  *   ES_QC_SLAB       q_slab at every pressure
  *   ES_QC_SLAB_BAND  q_slab for p_top <= p <= p_top + dp, 0 elsewhere */
 enum { ES_QC_POWER_LAW = 0, ES_QC_SLAB = 1, ES_QC_SLAB_BAND = 2 };
+/* Angles of the emergent-flux integral F = 2 pi int_0^1 I(mu) mu dmu (Sect. 5):
+ *   ES_QUAD_GAUSS_LEGENDRE  4-point Gauss-Legendre on [0, 1], F = 2 pi sum w_j mu_j I_j
+ *   ES_QUAD_GAUSS_JACOBI    4-point Gauss-Jacobi rule of the weight mu on [0, 1]
+ *                           ("8-stream": 4 angles per hemisphere), F = 2 pi sum W_j I_j */
+enum { ES_QUAD_GAUSS_LEGENDRE = 0, ES_QUAD_GAUSS_JACOBI = 1 };
 enum { ES_KIND_TRANSMISSION = 0, ES_KIND_EMISSION = 1 };
 enum { ES_TABLE_F32 = 0, ES_TABLE_BF16 = 1 };
 enum { ES_MEM_HOST = 0, ES_MEM_DEVICE = 1 };
@@ -136,6 +141,7 @@ enum {
  * the brown dwarf's distance D (> 0 with ES_FLUX_BROWN_DWARF).
  * cloud_profile selects the non-grey cloud's q_c profile (ES_QC_*);
  * cloud_feature = 1 adds the mid-infrared feature to its Q_ext.
+ * emission_quadrature selects the flux integral's angles (ES_QUAD_*).
  */
 typedef struct {
     int n_layers;
@@ -153,6 +159,7 @@ typedef struct {
     double distance_cm;
     int cloud_profile;           /* ES_QC_*          */
     int cloud_feature;           /* 0 or 1           */
+    int emission_quadrature;     /* ES_QUAD_*        */
 } es_model_desc;
 
 /*

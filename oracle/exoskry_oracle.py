@@ -31,7 +31,9 @@ Readings taken where the paper is silent:
    areas (in units of pi) A_i = r_up^2 - max(r_low^2, r_c^2), clipped at 0,
    and r_c the radius of an opaque grey deck (r_bot without a deck);
  - emission: absorption-only linear-in-tau RT with 4 Gauss-Legendre angles on
-   [0, 1], bottom boundary I = B(T_bottom level), F_* = pi B(T_*);
+   [0, 1], or the 4-angle Gauss-Jacobi rule of the flux integral (weight mu:
+   "8-stream" read as 4 angles per hemisphere), bottom boundary
+   I = B(T_bottom level), F_* = pi B(T_*);
  - modified Milne profile: q_inf fixed at the Hopf function's deep limit;
  - mid-infrared cloud feature: the Q_max = 2 cap applies to Q_ext / Q_1 (Q_1
    folded into q_c^eff); lambda_0 and omega in micron;
@@ -49,7 +51,7 @@ binning together) has no published worked example and rests on those pins.
 from __future__ import annotations
 
 import numpy as np
-from scipy.special import erf
+from scipy.special import erf, roots_jacobi
 
 # CODATA 2018 (cgs) and nominal radii
 K_B = 1.380649e-16          # erg K^-1
@@ -112,6 +114,28 @@ def gauss_legendre_01(n):
     """n-point Gauss-Legendre nodes and weights mapped from [-1, 1] to [0, 1]."""
     x, w = np.polynomial.legendre.leggauss(n)
     return 0.5 * (x + 1.0), 0.5 * w
+
+
+def gauss_jacobi_mu_01(n):
+    """Sect. 5 (Gauss-Jacobi angles for the intensity-to-flux integral): the
+    n-point Gaussian rule for int_0^1 f(mu) mu dmu, i.e. the Gauss-Jacobi rule
+    of weight (1 - x)^0 (1 + x)^1 on [-1, 1] mapped by mu = (1 + x)/2 (the
+    weight becomes 2 mu, dx = 2 dmu). Returns nodes mu_j and weights W_j with
+    sum_j W_j f(mu_j) ~ int_0^1 f(mu) mu dmu."""
+    x, w = roots_jacobi(n, 0.0, 1.0)
+    return 0.5 * (x + 1.0), 0.25 * w
+
+
+QUAD_GAUSS_LEGENDRE, QUAD_GAUSS_JACOBI = 0, 1
+
+
+def flux_quadrature(kind=QUAD_GAUSS_LEGENDRE, n_mu=4):
+    """Angles mu_j and flux weights a_j with F = 2 pi sum_j a_j I(mu_j):
+    Gauss-Legendre a_j = w_j mu_j, Gauss-Jacobi a_j = W_j."""
+    if kind == QUAD_GAUSS_JACOBI:
+        return gauss_jacobi_mu_01(n_mu)
+    mu, w = gauss_legendre_01(n_mu)
+    return mu, w * mu
 
 
 # --------------------------------------------------------------------------
@@ -407,14 +431,15 @@ def linear_source_factor(x):
     return np.where(small, series, exact)
 
 
-def emergent_flux(b_lev, dtau, n_mu=4):
+def emergent_flux(b_lev, dtau, n_mu=4, quadrature=QUAD_GAUSS_LEGENDRE):
     """Top-of-atmosphere flux for absorption-only RT with a source linear in
     optical depth within each layer, integrated from I = B(bottom level)
-    upward, for each Gauss-Legendre angle mu_j on [0, 1]:
+    upward, for each angle mu_j of the flux quadrature on [0, 1]:
         E = exp(-dtau/mu),
         I <- I E + B_top (1 - E) + (B_bot - B_top) [(mu/dtau)(1 - E) - E],
-    F = 2 pi sum_j w_j mu_j I_j.   b_lev [L+1, N] top to bottom, dtau [L, N]."""
-    mu, w = gauss_legendre_01(n_mu)
+    F = 2 pi sum_j a_j I_j (a_j = w_j mu_j for Gauss-Legendre, W_j for
+    Gauss-Jacobi).   b_lev [L+1, N] top to bottom, dtau [L, N]."""
+    mu, a = flux_quadrature(quadrature, n_mu)
     n = dtau.shape[0]
     flux = 0.0
     for j in range(n_mu):
@@ -423,7 +448,7 @@ def emergent_flux(b_lev, dtau, n_mu=4):
             x = dtau[l] / mu[j]
             e = np.exp(-x)
             inten = inten * e + b_lev[l] * (1.0 - e) + (b_lev[l + 1] - b_lev[l]) * linear_source_factor(x)
-        flux = flux + 2.0 * np.pi * w[j] * mu[j] * inten
+        flux = flux + 2.0 * np.pi * a[j] * inten
     return flux
 
 
@@ -537,9 +562,10 @@ def forward(model, tabs, theta, kind, members):
         dr = r_lev[:-1] - r_lev[1:]
         dtau = alpha * dr[:, None]
         b_lev = planck_wavenumber(atm["t_lev"][:, None], tabs.nu[None, :])
-        f_toa = emergent_flux(b_lev, dtau)
+        quad = getattr(model, "emission_quadrature", QUAD_GAUSS_LEGENDRE)
+        f_toa = emergent_flux(b_lev, dtau, quadrature=quad)
         if cloudy:
-            f_toa = f_cld * emergent_flux(b_lev, alpha_cld * dr[:, None]) + (1.0 - f_cld) * f_toa
+            f_toa = f_cld * emergent_flux(b_lev, alpha_cld * dr[:, None], quadrature=quad) + (1.0 - f_cld) * f_toa
         if getattr(model, "emission_flux", FLUX_PLANET_STAR) == FLUX_BROWN_DWARF:
             # Sect. 5: F_bd = s F_toa (R_bd / D)^2
             spec = theta[s + P_DILUTION] * f_toa * (atm["r_ref"] / model.distance_cm) ** 2

@@ -40,7 +40,8 @@ class es_model_desc(ctypes.Structure):
                 ("theta_fixed", ctypes.c_double * ES_MAX_PARAMS),
                 ("n_free", ctypes.c_int), ("free_idx", ctypes.c_int * ES_MAX_PARAMS),
                 ("emission_flux", ctypes.c_int), ("distance_cm", ctypes.c_double),
-                ("cloud_profile", ctypes.c_int), ("cloud_feature", ctypes.c_int)]
+                ("cloud_profile", ctypes.c_int), ("cloud_feature", ctypes.c_int),
+                ("emission_quadrature", ctypes.c_int)]
 
 
 class es_tables_desc(ctypes.Structure):
@@ -140,6 +141,7 @@ def model_desc(model) -> es_model_desc:
     d.distance_cm = float(getattr(model, "distance_cm", 0.0))
     d.cloud_profile = int(getattr(model, "cloud_profile", 0))
     d.cloud_feature = int(getattr(model, "cloud_feature", 0))
+    d.emission_quadrature = int(getattr(model, "emission_quadrature", 0))
     return d
 
 

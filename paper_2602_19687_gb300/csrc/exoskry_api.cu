@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "context.cuh"
+#include "quadrature.h"
 
 using namespace es;
 
@@ -361,6 +362,8 @@ es_status es_create(es_ctx **out, int device, const es_model_desc *d) {
     if (d->emission_flux == ES_FLUX_BROWN_DWARF && !(d->distance_cm > 0)) return ES_EINVAL;
     if (d->cloud_profile < ES_QC_POWER_LAW || d->cloud_profile > ES_QC_SLAB_BAND) return ES_EINVAL;
     if (d->cloud_feature != 0 && d->cloud_feature != 1) return ES_EINVAL;
+    if (d->emission_quadrature != ES_QUAD_GAUSS_LEGENDRE && d->emission_quadrature != ES_QUAD_GAUSS_JACOBI)
+        return ES_EINVAL;
     if (!(d->r_star_cm > 0) || !(d->t_star_k > 0)) return ES_EINVAL;
     const int nfull = d->n_species + ES_P_N_EXTRA;
     if (d->n_free < 1 || d->n_free > 32 || d->n_free > nfull) return ES_EINVAL;
@@ -400,15 +403,14 @@ es_status es_create(es_ctx **out, int device, const es_model_desc *d) {
     for (int s = 0; s < m.S; ++s) m.mass[s] = d->species_mass_amu[s];
     for (int k = 0; k < nfull; ++k) m.theta_fixed[k] = d->theta_fixed[k];
     for (int k = 0; k < m.nfree; ++k) m.free_idx[k] = d->free_idx[k];
-    // 4-point Gauss-Legendre on [0, 1]: x = +-sqrt(3/7 -+ 2/7 sqrt(6/5)),
-    // w = (18 +- sqrt(30))/36 on [-1, 1]
-    const double xa = std::sqrt(3.0 / 7.0 - 2.0 / 7.0 * std::sqrt(6.0 / 5.0));
-    const double xb = std::sqrt(3.0 / 7.0 + 2.0 / 7.0 * std::sqrt(6.0 / 5.0));
-    const double wa = (18.0 + std::sqrt(30.0)) / 36.0, wb = (18.0 - std::sqrt(30.0)) / 36.0;
-    const double xs[4] = {-xb, -xa, xa, xb}, ws[4] = {wb, wa, wa, wb};
-    for (int j = 0; j < 4; ++j) {
-        m.mu_gl[j] = 0.5 * (xs[j] + 1.0);
-        m.w_gl[j] = 0.5 * ws[j];
+    // flux angles: the kernels form 2 pi w_j mu_j, so a Gauss-Jacobi weight
+    // W_j (of the weight mu) is stored as W_j / mu_j
+    if (d->emission_quadrature == ES_QUAD_GAUSS_JACOBI) {
+        double W[N_MU];
+        gauss_jacobi_mu_01(N_MU, m.mu_gl, W);
+        for (int j = 0; j < N_MU; ++j) m.w_gl[j] = W[j] / m.mu_gl[j];
+    } else {
+        gauss_legendre4_01(m.mu_gl, m.w_gl);
     }
     // pressure levels (top to bottom) and layers
     std::vector<double> p_lev(m.L + 1), p_lay(m.L);

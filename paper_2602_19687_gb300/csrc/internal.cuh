@@ -69,7 +69,7 @@ struct Model {
     double mass[ES_MAX_SPECIES];
     int free_idx[ES_MAX_PARAMS];
     double theta_fixed[ES_MAX_PARAMS];
-    double mu_gl[N_MU], w_gl[N_MU];
+    double mu_gl[N_MU], w_gl[N_MU];   // flux angles mu_j and weights w_j (F = 2 pi sum w_j mu_j I_j)
     // device arrays
     const double *p_lev, *p_lay;  // [L+1], [L]
     const double *lnp_lev;        // [L+1] ln p_lev

@@ -64,6 +64,7 @@ class Model:
     distance_cm: float = 0.0
     cloud_profile: int = QC_POWER_LAW
     cloud_feature: int = 0        # 1: the mid-infrared feature of the non-grey cloud
+    emission_quadrature: int = 0  # 0: Gauss-Legendre, 1: Gauss-Jacobi flux angles
 
     @property
     def n_species(self):

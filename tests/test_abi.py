@@ -8,6 +8,8 @@ import re
 import subprocess
 import tempfile
 
+import numpy as np
+
 import pytest
 
 import __graft_entry__ as entry
@@ -46,10 +48,11 @@ def test_struct_layout_matches_c_header():
 #include <stddef.h>
 #include "exoskry.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(es_model_desc), offsetof(es_model_desc, theta_fixed),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(es_model_desc), offsetof(es_model_desc, theta_fixed),
          offsetof(es_model_desc, free_idx), offsetof(es_model_desc, emission_flux),
          offsetof(es_model_desc, distance_cm), offsetof(es_model_desc, cloud_profile),
-         offsetof(es_model_desc, cloud_feature), sizeof(es_tables_desc), offsetof(es_tables_desc, cia_h2he),
+         offsetof(es_model_desc, cloud_feature), offsetof(es_model_desc, emission_quadrature),
+         sizeof(es_tables_desc), offsetof(es_tables_desc, cia_h2he),
          offsetof(es_tables_desc, storage));
   return 0;
 }
@@ -62,7 +65,8 @@ int main(void) {
         vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     M, T = binding.es_model_desc, binding.es_tables_desc
     assert vals == [ctypes.sizeof(M), M.theta_fixed.offset, M.free_idx.offset, M.emission_flux.offset,
-                    M.distance_cm.offset, M.cloud_profile.offset, M.cloud_feature.offset, ctypes.sizeof(T),
+                    M.distance_cm.offset, M.cloud_profile.offset, M.cloud_feature.offset,
+                    M.emission_quadrature.offset, ctypes.sizeof(T),
                     T.cia_h2he.offset, T.storage.offset]
 
 
@@ -81,7 +85,7 @@ def test_null_context_calls(lib):
                                          ("n_species", 17), ("p_top_bar", -1.0), ("tp_kind", 7),
                                          ("cloud_kind", 3), ("n_free", 0), ("r_star_cm", 0.0),
                                          ("emission_flux", 2), ("cloud_profile", 3), ("cloud_profile", -1),
-                                         ("cloud_feature", 2)])
+                                         ("cloud_feature", 2), ("emission_quadrature", 2)])
 def test_create_rejects_bad_descriptions_before_touching_cuda(lib, field, value):
     w = synth.workload("tiny", n_nu=64)
     d = binding.model_desc(w.model)
@@ -109,3 +113,39 @@ def test_binding_refuses_to_run_without_the_library(tmp_path):
             binding.load_library(str(tmp_path / "missing.so"))
         finally:
             binding._lib = None
+
+
+def test_host_flux_quadratures_match_the_oracle_rules():
+    """The library's host-side angle rules (csrc/quadrature.h: closed-form
+    Gauss-Legendre, Golub-Welsch Gauss-Jacobi of the weight mu) against the
+    oracle's (numpy leggauss, scipy roots_jacobi), for 4 and 8 points."""
+    from oracle import exoskry_oracle as O
+    src = r'''
+#include <cstdio>
+#include "quadrature.h"
+int main() {
+  double mu[8], w[8];
+  es::gauss_legendre4_01(mu, w);
+  for (int j = 0; j < 4; ++j) std::printf("%.17g %.17g\n", mu[j], w[j]);
+  for (int n = 4; n <= 8; n += 4) {
+    es::gauss_jacobi_mu_01(n, mu, w);
+    for (int j = 0; j < n; ++j) std::printf("%.17g %.17g\n", mu[j], w[j]);
+  }
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "quad.cpp")
+        exe = os.path.join(d, "quad")
+        open(c, "w").write(src)
+        subprocess.run(["g++", "-O2", "-I", os.path.join(ROOT, "paper_2602_19687_gb300", "csrc"), c, "-o", exe],
+                       check=True)
+        v = np.array([[float(x) for x in line.split()] for line in
+                      subprocess.run([exe], capture_output=True, text=True, check=True).stdout.splitlines()])
+    mu, w = O.gauss_legendre_01(4)
+    np.testing.assert_allclose(v[:4, 0], mu, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(v[:4, 1], w, rtol=0, atol=1e-15)
+    for n, rows in ((4, slice(4, 8)), (8, slice(8, 16))):
+        mu, w = O.gauss_jacobi_mu_01(n)
+        np.testing.assert_allclose(v[rows, 0], mu, rtol=0, atol=1e-14)
+        np.testing.assert_allclose(v[rows, 1], w, rtol=0, atol=1e-14)

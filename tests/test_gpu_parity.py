@@ -161,6 +161,20 @@ def test_brown_dwarf_milne_emission():
         check_sample(out, b, ref, 1, grad=(b < 2))
 
 
+def test_gauss_jacobi_flux_angles():
+    """The brown-dwarf setup with the Gauss-Jacobi flux angles of Sect. 5
+    (the 4-point rule of the weight mu): spectra, ln L and gradients."""
+    w = synth.workload("browndwarf", batch=3, n_nu=2000)
+    w.model = dataclasses.replace(w.model, emission_quadrature=1)
+    tabs = oracle_tables(w)
+    ctx = binding.context_for(w)
+    out = gpu_eval(ctx, w, w.theta, np.ones(3, np.int32))
+    for b in range(3):
+        ref = oracle_eval(w, tabs, w.theta[b], 1, grad=(b < 2))
+        assert ref["valid"]
+        check_sample(out, b, ref, 1, grad=(b < 2))
+
+
 def test_cloudy_transmission():
     """Non-grey cloud (Sect. 2.5, base + power-law q_c, KH18 Q_ext) and cloud
     fraction: transit depth element by element, binned model, ln L, and the

@@ -238,6 +238,23 @@ def test_cloud_feature_skew_normal_area_mean_window_and_cap():
     assert capped[1] == 2.0 and np.all(capped <= 2.0)
 
 
+def test_gauss_jacobi_flux_rule_exactness():
+    """Sect. 5's Gauss-Jacobi flux angles (reading: the 4-point Gaussian rule
+    of int_0^1 f(mu) mu dmu): exact for f = mu^k, k <= 7, against the closed
+    form int_0^1 mu^(k+1) dmu = 1/(k+2), and not for k = 8; nodes inside
+    (0, 1), weights positive summing to 1/2; an isothermal column emits pi B
+    under either rule."""
+    mu, w = O.gauss_jacobi_mu_01(4)
+    for k in range(8):
+        assert np.sum(w * mu ** k) == pytest.approx(1.0 / (k + 2), rel=1e-13)
+    assert abs(np.sum(w * mu ** 8) - 0.1) > 1e-6
+    assert np.all((mu > 0) & (mu < 1)) and np.all(w > 0) and np.sum(w) == pytest.approx(0.5, rel=1e-15)
+    b_lev = np.full((11, 3), 2.5)
+    dtau = np.full((10, 3), 0.3)
+    for quad in (O.QUAD_GAUSS_LEGENDRE, O.QUAD_GAUSS_JACOBI):
+        assert np.allclose(O.emergent_flux(b_lev, dtau, quadrature=quad), np.pi * 2.5, rtol=1e-14)
+
+
 @pytest.mark.parametrize("kind", [0, 1])
 def test_slab_profiles_against_power_law_and_clear(kind):
     """Sect. 2.5.1's three q_c profiles checked against each other: the
