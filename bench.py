@@ -146,6 +146,45 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def measure_nested(device, n_live=1000, batch=100, walk_steps=5, iterations=6, seed=3):
+    """The batched nested sampler as the likelihood's consumer: a short run
+    (fixed iteration count) on the batched transmission workload's model and
+    tables with uniform priors, every call one es_set_batch + es_loglike on
+    host vectors with the ln L read back. Parameter vectors per second over
+    the whole run (sampler host work included) and the likelihood calls'
+    share of it."""
+    from paper_2602_19687_gb300 import binding, nested, synth
+    w = synth.workload("batched_trans", batch=8)
+    m = w.model
+    ctx = binding.context_for(w, device=device)
+    like = binding.LogLikeBatch(ctx, kind=0)
+    ranges = synth.prior_ranges(m)
+    lo = np.array([ranges[k][0] for k in m.free_idx])
+    hi = np.array([ranges[k][1] for k in m.free_idx])
+    rng = np.random.default_rng(seed)
+    for b in (n_live, batch, batch, batch):   # warm-up: graph capture for both batch shapes
+        like(lo + (hi - lo) * rng.random((b, lo.size)))
+    spent = [0.0]
+
+    def timed(theta):
+        t = time.perf_counter()
+        out = like(theta)
+        spent[0] += time.perf_counter() - t
+        return out
+
+    t0 = time.perf_counter()
+    res = nested.run(timed, lambda u: lo + (hi - lo) * u, lo.size, n_live=n_live, batch=batch,
+                     walk_steps=walk_steps, max_iterations=iterations, seed=seed)
+    dt = time.perf_counter() - t0
+    ctx.es_destroy()
+    return {"workload": "batched nested sampling on the batched_trans model (%d live points, %d replaced "
+                        "per iteration, %d walk steps, %d iterations), ln L through host buffers"
+                        % (n_live, batch, walk_steps, res.iterations),
+            "value": res.evaluations / dt, "unit": "parameter vectors/s", "calls": res.calls,
+            "evaluations": res.evaluations, "ms_per_call": 1e3 * spent[0] / res.calls,
+            "likelihood_share": spent[0] / dt}
+
+
 def kernel_work(name, w, n_valid):
     """Algorithmic work of one launch of each kernel at this workload:
     (amount, unit, bound), counted per kernel below."""
@@ -412,6 +451,7 @@ def run_gpu(args):
     extra = None
     if rank == 0 and not args.no_extra:
         extra = [measure_workload(n, local) for n in ("batched_emis", "highres", "browndwarf", "cloudy_trans", "cloudy_emis")]
+        extra.append(measure_nested(local))
     cpu = cpu_baseline(args.workload) if (rank == 0 and not args.no_cpu) else None
     if rank == 0:
         line = {
