@@ -736,3 +736,24 @@ def test_complex_step_gradient_cloud(kind, profile, feature):
         fd = (O.loglike(m, w.tables, a, kind, mem, y_obs, sig)
               - O.loglike(m, w.tables, b, kind, mem, y_obs, sig)) / (2 * h)
         assert g[k] == pytest.approx(fd, rel=2e-5, abs=1e-6 * np.max(np.abs(g))), slot
+
+
+def test_bf16_row_dequantization_matches_library_rounding():
+    """The BF16 table storage the oracle reproduces for parity: residuals about
+    the FP32 row mean rounded to BF16 exactly as a library float32 -> bfloat16
+    conversion rounds them (round to nearest even), the row offset equal to
+    the row mean, and the error at most half a BF16 ulp of the residual."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(11)
+    tab = (-24.0 + 3.0 * rng.standard_normal((2, 3, 4, 257))).astype(np.float32)
+    deq = O.bf16_row_dequantized(tab)
+    off = np.mean(tab.astype(np.float64), axis=-1).astype(np.float32)
+    resid = (tab - off[..., None]).astype(np.float32)
+    lib = torch.from_numpy(resid.copy()).to(torch.bfloat16).to(torch.float32).numpy()
+    np.testing.assert_array_equal(deq, lib.astype(np.float64) + off[..., None].astype(np.float64))
+    ulp = 2.0 ** (np.floor(np.log2(np.abs(resid.astype(np.float64)) + 1e-300)) - 7)
+    assert np.all(np.abs(deq - tab.astype(np.float64)) <= 0.5 * ulp + 1e-12)
+    ties = np.array([1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -1.0 - 2.0 ** -8], np.float32)   # halfway cases
+    row = np.concatenate([ties, -ties])[None, :]          # row mean exactly 0
+    got = O.bf16_row_dequantized(row)[0, :3]
+    np.testing.assert_array_equal(got, [1.0, 1.0 + 2.0 ** -6, -1.0])
