@@ -149,3 +149,22 @@ int main() {
         mu, w = O.gauss_jacobi_mu_01(n)
         np.testing.assert_allclose(v[rows, 0], mu, rtol=0, atol=1e-14)
         np.testing.assert_allclose(v[rows, 1], w, rtol=0, atol=1e-14)
+
+
+def test_parameter_slots_agree_across_header_binding_synth_and_oracle():
+    """The canonical parameter slots (include/exoskry.h ES_P_*) in the same order
+    and number in the binding, the synthetic-input module and the oracle."""
+    from oracle import exoskry_oracle as O
+    src = open(os.path.join(ROOT, "include", "exoskry.h")).read()
+    m = re.search(r"enum \{\s*(ES_P_T_ISO = 0,.*?ES_P_N_EXTRA)\s*\};", src, re.S)
+    names = [x.strip().split("=")[0].strip()[len("ES_P_"):] for x in m.group(1).split(",")]
+    assert names[-1] == "N_EXTRA"
+    slots = names[:-1]
+    assert len(slots) == binding.ES_P_N_EXTRA == synth.N_EXTRA
+    # header name -> the Python modules' name where they differ
+    alias = {"LOG_KAPPA_IR": "LOG_KAPPA", "LOG_GAMMA_V": "LOG_GAMMA", "LOG_P_T": "LOG_PT",
+             "LOG_P_CLOUD": "LOG_PCLOUD"}
+    for k, name in enumerate(slots):
+        py = "P_" + alias.get(name, name)
+        assert getattr(synth, py) == k, name
+        assert getattr(O, py) == k, name

@@ -80,3 +80,32 @@ def test_invalid_models_never_enter_the_live_set():
     assert np.isfinite(res.log_z)
     with pytest.raises(ValueError):
         nested.run(loglike, lambda u: u, 2, n_live=10, batch=10)
+
+
+def test_loglike_batch_marshals_host_vectors():
+    """binding.LogLikeBatch: one es_set_batch with the host vectors and a kind
+    vector of the chosen kind, then one es_loglike into a host buffer, per call."""
+    from paper_2602_19687_gb300 import binding
+
+    class FakeContext:
+        def __init__(self):
+            self.log = []
+
+        def es_set_batch(self, theta, kind=None, stream=None):
+            assert isinstance(theta, np.ndarray) and theta.dtype == np.float64 and theta.flags["C_CONTIGUOUS"]
+            assert kind.dtype == np.int32 and kind.shape == (theta.shape[0],)
+            self.log.append(("set", theta.copy(), kind.copy()))
+            self.theta = theta.copy()
+
+        def es_loglike(self, lnl, stream=None):
+            assert isinstance(lnl, np.ndarray) and lnl.dtype == np.float64
+            lnl[:] = -np.sum(self.theta ** 2, axis=1)
+            self.log.append(("loglike",))
+
+    ctx = FakeContext()
+    like = binding.LogLikeBatch(ctx, kind=1)
+    theta = np.asfortranarray(np.arange(12.0).reshape(4, 3))
+    out = like(theta)
+    np.testing.assert_array_equal(out, -np.sum(theta ** 2, axis=1))
+    assert [e[0] for e in ctx.log] == ["set", "loglike"] and like.calls == 1
+    assert np.all(ctx.log[0][2] == 1)
