@@ -494,10 +494,11 @@ def run_reference(args):
         return
     per = []
     for _ in range(args.warmup + args.steps):
-        sec, done, full_n = None, 0, 0
         env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1")
         cmd = [sys.executable, os.path.abspath(__file__), "--cpu-child", "%s:%d:%d" % (args.workload, 600, 1)]
         r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=600)
+        if r.returncode != 0:
+            raise RuntimeError("oracle timing child failed: " + r.stderr[-500:])
         d = json.loads(r.stdout.strip().splitlines()[-1])
         per.append(d["sec_per_spectrum"])
     timed = per[args.warmup:]

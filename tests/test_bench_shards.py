@@ -48,3 +48,22 @@ def test_two_rank_shards_and_max_over_ranks():
 def test_single_rank_is_identity():
     assert bench.max_over_ranks(3.5, 1, "cpu") == 3.5
     assert bench.job_throughput(1024, 1, 80.0) == pytest.approx(12800.0)
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference times the FP64 oracle on the host and prints
+    one JSON line with the contract's keys (its own cpu_baseline and an e2e
+    object without host-device bytes)."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(os.path.dirname(bench.__file__), "bench.py"), "--impl",
+                        "reference", "--steps", "1", "--warmup", "0"], capture_output=True, text=True, timeout=600,
+                       check=True)
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == bench.UNIT
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
