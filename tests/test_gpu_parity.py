@@ -3,9 +3,10 @@ by element, on seeded synthetic workloads (several tiles and a ragged tail),
 at the full batched size on sampled outputs, and on the edge cases.
 
 Tolerances (FP32 path vs FP64): native transit depth 1e-5 relative; emergent
-Fp/F* 1e-4 relative; ln L 1e-5 relative; gradient 2e-3 relative per component
+Fp/F* 1e-4 relative; ln L 1e-5 relative; gradient 1e-3 relative per component
 with a floor of 1e-4 of the largest component (the adjoint sums FP32 products
-over ~1e4 wavenumbers). BF16-table workloads are compared with the oracle run
+over ~1e4 wavenumbers; measured: at most 2.2e-4 relative on the components
+above 1% of the largest). BF16-table workloads are compared with the oracle run
 on the same dequantized table values.
 """
 import copy
@@ -78,7 +79,7 @@ def assert_spec(got, ref, kind):
 
 
 def assert_grad(got, ref):
-    tol = 2e-3 * np.abs(ref) + 1e-4 * np.max(np.abs(ref))
+    tol = 1e-3 * np.abs(ref) + 1e-4 * np.max(np.abs(ref))
     bad = np.abs(got - ref) > tol
     assert not bad.any(), "gradient mismatch:\n gpu %s\n ref %s" % (got, ref)
 
