@@ -80,6 +80,54 @@ def test_guillot_deep_limit_and_hopf_limits():
     assert q[0] == pytest.approx(0.2, abs=1e-6) and q[1] == pytest.approx(2.0 / 3.0, abs=1e-12)
 
 
+def test_modified_guillot_q_irr_enters_the_irradiation_term_only():
+    """Sect. 2.4.4, 7-parameter modified Guillot through the full profile
+    (atmosphere()): with q_irr0 far from 2/3 and T_eq >> T_int, the levels far
+    above p_t (q_irr -> q_irr0) follow Guillot (2010) with its irradiation
+    bracket's 2/3 replaced by q_irr0 and the internal term's q_int = 2/3 kept;
+    the levels far below p_t (q_irr -> 2/3) are Guillot (2010) itself; and at
+    p = p_t, q_irr = 2/3 + (q_irr0 - 2/3)/e. Written in Guillot's own variables
+    (T_irr^4 mu_* = 4 f_hem T_eq^4, mu_* = 1/sqrt 3), so q_irr placed in the
+    internal term, or the Hopf function taken in tau instead of p, fails."""
+    m = _model(L=30, tp=O.TP_GUILLOT_MOD)
+    s = m.n_species
+    th = m.theta_fixed.copy()
+    t_int, t_eq, kappa, gamma, q0, beta = 180.0, 1700.0, 10 ** -1.3, 10 ** -0.4, 0.12, 6.0
+    p_lev, _ = O.pressure_grid(m.n_layers, m.p_top_bar, m.p_bot_bar)
+    k_t = 14
+    p_t_bar = p_lev[k_t] / O.BAR                      # p_t on a level: that level sees q(p_t)
+    th[0] = -4.0
+    th[s + O.P_T_INT], th[s + O.P_T_EQ] = t_int, t_eq
+    th[s + O.P_LOG_KAPPA], th[s + O.P_LOG_GAMMA] = np.log10(kappa), np.log10(gamma)
+    th[s + O.P_Q_IRR0], th[s + O.P_LOG_PT], th[s + O.P_BETA] = q0, np.log10(p_t_bar), beta
+    g = 10 ** th[s + O.P_LOG_G]
+    atm = O.atmosphere(m, th)
+    mu_s = 1.0 / np.sqrt(3.0)
+    t_irr4_mu = 4.0 * 0.25 * t_eq ** 4
+
+    def guillot(p, q_irr):
+        tau = kappa * p / g
+        return (0.75 * t_int ** 4 * (2.0 / 3.0 + tau) + 0.75 * t_irr4_mu * (
+            q_irr + mu_s / gamma + (gamma / (3.0 * mu_s) - mu_s / gamma) * np.exp(-gamma * tau / mu_s))) ** 0.25
+
+    top = p_lev < 1e-2 * p_t_bar * O.BAR              # (p/p_t)^6 < 1e-12: q_irr = q_irr0
+    deep = p_lev > 1e2 * p_t_bar * O.BAR              # (p/p_t)^6 > 1e12: q_irr = 2/3
+    assert top.sum() >= 5 and deep.sum() >= 3
+    assert np.allclose(atm["t_lev"][top], guillot(p_lev[top], q0), rtol=1e-9)
+    assert np.allclose(atm["t_lev"][deep], guillot(p_lev[deep], 2.0 / 3.0), rtol=1e-13)
+    q_t = 2.0 / 3.0 + (q0 - 2.0 / 3.0) / np.e
+    assert atm["t_lev"][k_t] == pytest.approx(guillot(p_lev[k_t], q_t), rel=1e-13)
+    # the slip: q_irr in the internal term instead is far off at the top
+    tau = kappa * p_lev[top] / g
+    slip = (0.75 * t_int ** 4 * (q0 + tau) + 0.75 * t_irr4_mu * (
+        2.0 / 3.0 + mu_s / gamma + (gamma / (3.0 * mu_s) - mu_s / gamma) * np.exp(-gamma * tau / mu_s))) ** 0.25
+    assert np.min(np.abs(atm["t_lev"][top] / slip - 1.0)) > 1e-2
+    # layers use the same profile at their geometric-mean pressures
+    _, p_lay = O.pressure_grid(m.n_layers, m.p_top_bar, m.p_bot_bar)
+    top_l = p_lay < 1e-2 * p_t_bar * O.BAR
+    assert np.allclose(atm["t_lay"][top_l], guillot(p_lay[top_l], q0), rtol=1e-9)
+
+
 def test_milne_skin_eddington_deep_and_transition():
     """Modified Milne (Sect. 2.4.3): T -> T_ratio T_int at the top (q -> q0 =
     4/3 T_ratio^4, tau -> 0); with q0 = q_inf it is the Eddington-like Milne
@@ -422,6 +470,45 @@ def test_deck_depth_continuous_in_pressure():
     assert vals[0] == pytest.approx(vals[1], rel=1e-9)
 
 
+def test_deck_radius_is_ln_p_interpolation_of_the_levels():
+    """Grey deck reading: r_c = r(p_c) by ln p interpolation between the
+    bounding levels. For an isothermal atmosphere 1/r is exactly linear in
+    ln p (closed form), so ln-p interpolation of r matches the closed-form
+    r(p_c) to its second-order error, at most dr^2 / (4 r) within a layer
+    (r = 1/(a + b x) has r'' = 2 b^2 r^3); interpolation linear in p misses by
+    a fixed fraction of dr. With zero opacity the transit depth is r_c^2 / R_*^2,
+    so the deck's radius is also pinned through the forward model."""
+    L = 12
+    p_frac = (0.17, 0.5, 0.83)
+    checked = 0
+    for lp_layer in (4, 9):
+        for f in p_frac:
+            m, tabs, th, mem = _trans_setup(L, -99.0, deck=0.0)
+            m.ray_h2_cm2 = m.ray_he_cm2 = 0.0
+            p_lev, _ = O.pressure_grid(L, m.p_top_bar, m.p_bot_bar)
+            lpc = (1 - f) * np.log10(p_lev[lp_layer] / O.BAR) + f * np.log10(p_lev[lp_layer + 1] / O.BAR)
+            th[m.n_species + O.P_LOG_PCLOUD] = lpc
+            atm = O.atmosphere(m, th)
+            s = m.n_species
+            t, g, R = th[s + O.P_T_ISO], atm["g"], atm["r_ref"]
+            pc = 10.0 ** lpc * O.BAR
+            r_exact = 1.0 / (1.0 / R + O.K_B * t * np.log(pc / (m.p_ref_bar * O.BAR)) / (atm["mu"] * O.AMU * g * R ** 2))
+            r_lev = atm["r_lev"]
+            dr = r_lev[lp_layer] - r_lev[lp_layer + 1]
+            bound = dr * dr / (4.0 * r_lev[lp_layer + 1])
+            r_c = O.deck_radius(r_lev, p_lev, pc)
+            assert abs(r_c - r_exact) <= 1.01 * bound
+            # linear in p misses by far more than the bound
+            w_p = (pc - p_lev[lp_layer]) / (p_lev[lp_layer + 1] - p_lev[lp_layer])
+            r_lin_p = r_lev[lp_layer] + w_p * (r_lev[lp_layer + 1] - r_lev[lp_layer])
+            assert abs(r_lin_p - r_exact) > 20.0 * bound
+            spec, _ = O.forward(m, tabs, th, 0, mem)
+            assert np.allclose(spec, r_c ** 2 / m.r_star_cm ** 2, rtol=1e-13)
+            assert np.allclose(spec, r_exact ** 2 / m.r_star_cm ** 2, rtol=2.2 * bound / r_exact)
+            checked += 1
+    assert checked == 6
+
+
 def test_beer_lambert_single_layer():
     """One layer: the chord at the layer midpoint crosses it over
     s = 2 sqrt(r_up^2 - b^2) and transmits exp(-alpha s)."""
@@ -523,6 +610,44 @@ def test_interpolation_nodes_linear_and_clamp():
     v_lo = O.log10_sigma_bilinear(tab, t_grid, p_grid, 10.0, 1e-12 * O.BAR)
     v_hi = O.log10_sigma_bilinear(tab, t_grid, p_grid, 9000.0, 1e4 * O.BAR)
     assert np.allclose(v_lo, tab[0, 0]) and np.allclose(v_hi, tab[-1, -1])
+
+
+def test_cia_linear_in_temperature_between_nodes():
+    """CIA reading: log10 k linear in T (not in log T) between the two
+    bracketing nodes, clamped at both ends of the grid. A table linear in T is
+    reproduced exactly at off-node temperatures; a hand-computed case
+    (nodes 1000 K and 2000 K at -45 and -44, T = 1250 K: weight 1/4, -44.75)
+    rules out a log-T weight (-44.678) and a swapped weight (-44.25)."""
+    t_grid = np.array([400.0, 900.0, 1600.0, 3000.0])
+    a, b = -46.0, 1.0e-3
+    tab = a + b * t_grid[:, None] + np.array([0.0, 0.3, -0.2])[None, :]
+    for t in (400.0, 777.0, 1234.5, 2222.2, 3000.0):
+        v = O.log10_cia_linear(tab, t_grid, t)
+        assert np.allclose(v, a + b * t + np.array([0.0, 0.3, -0.2]), atol=1e-13)
+    assert np.array_equal(O.log10_cia_linear(tab, t_grid, 150.0), tab[0])
+    assert np.array_equal(O.log10_cia_linear(tab, t_grid, 9000.0), tab[-1])
+    two = np.array([[-45.0], [-44.0]])
+    assert O.log10_cia_linear(two, np.array([1000.0, 2000.0]), 1250.0)[0] == pytest.approx(-44.75, abs=1e-14)
+    # a table linear in log T is not reproduced between nodes (log-T interpolation would be)
+    tab_log = -46.0 + 1.7 * np.log10(t_grid)[:, None]
+    assert abs(O.log10_cia_linear(tab_log, t_grid, 1234.5)[0] - (-46.0 + 1.7 * np.log10(1234.5))) > 1e-3
+    # through the extinction: n^2 X_H2 (X_H2 k_H2H2 + X_He k_H2He) with two
+    # different tables (pins which table pairs with which background gas)
+    m = _model(L=4)
+    m.ray_h2_cm2 = m.ray_he_cm2 = 0.0
+    nu = np.array([1.0e4, 2.0e4])
+    tabs = _flat_tables(nu, -99.0)
+    tabs.cia_t_grid = np.array([1000.0, 2000.0])
+    tabs.cia_h2h2 = np.array([[-45.0, -44.0], [-44.0, -46.0]])
+    tabs.cia_h2he = np.array([[-46.0, -45.5], [-45.0, -45.5]])
+    x = np.array([1e-30])
+    x_h2, x_he = O.background_fill(x)
+    p = 3.0e5
+    alpha = O.extinction(tabs, m, x, x_h2, x_he, np.array([1250.0]), np.array([p]))
+    n = p / (O.K_B * 1250.0)
+    k11 = 10.0 ** np.array([-44.75, -44.5])
+    k12 = 10.0 ** np.array([-45.75, -45.5])
+    assert np.allclose(alpha[0], n * n * x_h2 * (x_h2 * k11 + x_he * k12), rtol=1e-12)
 
 
 def test_cia_and_rayleigh_scalings():
