@@ -66,7 +66,11 @@ enum { ES_QUAD_GAUSS_LEGENDRE = 0, ES_QUAD_GAUSS_JACOBI = 1 };
 enum { ES_KIND_TRANSMISSION = 0, ES_KIND_EMISSION = 1 };
 enum { ES_TABLE_F32 = 0, ES_TABLE_BF16 = 1 };
 enum { ES_MEM_HOST = 0, ES_MEM_DEVICE = 1 };
-enum { ES_FLAG_INVALID = 1 };
+/* Per-sample flags (es_get_flags): ES_FLAG_INVALID the sample's ln L is
+ * -1e300 (invalid forward-model output, Sect. 2.3); ES_FLAG_TIMEOUT a kernel
+ * of the call gave up on a bounded device-side wait, so every sample of that
+ * call is invalid (set together with ES_FLAG_INVALID). */
+enum { ES_FLAG_INVALID = 1, ES_FLAG_TIMEOUT = 2 };
 
 /*
  * Canonical parameter vector. Slots 0..S-1 hold log10 of the S absorber
@@ -182,7 +186,11 @@ typedef struct {
     int storage;                              /* ES_TABLE_F32 | ES_TABLE_BF16 */
 } es_tables_desc;
 
-/* Create a context on CUDA device `device` for the model `desc`.
+/* Create a context on CUDA device `device` for the model `desc`: the
+ * pressure grid (Sect. 6.3: L layers evenly spaced in log p), the T-p profile
+ * kind (Sect. 2.4), the absorbers (Sect. 3.1), the cloud scheme (Sect. 2.5),
+ * the emission output and flux angles (Sect. 5). The context itself (a device
+ * binding plus host state) has no counterpart in the paper.
  * Errors: ES_EINVAL (bad description), ES_ECUDA, ES_ENOMEM. */
 es_status es_create(es_ctx **out, int device, const es_model_desc *desc);
 
@@ -193,6 +201,9 @@ es_status es_load_tables(es_ctx *ctx, const es_tables_desc *tables);
 
 /* Instrument bins [lo, hi) in micron. The model of bin k is the equal-
  * weight mean of the native points with lambda = 1e4/nu in [lo_k, hi_k).
+ * The paper compares binned data with the native-resolution model (Sect. 6-7)
+ * but does not define the binning operator; this equal-weight mean is the
+ * library's reading, not a passage of the paper.
  * Bins must not share native points; a bin with no points is ES_EINVAL.
  * Requires tables (ES_ESTATE). */
 es_status es_set_grid(es_ctx *ctx, const double *bin_lo_um, const double *bin_hi_um, int n_bins);
@@ -217,7 +228,14 @@ es_status es_set_batch(es_ctx *ctx, const double *theta, const int32_t *kind, in
 es_status es_forward(es_ctx *ctx, float *spectrum, double *binned, double *lnL,
                      int mem, es_stream_t stream);
 
-/* ln L only (the sampler's call). Same requirements as es_forward. */
+/* ln L only (the sampler's call). Same requirements as es_forward.
+ *
+ * Bounded waits (es_forward, es_loglike, es_forward_backward): the
+ * tensor-core kernels wait on mbarriers with an iteration limit. If one gives
+ * up, every sample of the call gets ln L = -1e300, a zero gradient and the
+ * flags ES_FLAG_INVALID | ES_FLAG_TIMEOUT; with host buffers (ES_MEM_HOST) the
+ * call also returns ES_ETIMEOUT. The status is cleared at the start of every
+ * call, so a later call that completes returns ES_OK. */
 es_status es_loglike(es_ctx *ctx, double *lnL, int mem, es_stream_t stream);
 
 /* ln L and its gradient with respect to the free parameters,
@@ -256,13 +274,17 @@ es_status es_set_graphs(es_ctx *ctx, int on);
  * one fixed array of 32 MiB built into the library (present on every GPU
  * that loads the library, until the process exits). The paper has no
  * counterpart; this is a library convenience for callers that must not call
- * cudaMalloc on their hot path (code running during CUDA-graph stream
- * capture, frameworks that own all device memory through their own pool,
- * or long runs that must not risk an out-of-memory error mid-way).
+ * cudaMalloc on their hot path (frameworks that own all device memory
+ * through their own pool and forbid other allocations, or long runs that
+ * must not risk an out-of-memory error mid-way).
  *   theta [batch][n_free] device, kind [batch] device or NULL (all
  *   transmission), lnL [batch] device; asynchronous on `stream`.
  * Needs tables, grid and transmission data (and emission data when kind is
- * given). A batch whose workspace exceeds 32 MiB is rejected with ES_EINVAL
+ * given). kind values are not checked on the host (the call does not read
+ * device memory back): a value other than ES_KIND_TRANSMISSION or
+ * ES_KIND_EMISSION makes that sample invalid (ln L = -1e300). A kernel that
+ * gives up on a bounded wait makes every ln L of the call -1e300.
+ * A batch whose workspace exceeds 32 MiB is rejected with ES_EINVAL
  * (the message gives the bytes needed). The first call on a device looks up
  * the array's device address; make that first call before any stream
  * capture. All calls on a device share the array and leave their contents in
@@ -270,15 +292,32 @@ es_status es_set_graphs(es_ctx *ctx, int on);
 es_status es_loglike_noalloc(es_ctx *ctx, const double *theta, const int32_t *kind, int batch, double *lnL,
                              es_stream_t stream);
 
-/* Per-sample flags (ES_FLAG_INVALID) of the last forward, int32 [batch]. */
+/* Device memory limit of the context: `bytes` (0 = no limit, the default)
+ * caps the device memory the context holds at any time (tables, grid, data,
+ * workspace; es_query key 6). An allocation that would pass the limit fails
+ * with ES_ENOMEM before anything is allocated, and the context keeps what it
+ * held. No counterpart in the paper: sharing one GPU between contexts. */
+es_status es_set_memory_limit(es_ctx *ctx, uint64_t bytes);
+
+/* Test hooks, off (0) by default; no counterpart in the paper.
+ * ES_TEST_WAIT_TIMEOUT: the tensor-core kernels issue no product and their
+ * bounded waits give up after a few thousand polls (milliseconds), so the
+ * next call takes its timeout path (ES_ETIMEOUT, ES_FLAG_TIMEOUT) with no
+ * tensor-core operation in flight. Clearing it (hooks = 0) restores normal
+ * calls on the same context. */
+enum { ES_TEST_WAIT_TIMEOUT = 1 };
+es_status es_set_test_hooks(es_ctx *ctx, int hooks);
+
+/* Per-sample flags (ES_FLAG_*) of the last forward, int32 [batch]. */
 es_status es_get_flags(es_ctx *ctx, int32_t *flags, int mem, es_stream_t stream);
 
 /* Sizes: 0 n_nu, 1 n_bins, 2 n_free, 3 batch, 4 n_layers, 5 n_species,
- * 6 device workspace bytes, 7 kernel launches issued by the last call (a
+ * 6 device bytes the context holds, 7 kernel launches issued by the last call (a
  * replayed graph counts the launches it holds), 8 / 9 work-item size of the
  * fused transmission forward / adjoint kernel (0: built-in heuristic),
- * 10 graph replay enabled (1) or not (0), 11 device status word (0; nonzero
- * once a tensor-core kernel gave up on a bounded wait; synchronises).
+ * 10 graph replay enabled (1) or not (0), 11 device status word of the last
+ * call (0; nonzero when a tensor-core kernel gave up on a bounded wait;
+ * synchronises).
  * Returns -1 for an unknown key or a NULL context. */
 int64_t es_query(const es_ctx *ctx, int key);
 
@@ -302,10 +341,12 @@ es_status es_get_profile(es_ctx *ctx, int index, char *name, int name_len, doubl
  * and frees 1 KB. ES_EINVAL for NULL outputs, ES_ECUDA for a bad device. */
 es_status es_probe_rates(int device, double *ex2_per_s, double *ffma2_per_s);
 
-/* Message for the last error on this context (never NULL). */
+/* Message for the last error on this context (never NULL). Library
+ * plumbing with no counterpart in the paper. */
 const char *es_last_error(const es_ctx *ctx);
 
-/* Free every device and host resource of the context. NULL is a no-op. */
+/* Free every device and host resource of the context. NULL is a no-op.
+ * Library plumbing with no counterpart in the paper. */
 void es_destroy(es_ctx *ctx);
 
 #ifdef __cplusplus

@@ -18,6 +18,8 @@ LIB_PATH = os.path.join(HERE, "libexoskry.so")
 ES_OK, ES_EINVAL, ES_ENOMEM, ES_ECUDA, ES_ESTATE, ES_ETIMEOUT = range(6)
 ES_MEM_HOST, ES_MEM_DEVICE = 0, 1
 ES_TABLE_F32, ES_TABLE_BF16 = 0, 1
+ES_FLAG_INVALID, ES_FLAG_TIMEOUT = 1, 2
+ES_TEST_WAIT_TIMEOUT = 1
 ES_MAX_SPECIES = 16
 ES_P_N_EXTRA = 28
 ES_MAX_PARAMS = ES_MAX_SPECIES + ES_P_N_EXTRA
@@ -27,6 +29,7 @@ STATUS_NAMES = {0: "ES_OK", 1: "ES_EINVAL", 2: "ES_ENOMEM", 3: "ES_ECUDA", 4: "E
 EXPORTS = ["es_create", "es_load_tables", "es_set_grid", "es_set_data", "es_set_batch", "es_forward",
            "es_loglike", "es_forward_backward", "es_loglike_noalloc", "es_autotune", "es_set_graphs",
            "es_get_flags", "es_query", "es_set_profiling", "es_probe_rates",
+           "es_set_memory_limit", "es_set_test_hooks",
            "es_get_profile", "es_last_error", "es_destroy"]
 
 
@@ -80,6 +83,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.es_autotune.argtypes = [vp, vp]
     lib.es_probe_rates.argtypes = [ip, ctypes.POINTER(dp), ctypes.POINTER(dp)]
     lib.es_set_graphs.argtypes = [vp, ip]
+    lib.es_set_memory_limit.argtypes = [vp, ctypes.c_uint64]
+    lib.es_set_test_hooks.argtypes = [vp, ip]
     lib.es_query.argtypes = [vp, ip]
     lib.es_query.restype = ctypes.c_int64
     lib.es_set_profiling.argtypes = [vp, ip]
@@ -231,6 +236,12 @@ class Context:
 
     def es_set_graphs(self, on):
         self._check(self.lib.es_set_graphs(self.handle, 1 if on else 0), "es_set_graphs")
+
+    def es_set_memory_limit(self, nbytes):
+        self._check(self.lib.es_set_memory_limit(self.handle, int(nbytes)), "es_set_memory_limit")
+
+    def es_set_test_hooks(self, hooks):
+        self._check(self.lib.es_set_test_hooks(self.handle, int(hooks)), "es_set_test_hooks")
 
     def es_get_flags(self, flags, stream=None):
         self._check(self.lib.es_get_flags(self.handle, _ptr(flags), _mem(flags), _stream(stream)),

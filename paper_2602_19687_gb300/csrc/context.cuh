@@ -2,6 +2,7 @@
 #pragma once
 
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "internal.cuh"
@@ -20,7 +21,11 @@ struct es_ctx {
     std::vector<void *> bwd_bufs;     // adjoint workspace
     bool have_tables = false, have_grid = false, have_data[2] = {false, false};
     int cap_b = 0, cap_b_bwd = 0, batch = 0, n_kind[2] = {0, 0};
-    size_t ws_bytes = 0;
+    // device bytes held by the context (every allocation: tables, grids, data,
+    // workspace), the size of each allocation, and the limit (0: none)
+    size_t dev_bytes = 0, mem_limit = 0;
+    std::unordered_map<void *, size_t> dev_sizes;
+    int *h_err = nullptr;             // pinned copy of the device status word, written at the end of every call
     int64_t last_launches = 0;
     std::vector<double> y_host[2], s_host[2];
     std::vector<double> nu_host;      // FP64 wavenumber grid (bin membership)

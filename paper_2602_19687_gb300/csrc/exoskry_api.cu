@@ -14,6 +14,10 @@ using namespace es;
 
 namespace {
 
+// polls of a bounded mbarrier wait before a kernel gives up (seconds), and the
+// short limit of the wait-timeout test hook (milliseconds)
+constexpr unsigned WAIT_POLLS = 1u << 24, WAIT_POLLS_TEST = 1u << 12;
+
 es_status fail(es_ctx *c, es_status s, const std::string &msg) {
     if (c) c->err = msg;
     return s;
@@ -23,18 +27,45 @@ es_status cuda_fail(es_ctx *c, cudaError_t e, const char *where) {
     return fail(c, ES_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// Every device allocation of a context goes through dev_alloc / dev_free,
+// which keep the context's live byte count and enforce its limit
+// (es_set_memory_limit): a request past the limit fails with ES_ENOMEM
+// before cudaMalloc is called.
+es_status dev_alloc(es_ctx *c, void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 1;
+    if (c->mem_limit && c->dev_bytes + bytes > c->mem_limit)
+        return fail(c, ES_ENOMEM, "device memory limit of " + std::to_string(c->mem_limit) + " bytes: " +
+                                      std::to_string(c->dev_bytes) + " held, " + std::to_string(bytes) +
+                                      " more requested");
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(c, ES_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    c->dev_sizes[*p] = bytes;
+    c->dev_bytes += bytes;
+    return ES_OK;
+}
+
+void dev_free(es_ctx *c, void *p) {
+    if (!p) return;
+    auto it = c->dev_sizes.find(p);
+    if (it != c->dev_sizes.end()) {
+        c->dev_bytes -= it->second;
+        c->dev_sizes.erase(it);
+    }
+    cudaFree(p);
+}
+
 template <class T>
 es_status dalloc(es_ctx *c, std::vector<void *> &owner, T **p, size_t count) {
     *p = nullptr;
-    if (count == 0) count = 1;
     void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(c, ES_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
-    }
+    es_status s = dev_alloc(c, &q, (count ? count : 1) * sizeof(T));
+    if (s != ES_OK) return s;
     owner.push_back(q);
-    c->ws_bytes += count * sizeof(T);
     *p = static_cast<T *>(q);
     return ES_OK;
 }
@@ -47,8 +78,8 @@ es_status upload(es_ctx *c, std::vector<void *> &owner, T **p, const T *src, siz
     return e == cudaSuccess ? ES_OK : cuda_fail(c, e, "cudaMemcpy");
 }
 
-void free_all(std::vector<void *> &v) {
-    for (void *p : v) cudaFree(p);
+void free_all(es_ctx *c, std::vector<void *> &v) {
+    for (void *p : v) dev_free(c, p);
     v.clear();
 }
 
@@ -188,10 +219,13 @@ es_status launch_or_replay(es_ctx *c, es_ctx::GraphSlot &g, cudaStream_t st, F &
 es_status alloc_forward(es_ctx *c, int B) {
     if (B <= c->cap_b) return ES_OK;
     ++c->graph_epoch;
-    free_all(c->work_bufs);
-    free_all(c->bwd_bufs);
-    c->cap_b_bwd = 0;
-    c->ws_bytes = 0;
+    free_all(c, c->work_bufs);
+    free_all(c, c->bwd_bufs);
+    // until the new buffers are all in place the context holds no batch (a
+    // failed allocation leaves it in the "no batch set" state)
+    c->cap_b = c->cap_b_bwd = 0;
+    c->batch = 0;
+    c->n_kind[0] = c->n_kind[1] = 0;
     const Model &m = c->m;
     const size_t L = m.L, S = m.S, N = m.N;
     Work &w = c->w;
@@ -240,7 +274,8 @@ es_status alloc_backward(es_ctx *c) {
     const int B = c->cap_b;
     if (B <= c->cap_b_bwd) return ES_OK;
     ++c->graph_epoch;
-    free_all(c->bwd_bufs);
+    free_all(c, c->bwd_bufs);
+    c->cap_b_bwd = 0;
     const Model &m = c->m;
     const size_t L = m.L, S = m.S, N = m.N;
     Work &w = c->w;
@@ -268,14 +303,12 @@ es_status alloc_backward(es_ctx *c) {
 es_status ensure_big(es_ctx *c, float **p, size_t &cap, size_t count) {
     if (count <= cap && *p) return ES_OK;
     ++c->graph_epoch;
-    if (*p) cudaFree(*p);
+    dev_free(c, *p);
     *p = nullptr;
     cap = 0;
     void *q = nullptr;
-    if (cudaMalloc(&q, count * sizeof(float)) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(c, ES_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(float)) + " bytes failed");
-    }
+    es_status s = dev_alloc(c, &q, count * sizeof(float));
+    if (s != ES_OK) return s;
     *p = static_cast<float *>(q);
     cap = count;
     return ES_OK;
@@ -295,14 +328,12 @@ es_status ensure_ymod(es_ctx *c) {
     size_t need = (size_t)c->cap_b * c->m.nbins;
     if (need <= c->ymod_cap) return ES_OK;
     ++c->graph_epoch;
-    if (c->w.ymod) cudaFree(c->w.ymod);
+    dev_free(c, c->w.ymod);
     c->w.ymod = nullptr;
     c->ymod_cap = 0;
     void *q = nullptr;
-    if (cudaMalloc(&q, need * sizeof(double)) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(c, ES_ENOMEM, "cudaMalloc of the binned-model buffer failed");
-    }
+    es_status s = dev_alloc(c, &q, need * sizeof(double));
+    if (s != ES_OK) return s;
     c->w.ymod = static_cast<double *>(q);
     c->ymod_cap = need;
     return ES_OK;
@@ -328,12 +359,21 @@ es_status prepare(es_ctx *c, bool adjoint) {
     return ES_OK;
 }
 
+// The status word of the fused kernels' bounded waits: cleared at the start
+// of every call, copied to the context's pinned host word at its end (both
+// steps inside a captured graph too), read by finish() for host-buffer calls.
+void clear_status(es_ctx *c, cudaStream_t st) { cudaMemsetAsync(c->w.err, 0, sizeof(int), st); }
+void post_status(es_ctx *c, cudaStream_t st) {
+    cudaMemcpyAsync(c->h_err, c->w.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+}
+
 es_status run_forward(es_ctx *c, bool adjoint, float *spec_out, double *binned_out, double *lnl_out,
-                      cudaStream_t st) {
+                      cudaStream_t st, bool post = true) {
     Work w = c->w;
     w.B = c->batch;
     int launches = 0;
     const Hook &h = c->hook;
+    clear_status(c, st);
     launches += launch_setup(c->m, w, st, h);
     if (c->n_kind[0]) launches += launch_trans_fused_forward(c->m, w, adjoint, c->fwd_chunk, st, h);
     if (c->n_kind[1]) {
@@ -343,6 +383,7 @@ es_status run_forward(es_ctx *c, bool adjoint, float *spec_out, double *binned_o
         cudaMemsetAsync(w.dbar, 0, sizeof(float) * (size_t)w.B * c->m.Np, st);
     }
     launches += launch_bins(c->m, w, adjoint, spec_out, binned_out, lnl_out, st, h);
+    if (post) post_status(c, st);
     c->last_launches = launches;
     return check_launch(c, "forward launch");
 }
@@ -394,6 +435,8 @@ es_status es_create(es_ctx **out, int device, const es_model_desc *d) {
     m.distance = d->distance_cm;
     m.cloud_profile = d->cloud_profile;
     m.cloud_feature = d->cloud_feature;
+    m.wait_polls = WAIT_POLLS;
+    m.wait_test = 0;
     m.p_ref = d->p_ref_bar * BAR;
     m.r_star = d->r_star_cm;
     m.t_star = d->t_star_k;
@@ -428,7 +471,13 @@ es_status es_create(es_ctx **out, int device, const es_model_desc *d) {
     if ((s = upload(c, c->model_bufs, &dp, lnp.data(), lnp.size())) != ES_OK) { es_destroy(c); return s; }
     m.lnp_lev = dp;
     m.ln_p_ref = std::log(m.p_ref);
-    c->ws_bytes = 0;
+    if (cudaHostAlloc(reinterpret_cast<void **>(&c->h_err), sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        c->h_err = nullptr;
+        es_destroy(c);
+        return ES_ENOMEM;
+    }
+    *c->h_err = 0;
     *out = c;
     return ES_OK;
 }
@@ -445,14 +494,34 @@ es_status es_load_tables(es_ctx *c, const es_tables_desc *t) {
         !(t->nu[0] > 0))
         return fail(c, ES_EINVAL, "grids must be positive and strictly ascending");
     if (t->storage != ES_TABLE_F32 && t->storage != ES_TABLE_BF16) return fail(c, ES_EINVAL, "bad storage");
+    {
+        // every table value finite (a NaN or Inf would reach every spectrum silently)
+        const size_t per_row = (size_t)t->n_nu, rows = (size_t)c->m.S * t->n_t * t->n_p;
+        for (size_t r = 0; r < rows; ++r)
+            for (size_t n = 0; n < per_row; ++n)
+                if (!std::isfinite(t->log10_sigma[r * per_row + n])) {
+                    const size_t ip = r % t->n_p, it = (r / t->n_p) % t->n_t, sp = r / ((size_t)t->n_p * t->n_t);
+                    return fail(c, ES_EINVAL, "log10_sigma[" + std::to_string(sp) + "][" + std::to_string(it) + "][" +
+                                                  std::to_string(ip) + "][" + std::to_string(n) + "] is not finite");
+                }
+        for (int pair = 0; pair < 2; ++pair) {
+            const float *src = pair ? t->cia_h2he : t->cia_h2h2;
+            for (size_t k = 0; k < (size_t)t->n_t_cia * per_row; ++k)
+                if (!std::isfinite(src[k]))
+                    return fail(c, ES_EINVAL, std::string(pair ? "cia_h2he" : "cia_h2h2") + " value " +
+                                                  std::to_string(k) + " is not finite");
+        }
+    }
     cudaSetDevice(c->device);
-    free_all(c->table_bufs);
-    free_all(c->grid_bufs);
+    free_all(c, c->table_bufs);
+    free_all(c, c->grid_bufs);
     c->have_tables = c->have_grid = false;
     c->have_data[0] = c->have_data[1] = false;
     c->cap_b = c->cap_b_bwd = 0;
-    free_all(c->work_bufs);
-    free_all(c->bwd_bufs);
+    c->batch = 0;   // the workspace is gone: the batch must be set again
+    c->n_kind[0] = c->n_kind[1] = 0;
+    free_all(c, c->work_bufs);
+    free_all(c, c->bwd_bufs);
     Model &m = c->m;
     m.N = t->n_nu;
     m.NT = t->n_t;
@@ -609,8 +678,8 @@ es_status es_set_grid(es_ctx *c, const double *lo, const double *hi, int nbins) 
         blo[k] = first;
         bhi[k] = end;
     }
-    free_all(c->grid_bufs);
-    free_all(c->data_bufs);
+    free_all(c, c->grid_bufs);
+    free_all(c, c->data_bufs);
     c->have_grid = false;
     c->have_data[0] = c->have_data[1] = false;
     es_status s;
@@ -704,10 +773,17 @@ es_status copy_out(es_ctx *c, void *dst, const void *src, size_t bytes, cudaStre
     return e == cudaSuccess ? ES_OK : cuda_fail(c, e, "result copy");
 }
 
+// Host-buffer calls synchronise here and report a kernel that gave up on a
+// bounded wait as ES_ETIMEOUT; device-buffer calls return at once (their
+// samples carry ES_FLAG_TIMEOUT and ln L = -1e300 instead).
 es_status finish(es_ctx *c, int mem, cudaStream_t st) {
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && mem == ES_MEM_HOST) e = cudaStreamSynchronize(st);
-    return e == cudaSuccess ? ES_OK : cuda_fail(c, e, "kernel execution");
+    if (e != cudaSuccess) return cuda_fail(c, e, "kernel execution");
+    if (mem == ES_MEM_HOST && *c->h_err)
+        return fail(c, ES_ETIMEOUT, "a tensor-core kernel gave up on a bounded wait; every sample of the call "
+                                    "is flagged invalid (ES_FLAG_TIMEOUT)");
+    return ES_OK;
 }
 
 }  // namespace
@@ -727,7 +803,7 @@ es_status es_forward(es_ctx *c, float *spectrum, double *binned, double *lnl, in
     if (mem == ES_MEM_HOST) {
         d_lnl = lnl ? c->d_lnl : nullptr;
         if (spectrum && (s = dalloc(c, tmp, &d_spec, (size_t)B * c->m.N)) != ES_OK) return s;
-        if (binned && (s = dalloc(c, tmp, &d_bin, (size_t)B * c->m.nbins)) != ES_OK) { free_all(tmp); return s; }
+        if (binned && (s = dalloc(c, tmp, &d_bin, (size_t)B * c->m.nbins)) != ES_OK) { free_all(c, tmp); return s; }
     }
     s = run_forward(c, false, d_spec, d_bin, d_lnl, st);
     if (s == ES_OK && mem == ES_MEM_HOST) {
@@ -738,7 +814,7 @@ es_status es_forward(es_ctx *c, float *spectrum, double *binned, double *lnl, in
     if (s == ES_OK) s = finish(c, mem, st);
     if (!tmp.empty()) {
         cudaStreamSynchronize(st);
-        free_all(tmp);
+        free_all(c, tmp);
     }
     return s;
 }
@@ -777,7 +853,7 @@ es_status enqueue_forward_backward(es_ctx *c, cudaStream_t st) {
     cudaMemsetAsync(w.lbar, 0, sizeof(float) * B * L * L, st);
     cudaMemsetAsync(w.cloud_dbar, 0, sizeof(double) * B * L, st);
     cudaMemsetAsync(w.cloud_pbar, 0, sizeof(double) * B * N_CG, st);
-    es_status s = run_forward(c, true, nullptr, nullptr, c->d_lnl, st);
+    es_status s = run_forward(c, true, nullptr, nullptr, c->d_lnl, st, false);
     if (s != ES_OK) return s;
     int launches = (int)c->last_launches;
     const Hook &h = c->hook;
@@ -785,7 +861,8 @@ es_status enqueue_forward_backward(es_ctx *c, cudaStream_t st) {
     if (c->n_kind[1]) {
         launches += launch_emis_fused_backward(m, w, st, h);
     }
-    launches += launch_setup_backward(m, w, st, h);
+    launches += launch_setup_backward(m, w, c->d_lnl, st, h);
+    post_status(c, st);
     c->last_launches = launches;
     return check_launch(c, "backward launch");
 }
@@ -864,6 +941,22 @@ es_status es_set_graphs(es_ctx *c, int on) {
     return ES_OK;
 }
 
+es_status es_set_memory_limit(es_ctx *c, uint64_t bytes) {
+    if (!c) return ES_EINVAL;
+    c->mem_limit = (size_t)bytes;
+    return ES_OK;
+}
+
+es_status es_set_test_hooks(es_ctx *c, int hooks) {
+    if (!c) return ES_EINVAL;
+    if (hooks & ~ES_TEST_WAIT_TIMEOUT) return fail(c, ES_EINVAL, "unknown test hook");
+    const bool wt = (hooks & ES_TEST_WAIT_TIMEOUT) != 0;
+    c->m.wait_test = wt ? 1 : 0;
+    c->m.wait_polls = wt ? WAIT_POLLS_TEST : WAIT_POLLS;
+    ++c->graph_epoch;   // the model is baked into captured graphs
+    return ES_OK;
+}
+
 es_status es_get_flags(es_ctx *c, int32_t *flags, int mem, es_stream_t stream) {
     if (!c) return ES_EINVAL;
     if (!flags || c->batch <= 0) return fail(c, ES_EINVAL, "no batch or NULL flags");
@@ -884,9 +977,7 @@ int64_t es_query(const es_ctx *c, int key) {
         case 3: return c->batch;
         case 4: return c->m.L;
         case 5: return c->m.S;
-        case 6:
-            return (int64_t)(c->ws_bytes + sizeof(float) * (c->alpha_cap + c->estore_cap) +
-                             sizeof(double) * c->ymod_cap);
+        case 6: return (int64_t)c->dev_bytes;
         case 7: return c->last_launches;
         case 8: return c->fwd_chunk;
         case 9: return c->bwd_chunk;
@@ -936,12 +1027,12 @@ void es_destroy(es_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
-    free_all(c->bwd_bufs);
-    free_all(c->work_bufs);
-    free_all(c->data_bufs);
-    free_all(c->grid_bufs);
-    free_all(c->table_bufs);
-    free_all(c->model_bufs);
+    free_all(c, c->bwd_bufs);
+    free_all(c, c->work_bufs);
+    free_all(c, c->data_bufs);
+    free_all(c, c->grid_bufs);
+    free_all(c, c->table_bufs);
+    free_all(c, c->model_bufs);
     drop_graph(c->graph_fb);
     drop_graph(c->graph_ll);
     if (c->gstream) {
@@ -950,9 +1041,10 @@ void es_destroy(es_ctx *c) {
         cudaEventDestroy(c->ev_fork);
         cudaEventDestroy(c->ev_join);
     }
-    if (c->w.ymod) cudaFree(c->w.ymod);
-    if (c->w.itop) cudaFree(c->w.itop);
-    if (c->w.estore) cudaFree(c->w.estore);
+    dev_free(c, c->w.ymod);
+    dev_free(c, c->w.itop);
+    dev_free(c, c->w.estore);
+    if (c->h_err) cudaFreeHost(c->h_err);
     prof_resolve(c);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;

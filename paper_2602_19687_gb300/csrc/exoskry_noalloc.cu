@@ -3,11 +3,10 @@
 // the library image, so the call itself never allocates device memory.
 //
 // Who needs this: callers that must not call cudaMalloc on the hot path, for
-// example code running while a CUDA stream is being captured into a graph
-// (allocation during capture invalidates it), a host framework that owns all
-// device memory through its own pool and forbids other allocations (custom
-// operators of array frameworks), or a long-running sampler that has to be
-// sure it cannot hit an out-of-memory error in the middle of a run.
+// example a host framework that owns all device memory through its own pool
+// and forbids other allocations (custom operators of array frameworks), or a
+// long-running sampler that has to be sure it cannot hit an out-of-memory
+// error in the middle of a run.
 //
 // The array (NOALLOC_SCRATCH_BYTES, 32 MiB) exists on every GPU that loads
 // the library, from module load until the process exits. Every call on a GPU
@@ -58,7 +57,7 @@ struct Carver {
 };
 
 // Lay out the forward workspace of a batch of B vectors; returns bytes needed.
-size_t carve(const es::Model &m, int B, bool emission, unsigned char *base, es::Work &w, int **kind_slot) {
+size_t carve(const es::Model &m, int B, unsigned char *base, es::Work &w, int **kind_slot) {
     Carver c{base};
     const size_t L = m.L, S = m.S, N = m.N;
     w.B = B;
@@ -115,7 +114,7 @@ extern "C" es_status es_loglike_noalloc(es_ctx *c, const double *theta, const in
     if (c->device < 0 || c->device >= MAX_DEVICES) return fail(c, ES_EINVAL, "device ordinal too large");
     es::Work w{};
     int *kind_slot = nullptr;
-    const size_t need = carve(c->m, batch, kind != nullptr, nullptr, w, &kind_slot);
+    const size_t need = carve(c->m, batch, nullptr, w, &kind_slot);
     if (need > NOALLOC_SCRATCH_BYTES)
         return fail(c, ES_EINVAL,
                     "es_loglike_noalloc: batch of " + std::to_string(batch) + " needs " + std::to_string(need) +
@@ -125,7 +124,7 @@ extern "C" es_status es_loglike_noalloc(es_ctx *c, const double *theta, const in
     unsigned char *base = nullptr;
     if (e == cudaSuccess) e = scratch_address(c->device, &base);
     if (e != cudaSuccess) return fail(c, ES_ECUDA, std::string("scratch address: ") + cudaGetErrorString(e));
-    carve(c->m, batch, kind != nullptr, base, w, &kind_slot);
+    carve(c->m, batch, base, w, &kind_slot);
     w.theta_user = theta;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (kind) {

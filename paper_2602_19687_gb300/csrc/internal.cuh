@@ -62,6 +62,11 @@ struct Model {
     int cloud_profile;            // ES_QC_* (non-grey cloud)
     int cloud_feature;            // 1: the mid-infrared feature in Q_ext
     int emis_flux;                // ES_FLUX_*
+    // bounded mbarrier waits of the tensor-core kernels: polls before giving
+    // up; wait_test = 1 (es_set_test_hooks) also skips issuing their products,
+    // so that every wait runs out with no tensor-core operation in flight
+    unsigned wait_polls;
+    int wait_test;
     double distance;              // cm (brown-dwarf flux)
     double p_ref;                 // dyn cm^-2
     double r_star, t_star;
@@ -101,7 +106,7 @@ struct Work {
     const double *theta_user;     // [B][nfree]
     double *theta;                // [B][nfull]
     int *kind, *flags;            // [B]
-    int *err;                     // [1] nonzero once a kernel gave up on a bounded wait (sticky)
+    int *err;                     // [1] nonzero once a kernel gave up on a bounded wait (cleared per call)
     double *t_lay, *t_lev, *r_lev;// [B][L], [B][L+1], [B][L+1]
     double *xs;                   // [B][S+2] X_s..., X_H2, X_He
     double *n_lay;                // [B][L]
@@ -167,6 +172,7 @@ int launch_trans_fused_forward(const Model &m, const Work &w, bool store_e, int 
 int launch_trans_fused_backward(const Model &m, const Work &w, int chunk, cudaStream_t st, const Hook &h);
 int launch_bins(const Model &m, const Work &w, bool want_adjoint, float *spectrum_out,
                 double *binned_out, double *lnl_out, cudaStream_t st, const Hook &h);
-int launch_setup_backward(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
+// lnl_out: the call's ln L output, set to -1e300 for every sample when a kernel gave up on a bounded wait
+int launch_setup_backward(const Model &m, const Work &w, double *lnl_out, cudaStream_t st, const Hook &h);
 
 }  // namespace es

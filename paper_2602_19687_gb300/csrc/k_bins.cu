@@ -29,10 +29,21 @@ __device__ __forceinline__ double block_sum_d(double v, double *scratch) {
 __global__ void __launch_bounds__(BIN_THREADS) k_bins(Model m, Work w, int adjoint, float *spec_out,
                                                       double *binned_out, double *lnl_out) {
     const int b = blockIdx.x;
-    const int N = m.N, S = m.S, kind = w.kind[b];
+    // a kind other than transmission / emission (possible only through the
+    // no-allocation entry point, whose device-side kinds are not checked on the
+    // host) makes the sample invalid; it never indexes the data
+    const int kind_in = w.kind[b];
+    const bool kind_ok = kind_in == ES_KIND_TRANSMISSION || kind_in == ES_KIND_EMISSION;
+    const int N = m.N, S = m.S, kind = kind_ok ? kind_in : ES_KIND_TRANSMISSION;
     __shared__ double scratch[BIN_THREADS / 32];
-    __shared__ int s_bad;
-    if (threadIdx.x == 0) s_bad = w.flags[b];
+    __shared__ int s_bad, s_flag;
+    if (threadIdx.x == 0) {
+        // a fused kernel that gave up on a bounded wait left its spectra
+        // unfinished: every sample of the call is invalid
+        const int timed_out = *w.err != 0;
+        s_flag = w.flags[b] | ((kind_ok && !timed_out) ? 0 : ES_FLAG_INVALID) | (timed_out ? ES_FLAG_TIMEOUT : 0);
+        s_bad = s_flag;
+    }
     __syncthreads();
     const double base = (kind == ES_KIND_TRANSMISSION) ? w.base[b] : 0.0;
     const double c = w.theta[(size_t)b * m.nfull + S + ES_P_C_INFL];
@@ -72,7 +83,7 @@ __global__ void __launch_bounds__(BIN_THREADS) k_bins(Model m, Work w, int adjoi
     bbar = block_sum_d(bbar, scratch);
     const bool bad = s_bad != 0;
     if (threadIdx.x == 0) {
-        w.flags[b] = bad ? ES_FLAG_INVALID : 0;
+        w.flags[b] = bad ? (s_flag | ES_FLAG_INVALID) : 0;
         const double v = bad ? INVALID_LNL : lsum;
         w.lnl[b] = v;
         if (lnl_out) lnl_out[b] = v;

@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, in
     int spec_b = -1, spec_t = 0, spec_buf = 0;
     bool abort = false;
     auto wait_mma = [&](int buf) {
-        if (!mbar_wait(mbar0 + 8u * (uint32_t)buf, (phases >> buf) & 1u)) sm.abort = 1;
+        if (!mbar_wait(mbar0 + 8u * (uint32_t)buf, (phases >> buf) & 1u, m.wait_polls)) sm.abort = 1;
         phases ^= 1u << buf;
         tc_fence_after();
     };
@@ -293,7 +293,8 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, in
                 write_spec(spec_b, spec_t, spec_buf);
                 spec_b = -1;
             }
-            if (threadIdx.x == 12 * 32) {   // warp 12's epilogue share is the lightest: 7 k-steps x 3 split terms
+            // (wait_test: no product is issued, so the wait below runs out and the block aborts)
+            if (threadIdx.x == 12 * 32 && !m.wait_test) {   // warp 12's epilogue share is the lightest: 7 k-steps x 3 split terms
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(buf * 128);
                 // descriptors of k-step 0; a k-step advances the start address field
@@ -580,7 +581,7 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
 
     auto wait_lbar = [&]() {
         if (l_pending) {
-            if (!mbar_wait(mbar_l, pl)) sm.abort = 1;
+            if (!mbar_wait(mbar_l, pl, m.wait_polls)) sm.abort = 1;
             pl ^= 1;
             l_pending = false;
             tc_fence_after();
@@ -769,7 +770,7 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
                 abort = true;
                 break;
             }
-            if (threadIdx.x == 0) {   // alpha_bar: 7 k-steps over impact parameters x (L hi, L lo)
+            if (threadIdx.x == 0 && !m.wait_test) {   // alpha_bar: 7 k-steps over impact parameters x (L hi, L lo)
                 tc_fence_after();
                 const uint64_t a_h = desc_mn_major(th_s, SBO_NU);
                 const uint64_t b_h = desc_mn_major(lh_s, SBO_LP), b_l = desc_mn_major(ll_s, SBO_LP);
@@ -791,7 +792,7 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
             }
             interp_backward<SPL>(m, sm.sc, sm.sc.gb[grp], sm.sc.gb[grp + 1], nt0 + 2 * pair, half, lane, abar_t, a_dst,
                                  sm.red, sm.qtot, stg, t > c * chunk_tiles, t + 1 < t1 ? BT : 0, [&]() {
-                                     if (!mbar_wait(mbar_a, pa)) sm.abort = 1;
+                                     if (!mbar_wait(mbar_a, pa, m.wait_polls)) sm.abort = 1;
                                      tc_fence_after();
                                  });
             pa ^= 1;
@@ -802,7 +803,7 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
                 abort = true;
                 break;
             }
-            if (threadIdx.x == 32) {   // L_bar (from another warp than alpha_bar's issuer): 8 k-steps
+            if (threadIdx.x == 32 && !m.wait_test) {   // L_bar (from another warp than alpha_bar's issuer): 8 k-steps
                 tc_fence_after();
                 const uint32_t d = tmem + 128u;
                 const uint64_t a_h = desc_k_major(th_s, SBO_NU), b_h = desc_k_major(ah_s, SBO_NU);

@@ -206,8 +206,18 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup(Model m, Work w) {
 // ---------------------------------------------------------------------------
 // adjoint of the setup
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(SETUP_THREADS) k_setup_bwd(Model m, Work w) {
+__global__ void __launch_bounds__(SETUP_THREADS) k_setup_bwd(Model m, Work w, double *lnl_out) {
     const int b = blockIdx.x, tid = threadIdx.x;
+    // an adjoint kernel that gave up on a bounded wait left its sums
+    // unfinished: zero gradient, ln L = -1e300 and the timeout flag for every sample
+    if (*w.err != 0) {
+        if (tid < m.nfree) w.grad[(size_t)b * m.nfree + tid] = 0.0;
+        if (tid == 0) {
+            w.flags[b] |= ES_FLAG_INVALID | ES_FLAG_TIMEOUT;
+            if (lnl_out) lnl_out[b] = INVALID_LNL;
+        }
+        return;
+    }
     const int L = m.L, S = m.S;
     __shared__ double rl[ES_MAX_LAYERS + 1], rbar[ES_MAX_LAYERS + 1], tvbar[ES_MAX_LAYERS + 1];
     __shared__ double tlbar[ES_MAX_LAYERS];
@@ -449,8 +459,8 @@ int launch_setup(const Model &m, const Work &w, cudaStream_t st, const Hook &h) 
     return 1;
 }
 
-int launch_setup_backward(const Model &m, const Work &w, cudaStream_t st, const Hook &h) {
-    ES_LAUNCH(h, "k_setup_bwd", st, k_setup_bwd<<<w.B, SETUP_THREADS, 0, st>>>(m, w));
+int launch_setup_backward(const Model &m, const Work &w, double *lnl_out, cudaStream_t st, const Hook &h) {
+    ES_LAUNCH(h, "k_setup_bwd", st, k_setup_bwd<<<w.B, SETUP_THREADS, 0, st>>>(m, w, lnl_out));
     return 1;
 }
 

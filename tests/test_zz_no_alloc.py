@@ -1,7 +1,7 @@
 """es_loglike_noalloc: the log-likelihood entry point that allocates no device
 memory (its workspace is a fixed 32 MiB array inside the library), for callers
-that cannot call cudaMalloc on their hot path, e.g. during CUDA-graph stream
-capture or inside a framework that owns all device memory.
+that cannot call cudaMalloc on their hot path, e.g. inside a framework that owns
+all device memory through its own pool.
 
 Checked through the C ABI against es_loglike on the same inputs, on two calls
 in a row (the second call reuses the array with the first call's contents
@@ -70,6 +70,57 @@ def test_no_alloc_non_grey_cloud_mixed_kinds_twice():
         ctx.es_loglike_noalloc(theta, kind, out)
         torch.cuda.synchronize()
         np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-5, atol=1e-3)
+
+
+def test_no_alloc_takes_no_device_memory():
+    """After a first call, further calls leave the device's free memory unchanged."""
+    w = synth.workload("tiny", batch=4)
+    ctx = binding.context_for(w)
+    theta = torch.tensor(w.theta, dtype=torch.float64, device=DEV)
+    out = torch.empty(4, dtype=torch.float64, device=DEV)
+    ctx.es_loglike_noalloc(theta, None, out)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        ctx.es_loglike_noalloc(theta, None, out)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+
+
+def test_no_alloc_unknown_kind_is_an_invalid_sample():
+    """kind values other than 0 / 1 (not checked on the host) give ln L = -1e300
+    for those samples and leave the others equal to es_loglike's."""
+    w = synth.workload("tiny", batch=3)
+    ctx = binding.context_for(w)
+    theta = torch.tensor(w.theta, dtype=torch.float64, device=DEV)
+    ref = _reference(ctx, theta, torch.zeros(3, dtype=torch.int32, device=DEV))
+    kind = torch.tensor([0, 7, -1], dtype=torch.int32, device=DEV)
+    for _ in range(2):
+        out = torch.full((3,), float("nan"), dtype=torch.float64, device=DEV)
+        ctx.es_loglike_noalloc(theta, kind, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        np.testing.assert_allclose(got[0], ref[0], rtol=1e-5, atol=1e-3)
+        assert got[1] == -1e300 and got[2] == -1e300
+
+
+def test_no_alloc_bounded_wait_timeout_invalidates_the_call():
+    """With the wait-timeout test hook the transmission kernel's bounded waits
+    run out (no tensor-core product is issued): every ln L of the call is
+    -1e300. Clearing the hook restores the normal result on the same context."""
+    w = synth.workload("tiny", batch=2)
+    ctx = binding.context_for(w)
+    theta = torch.tensor(w.theta, dtype=torch.float64, device=DEV)
+    ref = _reference(ctx, theta, None)
+    out = torch.full((2,), float("nan"), dtype=torch.float64, device=DEV)
+    ctx.es_set_test_hooks(binding.ES_TEST_WAIT_TIMEOUT)
+    ctx.es_loglike_noalloc(theta, None, out)
+    torch.cuda.synchronize()
+    assert np.all(out.cpu().numpy() == -1e300)
+    ctx.es_set_test_hooks(0)
+    ctx.es_loglike_noalloc(theta, None, out)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-5, atol=1e-3)
 
 
 def test_no_alloc_rejects_a_batch_beyond_the_fixed_workspace():
