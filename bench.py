@@ -42,58 +42,174 @@ def parse():
     ap.add_argument("--batch", type=int, default=None, help="override the workload's batch size")
     ap.add_argument("--no-tune", action="store_true", help="keep the built-in work-item sizes")
     ap.add_argument("--no-extra", action="store_true", help="skip the emission and high-resolution lines")
-    ap.add_argument("--cpu-child", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-vectors", type=int, default=None,
+                    help="parameter vectors the cpu_baseline leg runs through the oracle (default: host cores)")
     return ap.parse_args()
 
 
-# --------------------------------------------------------------------------- CPU oracle timing
-def oracle_sample_time(workload, n_sub, n_vec, seconds_cap=25.0):
-    """Time the FP64 oracle (forward + complex-step gradient) on a bounded
-    sample: the first `n_vec` valid parameter vectors of the workload on the
-    first `n_sub` wavenumbers (same tables, layers, species). Returns seconds
-    per full-resolution spectrum+gradient, scaled by N / n_sub."""
+# --------------------------------------------------------------------------- the oracle on the host cores
+# The FP64 oracle runs in a process pool (spawn) over all host cores, on whole
+# spectra: one task is the forward model of one parameter vector, or the
+# complex-step derivative of its ln L with respect to one free parameter, so
+# the n_free + 1 tasks of a vector's forward + gradient run in parallel. It is
+# used by the cpu_baseline leg and by the reference arm only. Its FP64-table
+# outputs are also what the BF16-table GPU path's error is measured against.
+_ORACLE_CACHE = {}
+
+
+def _oracle_setup(key, tables):
     from oracle import exoskry_oracle as O
     from paper_2602_19687_gb300 import synth
-    w = synth.workload(workload, batch=max(8, n_vec * 4), n_nu=None)
-    tabs = w.tables
-    full_n = tabs.nu.size
-    sub = synth.Tables(nu=tabs.nu[:n_sub], t_grid=tabs.t_grid, p_grid_bar=tabs.p_grid_bar,
-                       log10_sigma=tabs.log10_sigma[..., :n_sub], cia_t_grid=tabs.cia_t_grid,
-                       cia_h2h2=tabs.cia_h2h2[:, :n_sub], cia_h2he=tabs.cia_h2he[:, :n_sub])
-    if w.table_dtype == "bf16":
-        sub.log10_sigma = O.bf16_row_dequantized(sub.log10_sigma)
-    lam_sub = 1e4 / sub.nu
-    keep = (w.bin_hi_um <= lam_sub.max()) & (w.bin_lo_um >= lam_sub.min())
-    lo, hi = w.bin_lo_um[keep], w.bin_hi_um[keep]
-    mem = O.bin_members(sub.nu, lo, hi)
+    if key not in _ORACLE_CACHE:
+        name, batch, seed = key[:3]
+        w = synth.workload(name, batch=batch, seed=seed, n_nu=key[3] if len(key) > 3 else None)
+        _ORACLE_CACHE[key] = {"w": w, "mem": O.bin_members(w.tables.nu, w.bin_lo_um, w.bin_hi_um)}
+    ent = _ORACLE_CACHE[key]
+    if tables == "bf16" and "bf16" not in ent:
+        w = ent["w"]
+        t = synth.Tables(**{f: getattr(w.tables, f) for f in ("nu", "t_grid", "p_grid_bar", "log10_sigma",
+                                                             "cia_t_grid", "cia_h2h2", "cia_h2he")})
+        t.log10_sigma = O.bf16_row_dequantized(w.tables.log10_sigma)
+        ent["bf16"] = t
+    return ent["w"], ent["mem"], (ent["bf16"] if tables == "bf16" else ent["w"].tables)
+
+
+def oracle_task(task):
+    """task = (workload key (name, batch, seed[, n_nu]), vector index, tables, slot):
+    slot None is the forward model (native spectrum, binned model, ln L);
+    slot k the complex-step derivative of ln L with respect to free parameter
+    k. tables "fp64": the synthetic tables as generated; "bf16": the values
+    the BF16 storage holds (row offset + rounded residual)."""
+    from oracle import exoskry_oracle as O
+    key, b, tables, slot = task
+    w, mem, tabs = _oracle_setup(key, tables)
     m = w.model
-    done, t0 = 0, time.perf_counter()
+    th = m.full_theta(w.theta[b])[0]
+    kind = int(w.kind[b])
+    y, sig = w.y_obs[kind], w.sigma[kind]
+    t0 = time.perf_counter()
+    if slot is None:
+        out = O.forward(m, tabs, th, kind, mem)
+        if out is None:
+            res = {"valid": False, "lnl": O.INVALID_LNL}
+        else:
+            res = {"valid": True, "spec": out[0], "binned": out[1],
+                   "lnl": O.log_likelihood(out[1], y, sig, th[m.n_species + O.P_C_INFL])}
+    else:
+        res = {"grad": float(O.loglike_gradient(m, tabs, th, kind, mem, y, sig, [m.free_idx[slot]])[0])}
+    res.update(key=key, b=b, tables=tables, slot=slot, seconds=time.perf_counter() - t0)
+    return res
+
+
+REF_VECTORS = 4   # parameter vectors per step of the reference arm
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_pool(n=None):
+    import multiprocessing as mp
+    n = n or host_cores()
+    env = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
+    os.environ.update(env)   # one thread per worker: the pool supplies the parallelism
+    return mp.get_context("spawn").Pool(n), n
+
+
+def valid_vectors(w, count):
+    """The first `count` parameter vectors the oracle's own profile,
+    chemistry and hydrostatics accept."""
+    from oracle import exoskry_oracle as O
+    out = []
     for b in range(w.theta.shape[0]):
-        kind = int(w.kind[b])
-        th = m.full_theta(w.theta[b])[0]
-        if not O.atmosphere(m, th)["valid"]:
-            continue
-        O.loglike_gradient(m, sub, th, kind, mem, w.y_obs[kind][keep], w.sigma[kind][keep],
-                           list(m.free_idx))
-        done += 1
-        if done >= n_vec or time.perf_counter() - t0 > seconds_cap:
-            break
-    dt = time.perf_counter() - t0
-    return dt / max(done, 1) * (full_n / n_sub), done, full_n
+        if O.atmosphere(w.model, w.model.full_theta(w.theta[b])[0])["valid"]:
+            out.append(b)
+            if len(out) == count:
+                break
+    return out
 
 
-def cpu_baseline(workload, n_sub=1500, n_vec=2):
-    """Run the oracle timing in a child process pinned to one thread."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-child", "%s:%d:%d" % (workload, n_sub, n_vec)]
-    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=600)
-    if r.returncode != 0:
-        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-300:]}
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": 1.0 / d["sec_per_spectrum"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d parameter vector(s) x first %d of %d wavenumbers, forward + complex-step gradient "
-                      "(%s), scaled to a full spectrum; host cores available %d"
-                      % (d["done"], n_sub, d["full_n"], workload, os.cpu_count() or 0)}
+def oracle_gradients(pool, key, vectors, nfree, tables="fp64"):
+    """Forward + gradient of each vector on whole spectra over the pool:
+    (per-vector results, wall seconds)."""
+    tasks = [(key, b, tables, None) for b in vectors] + [(key, b, tables, k) for b in vectors for k in range(nfree)]
+    t0 = time.perf_counter()
+    res = pool.map(oracle_task, tasks, chunksize=1)
+    wall = time.perf_counter() - t0
+    out = {b: {"grad": np.zeros(nfree)} for b in vectors}
+    for r in res:
+        if r["slot"] is None:
+            out[r["b"]].update({k: v for k, v in r.items() if k in ("valid", "spec", "binned", "lnl")})
+        else:
+            out[r["b"]]["grad"][r["slot"]] = r["grad"]
+    return out, wall
+
+
+def oracle_forwards(pool, key, vectors, tables):
+    res = pool.map(oracle_task, [(key, b, tables, None) for b in vectors], chunksize=1)
+    return {r["b"]: r for r in res}
+
+
+def cpu_baseline(pool, cores, key, vectors, nfree):
+    """The oracle as it stands, timed on the host cores: forward + complex-step
+    gradient of whole spectra for `vectors` (one pool task per vector and per
+    gradient slot). Returns (cpu_baseline record, oracle outputs)."""
+    out, wall = oracle_gradients(pool, key, vectors, nfree)
+    rec = {"value": len(vectors) / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "seconds": wall,
+           "sample": "%d parameter vectors of %s (seed %d), whole spectra (all wavenumbers), forward + "
+                     "complex-step gradient of ln L in %d free parameters, FP64 on the unquantized tables; "
+                     "one task per vector and gradient slot over a %d-process pool"
+                     % (len(vectors), key[0], key[2], nfree, cores)}
+    return rec, out
+
+
+def _rel(a, b, floor=0.0):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return np.abs(a - b) / np.maximum(np.abs(b), floor)
+
+
+def _stats(x):
+    x = np.asarray(x, np.float64).ravel()
+    return {"max": float(np.max(x)), "median": float(np.median(x))} if x.size else None
+
+
+def bf16_error(gpu, ref, ref_bf16=None):
+    """Error of the GPU path (BF16 tables, FP32 arithmetic) against the FP64
+    oracle on the unquantized tables, over the sampled vectors: native
+    spectrum and binned model (relative), ln L (absolute and relative), and
+    the gradient per component (relative, components smaller than 1e-3 of the
+    vector's largest measured against that floor; and in units of the
+    gradient parity tolerance 1e-3 |ref| + 1e-4 max |ref|). With ref_bf16 (the oracle
+    on the BF16-stored table values) also the GPU arithmetic's own error."""
+    vecs = [b for b in ref if ref[b].get("valid")]
+    out = {"vectors": len(vecs)}
+    if not vecs:
+        return out
+    out["native"] = _stats(np.concatenate([_rel(gpu["spec"][b], ref[b]["spec"]) for b in vecs]))
+    out["binned"] = _stats(np.concatenate([_rel(gpu["binned"][b], ref[b]["binned"]) for b in vecs]))
+    dl = np.array([gpu["lnl"][b] - ref[b]["lnl"] for b in vecs])
+    out["lnl_abs"] = _stats(np.abs(dl))
+    out["lnl_rel"] = _stats(np.abs(dl) / np.abs([ref[b]["lnl"] for b in vecs]))
+    gv = [b for b in vecs if b in gpu.get("grad", {}) and "grad" in ref[b]]
+    if gv:
+        g = [_rel(gpu["grad"][b], ref[b]["grad"], 1e-3 * np.max(np.abs(ref[b]["grad"]))) for b in gv]
+        out["grad"] = _stats(np.concatenate(g))
+        # in units of the gradient parity tolerance, 1e-3 |ref| + 1e-4 max |ref| (1 = at the tolerance)
+        t = [np.abs(gpu["grad"][b] - ref[b]["grad"]) /
+             (1e-3 * np.abs(ref[b]["grad"]) + 1e-4 * np.max(np.abs(ref[b]["grad"]))) for b in gv]
+        out["grad_over_tolerance"] = _stats(np.concatenate(t))
+        out["grad_vectors"] = len(gv)
+    if ref_bf16:
+        v2 = [b for b in ref_bf16 if ref_bf16[b].get("valid")]
+        if v2:
+            out["gpu_arithmetic_only"] = {
+                "native": _stats(np.concatenate([_rel(gpu["spec"][b], ref_bf16[b]["spec"]) for b in v2])),
+                "lnl_abs": _stats(np.abs([gpu["lnl"][b] - ref_bf16[b]["lnl"] for b in v2]))}
+    return out
 
 
 # --------------------------------------------------------------------------- clocks
@@ -213,6 +329,25 @@ def kernel_work(name, w, n_valid):
     return None
 
 
+def emission_fp32_ops(name, w, n_valid):
+    """Algorithmic FP32 operations (an FMA counts as one) of one launch of an
+    emission kernel, per (emission vector, layer, wavenumber): 4 per species
+    (the bilinear exponent in coefficient form, 3, and its sum), 6 for the
+    two CIA pairs, the number density and Rayleigh, 1 for dtau = alpha dr, 3
+    for the Planck function at the level and 7 per flux angle for the
+    linear-in-tau step (x = dtau/mu, 1 - E, the linear-source factor and the
+    intensity update): 4 S + 10 + 7 n_mu. The adjoint counts three times the
+    forward's (the recompute plus two operations per forward operation for
+    the reverse sweep). The non-grey cloud's second column adds 7 n_mu + 1."""
+    from paper_2602_19687_gb300 import synth
+    m = w.model
+    n_e = int(np.sum((w.kind == 1)[:n_valid]))
+    cloud = 1 if m.cloud_kind == synth.CLOUD_KH18 else 0
+    per = 4 * m.n_species + 10 + 7 * 4 + cloud * (7 * 4 + 1)
+    ops = n_e * m.n_layers * w.tables.nu.size * per
+    return ops * (3 if name == "k_emis_bwd" else 1)
+
+
 def measured_traffic(name, n_vectors):
     """DRAM bytes per launch of `name` from the committed ncu capture, scaled
     from its batch to n_vectors transmission vectors; None when the kernel
@@ -243,9 +378,13 @@ def alu_peak(kind, sm_mhz):
 
 # --------------------------------------------------------------------------- main arms
 # --------------------------------------------------------------------------- other workloads
-def measure_workload(name, device, steps=5, warmup=3):
-    """Forward+gradient throughput of another synthetic workload (graph
-    replay, device-resident inputs, CUDA events): spectra/s and ms/step."""
+def measure_workload(name, device, steps=5, warmup=3, out_vectors=None, probe=None):
+    """Forward+gradient and forward-only throughput of another synthetic
+    workload (graph replay, device-resident inputs, CUDA events): spectra/s
+    and ms/step; per-kernel times of two directly launched steps (with the
+    emission kernels' roofline when they run); and, for `out_vectors`, the
+    GPU's native spectrum, binned model, ln L and gradient (for the error
+    against the FP64 oracle)."""
     import torch
     from paper_2602_19687_gb300 import binding, synth
     w = synth.workload(name)
@@ -257,21 +396,67 @@ def measure_workload(name, device, steps=5, warmup=3):
     lnl = torch.empty(B, dtype=torch.float64, device=dev)
     grad = torch.empty_like(th)
     ctx.es_autotune()
-    for _ in range(warmup):
-        ctx.es_forward_backward(lnl, grad)
-    torch.cuda.synchronize(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stream = torch.cuda.current_stream(dev)
-    e0.record(stream)
-    for _ in range(steps):
+
+    def timed(call):
+        for _ in range(warmup):
+            call()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            call()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / steps
+
+    ms = timed(lambda: ctx.es_forward_backward(lnl, grad))
+    ms_fwd = timed(lambda: ctx.es_loglike(lnl))
+    ctx.es_set_profiling(True)
+    for _ in range(2):
         ctx.es_forward_backward(lnl, grad)
-    e1.record(stream)
     torch.cuda.synchronize(dev)
-    ms = e0.elapsed_time(e1) / steps
+    prof = ctx.es_get_profile()
+    ctx.es_set_profiling(False)
+    flags = torch.empty(B, dtype=torch.int32, device=dev)
+    ctx.es_forward_backward(lnl, grad)
+    ctx.es_get_flags(flags)
+    n_valid = int((flags == 0).sum().item())
+    kernels = {k: {"ms_per_launch": t / max(n, 1), "launches": n} for k, t, n in prof}
+    roof = {}
+    for k in ("k_emis_fwd", "k_emis_bwd"):
+        if k in kernels and probe:
+            sec = kernels[k]["ms_per_launch"] / 1e3
+            ex2 = kernel_work(k, w, B)[0] / sec
+            fp32 = emission_fp32_ops(k, w, B) / sec
+            roof[k] = {"bound": "alu", "ms_per_launch": kernels[k]["ms_per_launch"],
+                       "ex2": {"achieved": ex2 / 1e12, "peak": probe[0] / 1e12, "unit": "Tex2/s",
+                               "frac": ex2 / probe[0]},
+                       "fp32": {"achieved": fp32 / 1e12, "peak": 2 * probe[1] / 1e12, "unit": "Top/s",
+                                "frac": fp32 / (2 * probe[1]),
+                                "peak_source": "measured: es_probe_rates packed FFMA2 rate x 2 lanes"}}
+    gpu_out = None
+    if out_vectors:
+        N, nb = w.tables.nu.size, w.bin_lo_um.size
+        spec = torch.empty((B, N), dtype=torch.float32, device=dev)
+        binned = torch.empty((B, nb), dtype=torch.float64, device=dev)
+        lnl_f = torch.empty(B, dtype=torch.float64, device=dev)
+        ctx.es_forward(spectrum=spec, binned=binned, lnl=lnl_f)
+        torch.cuda.synchronize(dev)
+        idx = list(out_vectors)
+        gpu_out = {"spec": dict(zip(idx, spec[idx].cpu().numpy().astype(np.float64))),
+                   "binned": dict(zip(idx, binned[idx].cpu().numpy())),
+                   "lnl": dict(zip(idx, lnl_f[idx].cpu().numpy())),
+                   "grad": dict(zip(idx, grad[idx].cpu().numpy()))}
     n_em = int(np.sum(w.kind == 1))
     ctx.es_destroy()
-    return {"workload": name + ": " + w.description, "vectors": B, "emission_vectors": n_em,
-            "value": B / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps, "warmup": warmup}
+    rec = {"workload": name + ": " + w.description, "vectors": B, "emission_vectors": n_em,
+           "valid_vectors": n_valid, "value": B / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+           "forward_only": {"value": B / (ms_fwd / 1e3), "unit": "spectra/s (ln L only)", "ms_per_step": ms_fwd},
+           "kernels": kernels, "steps": steps, "warmup": warmup}
+    if roof:
+        rec["roofline"] = roof
+    return rec, w, gpu_out
 
 
 # --------------------------------------------------------------------------- sharding
@@ -387,6 +572,39 @@ def run_gpu(args):
     e2e_ms = (t1 - t0) * 1e3 / args.steps
     e2e_value = job_throughput(B, world, max_over_ranks(e2e_ms, world, dev))
 
+    # ---- forward only (ln L, the sampler's call): graph replay, device buffers
+    ctx.es_set_batch(theta, kind)
+    for _ in range(args.warmup):
+        ctx.es_loglike(lnl)
+    torch.cuda.synchronize(dev)
+    barrier()
+    ef0, ef1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ef0.record(stream)
+    for _ in range(args.steps):
+        ctx.es_loglike(lnl)
+    ef1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    fwd_ms = max_over_ranks(ef0.elapsed_time(ef1) / args.steps, world, dev)
+    forward_only = {"value": job_throughput(B, world, fwd_ms), "unit": "spectra/s (ln L only, es_loglike)",
+                    "ms_per_step": fwd_ms}
+
+    # ---- the GPU's outputs for the vectors the oracle legs sample (BF16-table error)
+    gpu_head = None
+    if rank == 0 and not args.no_cpu:
+        sample = valid_vectors(w, args.oracle_vectors)
+        spec_d = torch.empty((B, w.tables.nu.size), dtype=torch.float32, device=dev)
+        bin_d = torch.empty((B, w.bin_lo_um.size), dtype=torch.float64, device=dev)
+        lnl_d = torch.empty(B, dtype=torch.float64, device=dev)
+        ctx.es_forward(spectrum=spec_d, binned=bin_d, lnl=lnl_d)
+        ctx.es_forward_backward(lnl, grad)
+        torch.cuda.synchronize(dev)
+        gpu_head = {"spec": {b: spec_d[b].cpu().numpy().astype(np.float64) for b in sample},
+                    "binned": {b: bin_d[b].cpu().numpy() for b in sample},
+                    "lnl": {b: float(lnl_d[b]) for b in sample},
+                    "grad": {b: grad[b].cpu().numpy() for b in sample}}
+        del spec_d, bin_d
+
     # ---- roofline of the dominant kernel (live CUDA-event times)
     peaks, peak_src = measured_peaks()
     ex2_rate, ffma2_rate = binding.probe_rates(local)
@@ -448,11 +666,50 @@ def run_gpu(args):
                       "workload": args.workload + ": " + w.description +
                       " (one vector per call, forward+gradient)"}
 
-    extra = None
+    extra, extra_out, roof_emis = None, {}, None
     if rank == 0 and not args.no_extra:
-        extra = [measure_workload(n, local) for n in ("batched_emis", "highres", "browndwarf", "cloudy_trans", "cloudy_emis")]
+        extra = []
+        for n in ("batched_emis", "highres", "browndwarf", "cloudy_trans", "cloudy_emis"):
+            want = list(range(8)) if (n in ("batched_emis", "highres") and not args.no_cpu) else None
+            rec, wx, gx = measure_workload(n, local, out_vectors=want, probe=(ex2_rate, ffma2_rate))
+            extra.append(rec)
+            if gx is not None:
+                extra_out[n] = (wx, gx)
+            if n == "batched_emis":
+                roof_emis = rec.get("roofline")
         extra.append(measure_nested(local))
-    cpu = cpu_baseline(args.workload) if (rank == 0 and not args.no_cpu) else None
+
+    # ---- the FP64 oracle on the host cores (after every GPU timing): the
+    # cpu_baseline record, and from the same oracle outputs the BF16-table
+    # path's error against the unquantized tables
+    cpu, bf16 = None, None
+    if rank == 0 and not args.no_cpu:
+        pool, cores = oracle_pool()
+        try:
+            key = (args.workload, args.batch, shard_seed(0))
+            cpu, ref = cpu_baseline(pool, cores, key, sample, nfree)
+            ref_q = oracle_forwards(pool, key, sample[:4], "bf16") if w.table_dtype == "bf16" else None
+            bf16 = {args.workload: bf16_error(gpu_head, ref, ref_q)}
+            for n, (wx, gx) in extra_out.items():
+                cand = [b for b in valid_vectors(wx, 8) if b in gx["spec"]]
+                # one vector of each kind the workload holds, the first with the gradient
+                picks = []
+                for k in (0, 1):
+                    kb = [b for b in cand if int(wx.kind[b]) == k]
+                    if kb:
+                        picks.append(kb[0])
+                keyx = (n, None, 42)
+                refx, _ = oracle_gradients(pool, keyx, picks[:1], wx.theta.shape[1])
+                refx.update(oracle_forwards(pool, keyx, picks[1:], "fp64"))
+                refqx = oracle_forwards(pool, keyx, picks, "bf16")
+                gsub = {f: {b: gx[f][b] for b in picks} for f in ("spec", "binned", "lnl")}
+                gsub["grad"] = {b: gx["grad"][b] for b in picks[:1]}
+                e = bf16_error(gsub, {b: refx[b] for b in picks}, refqx)
+                e["kinds"] = [int(wx.kind[b]) for b in picks]
+                bf16[n] = e
+        finally:
+            pool.close()
+            pool.join()
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -465,17 +722,20 @@ def run_gpu(args):
                        "parallelism": "independent shards, one process per GPU"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(B * nfree * 8 + B * 4),
                     "d2h_bytes_per_step": int(B * 8 + B * nfree * 8)},
+            "forward_only": forward_only,
             "gpu_launches": int(launches),
             "graph_replay": bool(ctx.es_query(10)),
             "work_item_tiles": {"k_trans_fwd": tuned[0], "k_trans_bwd": tuned[1]},
             "ms_per_step_direct_launches": ms_profiled,
             "roofline": roof,
+            "roofline_emission": roof_emis,
             "kernels": per_kernel,
             "plain": plain,
             "batched_over_plain": (value / world / plain["value"]) if plain else None,
             "plain_same_workload": plain_same,
             "batched_over_plain_same_workload": (value / world / plain_same["value"]) if plain_same else None,
             "cpu_baseline": cpu,
+            "bf16_error": bf16,
             "other_workloads": extra,
             "clocks": clk,
             "peaks_source": peak_src,
@@ -488,39 +748,48 @@ def run_gpu(args):
 
 
 def run_reference(args):
-    """The FP64 oracle as it stands, timed on the host cores (rank 0 only)."""
+    """The FP64 oracle as it stands on the host cores (rank 0 only): each step
+    is the forward model and complex-step gradient of `REF_VECTORS` parameter
+    vectors on whole spectra, one pool task per vector and gradient slot."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    from paper_2602_19687_gb300 import synth
+    key = (args.workload, args.batch, shard_seed(0))
+    w = synth.workload(args.workload, batch=args.batch, seed=shard_seed(0))
+    nfree = w.theta.shape[1]
+    cand = valid_vectors(w, REF_VECTORS * (args.warmup + args.steps))
+    pool, cores = oracle_pool()
     per = []
-    for _ in range(args.warmup + args.steps):
-        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1")
-        cmd = [sys.executable, os.path.abspath(__file__), "--cpu-child", "%s:%d:%d" % (args.workload, 600, 1)]
-        r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=600)
-        if r.returncode != 0:
-            raise RuntimeError("oracle timing child failed: " + r.stderr[-500:])
-        d = json.loads(r.stdout.strip().splitlines()[-1])
-        per.append(d["sec_per_spectrum"])
+    try:
+        for step in range(args.warmup + args.steps):
+            vec = [cand[(step * REF_VECTORS + k) % len(cand)] for k in range(REF_VECTORS)]
+            _, wall = oracle_gradients(pool, key, vec, nfree)
+            per.append(wall)
+    finally:
+        pool.close()
+        pool.join()
     timed = per[args.warmup:]
-    sps = 1.0 / float(np.mean(timed))
+    sec = float(np.mean(timed))
+    sps = REF_VECTORS / sec
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": sps, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(timed)) * 1e3,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": args.workload},
-        "cpu_baseline": {"value": sps, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "per step: 1 parameter vector x first 600 wavenumbers, forward + "
-                                   "complex-step gradient, scaled to a full spectrum"},
+        "data": "synthetic (seeded tables, data and parameter batches)",
+        "config": {"workload": args.workload + ": " + w.description},
+        "cpu_baseline": {"value": sps, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "per step: %d parameter vectors, whole spectra (all %d wavenumbers), forward + "
+                                   "complex-step gradient in %d free parameters, FP64 on the unquantized tables, "
+                                   "one task per vector and gradient slot over a %d-process pool"
+                                   % (REF_VECTORS, w.tables.nu.size, nfree, cores)},
         "e2e": {"value": sps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
 def main():
     args = parse()
-    if args.cpu_child:
-        name, n_sub, n_vec = args.cpu_child.split(":")
-        sec, done, full_n = oracle_sample_time(name, int(n_sub), int(n_vec))
-        print(json.dumps({"sec_per_spectrum": sec, "done": done, "full_n": full_n}))
-        return
+    if args.oracle_vectors is None:
+        args.oracle_vectors = host_cores()
     if args.impl == "reference":
         run_reference(args)
         return

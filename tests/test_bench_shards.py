@@ -58,12 +58,42 @@ def test_reference_arm_prints_the_contract_line():
     import subprocess
     import sys
     r = subprocess.run([sys.executable, os.path.join(os.path.dirname(bench.__file__), "bench.py"), "--impl",
-                        "reference", "--steps", "1", "--warmup", "0"], capture_output=True, text=True, timeout=600,
-                       check=True)
+                        "reference", "--steps", "1", "--warmup", "0", "--workload", "tiny"], capture_output=True,
+                       text=True, timeout=600, check=True)
     line = json.loads(r.stdout.strip().splitlines()[-1])
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
                 "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert key in line, key
     assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == bench.UNIT
-    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == bench.host_cores()
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_pooled_oracle_gradient_equals_the_serial_one():
+    """The oracle legs split a vector's forward + gradient into one pool task
+    per gradient slot; reassembled, it is the oracle's own serial gradient,
+    and the error report of identical outputs is zero."""
+    from oracle import exoskry_oracle as O
+    from paper_2602_19687_gb300 import synth
+    key = ("tiny", 3, 42)
+    w = synth.workload("tiny", batch=3, seed=42)
+    vec = bench.valid_vectors(w, 2)
+    nfree = w.theta.shape[1]
+    pool, cores = bench.oracle_pool(2)
+    try:
+        out, wall = bench.oracle_gradients(pool, key, vec, nfree)
+    finally:
+        pool.close()
+        pool.join()
+    assert cores == 2 and wall > 0
+    mem = O.bin_members(w.tables.nu, w.bin_lo_um, w.bin_hi_um)
+    for b in vec:
+        th = w.model.full_theta(w.theta[b])[0]
+        k = int(w.kind[b])
+        g = O.loglike_gradient(w.model, w.tables, th, k, mem, w.y_obs[k], w.sigma[k], list(w.model.free_idx))
+        assert np.array_equal(out[b]["grad"], g)
+        assert out[b]["lnl"] == O.loglike(w.model, w.tables, th, k, mem, w.y_obs[k], w.sigma[k])
+    gpu = {f: {b: out[b][f] for b in vec} for f in ("spec", "binned", "lnl", "grad")}
+    e = bench.bf16_error(gpu, out)
+    assert e["vectors"] == len(vec) and e["native"]["max"] == 0 and e["grad"]["max"] == 0
+    assert e["lnl_abs"]["max"] == 0
