@@ -515,7 +515,7 @@ def run_gpu(args):
     lnl = torch.empty(B, dtype=torch.float64, device=dev)
     grad = torch.empty((B, nfree), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
-    tuned = ctx.es_autotune() if not args.no_tune else (0, 0)   # work-item sizes, outside the timed region
+    tuned = ctx.es_autotune() if not args.no_tune else ctx.launch_shapes()   # outside the timed region
     for _ in range(args.warmup):
         ctx.es_forward_backward(lnl, grad)
     torch.cuda.synchronize(dev)
@@ -725,7 +725,7 @@ def run_gpu(args):
             "forward_only": forward_only,
             "gpu_launches": int(launches),
             "graph_replay": bool(ctx.es_query(10)),
-            "work_item_tiles": {"k_trans_fwd": tuned[0], "k_trans_bwd": tuned[1]},
+            "launch_shapes": tuned,
             "ms_per_step_direct_launches": ms_profiled,
             "roofline": roof,
             "roofline_emission": roof_emis,

@@ -255,14 +255,18 @@ es_status es_loglike(es_ctx *ctx, double *lnL, int mem, es_stream_t stream);
 es_status es_forward_backward(es_ctx *ctx, double *lnL, double *grad, int mem,
                               es_stream_t stream);
 
-/* Time the fused transmission kernels at several work-item sizes
- * (wavenumber tiles per persistent work item) on the current batch and keep
- * the fastest for later calls of this context; the results are readable
- * through es_query keys 8 and 9. Runs a full forward + adjoint plus about
- * twenty timed kernel launches on `stream` and synchronises it; leaves the
- * context's outputs undefined until the next es_loglike /
- * es_forward_backward. A batch with no transmission samples is a no-op.
- * Not a step of the paper's method: launch-shape tuning for this GPU. */
+/* Launch-shape autotuner of the fused persistent kernels (not a step of the
+ * paper's method: tuning for this GPU). For the current batch's composition
+ * (transmission only, emission only, or mixed: one kernel per direction over
+ * both kinds) it times each kernel at several work-item sizes (wavenumber
+ * tiles per item: 128-wavenumber tiles for transmission and mixed windows,
+ * 512-wavenumber tiles for emission) and both work-item orders
+ * (chunk-major: blocks running together share a wavenumber window of the
+ * coefficient table in L2; sample-major: fewer sample stagings per block),
+ * and keeps the fastest for later calls of this context (es_query keys 8, 9,
+ * 12-16). Runs a full forward + adjoint plus a few dozen timed kernel
+ * launches on `stream` and synchronises it; leaves the context's outputs
+ * undefined until the next es_loglike / es_forward_backward. */
 es_status es_autotune(es_ctx *ctx, es_stream_t stream);
 
 /* CUDA-graph replay of es_loglike / es_forward_backward on (1, default) or
@@ -317,7 +321,11 @@ es_status es_get_flags(es_ctx *ctx, int32_t *flags, int mem, es_stream_t stream)
  * fused transmission forward / adjoint kernel (0: built-in heuristic),
  * 10 graph replay enabled (1) or not (0), 11 device status word of the last
  * call (0; nonzero when a tensor-core kernel gave up on a bounded wait;
- * synchronises).
+ * synchronises), 12 / 13 work-item size of the fused emission forward /
+ * adjoint (512-wavenumber tiles), 14 / 15 window of the mixed forward /
+ * adjoint (128-wavenumber tiles), 16 work-item orders (bit k set: kernel k
+ * of trans fwd, trans bwd, emis fwd, emis bwd, mixed fwd, mixed bwd runs its
+ * items sample-major). Sizes 0: the built-in heuristic.
  * Returns -1 for an unknown key or a NULL context. */
 int64_t es_query(const es_ctx *ctx, int key);
 

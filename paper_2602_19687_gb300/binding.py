@@ -230,9 +230,18 @@ class Context:
                                                 _ptr(lnl), _stream(stream)), "es_loglike_noalloc")
 
     def es_autotune(self, stream=None):
-        """Pick the fused transmission kernels' work-item sizes by timing them on the current batch."""
+        """Pick the fused kernels' launch shapes (work-item size, item order) by
+        timing them on the current batch; returns {kernel: (size, order)} with
+        order "chunk-major" or "sample-major" and size 0 for untuned kernels."""
         self._check(self.lib.es_autotune(self.handle, _stream(stream)), "es_autotune")
-        return self.es_query(8), self.es_query(9)
+        return self.launch_shapes()
+
+    def launch_shapes(self):
+        bits = self.es_query(16)
+        names = ("trans_fwd", "trans_bwd", "emis_fwd", "emis_bwd", "mixed_fwd", "mixed_bwd")
+        keys = (8, 9, 12, 13, 14, 15)
+        return {n: (self.es_query(k), "sample-major" if (bits >> i) & 1 else "chunk-major")
+                for i, (n, k) in enumerate(zip(names, keys))}
 
     def es_set_graphs(self, on):
         self._check(self.lib.es_set_graphs(self.handle, 1 if on else 0), "es_set_graphs")

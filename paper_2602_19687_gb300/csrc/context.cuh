@@ -42,8 +42,12 @@ struct es_ctx {
     int open_entry = -1;
     cudaEvent_t open_ev = nullptr;
     es::Hook hook;
-    // tuned work-item sizes of the fused transmission kernels (0: heuristic)
-    int fwd_chunk = 0, bwd_chunk = 0;
+    // launch shapes of the fused kernels (es_autotune): work-item size (0: the
+    // built-in heuristic) and item order, per kernel (FUSED_* indices)
+    struct Shape { int chunk = 0, sample_major = 0; };
+    enum { FUSED_TRANS_FWD, FUSED_TRANS_BWD, FUSED_EMIS_FWD, FUSED_EMIS_BWD, FUSED_MIXED_FWD, FUSED_MIXED_BWD,
+           N_FUSED };
+    Shape shape[N_FUSED];
     // CUDA-graph replay of es_loglike / es_forward_backward
     bool use_graph = true;
     int graph_epoch = 0;

@@ -375,9 +375,16 @@ es_status run_forward(es_ctx *c, bool adjoint, float *spec_out, double *binned_o
     const Hook &h = c->hook;
     clear_status(c, st);
     launches += launch_setup(c->m, w, st, h);
-    if (c->n_kind[0]) launches += launch_trans_fused_forward(c->m, w, adjoint, c->fwd_chunk, st, h);
-    if (c->n_kind[1]) {
-        launches += launch_emis_fused_forward(c->m, w, adjoint, st, h);
+    const es_ctx::Shape *sh = c->shape;
+    if (c->n_kind[0] && c->n_kind[1]) {   // both kinds: one kernel over all items
+        const es_ctx::Shape &x = sh[es_ctx::FUSED_MIXED_FWD];
+        launches += launch_mixed_fused_forward(c->m, w, adjoint, x.chunk, x.sample_major, st, h);
+    } else if (c->n_kind[0]) {
+        const es_ctx::Shape &x = sh[es_ctx::FUSED_TRANS_FWD];
+        launches += launch_trans_fused_forward(c->m, w, adjoint, x.chunk, x.sample_major, st, h);
+    } else if (c->n_kind[1]) {
+        const es_ctx::Shape &x = sh[es_ctx::FUSED_EMIS_FWD];
+        launches += launch_emis_fused_forward(c->m, w, adjoint, x.chunk, x.sample_major, st, h);
     }
     if (adjoint) {
         cudaMemsetAsync(w.dbar, 0, sizeof(float) * (size_t)w.B * c->m.Np, st);
@@ -857,9 +864,16 @@ es_status enqueue_forward_backward(es_ctx *c, cudaStream_t st) {
     if (s != ES_OK) return s;
     int launches = (int)c->last_launches;
     const Hook &h = c->hook;
-    if (c->n_kind[0]) launches += launch_trans_fused_backward(m, w, c->bwd_chunk, st, h);
-    if (c->n_kind[1]) {
-        launches += launch_emis_fused_backward(m, w, st, h);
+    const es_ctx::Shape *sh = c->shape;
+    if (c->n_kind[0] && c->n_kind[1]) {
+        const es_ctx::Shape &x = sh[es_ctx::FUSED_MIXED_BWD];
+        launches += launch_mixed_fused_backward(m, w, x.chunk, x.sample_major, st, h);
+    } else if (c->n_kind[0]) {
+        const es_ctx::Shape &x = sh[es_ctx::FUSED_TRANS_BWD];
+        launches += launch_trans_fused_backward(m, w, x.chunk, x.sample_major, st, h);
+    } else if (c->n_kind[1]) {
+        const es_ctx::Shape &x = sh[es_ctx::FUSED_EMIS_BWD];
+        launches += launch_emis_fused_backward(m, w, x.chunk, x.sample_major, st, h);
     }
     launches += launch_setup_backward(m, w, c->d_lnl, st, h);
     post_status(c, st);
@@ -894,9 +908,9 @@ es_status es_autotune(es_ctx *c, es_stream_t stream) {
     cudaSetDevice(c->device);
     if ((s = prepare(c, true)) != ES_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (!c->n_kind[0]) return ES_OK;   // only the fused transmission kernels have tunables
-    // one full pass so the forward's exp(-tau) and dbar the backward reads are valid
-    c->fwd_chunk = c->bwd_chunk = 0;
+    // one full pass with the built-in shapes, so that the forward's stores the
+    // adjoint kernels read (exp(-tau), I_toa, dbar) are valid while they are timed
+    for (auto &x : c->shape) x = es_ctx::Shape{};
     if ((s = enqueue_forward_backward(c, st)) != ES_OK) return s;
     Work w = c->w;
     w.B = c->batch;
@@ -917,16 +931,34 @@ es_status es_autotune(es_ctx *c, es_stream_t stream) {
         }
         return best;
     };
-    const int fwd_cand[] = {2, 4, 8, 16, 32, 64, 128}, bwd_cand[] = {2, 4, 8, 16, 32, 64};
-    float best = 1e30f;
-    for (int ch : fwd_cand) {
-        const float ms = time_it([&]() { launch_trans_fused_forward(c->m, w, true, ch, st, none); });
-        if (ms < best) { best = ms; c->fwd_chunk = ch; }
-    }
-    best = 1e30f;
-    for (int ch : bwd_cand) {
-        const float ms = time_it([&]() { launch_trans_fused_backward(c->m, w, ch, st, none); });
-        if (ms < best) { best = ms; c->bwd_chunk = ch; }
+    // the fastest (work-item size, item order) of one kernel
+    auto tune = [&](int which, const std::vector<int> &sizes, auto &&launch) {
+        float best = 1e30f;
+        for (int order = 0; order < 2; ++order)
+            for (int ch : sizes) {
+                const float ms = time_it([&]() { launch(ch, order); });
+                if (ms < best) {
+                    best = ms;
+                    c->shape[which] = es_ctx::Shape{ch, order};
+                }
+            }
+    };
+    const Model &m = c->m;
+    if (c->n_kind[0] && c->n_kind[1]) {
+        const std::vector<int> win = {4, 8, 16, 32, 64};
+        tune(es_ctx::FUSED_MIXED_FWD, win,
+             [&](int ch, int o) { launch_mixed_fused_forward(m, w, true, ch, o, st, none); });
+        tune(es_ctx::FUSED_MIXED_BWD, win, [&](int ch, int o) { launch_mixed_fused_backward(m, w, ch, o, st, none); });
+    } else if (c->n_kind[0]) {
+        tune(es_ctx::FUSED_TRANS_FWD, {2, 4, 8, 16, 32, 64, 128},
+             [&](int ch, int o) { launch_trans_fused_forward(m, w, true, ch, o, st, none); });
+        tune(es_ctx::FUSED_TRANS_BWD, {2, 4, 8, 16, 32, 64},
+             [&](int ch, int o) { launch_trans_fused_backward(m, w, ch, o, st, none); });
+    } else if (c->n_kind[1]) {
+        tune(es_ctx::FUSED_EMIS_FWD, {1, 2, 4, 8, 16},
+             [&](int ch, int o) { launch_emis_fused_forward(m, w, true, ch, o, st, none); });
+        tune(es_ctx::FUSED_EMIS_BWD, {1, 2, 4, 8, 16},
+             [&](int ch, int o) { launch_emis_fused_backward(m, w, ch, o, st, none); });
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -979,8 +1011,17 @@ int64_t es_query(const es_ctx *c, int key) {
         case 5: return c->m.S;
         case 6: return (int64_t)c->dev_bytes;
         case 7: return c->last_launches;
-        case 8: return c->fwd_chunk;
-        case 9: return c->bwd_chunk;
+        case 8: return c->shape[es_ctx::FUSED_TRANS_FWD].chunk;
+        case 9: return c->shape[es_ctx::FUSED_TRANS_BWD].chunk;
+        case 12: return c->shape[es_ctx::FUSED_EMIS_FWD].chunk;
+        case 13: return c->shape[es_ctx::FUSED_EMIS_BWD].chunk;
+        case 14: return c->shape[es_ctx::FUSED_MIXED_FWD].chunk;
+        case 15: return c->shape[es_ctx::FUSED_MIXED_BWD].chunk;
+        case 16: {
+            int64_t bits = 0;
+            for (int k = 0; k < es_ctx::N_FUSED; ++k) bits |= (int64_t)(c->shape[k].sample_major ? 1 : 0) << k;
+            return bits;
+        }
         case 10: return c->use_graph ? 1 : 0;
         case 11: {
             int v = -1;

@@ -139,9 +139,10 @@ extern "C" es_status es_loglike_noalloc(es_ctx *c, const double *theta, const in
     const es::Hook none{};
     int launches = 0;
     launches += es::launch_setup(c->m, w, st, none);
-    launches += es::launch_trans_fused_forward(c->m, w, false, 0, st, none);
+    // (the kinds are device data here: one kernel per kind, each skipping the other kind's items)
+    launches += es::launch_trans_fused_forward(c->m, w, false, 0, 0, st, none);
     if (kind) {
-        launches += es::launch_emis_fused_forward(c->m, w, false, st, none);
+        launches += es::launch_emis_fused_forward(c->m, w, false, 0, 0, st, none);
     }
     launches += es::launch_bins(c->m, w, false, nullptr, nullptr, lnl, st, none);
     c->last_launches = launches;

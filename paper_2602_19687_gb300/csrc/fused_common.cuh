@@ -328,6 +328,25 @@ __device__ __forceinline__ void extinction_pair(const Model &m, const SampleCons
     }
 }
 
+// Work items (sample b, wavenumber chunk c) of the persistent kernels, in one
+// of two orders: chunk-major (all samples of chunk 0, then chunk 1, ...: the
+// blocks running together share a wavenumber window of the coefficient table
+// in L2) or sample-major (all chunks of sample 0, then sample 1, ...: each
+// block stages fewer samples). The autotuner picks the order.
+struct ItemOrder {
+    int B, nchunks, sample_major;
+    __device__ __forceinline__ long long total() const { return (long long)B * nchunks; }
+    __device__ __forceinline__ void at(long long item, int &c, int &b) const {
+        if (sample_major) {
+            b = (int)(item / nchunks);
+            c = (int)(item % nchunks);
+        } else {
+            c = (int)(item / B);
+            b = (int)(item % B);
+        }
+    }
+};
+
 // Sum over the warp, on every lane.
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll

@@ -164,12 +164,27 @@ struct Hook {
 // kernel launchers (each returns the number of kernels launched)
 int launch_build_coef(const Model &m, float4 *coef, cudaStream_t st);
 int launch_setup(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
+// Fused persistent kernels. chunk: wavenumber tiles per work item (<= 0:
+// built-in heuristic); sample_major: work-item order (0 chunk-major, 1
+// sample-major). Transmission tiles are 128 wavenumbers, emission tiles 512;
+// the mixed kernels' window `wtiles` counts 128-wavenumber tiles (rounded to
+// whole emission tiles).
 // fused emission: interpolation + Schwarzschild integration (store_i keeps I_toa for the adjoint)
-int launch_emis_fused_forward(const Model &m, const Work &w, bool store_i, cudaStream_t st, const Hook &h);
-int launch_emis_fused_backward(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
-// chunk: wavenumber tiles per persistent work item (<= 0: built-in heuristic)
-int launch_trans_fused_forward(const Model &m, const Work &w, bool store_e, int chunk, cudaStream_t st, const Hook &h);
-int launch_trans_fused_backward(const Model &m, const Work &w, int chunk, cudaStream_t st, const Hook &h);
+int launch_emis_fused_forward(const Model &m, const Work &w, bool store_i, int chunk, int sample_major,
+                              cudaStream_t st, const Hook &h);
+int launch_emis_fused_backward(const Model &m, const Work &w, int chunk, int sample_major, cudaStream_t st,
+                               const Hook &h);
+int launch_trans_fused_forward(const Model &m, const Work &w, bool store_e, int chunk, int sample_major,
+                               cudaStream_t st, const Hook &h);
+int launch_trans_fused_backward(const Model &m, const Work &w, int chunk, int sample_major, cudaStream_t st,
+                                const Hook &h);
+// one kernel per direction over both kinds of a mixed batch (store: exp(-tau) and I_toa for the adjoint)
+int launch_mixed_fused_forward(const Model &m, const Work &w, bool store, int wtiles, int sample_major,
+                               cudaStream_t st, const Hook &h);
+int launch_mixed_fused_backward(const Model &m, const Work &w, int wtiles, int sample_major, cudaStream_t st,
+                                const Hook &h);
+// tiles per work item of the transmission kernels' heuristic
+int chunk_tiles(const Model &m, int B, int blocks, int tile);
 int launch_bins(const Model &m, const Work &w, bool want_adjoint, float *spectrum_out,
                 double *binned_out, double *lnl_out, cudaStream_t st, const Hook &h);
 // lnl_out: the call's ln L output, set to -1e300 for every sample when a kernel gave up on a bounded wait

@@ -122,13 +122,45 @@ def test_graph_replay_on_a_side_stream():
         _close(_run(ctx, w.theta, kind, stream=side), ref)
 
 
-def test_autotune_keeps_results():
-    w = synth.workload("batched_trans", batch=16, n_nu=5000)
+@pytest.mark.parametrize("kinds", ["trans", "emis", "mixed"])
+def test_autotune_keeps_results(kinds):
+    """The autotuner picks a work-item size and order for the kernels the
+    batch runs (transmission, emission, or the mixed kernel) and the results
+    stay those of the built-in shapes."""
+    w = synth.workload("highres", batch=12, n_nu=6000)
+    kind = {"trans": np.zeros(12, np.int32), "emis": np.ones(12, np.int32),
+            "mixed": (np.arange(12) % 2).astype(np.int32)}[kinds]
     ctx = binding.context_for(w)
-    kind = np.zeros(16, np.int32)
-    assert ctx.es_query(8) == 0 and ctx.es_query(9) == 0
+    assert all(v[0] == 0 for v in ctx.launch_shapes().values())
     ref = _run(ctx, w.theta, kind)
-    fwd, bwd = ctx.es_autotune()
-    assert fwd >= 1 and bwd >= 1
+    shapes = ctx.es_autotune()
+    tuned = {"trans": ("trans_fwd", "trans_bwd"), "emis": ("emis_fwd", "emis_bwd"),
+             "mixed": ("mixed_fwd", "mixed_bwd")}[kinds]
+    for k, (size, order) in shapes.items():
+        assert (size >= 1) == (k in tuned), (k, size)
+        assert order in ("chunk-major", "sample-major")
+    if kinds == "mixed":
+        assert shapes["mixed_fwd"][0] % 4 == 0 and shapes["mixed_bwd"][0] % 4 == 0
     for _ in range(3):
         _close(_run(ctx, w.theta, kind), ref)
+
+
+def test_mixed_batch_runs_one_kernel_per_direction_and_matches_single_kind_runs():
+    """A batch of both kinds runs setup, one mixed forward kernel and the
+    binning (3 launches for ln L; 5 with the adjoint), and each sample's ln L
+    and gradient equal those of the same sample in a single-kind batch (the
+    transmission-only and emission-only kernels)."""
+    w = synth.workload("highres", batch=10, n_nu=6000)
+    kind = np.array([0, 1, 1, 0, 1, 0, 0, 1, 0, 1], np.int32)
+    ctx = binding.context_for(w)
+    ctx.es_set_graphs(False)
+    lm, gm = _run(ctx, w.theta, kind)
+    assert ctx.es_query(7) == 5
+    _run(ctx, w.theta, kind, loglike_only=True)
+    assert ctx.es_query(7) == 3
+    for k in (0, 1):
+        sel = np.nonzero(kind == k)[0]
+        ls, gs = _run(ctx, w.theta[sel], kind[sel])
+        assert ctx.es_query(7) == 5
+        np.testing.assert_allclose(lm[sel], ls, rtol=1e-12, atol=0)
+        np.testing.assert_allclose(gm[sel], gs, rtol=1e-5, atol=1e-7 * max(1.0, np.abs(gs).max()))
