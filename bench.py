@@ -349,11 +349,12 @@ def emission_fp32_ops(name, w, n_valid):
 
 
 def measured_traffic(name, n_vectors):
-    """DRAM bytes per launch of `name` from the committed ncu capture, scaled
-    from its batch to n_vectors transmission vectors; None when the kernel
-    sources changed since the capture."""
+    """DRAM bytes per launch of `name` from the committed ncu captures
+    (profiles/traffic_k_trans.json: one capture per batch size), scaled from
+    the capture with the batch nearest to n_vectors transmission vectors;
+    None when the kernel sources changed since the captures."""
     import hashlib
-    p = os.path.join(ROOT, "profiles", "traffic_k_trans_b128.json")
+    p = os.path.join(ROOT, "profiles", "traffic_k_trans.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
@@ -361,8 +362,11 @@ def measured_traffic(name, n_vectors):
         with open(os.path.join(ROOT, rel), "rb") as f:
             if hashlib.sha256(f.read()).hexdigest() != digest:
                 return None
-    b = d["dram_bytes_per_launch"].get(name)
-    return None if b is None else b * n_vectors / d["capture_vectors"]
+    caps = [c for c in d["captures"] if name in c["dram_bytes_per_launch"]]
+    if not caps:
+        return None
+    c = min(caps, key=lambda c: abs(c["vectors"] - n_vectors))
+    return c["dram_bytes_per_launch"][name] * n_vectors / c["vectors"]
 
 
 def alu_peak(kind, sm_mhz):
@@ -627,7 +631,7 @@ def run_gpu(args):
                     "peak": peak / scale if peak else None,
                     "unit": "T%s/s" % unit_kind, "frac": (achieved / peak) if peak else None,
                     "traffic": measured_traffic(top, int(np.sum(w.kind[:n_valid] == 0))),
-                    "traffic_unit": "bytes per launch (ncu capture at B=128, scaled by vectors)",
+                    "traffic_unit": "bytes per launch (ncu capture at the nearest batch size, scaled by vectors)",
                     "ms_per_launch": ms_launch,
                     "peak_source": ("measured: es_probe_rates MUFU ex2 throughput on this GPU"
                                     if unit_kind == "ex2" else

@@ -95,7 +95,7 @@ struct __align__(16) LayerConst {
 struct SampleConst {
     LayerConst lay[ES_MAX_LAYERS];
     float lx[ES_MAX_SPECIES];   // log2 X_s + KSHIFT
-    int gb[8];                  // layer-group boundaries gb[0] = 0 < ... < gb[4] = L
+    int gb[12];                 // layer-group boundaries gb[0] = 0 <= ... <= gb[groups] = L
 };
 
 // Relative cost of starting a run of layers (a coefficient reload from L2)
@@ -104,9 +104,10 @@ struct SampleConst {
 // layers cost more: reductions and the pair exchange of alpha_bar).
 constexpr float RUN_COST_FWD = 3.f, RUN_COST_BWD = 1.f;
 
-// All threads of the block: per-layer constants of sample b into shared memory.
+// All threads of the block: per-layer constants of sample b into shared memory,
+// and the boundaries of `groups` (<= 11) layer groups of equal cost.
 __device__ inline void stage_sample(const Model &m, const Work &w, int b, SampleConst &sc, float run_cost,
-                                    int asbo = 0) {
+                                    int asbo = 0, int groups = 4) {
     const float ry = (float)(1.0 / ((double)m.ray_nu_ref * m.ray_nu_ref * m.ray_nu_ref * m.ray_nu_ref));
     const float il2 = (float)(1.0 / LOG2_10);
     const int L = m.L;
@@ -145,19 +146,20 @@ __device__ inline void stage_sample(const Model &m, const Work &w, int b, Sample
         sc.lay[l].run_end = r;
     }
     __syncthreads();
-    // four layer groups of equal cost: one per layer plus run_cost per run start
+    // layer groups of equal cost: one per layer plus run_cost per run start
     if (threadIdx.x == 0) {
         float total = 0.f;
         for (int l = 0; l < L; ++l) total += 1.f + ((l == 0 || sc.lay[l - 1].run_end == l) ? run_cost : 0.f);
+        const float share = 1.f / (float)groups;
         int g = 1;
         float acc = 0.f;
         sc.gb[0] = 0;
-        for (int l = 0; l < L && g < 4; ++l) {
+        for (int l = 0; l < L && g < groups; ++l) {
             acc += 1.f + ((l == 0 || sc.lay[l - 1].run_end == l) ? run_cost : 0.f);
-            if (acc >= total * (float)g * 0.25f) sc.gb[g++] = l + 1;
+            if (acc >= total * (float)g * share) sc.gb[g++] = l + 1;
         }
-        while (g < 4) sc.gb[g++] = L;
-        sc.gb[4] = L;
+        while (g < groups) sc.gb[g++] = L;
+        sc.gb[groups] = L;
     }
 }
 

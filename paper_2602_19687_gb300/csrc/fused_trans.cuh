@@ -30,7 +30,7 @@ namespace {
 
 constexpr float LOG2E_F = 1.4426950408889634f;
 
-// Forward block: 16 warps, 128-wavenumber tiles; the chord product runs on
+// Forward block: NW (16 or 24) warps, 128-wavenumber tiles; the chord product runs on
 // the tcgen05 tensor cores with the accumulator in TMEM, double-buffered: the
 // epilogue of tile t - 1 overlaps the product of tile t, whose completion
 // then frees the (single) extinction operand for tile t + 1 (one block
@@ -43,20 +43,24 @@ constexpr int SBO_NU = (FT2 / 8) * CORE_STRIDE;   // 8-row group stride of [row]
 constexpr int SBO_LP = (LP / 8) * CORE_STRIDE;    // 8-row group stride of [row][112 layers] operands (2016 B)
 constexpr int F2_TMEM_COLS = 256;                 // two 112-column accumulators
 
-struct TransFwdSmem {
+// NW warps: NW / 4 layer groups x 4 wavenumber quarters (the TMEM lane
+// quadrants) in the interpolation, NW / 4 impact-parameter chunks in the epilogue
+template <int NW>
+struct TransFwdSmemT {
     SampleConst sc;
     alignas(128) unsigned char lh[(LP / 8) * SBO_LP], ll[(LP / 8) * SBO_LP];    // L[i][l], split BF16
     alignas(128) unsigned char ah[1][(LP / 8) * SBO_NU], al[1][(LP / 8) * SBO_NU];   // alpha[l][nu], split BF16
     float area[LP];
     float cd[LP];                                  // non-grey cloud: D_i (0 beyond L)
     float cg[N_CG];                                // non-grey cloud: g(nu) constants (kh18_g)
-    float part[2][4][FT2];                         // per-column-chunk partial transit sums, per buffer
+    float part[2][NW / 4][FT2];                    // per-column-chunk partial transit sums, per buffer
     alignas(8) uint64_t mbar[2];
     uint32_t tmem_base;
     int abort;
 };
+using TransFwdSmem = TransFwdSmemT<16>;
 
-// Backward block: 16 warps, 128-wavenumber tiles; both products on the
+// Backward block: NW (16 or 24) warps, 128-wavenumber tiles; both products on the
 // tcgen05 tensor cores: alpha_bar^T = tau_bar^T L into TMEM columns [0, 112)
 // (read there by the interpolation warps) and L_bar = tau_bar alpha^T
 // accumulated over the sample's tiles in TMEM columns [128, 256).
@@ -69,9 +73,13 @@ constexpr int LB_ROWS = 128;         // rows of the alpha operand: layers, the R
 // the Rayleigh reduction W4_l = sum_nu alpha_bar_l(nu) w(nu) = sum_i L_il z_i
 // follows.
 
-struct TransBwdSmem {
+// STAGE: per-warp shared-memory staging of the coefficients (see
+// interp_backward); LSPLIT: L as split BF16 (hi + lo) in alpha_bar = L^T tau_bar,
+// else single BF16 (tau_bar is single BF16 there in any case)
+template <int NW, bool STAGE, bool LSPLIT = true>
+struct TransBwdSmemT {
     SampleConst sc;
-    alignas(128) unsigned char lh[(LP / 8) * SBO_LP], ll[(LP / 8) * SBO_LP];      // L[i][l]
+    alignas(128) unsigned char lh[(LP / 8) * SBO_LP], ll[LSPLIT ? (LP / 8) * SBO_LP : 16];      // L[i][l]
     // adjoint operands as single BF16 (the gradient tolerance is 1e-3; the
     // measured error of these products is ~1e-6 relative): tau_bar[i][nu], alpha[l][nu]
     alignas(128) unsigned char th[(LP / 8) * SBO_NU];
@@ -85,11 +93,12 @@ struct TransBwdSmem {
     // non-grey cloud: D_i, its adjoint, d lnL / d g(nu) of the tile, the
     // g(nu) constants and the parameter adjoints of the sample
     float cd[LP], cdbar[LP], gbar[BT], cg[N_CG], cpbar[N_CG];
-    alignas(16) unsigned char stage[BW_WARPS][STAGE_BYTES_PER_WARP];   // per-warp coefficient staging
+    alignas(16) unsigned char stage[STAGE ? NW : 1][STAGE_BYTES_PER_WARP];   // per-warp coefficient staging
     alignas(8) uint64_t mbar_a, mbar_l;
     uint32_t tmem_base;
     int abort;
 };
+using TransBwdSmem = TransBwdSmemT<16, true>;
 
 // Path-length matrix of sample b as the split BF16 tensor-core operand
 // L[i][l] (112 x 112, zero-padded, core-matrix layout) and the annulus areas.
@@ -108,7 +117,7 @@ __device__ void stage_lmat_tc(const Model &m, const Work &w, int b, unsigned cha
         split2(v, hi, lo);
         const uint32_t o = op_off(i, l, SBO_LP);
         *reinterpret_cast<uint32_t *>(lh + o) = hi;
-        *reinterpret_cast<uint32_t *>(ll + o) = lo;
+        if (ll) *reinterpret_cast<uint32_t *>(ll + o) = lo;   // (ll NULL: single BF16 L)
     }
     for (int i = threadIdx.x; i < LP; i += blockDim.x) area[i] = (i < L) ? w.area[(size_t)b * L + i] : 0.f;
 }
@@ -121,11 +130,15 @@ __device__ void stage_lmat_tc(const Model &m, const Work &w, int b, unsigned cha
 // drive it with their own work-item loops.
 // CLOUD: the non-grey cloud and cloud fraction (ES_CLOUD_KH18) as a separate
 // instantiation, so that the cloud-free kernels carry none of its code.
-template <int SPL, bool STORE_E, bool CLOUD>
+template <int SPL, bool STORE_E, bool CLOUD, int NW = 16>
 struct TransFwdEngine {
+    static constexpr int NT = NW * 32, NCK = NW / 4;
+    // the warp that issues the chord product: one of the lightest epilogue shares
+    static constexpr int ISSUER = NW == 16 ? 12 : (NW == 24 ? 20 : NW - 4);
+    static_assert(NW == 16 || NW == 24 || NW == 32, "4, 6 or 8 layer groups");
     const Model &m;
     const Work &w;
-    TransFwdSmem &sm;
+    TransFwdSmemT<NW> &sm;
     const int warp, lane, half, vq, pair, grp, ck, L, N, ntiles;
     // interpolation: 4 layer groups x 4 quarters (32 wavenumbers) of the tile;
     // a wavenumber pair is shared by a lane pair splitting the species. Lane
@@ -145,7 +158,7 @@ struct TransFwdEngine {
     int spec_b = -1, spec_t = 0, spec_buf = 0;
     bool abort = false;
 
-    __device__ __forceinline__ TransFwdEngine(const Model &m_, const Work &w_, TransFwdSmem &sm_)
+    __device__ __forceinline__ TransFwdEngine(const Model &m_, const Work &w_, TransFwdSmemT<NW> &sm_)
         : m(m_), w(w_), sm(sm_), warp(threadIdx.x >> 5), lane(threadIdx.x & 31), half(lane & 1), vq(warp & 3),
           pair(16 * vq + (lane >> 1)), grp(warp >> 2), ck(warp >> 2), L(m_.L), N(m_.N), ntiles((m_.N + FT2 - 1) / FT2),
           a_off(op_off(0, 2 * pair, SBO_NU)), mbar0(smem_u32(&sm_.mbar[0])), lh_s(smem_u32(sm_.lh)),
@@ -154,7 +167,7 @@ struct TransFwdEngine {
     // whole block, once: zero padding rows, mbarriers (mbar[1] 8 bytes above mbar[0]), TMEM
     __device__ __forceinline__ void setup() {
         // extinction rows of the padding layers stay zero
-        for (int idx = threadIdx.x; idx < (LP - L) * (FT2 / 2); idx += F2_THREADS) {
+        for (int idx = threadIdx.x; idx < (LP - L) * (FT2 / 2); idx += NT) {
             const uint32_t o = op_off(L + idx / (FT2 / 2), 2 * (idx % (FT2 / 2)), SBO_NU);
             *reinterpret_cast<uint32_t *>(sm.ah[0] + o) = 0u;
             *reinterpret_cast<uint32_t *>(sm.al[0] + o) = 0u;
@@ -177,20 +190,36 @@ struct TransFwdEngine {
         tc_fence_after();
     }
 
+    // impact parameters of epilogue chunk ck from cstart(): 4 chunks of 28 (16
+    // warps), 4 of 20 and 2 of 16 (24 warps), or 8 of 14 (32 warps)
+    __device__ __forceinline__ int cstart() const {
+        return NCK == 4 ? 28 * ck : (NCK == 8 ? 14 * ck : (ck < 4 ? 20 * ck : 80 + 16 * (ck - 4)));
+    }
+
     __device__ __forceinline__ void epilogue(int pb, int pt, int buf) {
         const int nl = 32 * vq + lane;
-        const uint32_t taddr = tmem + (uint32_t)(buf * 128 + 28 * ck) + ((uint32_t)(32 * vq) << 16);
-        float v16[16], v8[8], v4[4];
-        tmem_ld16(taddr, v16);
-        tmem_ld8(taddr + 16, v8);
-        tmem_ld4(taddr + 24, v4);
+        const int c0 = cstart();
+        // (24 warps: the x8 load and the last columns of the x4 load lie past a
+        // 20- or 16-column chunk; they stay inside the allocation and are unused)
+        const bool wide = NCK == 4 || ck < 4;   // chunk of 28 / 20 (vs 16) columns
+        const uint32_t taddr = tmem + (uint32_t)(buf * 128 + c0) + ((uint32_t)(32 * vq) << 16);
+        float v16[16], v8[8], v4[4], v2[2];
+        if (NCK == 8) {   // 14 = 8 + 4 + 2 columns
+            tmem_ld8(taddr, v8);
+            tmem_ld4(taddr + 8, v4);
+            tmem_ld2(taddr + 12, v2);
+        } else {
+            tmem_ld16(taddr, v16);
+            if (NCK == 4) tmem_ld8(taddr + 16, v8);
+            tmem_ld4(taddr + (NCK == 4 ? 24 : 16), v4);
+        }
         tmem_wait_ld();
         // exp(-tau) store, tile-contiguous: [vector][tile][impact parameter][128 nu]
-        float *eb = w.estore + (((size_t)pb * ntiles + pt) * L + 28 * ck) * FT2 + nl;
+        float *eb = w.estore + (((size_t)pb * ntiles + pt) * L + c0) * FT2 + nl;
         float2 s2 = f2(0.f);
-        // terms i0 = 28 ck + k and i0 + 1 in packed pairs; area[i] = 0 beyond L
+        // terms i0 = c0 + k and i0 + 1 in packed pairs; area[i] = 0 beyond L
         auto term2 = [&](int k, float t0, float t1) {
-            const int i0 = 28 * ck + k;
+            const int i0 = c0 + k;
             const float2 e = ex2x2(mul2(make_float2(t0, t1), f2(-LOG2E_F)));
             const float2 a = *reinterpret_cast<const float2 *>(&sm.area[i0]);
             s2 = fma2(a, fma2(e, f2(-1.f), f2(1.f)), s2);
@@ -201,13 +230,25 @@ struct TransFwdEngine {
             }
         };
         float s;
-        if (!CLOUD) {
+        if (!CLOUD && NCK == 8) {
+#pragma unroll
+            for (int k = 0; k < 8; k += 2) term2(k, v8[k], v8[k + 1]);
+#pragma unroll
+            for (int k = 0; k < 4; k += 2) term2(8 + k, v4[k], v4[k + 1]);
+            term2(12, v2[0], v2[1]);
+            s = s2.x + s2.y;
+        } else if (!CLOUD) {
 #pragma unroll
             for (int k = 0; k < 16; k += 2) term2(k, v16[k], v16[k + 1]);
+            if (NCK == 4) {
 #pragma unroll
-            for (int k = 0; k < 8; k += 2) term2(16 + k, v8[k], v8[k + 1]);
+                for (int k = 0; k < 8; k += 2) term2(16 + k, v8[k], v8[k + 1]);
 #pragma unroll
-            for (int k = 0; k < 4; k += 2) term2(24 + k, v4[k], v4[k + 1]);
+                for (int k = 0; k < 4; k += 2) term2(24 + k, v4[k], v4[k + 1]);
+            } else if (NCK == 6 && wide) {
+#pragma unroll
+                for (int k = 0; k < 4; k += 2) term2(16 + k, v4[k], v4[k + 1]);
+            }
             s = s2.x + s2.y;
         } else {
             // non-grey cloud (Sect. 2.5): the cloudy chord depth is tau_i + g(nu) D_i,
@@ -217,7 +258,7 @@ struct TransFwdEngine {
             const float2 gl = f2(-g * LOG2E_F);
             float2 s2c = f2(0.f);
             auto term2c = [&](int k, float t0, float t1) {
-                const int i0 = 28 * ck + k;
+                const int i0 = c0 + k;
                 const float2 e = ex2x2(mul2(make_float2(t0, t1), f2(-LOG2E_F)));
                 const float2 a = *reinterpret_cast<const float2 *>(&sm.area[i0]);
                 const float2 d = *reinterpret_cast<const float2 *>(&sm.cd[i0]);
@@ -229,12 +270,25 @@ struct TransFwdEngine {
                     if (i0 + 1 < L) __stcs(eb + (k + 1) * FT2, e.y);
                 }
             };
+            if (NCK == 8) {
+#pragma unroll
+                for (int k = 0; k < 8; k += 2) term2c(k, v8[k], v8[k + 1]);
+#pragma unroll
+                for (int k = 0; k < 4; k += 2) term2c(8 + k, v4[k], v4[k + 1]);
+                term2c(12, v2[0], v2[1]);
+            } else {
 #pragma unroll
             for (int k = 0; k < 16; k += 2) term2c(k, v16[k], v16[k + 1]);
+            }
+            if (NCK == 4) {
 #pragma unroll
-            for (int k = 0; k < 8; k += 2) term2c(16 + k, v8[k], v8[k + 1]);
+                for (int k = 0; k < 8; k += 2) term2c(16 + k, v8[k], v8[k + 1]);
 #pragma unroll
-            for (int k = 0; k < 4; k += 2) term2c(24 + k, v4[k], v4[k + 1]);
+                for (int k = 0; k < 4; k += 2) term2c(24 + k, v4[k], v4[k + 1]);
+            } else if (NCK == 6 && wide) {
+#pragma unroll
+                for (int k = 0; k < 4; k += 2) term2c(16 + k, v4[k], v4[k + 1]);
+            }
             s = sm.cg[3] * (s2c.x + s2c.y) + (1.f - sm.cg[3]) * (s2.x + s2.y);
         }
         sm.part[buf][ck][nl] = s;
@@ -244,9 +298,10 @@ struct TransFwdEngine {
         if (threadIdx.x < FT2) {
             const int n = pt * FT2 + threadIdx.x;
             const float(*pp)[FT2] = sm.part[buf];
-            if (n < N)
-                w.spec[(size_t)pb * N + n] = (pp[0][threadIdx.x] + pp[1][threadIdx.x]) +
-                                             (pp[2][threadIdx.x] + pp[3][threadIdx.x]);
+            float v = (pp[0][threadIdx.x] + pp[1][threadIdx.x]) + (pp[2][threadIdx.x] + pp[3][threadIdx.x]);
+            if (NCK >= 6) v += pp[4][threadIdx.x] + pp[5][threadIdx.x];
+            if (NCK == 8) v += pp[6][threadIdx.x] + pp[7][threadIdx.x];
+            if (n < N) w.spec[(size_t)pb * N + n] = v;
         }
     }
 
@@ -265,7 +320,7 @@ struct TransFwdEngine {
     __device__ __forceinline__ void stage_operands(int b) {
         stage_lmat_tc(m, w, b, sm.lh, sm.ll, sm.area);
         if (CLOUD) {
-            for (int i = threadIdx.x; i < LP; i += F2_THREADS) sm.cd[i] = (i < L) ? w.cloud_d[(size_t)b * L + i] : 0.f;
+            for (int i = threadIdx.x; i < LP; i += NT) sm.cd[i] = (i < L) ? w.cloud_d[(size_t)b * L + i] : 0.f;
             if (threadIdx.x < N_CG) sm.cg[threadIdx.x] = w.cloud_g[(size_t)b * N_CG + threadIdx.x];
         }
     }
@@ -296,7 +351,7 @@ struct TransFwdEngine {
                 spec_b = -1;
             }
             // (wait_test: no product is issued, so the wait below runs out and the block aborts)
-            if (threadIdx.x == 12 * 32 && !m.wait_test) {   // warp 12's epilogue share is the lightest: 7 k-steps x 3 split terms
+            if (threadIdx.x == ISSUER * 32 && !m.wait_test) {   // 7 k-steps x 3 split terms
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(buf * 128);
                 // descriptors of k-step 0; a k-step advances the start address field
@@ -443,7 +498,7 @@ __device__ __forceinline__ void tmem_wait1(uint32_t &r) {
 // adds them and applies the per-layer weight slopes gts, gtcs); per species
 // Q_s = sum_l sum abar n e_s. The Rayleigh sum over wavenumber comes from the
 // L_bar product.
-template <int SPL, class Wait>
+template <int SPL, bool STAGE, class Wait>
 __device__ void interp_backward(const Model &m, const SampleConst &sc, int lb, int le, int n, int half, int lane,
                                 uint32_t abar_t, unsigned char *a_dst, float *red, float *qtot, uint32_t stg,
                                 bool prestaged, int next_shift, Wait &&wait_abar) {
@@ -463,7 +518,7 @@ __device__ void interp_backward(const Model &m, const SampleConst &sc, int lb, i
     // loop bounds broadcast from lane 0: provably warp-uniform for the compiler
     lb = __shfl_sync(0xffffffffu, lb, 0);
     le = __shfl_sync(0xffffffffu, le, 0);
-    constexpr bool STAGED = 2 * SPL + 1 <= STAGE_BLOCKS;   // else direct loads with an L1 prefetch
+    constexpr bool STAGED = STAGE && 2 * SPL + 1 <= STAGE_BLOCKS;   // else direct loads with an L1 prefetch
     if (STAGED && lb < le && !prestaged) pi.stage(stg, sc.lay[lb].cell, sc.lay[lb].itc, 0);
     for (int l = lb; l < le;) {
         const int end = __shfl_sync(0xffffffffu, min(sc.lay[l].run_end, le), 0);
@@ -540,13 +595,19 @@ __device__ void interp_backward(const Model &m, const SampleConst &sc, int lb, i
 // of one work item with the L2 prefetch of the next item's first tile, the
 // flush of a sample's sums, teardown), driven by the transmission-only and
 // the mixed kernels.
-template <int SPL, bool CLOUD>
+// NW warps (16, 20 or 24); STAGE: coefficients through the per-warp staging
+// slots; LSPLIT: split BF16 L in alpha_bar = L^T tau_bar.
+template <int SPL, bool CLOUD, int NW = 16, bool STAGE = true, bool LSPLIT = true>
 struct TransBwdEngine {
+    static constexpr int NT = NW * 32;
+    // tau_bar phase: NW / 2 row groups of two warps (128 wavenumbers), rows
+    // i = group + ROWG k for k < KR
+    static constexpr int ROWG = NW / 2, KR = (LP + ROWG - 1) / ROWG;
     const Model &m;
     const Work &w;
-    TransBwdSmem &sm;
+    TransBwdSmemT<NW, STAGE, LSPLIT> &sm;
     const int warp, lane, L, N, S, ntiles;
-    const int group;                                     // tau_bar phase: rows i = group + 8 k
+    const int group;
     // interpolation: 4 layer groups x 4 quarters (32 wavenumbers); lane pairs split species
     const int half, vq, pair, grp;
     const int NL;                                        // L_bar product N: layers and the weight row
@@ -564,7 +625,7 @@ struct TransBwdEngine {
     uint32_t pa = 0, pl = 0;
     bool l_pending = false, l_started = false, abort = false;
 
-    __device__ __forceinline__ TransBwdEngine(const Model &m_, const Work &w_, TransBwdSmem &sm_)
+    __device__ __forceinline__ TransBwdEngine(const Model &m_, const Work &w_, TransBwdSmemT<NW, STAGE, LSPLIT> &sm_)
         : m(m_), w(w_), sm(sm_), warp(threadIdx.x >> 5), lane(threadIdx.x & 31), L(m_.L), N(m_.N), S(m_.S),
           ntiles((m_.N + BT - 1) / BT), group(warp >> 1), half(lane & 1), vq(warp & 3), pair(16 * vq + (lane >> 1)),
           grp(warp >> 2), NL((m_.L + 1 + 15) & ~15),
@@ -572,18 +633,18 @@ struct TransBwdEngine {
           mbar_a(smem_u32(&sm_.mbar_a)), mbar_l(smem_u32(&sm_.mbar_l)), idesc_a(idesc_bf16(BT, LP, true, true)),
           idesc_l(idesc_bf16(LB_ROWS, NL, false, false)), lh_s(smem_u32(sm_.lh)), ll_s(smem_u32(sm_.ll)),
           th_s(smem_u32(sm_.th)), ah_s(smem_u32(sm_.ah)), a_dst(sm_.ah + op_off(0, 2 * pair, SBO_NU)),
-          stg(smem_u32(sm_.stage[warp]) + 16u * (uint32_t)lane) {}
+          stg(smem_u32(sm_.stage[STAGE ? warp : 0]) + 16u * (uint32_t)lane) {}
 
     // whole block, once: zero padding rows, mbarriers, TMEM
     __device__ __forceinline__ void setup() {
         if (CLOUD)
-            for (int i = threadIdx.x; i < BT; i += BW_THREADS) sm.gbar[i] = 0.f;
+            for (int i = threadIdx.x; i < BT; i += NT) sm.gbar[i] = 0.f;
         // padding rows stay zero: tau_bar rows [L, 112), alpha rows [L + 1, 128)
-        for (int idx = threadIdx.x; idx < (LP - L) * (BT / 2); idx += BW_THREADS) {
+        for (int idx = threadIdx.x; idx < (LP - L) * (BT / 2); idx += NT) {
             const uint32_t o = op_off(L + idx / (BT / 2), 2 * (idx % (BT / 2)), SBO_NU);
             *reinterpret_cast<uint32_t *>(sm.th + o) = 0u;
         }
-        for (int idx = threadIdx.x; idx < (LB_ROWS - L - 1) * (BT / 2); idx += BW_THREADS) {
+        for (int idx = threadIdx.x; idx < (LB_ROWS - L - 1) * (BT / 2); idx += NT) {
             const uint32_t o = op_off(L + 1 + idx / (BT / 2), 2 * (idx % (BT / 2)), SBO_NU);
             *reinterpret_cast<uint32_t *>(sm.ah + o) = 0u;
         }
@@ -615,6 +676,8 @@ struct TransBwdEngine {
         float *lbar = w.lbar + (size_t)b * L * L;
         double *zbar = w.zbar + (size_t)b * L;
         const int ck = warp >> 2, ii = 32 * vq + lane;
+        // the L_bar columns [128, 256): 4 chunks of 32 over the first 16 warps
+        if (ck < 4) {
         float v0[16], v1[16];
         const uint32_t ta = tmem + (uint32_t)(128 + 32 * ck) + ((uint32_t)(32 * vq) << 16);
         tmem_ld16(ta, v0);
@@ -630,9 +693,10 @@ struct TransBwdEngine {
                 else if (ll <= ii) atomicAdd(lbar + (size_t)ii * L + ll, v);
             }
         }
+        }
         tc_fence_before();
         __syncthreads();
-        for (int idx = threadIdx.x; idx < L * 8; idx += BW_THREADS) {
+        for (int idx = threadIdx.x; idx < L * 8; idx += NT) {
             const int l = idx >> 3, s = idx & 7;
             const float *q = sm.red + l * 32 + 4 * s;
             float v = (q[0] + q[1]) + (q[2] + q[3]);
@@ -640,12 +704,12 @@ struct TransBwdEngine {
             if (s >= 6) v *= sm.sc.lay[l].gtcs;            // CT: of the CIA exponents
             if (v != 0.f) atomicAdd(w.red + ((size_t)b * L + l) * N_RED + s, (double)v);
         }
-        for (int i = threadIdx.x; i < L; i += BW_THREADS)
+        for (int i = threadIdx.x; i < L; i += NT)
             if (sm.area_acc[i] != 0.f) atomicAdd(w.areabar + (size_t)b * L + i, (double)sm.area_acc[i]);
-        for (int s2 = threadIdx.x; s2 < S; s2 += BW_THREADS)
+        for (int s2 = threadIdx.x; s2 < S; s2 += NT)
             if (sm.qtot[s2] != 0.f) atomicAdd(w.qtot + (size_t)b * S + s2, (double)sm.qtot[s2]);
         if (CLOUD) {
-            for (int i = threadIdx.x; i < L; i += BW_THREADS)
+            for (int i = threadIdx.x; i < L; i += NT)
                 if (sm.cdbar[i] != 0.f) atomicAdd(w.cloud_dbar + (size_t)b * L + i, (double)sm.cdbar[i]);
             if (threadIdx.x < N_CG && sm.cpbar[threadIdx.x] != 0.f)
                 atomicAdd(w.cloud_pbar + (size_t)b * N_CG + threadIdx.x, (double)sm.cpbar[threadIdx.x]);
@@ -669,12 +733,12 @@ struct TransBwdEngine {
     // per-sample sums and cloud constants (its layer constants are staged by
     // the caller); the L_bar accumulator restarts
     __device__ __forceinline__ void stage_operands(int b) {
-        stage_lmat_tc(m, w, b, sm.lh, sm.ll, sm.area);
-        for (int idx = threadIdx.x; idx < L * 32; idx += BW_THREADS) sm.red[idx] = 0.f;
-        for (int i = threadIdx.x; i < LP; i += BW_THREADS) sm.area_acc[i] = 0.f;
-        for (int s2 = threadIdx.x; s2 < ES_MAX_SPECIES; s2 += BW_THREADS) sm.qtot[s2] = 0.f;
+        stage_lmat_tc(m, w, b, sm.lh, LSPLIT ? sm.ll : nullptr, sm.area);
+        for (int idx = threadIdx.x; idx < L * 32; idx += NT) sm.red[idx] = 0.f;
+        for (int i = threadIdx.x; i < LP; i += NT) sm.area_acc[i] = 0.f;
+        for (int s2 = threadIdx.x; s2 < ES_MAX_SPECIES; s2 += NT) sm.qtot[s2] = 0.f;
         if (CLOUD) {
-            for (int i = threadIdx.x; i < LP; i += BW_THREADS) {
+            for (int i = threadIdx.x; i < LP; i += NT) {
                 sm.cd[i] = (i < L) ? w.cloud_d[(size_t)b * L + i] : 0.f;
                 sm.cdbar[i] = 0.f;
             }
@@ -701,10 +765,10 @@ struct TransBwdEngine {
             const int nl = nt0 + col;
             const float2 db = *reinterpret_cast<const float2 *>(w.dbar + (size_t)b * m.Np + nl);
             const float *eb = w.estore + ((size_t)b * ntiles + t) * L * BT + col;
-            float2 ev[14];
+            float2 ev[KR];
 #pragma unroll
-            for (int k = 0; k < 14; ++k) {
-                const int i = group + 8 * k;
+            for (int k = 0; k < KR; ++k) {
+                const int i = group + ROWG * k;
                 ev[k] = (i < L) ? *reinterpret_cast<const float2 *>(eb + i * BT) : make_float2(1.f, 1.f);
             }
             wait_lbar();
@@ -721,8 +785,8 @@ struct TransBwdEngine {
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
                     av[k] = 0.f;
-                    const int i = group + 8 * k;
-                    if (k < 14 && i < L) {
+                    const int i = group + ROWG * k;
+                    if (k < KR && i < L) {
                         const float2 e = ev[k];
                         const float a = sm.area[i];
                         const uint32_t o = op_off(i, col, SBO_NU);
@@ -731,8 +795,8 @@ struct TransBwdEngine {
                     }
                 }
                 const float tot = transpose_reduce16(av, lane);
-                const int k = reduce_index(lane), i = group + 8 * k;
-                if ((lane & 1) == 0 && k < 14 && i < L && tot != 0.f) atomicAdd(sm.area_acc + i, tot);
+                const int k = reduce_index(lane), i = group + ROWG * k;
+                if ((lane & 1) == 0 && k < KR && i < L && tot != 0.f) atomicAdd(sm.area_acc + i, tot);
             } else {
                 // non-grey cloud: E_i = f e_cld + (1 - f) e with e_cld = e 2^(-g D_i log2 e);
                 // tau_bar = dbar A_i E_i, area_bar += dbar (1 - E_i), and the
@@ -746,8 +810,8 @@ struct TransBwdEngine {
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
                     av[k] = dv[k] = 0.f;
-                    const int i = group + 8 * k;
-                    if (k < 14 && i < L) {
+                    const int i = group + ROWG * k;
+                    if (k < KR && i < L) {
                         const float2 e = ev[k];
                         const float a = sm.area[i], d = sm.cd[i];
                         const float2 ec = mul2(e, ex2x2(mul2(gl, f2(d))));
@@ -763,8 +827,8 @@ struct TransBwdEngine {
                 }
                 const float tot = transpose_reduce16(av, lane);
                 const float totd = transpose_reduce16(dv, lane);
-                const int k = reduce_index(lane), i = group + 8 * k;
-                if ((lane & 1) == 0 && k < 14 && i < L) {
+                const int k = reduce_index(lane), i = group + ROWG * k;
+                if ((lane & 1) == 0 && k < KR && i < L) {
                     if (tot != 0.f) atomicAdd(sm.area_acc + i, tot);
                     if (totd != 0.f) atomicAdd(sm.cdbar + i, totd);
                 }
@@ -787,7 +851,7 @@ struct TransBwdEngine {
                 for (int k = 0; k < LP / 16; ++k) {   // start address field advances by 2 row groups
                     const uint64_t da = (uint64_t)(k * 2 * SBO_NU / 16), db2 = (uint64_t)(k * 2 * SBO_LP / 16);
                     tc_mma(tmem, a_h + da, b_h + db2, idesc_a, k > 0);
-                    tc_mma(tmem, a_h + da, b_l + db2, idesc_a, true);
+                    if (LSPLIT) tc_mma(tmem, a_h + da, b_l + db2, idesc_a, true);
                 }
                 tc_commit(mbar_a);
             }
@@ -799,7 +863,7 @@ struct TransBwdEngine {
                 if (gb != 0.f) kh18_g_adjoint(sm.cg, m.nu[nt0 + threadIdx.x], gb, o);
                 cloud_pbar_add(sm.cg, o, sm.cpbar, lane);
             }
-            interp_backward<SPL>(m, sm.sc, sm.sc.gb[grp], sm.sc.gb[grp + 1], nt0 + 2 * pair, half, lane, abar_t, a_dst,
+            interp_backward<SPL, STAGE>(m, sm.sc, sm.sc.gb[grp], sm.sc.gb[grp + 1], nt0 + 2 * pair, half, lane, abar_t, a_dst,
                                  sm.red, sm.qtot, stg, t > t0, t + 1 < t1 ? BT : 0, [&]() {
                                      if (!mbar_wait(mbar_a, pa, m.wait_polls)) sm.abort = 1;
                                      tc_fence_after();

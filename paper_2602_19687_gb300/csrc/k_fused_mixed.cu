@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_mixed_fwd(Model m, Work w, in
             }
             tc_fence_before();
             __syncthreads();
-            stage_sample(m, w, b, sm.t.sc, RUN_COST_FWD, SBO_NU);
+            stage_sample(m, w, b, sm.t.sc, RUN_COST_FWD, SBO_NU, F2_WARPS / 4);
             if (trans) te.stage_operands(b);
             else stage_levels<CLOUD>(m, w, b, v);
             cur_b = b;
@@ -125,10 +125,10 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_mixed_bwd(Model m, Work w, in
             tc_fence_before();
             __syncthreads();
             if (trans) {
-                stage_sample(m, w, b, sm.t.sc, RUN_COST_BWD, SBO_NU);
+                stage_sample(m, w, b, sm.t.sc, RUN_COST_BWD, SBO_NU, BW_WARPS / 4);
                 te.stage_operands(b);
             } else {
-                stage_sample(m, w, b, sm.t.sc, RUN_COST_FWD, SBO_NU);
+                stage_sample(m, w, b, sm.t.sc, RUN_COST_FWD, SBO_NU, BW_WARPS / 4);
                 stage_levels<CLOUD>(m, w, b, v);
                 Emis(m, w, v).reset();
             }

@@ -10,11 +10,20 @@ namespace es {
 
 namespace {
 
+// Block shapes of the transmission-only kernels (measured at B = 1024): the
+// forward with 24 warps (6 layer groups x 4 wavenumber quarters, 78-80
+// registers) per SM; the adjoint with 16 warps, its coefficients staged
+// per warp through shared memory, L split in alpha_bar = L^T tau_bar.
+constexpr int FWD_WARPS = 24, BWD_WARPS = 16;
+constexpr bool BWD_STAGE = true, BWD_LSPLIT = true;
+using FwdSmem = TransFwdSmemT<FWD_WARPS>;
+using BwdSmem = TransBwdSmemT<BWD_WARPS, BWD_STAGE, BWD_LSPLIT>;
+
 template <int SPL, bool STORE_E, bool CLOUD>
-__global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, int chunk_tiles, int sample_major) {
+__global__ void __launch_bounds__(FWD_WARPS * 32, 1) k_trans_fwd(Model m, Work w, int chunk_tiles, int sample_major) {
     extern __shared__ float4 smem4[];
-    TransFwdSmem &sm = *reinterpret_cast<TransFwdSmem *>(smem4);
-    TransFwdEngine<SPL, STORE_E, CLOUD> e(m, w, sm);
+    FwdSmem &sm = *reinterpret_cast<FwdSmem *>(smem4);
+    TransFwdEngine<SPL, STORE_E, CLOUD, FWD_WARPS> e(m, w, sm);
     e.setup();
     const int ntiles = (m.N + FT2 - 1) / FT2;
     const ItemOrder order{w.B, (ntiles + chunk_tiles - 1) / chunk_tiles, sample_major};
@@ -31,7 +40,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, in
             }
             tc_fence_before();
             __syncthreads();
-            stage_sample(m, w, b, sm.sc, RUN_COST_FWD, SBO_NU);
+            stage_sample(m, w, b, sm.sc, RUN_COST_FWD, SBO_NU, FWD_WARPS / 4);
             e.stage_operands(b);
             cur_b = b;
             fence_async_smem();
@@ -43,10 +52,10 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_trans_fwd(Model m, Work w, in
 }
 
 template <int SPL, bool CLOUD>
-__global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, int chunk_tiles, int sample_major) {
+__global__ void __launch_bounds__(BWD_WARPS * 32, 1) k_trans_bwd(Model m, Work w, int chunk_tiles, int sample_major) {
     extern __shared__ float4 smem4[];
-    TransBwdSmem &sm = *reinterpret_cast<TransBwdSmem *>(smem4);
-    TransBwdEngine<SPL, CLOUD> e(m, w, sm);
+    BwdSmem &sm = *reinterpret_cast<BwdSmem *>(smem4);
+    TransBwdEngine<SPL, CLOUD, BWD_WARPS, BWD_STAGE, BWD_LSPLIT> e(m, w, sm);
     e.setup();
     const int ntiles = (m.N + BT - 1) / BT;
     const ItemOrder order{w.B, (ntiles + chunk_tiles - 1) / chunk_tiles, sample_major};
@@ -81,7 +90,7 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
             }
             tc_fence_before();
             __syncthreads();
-            stage_sample(m, w, b, sm.sc, RUN_COST_BWD, SBO_NU);
+            stage_sample(m, w, b, sm.sc, RUN_COST_BWD, SBO_NU, BWD_WARPS / 4);
             e.stage_operands(b);
             cur_b = b;
             fence_async_smem();
@@ -98,8 +107,8 @@ __global__ void __launch_bounds__(BW_THREADS, 1) k_trans_bwd(Model m, Work w, in
     e.teardown();
 }
 
-size_t fwd_smem() { return sizeof(TransFwdSmem); }
-size_t bwd_smem() { return sizeof(TransBwdSmem); }
+size_t fwd_smem() { return sizeof(FwdSmem); }
+size_t bwd_smem() { return sizeof(BwdSmem); }
 
 int sm_count() {
     int dev = 0, n = 0;
@@ -128,7 +137,7 @@ int launch_trans_fused_forward(const Model &m, const Work &w, bool store_e, int 
 #define ES_FWD1(SPL, SE, CL)                                                                    \
     do {                                                                                        \
         cudaFuncSetAttribute(k_trans_fwd<SPL, SE, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-        ES_LAUNCH(h, "k_trans_fwd", st, k_trans_fwd<SPL, SE, CL><<<grid, F2_THREADS, sm, st>>>(m, w, chunk, sample_major)); \
+        ES_LAUNCH(h, "k_trans_fwd", st, k_trans_fwd<SPL, SE, CL><<<grid, FWD_WARPS * 32, sm, st>>>(m, w, chunk, sample_major)); \
     } while (0)
 #define ES_FWD(SPL, SE) \
     do { if (cloud) ES_FWD1(SPL, SE, true); else ES_FWD1(SPL, SE, false); } while (0)
@@ -152,7 +161,7 @@ int launch_trans_fused_backward(const Model &m, const Work &w, int chunk_req, in
 #define ES_BWD1(SPL, CL)                                                                        \
     do {                                                                                        \
         cudaFuncSetAttribute(k_trans_bwd<SPL, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-        ES_LAUNCH(h, "k_trans_bwd", st, k_trans_bwd<SPL, CL><<<grid, BW_THREADS, sm, st>>>(m, w, chunk, sample_major)); \
+        ES_LAUNCH(h, "k_trans_bwd", st, k_trans_bwd<SPL, CL><<<grid, BWD_WARPS * 32, sm, st>>>(m, w, chunk, sample_major)); \
     } while (0)
 #define ES_BWD(SPL) \
     do { if (cloud) ES_BWD1(SPL, true); else ES_BWD1(SPL, false); } while (0)

@@ -149,7 +149,10 @@ def test_mixed_batch_runs_one_kernel_per_direction_and_matches_single_kind_runs(
     """A batch of both kinds runs setup, one mixed forward kernel and the
     binning (3 launches for ln L; 5 with the adjoint), and each sample's ln L
     and gradient equal those of the same sample in a single-kind batch (the
-    transmission-only and emission-only kernels)."""
+    transmission-only and emission-only kernels). The transmission-only
+    forward runs 24 warps (the transit depth summed over 6 impact-parameter
+    chunks), the mixed kernel 16 (4 chunks): FP32 summation order, so ln L is
+    compared at 1e-6 relative rather than bit for bit."""
     w = synth.workload("highres", batch=10, n_nu=6000)
     kind = np.array([0, 1, 1, 0, 1, 0, 0, 1, 0, 1], np.int32)
     ctx = binding.context_for(w)
@@ -162,5 +165,5 @@ def test_mixed_batch_runs_one_kernel_per_direction_and_matches_single_kind_runs(
         sel = np.nonzero(kind == k)[0]
         ls, gs = _run(ctx, w.theta[sel], kind[sel])
         assert ctx.es_query(7) == 5
-        np.testing.assert_allclose(lm[sel], ls, rtol=1e-12, atol=0)
+        np.testing.assert_allclose(lm[sel], ls, rtol=1e-6, atol=0)
         np.testing.assert_allclose(gm[sel], gs, rtol=1e-5, atol=1e-7 * max(1.0, np.abs(gs).max()))
