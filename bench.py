@@ -348,6 +348,26 @@ def emission_fp32_ops(name, w, n_valid):
     return ops * (3 if name == "k_emis_bwd" else 1)
 
 
+def trans_fp32_ops(name, w, n_valid):
+    """Algorithmic FP32 operations (an FMA counts as one) of one launch of a
+    transmission kernel, per (transmission vector, layer, wavenumber).
+    Forward: 4 per species (the bilinear exponent in coefficient form, 3, and
+    its sum), 4 for the two CIA pairs, 3 to assemble alpha (number density,
+    Rayleigh, the lane pair's sum), 1 for the BF16 residual of the split
+    operand, and 3 per impact parameter in the epilogue (exponent argument,
+    1 - exp(-tau), area weight): 4 S + 11. Adjoint: the forward's 4 S + 4
+    recompute, 2 per species for the per-species and temperature-slope sums,
+    9 for the per-layer reduction inputs (alpha_bar n, the CIA products and
+    the four values), 3 to assemble alpha and 4 per impact parameter in the
+    tau_bar phase (dbar A exp(-tau) and the area sum): 6 S + 20. The chord
+    products run on the tensor cores and are not counted here."""
+    m = w.model
+    n_t = int(np.sum((w.kind == 0)[:n_valid]))
+    S = m.n_species
+    per = 4 * S + 11 if name == "k_trans_fwd" else 6 * S + 20
+    return n_t * m.n_layers * w.tables.nu.size * per
+
+
 def measured_traffic(name, n_vectors):
     """DRAM bytes per launch of `name` from the committed ncu captures
     (profiles/traffic_k_trans.json: one capture per batch size), scaled from
@@ -637,6 +657,12 @@ def run_gpu(args):
                                     if unit_kind == "ex2" else
                                     "derived from unit counts x median SM clock %.0f MHz" % sm_mhz),
                     "nominal_peak": alu_peak(unit_kind, sm_mhz) / scale if alu_peak(unit_kind, sm_mhz) else None}
+            if top in ("k_trans_fwd", "k_trans_bwd"):
+                # the same launch as FP32 operations against the probed packed-FMA rate
+                ops = trans_fp32_ops(top, w, n_valid) / (ms_launch / 1e3)
+                roof["fp32"] = {"achieved": ops / 1e12, "peak": 2 * ffma2_rate / 1e12, "unit": "Top/s",
+                                "frac": ops / (2 * ffma2_rate),
+                                "peak_source": "measured: es_probe_rates packed FFMA2 rate x 2 lanes"}
 
     # ---- plain per-sample path (batched vs plain): the plain JWST-shaped
     # workload, and the batched workload itself one vector per call
