@@ -215,7 +215,9 @@ es_status es_set_data(es_ctx *ctx, int kind, const double *y_obs, const double *
 
 /* Set the batch: theta [batch][n_free] (the model's free slots, in
  * free_idx order) and kind [batch] (ES_KIND_*; NULL = all transmission),
- * both in `mem`. Grows the device workspace as needed (ES_ENOMEM). */
+ * both in `mem`: the parameter vectors a sampler proposes (Sect. 2.1-2.2; a
+ * batch of live points per call is the library's addition). Grows the device
+ * workspace as needed (ES_ENOMEM). */
 es_status es_set_batch(es_ctx *ctx, const double *theta, const int32_t *kind, int batch,
                        int mem, es_stream_t stream);
 
@@ -240,7 +242,8 @@ es_status es_loglike(es_ctx *ctx, double *lnL, int mem, es_stream_t stream);
 
 /* ln L and its gradient with respect to the free parameters,
  * grad [batch][n_free] (double), by a hand-written adjoint that recomputes
- * the interpolated opacities. Invalid samples get a zero gradient.
+ * the interpolated opacities (the paper motivates gradients through
+ * automatic differentiation, Sect. 2.1, without computing them). Invalid samples get a zero gradient.
  * lnL or grad may be NULL (not copied out).
  *
  * CUDA-graph replay (es_loglike and es_forward_backward): the first call
@@ -270,7 +273,8 @@ es_status es_forward_backward(es_ctx *ctx, double *lnL, double *grad, int mem,
 es_status es_autotune(es_ctx *ctx, es_stream_t stream);
 
 /* CUDA-graph replay of es_loglike / es_forward_backward on (1, default) or
- * off (0). Either way drops any captured graph. */
+ * off (0). Either way drops any captured graph. No counterpart in the paper
+ * (launch mechanics). */
 es_status es_set_graphs(es_ctx *ctx, int on);
 
 /* ln L of `batch` parameter vectors, like es_set_batch + es_loglike, but
@@ -312,10 +316,11 @@ es_status es_set_memory_limit(es_ctx *ctx, uint64_t bytes);
 enum { ES_TEST_WAIT_TIMEOUT = 1 };
 es_status es_set_test_hooks(es_ctx *ctx, int hooks);
 
-/* Per-sample flags (ES_FLAG_*) of the last forward, int32 [batch]. */
+/* Per-sample flags (ES_FLAG_*) of the last forward, int32 [batch]: which
+ * samples got the paper's invalid-output ln L = -1e300 (Sect. 2.3), and why. */
 es_status es_get_flags(es_ctx *ctx, int32_t *flags, int mem, es_stream_t stream);
 
-/* Sizes: 0 n_nu, 1 n_bins, 2 n_free, 3 batch, 4 n_layers, 5 n_species,
+/* Sizes and state of the context (no counterpart in the paper): 0 n_nu, 1 n_bins, 2 n_free, 3 batch, 4 n_layers, 5 n_species,
  * 6 device bytes the context holds, 7 kernel launches issued by the last call (a
  * replayed graph counts the launches it holds), 8 / 9 work-item size of the
  * fused transmission forward / adjoint kernel (0: built-in heuristic),
@@ -331,10 +336,12 @@ int64_t es_query(const es_ctx *ctx, int key);
 
 /* Per-kernel timing with CUDA events recorded on the launching stream
  * around every kernel launch of later calls (on = 1) or off (on = 0, the
- * default). Turning it on or off clears the accumulated times. */
+ * default). Turning it on or off clears the accumulated times. No
+ * counterpart in the paper (measurement). */
 es_status es_set_profiling(es_ctx *ctx, int on);
 
-/* Accumulated profile entry `index` (0-based, in first-launch order):
+/* Accumulated profile entry `index` (0-based, in first-launch order; no
+ * counterpart in the paper):
  * copies the kernel's name (NUL-terminated, at most name_len bytes), its
  * total device time in milliseconds and its launch count. Synchronises the
  * device. Returns ES_EINVAL when index is past the last entry. */

@@ -112,6 +112,24 @@ def test_tiny_transmission_and_emission(kind):
     check_sample(out, 0, ref, kind)
 
 
+@pytest.mark.parametrize("kind", [0, 1])
+def test_temperatures_and_pressures_outside_the_table_grid(kind):
+    """Layers beyond the tables' pressure range (the model spans 1e-8..1e3 bar,
+    the cross-section tables 1e-6..1e2 bar) and isothermal temperatures above
+    and below both temperature grids (cross-sections 300-3000 K, CIA
+    200-4000 K): the device clamps every bracket as the oracle does, and the
+    gradient has no derivative along a clamped coordinate (the oracle's
+    complex step sees none there either)."""
+    w = synth.workload("tiny", batch=3)
+    w.model = dataclasses.replace(w.model, p_top_bar=1e-8, p_bot_bar=1e3)
+    theta = np.array([[-3.0, -4.0, -5.0, t, 1.0, -2.37] for t in (4500.0, 150.0, 1500.0)])
+    ctx = binding.context_for(w)
+    out = gpu_eval(ctx, w, theta, np.full(3, kind, np.int32))
+    for b in range(3):
+        ref = oracle_eval(w, w.tables, theta[b], kind, grad=True)
+        check_sample(out, b, ref, kind)
+
+
 def test_jwst_plain_reduced_grid():
     w = synth.workload("jwst_plain", n_nu=3000)
     ctx = binding.context_for(w)
