@@ -91,9 +91,11 @@ __device__ __forceinline__ void stage_levels(const Model &m, const Work &w, int 
     }
 }
 
-// Planck function per unit wavenumber at a level: B = nu3c / (2^a - 1) with
-// nu3c = 2 h c^2 nu^3 and a = (h c nu / k T) log2 e, clamped so that 2^a
-// stays finite (B is then below 1e-38 of its peak). Optionally dB/dT.
+// Planck function per unit wavenumber at a level: B = nu3c e / (1 - e) with
+// nu3c = 2 h c^2 nu^3, e = 2^-a and a = (h c nu / k T) log2 e (the same as
+// nu3c / (2^a - 1), with the same precision where a is small). Where a
+// passes 126, e flushes to zero and so does B (its true value is then below
+// 2^-126 of nu3c). Optionally dB/dT = B a ln 2 / ((1 - e) T).
 struct Planck {
     float nu3c, xc;   // 2 h c^2 nu^3; (h c / k) nu log2 e
     __device__ __forceinline__ void init(float nu) {
@@ -101,15 +103,14 @@ struct Planck {
         xc = (float)(C2_RAD * 1.4426950408889634) * nu;
     }
     __device__ __forceinline__ float value(float inv_t) const {
-        const float a = fminf(xc * inv_t, 126.f);
-        return nu3c * __frcp_rn(ex2f(a) - 1.f);
+        const float e = ex2f(-xc * inv_t);
+        return nu3c * e * __frcp_rn(1.f - e);
     }
     __device__ __forceinline__ float value_dt(float inv_t, float &dbdt) const {
-        const float a = fminf(xc * inv_t, 126.f);
-        const float ex = ex2f(a), r = __frcp_rn(ex - 1.f);
-        const float bv = nu3c * r;
-        // dB/dT = B x e^x / ((e^x - 1) T),  x = a ln 2
-        dbdt = bv * (a * 0.6931471805599453f) * ex * r * inv_t;
+        const float a = xc * inv_t;
+        const float e = ex2f(-a), r = __frcp_rn(1.f - e);
+        const float bv = nu3c * e * r;
+        dbdt = bv * (a * 0.6931471805599453f) * r * inv_t;
         return bv;
     }
 };

@@ -87,7 +87,10 @@ def assert_grad(got, ref):
 def check_sample(out, b, ref, kind, grad=True):
     assert out["flags"][b] == 0
     assert_spec(out["spec"][b], ref["spec"], kind)
-    np.testing.assert_allclose(out["binned"][b], ref["binned"], rtol=1e-5 if kind else 1e-6)
+    # emission: as for the native flux, an absolute floor of 1e-7 of the largest
+    # binned value (cold layers' flux at high wavenumber is far below FP32 range)
+    np.testing.assert_allclose(out["binned"][b], ref["binned"], rtol=1e-5 if kind else 1e-6,
+                               atol=1e-7 * np.max(np.abs(ref["binned"])) if kind else 0.0)
     np.testing.assert_allclose(out["lnl"][b], ref["lnl"], rtol=1e-5, atol=1e-3)
     np.testing.assert_allclose(out["lnl2"][b], out["lnl"][b], rtol=1e-12)
     if grad:
