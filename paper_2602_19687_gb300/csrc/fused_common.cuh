@@ -276,32 +276,22 @@ __device__ __forceinline__ float2 shfl_xor2(float2 v, int o) {
 // Extinction alpha_l(nu) at wavenumber pair n, n+1 for layers [lb, le), the
 // lane pair (lane, lane ^ 1) splitting species and CIA pairs:
 //   alpha = n 2^-K sum_s 2^e_s + CIA_H2H2 + CIA_H2He + Rayleigh.
-// Calls out(layer constants, alpha) on both lanes of the pair.
-// With STAGE, coefficients come through the per-warp staging slots (`stg`:
-// this lane's slot 0): each run's copy is issued one run ahead, and the last
-// run of a tile stages the first run of the next tile (`next_shift` 128, or 0
-// at the last tile of an item); `prestaged` says the first run was staged
-// that way. Without it, direct loads with an L1 prefetch of the next run.
-template <int SPL, bool STAGE, class Out>
+// Calls out(layer constants, alpha) on both lanes of the pair. Coefficients
+// are loaded directly at each run's start, with an L1 prefetch of the next
+// run (staging them through shared memory costs the forward more in queue
+// throttling and L1 than it saves).
+template <int SPL, class Out>
 __device__ __forceinline__ void extinction_pair(const Model &m, const SampleConst &sc, int lb, int le, int n,
-                                                int half, uint32_t stg, bool prestaged, int next_shift, Out &&out) {
+                                                int half, Out &&out) {
     PairInterp<SPL> pi;
     pi.init(m, n, half, threadIdx.x & 31);
     // loop bounds broadcast from lane 0: provably warp-uniform for the compiler
     lb = __shfl_sync(0xffffffffu, lb, 0);
     le = __shfl_sync(0xffffffffu, le, 0);
-    constexpr bool STAGED = STAGE && 2 * SPL + 1 <= STAGE_BLOCKS;
-    if (STAGED && lb < le && !prestaged) pi.stage(stg, sc.lay[lb].cell, sc.lay[lb].itc, 0);
     for (int l = lb; l < le;) {
         const int end = __shfl_sync(0xffffffffu, min(sc.lay[l].run_end, le), 0);
-        if constexpr (STAGED) {
-            pi.load_staged(sc, stg);
-            if (end < le) pi.stage(stg, sc.lay[end].cell, sc.lay[end].itc, 0);
-            else if (next_shift) pi.stage(stg, sc.lay[lb].cell, sc.lay[lb].itc, next_shift);
-        } else {
-            pi.load(sc, sc.lay[l].cell, sc.lay[l].itc);
-            if (end < le) pi.prefetch(sc.lay[end].cell, sc.lay[end].itc);
-        }
+        pi.load(sc, sc.lay[l].cell, sc.lay[l].itc);
+        if (end < le) pi.prefetch(sc.lay[end].cell, sc.lay[end].itc);
         const LayerConst *lp = &sc.lay[l], *const lend = &sc.lay[end];
         // two layers per iteration: independent chains for the schedulers
         for (; lp + 1 < lend; lp += 2) {

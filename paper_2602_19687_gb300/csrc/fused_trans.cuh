@@ -331,10 +331,8 @@ struct TransFwdEngine {
             const int nt0 = t * FT2;
             const int buf = issued & 1;
             unsigned char *const a_dst = (half ? sm.al[0] : sm.ah[0]) + a_off;
-            // direct coefficient loads: staging them through shared memory costs
-            // the forward more in queue throttling and L1 than it saves here
-            extinction_pair<SPL, false>(m, sm.sc, sm.sc.gb[grp], sm.sc.gb[grp + 1], nt0 + 2 * pair, half, 0u,
-                                        false, 0, [&](const LayerConst &lc, float2 a) {
+            extinction_pair<SPL>(m, sm.sc, sm.sc.gb[grp], sm.sc.gb[grp + 1], nt0 + 2 * pair, half,
+                                 [&](const LayerConst &lc, float2 a) {
                 uint32_t hi, lo;
                 split2(a, hi, lo);
                 *reinterpret_cast<uint32_t *>(a_dst + lc.aoff) = half ? lo : hi;
