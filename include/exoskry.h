@@ -226,7 +226,12 @@ es_status es_set_batch(es_ctx *ctx, const double *theta, const int32_t *kind, in
  *   spectrum [batch][n_nu]  native-resolution transit depth or Fp/F* (float)
  *   binned   [batch][n_bins] binned model (double)
  *   lnL      [batch]          ln L (double); -1e300 for invalid samples
- * Needs tables, grid, data for every kind present, and a batch. */
+ * Needs tables, grid, data for every kind present, and a batch.
+ * A batch of one transmission vector (the plain per-sample call) runs the
+ * opacity stage (Sect. 3) as a kernel of its own: the raw table rows that
+ * bracket the vector's layers, each read once, into the layer extinction,
+ * which the chord kernel (Sect. 4) then reads (es_query key 17 gives the
+ * row bytes); larger batches interpolate inside the fused kernels. */
 es_status es_forward(es_ctx *ctx, float *spectrum, double *binned, double *lnL,
                      int mem, es_stream_t stream);
 
@@ -331,6 +336,10 @@ es_status es_get_flags(es_ctx *ctx, int32_t *flags, int mem, es_stream_t stream)
  * adjoint (128-wavenumber tiles), 16 work-item orders (bit k set: kernel k
  * of trans fwd, trans bwd, emis fwd, emis bwd, mixed fwd, mixed bwd runs its
  * items sample-major). Sizes 0: the built-in heuristic.
+ * 17 bytes of raw table rows and CIA rows the one-vector opacity stage read
+ * for the last call (the union of the rows bracketing the vector's layers,
+ * over all wavenumbers; 0 when the last call did not run that stage;
+ * synchronises).
  * Returns -1 for an unknown key or a NULL context. */
 int64_t es_query(const es_ctx *ctx, int key);
 

@@ -27,9 +27,11 @@ struct es_ctx {
     std::unordered_map<void *, size_t> dev_sizes;
     int *h_err = nullptr;             // pinned copy of the device status word, written at the end of every call
     int64_t last_launches = 0;
+    bool last_one_vector = false;     // the last forward ran the one-vector path
     std::vector<double> y_host[2], s_host[2];
     std::vector<double> nu_host;      // FP64 wavenumber grid (bin membership)
     size_t ymod_cap = 0, alpha_cap = 0, estore_cap = 0;   // alpha_cap: the emission I_toa store
+    size_t ext_cap = 0;               // the one-vector path's extinction buffer
     double *d_data = nullptr;         // [2][nbins] y_obs then sigma
     double *d_lnl = nullptr, *d_grad = nullptr;
     // per-kernel CUDA-event profiling

@@ -261,6 +261,7 @@ es_status alloc_forward(es_ctx *c, int B) {
     ALLOC(w.cloud_d, B * L);
     ALLOC(w.cloud_g, B * N_CG);
     ALLOC(w.spec, (size_t)B * N);
+    ALLOC(w.arows, (size_t)B * 2);
     ALLOC(w.lnl, B);
     ALLOC(w.misc, (size_t)B * 4);
     ALLOC(c->d_lnl, B);
@@ -339,11 +340,19 @@ es_status ensure_ymod(es_ctx *c) {
     return ES_OK;
 }
 
+// The one-vector (plain per-sample) transmission path: a batch of a single
+// transmission vector runs its opacity stage as a table stream of its own
+// (k_trans_alpha, the raw bracketing rows read once) and the chord kernel on
+// the extinction it wrote, instead of the fused interpolating forward.
+bool one_vector_path(const es_ctx *c) { return c->batch == 1 && c->n_kind[0] == 1; }
+
 // Device buffers a call needs (allocated before any launch or capture).
 es_status prepare(es_ctx *c, bool adjoint) {
     es_status s;
-    const size_t big = (size_t)c->batch * c->m.L * c->m.N;
     if ((s = ensure_ymod(c)) != ES_OK) return s;
+    if (one_vector_path(c) &&
+        (s = ensure_big(c, &c->w.ext, c->ext_cap, (size_t)c->batch * c->m.L * c->m.Np)) != ES_OK)
+        return s;
 
     if (adjoint) {
         if ((s = alloc_backward(c)) != ES_OK) return s;
@@ -375,10 +384,15 @@ es_status run_forward(es_ctx *c, bool adjoint, float *spec_out, double *binned_o
     const Hook &h = c->hook;
     clear_status(c, st);
     launches += launch_setup(c->m, w, st, h);
+    c->last_one_vector = false;
     const es_ctx::Shape *sh = c->shape;
     if (c->n_kind[0] && c->n_kind[1]) {   // both kinds: one kernel over all items
         const es_ctx::Shape &x = sh[es_ctx::FUSED_MIXED_FWD];
         launches += launch_mixed_fused_forward(c->m, w, adjoint, x.chunk, x.sample_major, st, h);
+    } else if (one_vector_path(c)) {
+        c->last_one_vector = true;
+        launches += launch_trans_alpha(c->m, w, st, h);
+        launches += launch_trans_chord_forward(c->m, w, adjoint, st, h);
     } else if (c->n_kind[0]) {
         const es_ctx::Shape &x = sh[es_ctx::FUSED_TRANS_FWD];
         launches += launch_trans_fused_forward(c->m, w, adjoint, x.chunk, x.sample_major, st, h);
@@ -1028,6 +1042,13 @@ int64_t es_query(const es_ctx *c, int key) {
             if (!c->w.err || cudaMemcpy(&v, c->w.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
             return v;
         }
+        case 17: {   // bytes of raw table and CIA rows the one-vector opacity stage read
+            if (!c->last_one_vector || !c->w.arows) return 0;
+            int r[2] = {0, 0};
+            if (cudaMemcpy(r, c->w.arows, sizeof(r), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+            const int64_t esz = c->m.bf16 ? 2 : 4;
+            return ((int64_t)r[0] * esz + (int64_t)r[1] * 4) * c->m.N;
+        }
         default: return -1;
     }
 }
@@ -1085,6 +1106,7 @@ void es_destroy(es_ctx *c) {
     dev_free(c, c->w.ymod);
     dev_free(c, c->w.itop);
     dev_free(c, c->w.estore);
+    dev_free(c, c->w.ext);
     if (c->h_err) cudaFreeHost(c->h_err);
     prof_resolve(c);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);

@@ -325,18 +325,14 @@ struct TransFwdEngine {
         }
     }
 
-    // tiles [t0, t1) of the staged sample b; sets `abort` if a wait gave up
-    __device__ __forceinline__ void tiles(int b, int t0, int t1) {
+    // tiles [t0, t1) of the staged sample b, the extinction operand of each
+    // written by fill(first wavenumber of the tile); sets `abort` if a wait gave up
+    template <class Fill>
+    __device__ __forceinline__ void tiles_with(int b, int t0, int t1, Fill &&fill) {
         for (int t = t0; t < t1; ++t) {
             const int nt0 = t * FT2;
             const int buf = issued & 1;
-            unsigned char *const a_dst = (half ? sm.al[0] : sm.ah[0]) + a_off;
-            extinction_pair<SPL>(m, sm.sc, sm.sc.gb[grp], sm.sc.gb[grp + 1], nt0 + 2 * pair, half,
-                                 [&](const LayerConst &lc, float2 a) {
-                uint32_t hi, lo;
-                split2(a, hi, lo);
-                *reinterpret_cast<uint32_t *>(a_dst + lc.aoff) = half ? lo : hi;
-            });
+            fill(nt0);
             fence_async_smem();
             tc_fence_before();
             __syncthreads();
@@ -380,6 +376,46 @@ struct TransFwdEngine {
             pend_buf = buf;
             ++issued;
         }
+    }
+
+    // the extinction interpolated here (the sample's layer constants staged)
+    __device__ __forceinline__ void tiles(int b, int t0, int t1) {
+        unsigned char *const a_dst = (half ? sm.al[0] : sm.ah[0]) + a_off;
+        tiles_with(b, t0, t1, [&](int nt0) {
+            extinction_pair<SPL>(m, sm.sc, sm.sc.gb[grp], sm.sc.gb[grp + 1], nt0 + 2 * pair, half,
+                                 [&](const LayerConst &lc, float2 a) {
+                uint32_t hi, lo;
+                split2(a, hi, lo);
+                *reinterpret_cast<uint32_t *>(a_dst + lc.aoff) = half ? lo : hi;
+            });
+        });
+    }
+
+    // the extinction read from ext[b][l][Np] (written by the opacity-stage
+    // kernel): every thread converts wavenumber pairs of the tile's rows to
+    // the split operand, all its loads in flight together
+    __device__ __forceinline__ void tiles_from(int b, int t0, int t1, const float *ext) {
+        tiles_with(b, t0, t1, [&](int nt0) {
+            const float *src = ext + (size_t)b * L * m.Np + nt0;
+            constexpr int PER_ROW = FT2 / 2, ITER = (LP * PER_ROW + NT - 1) / NT;
+            float2 v[ITER];
+#pragma unroll
+            for (int k = 0; k < ITER; ++k) {
+                const int idx = threadIdx.x + k * NT, l = idx / PER_ROW, c = 2 * (idx % PER_ROW);
+                if (l < L) v[k] = *reinterpret_cast<const float2 *>(src + (size_t)l * m.Np + c);
+            }
+#pragma unroll
+            for (int k = 0; k < ITER; ++k) {
+                const int idx = threadIdx.x + k * NT, l = idx / PER_ROW, c = 2 * (idx % PER_ROW);
+                if (l < L) {
+                    uint32_t hi, lo;
+                    split2(v[k], hi, lo);
+                    const uint32_t o = op_off(l, c, SBO_NU);
+                    *reinterpret_cast<uint32_t *>(sm.ah[0] + o) = hi;
+                    *reinterpret_cast<uint32_t *>(sm.al[0] + o) = lo;
+                }
+            }
+        });
     }
 
     // whole block, once at the end: the tiles in flight, the status word, TMEM

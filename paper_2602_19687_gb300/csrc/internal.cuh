@@ -126,6 +126,10 @@ struct Work {
     float *cloud_d;               // [B][L] D_i = sum_l L_il C_l: cloudy chord depth = tau_i + g(nu) D_i
     float *cloud_g;               // [B][N_CG] 2 pi r_eff [cm], a, Q0, f_cld, A (0: no feature), lambda_0, omega, xi
     float *spec;                  // [B][N] transmission: depth - base; emission: Fp/F*
+    // one-vector transmission path: the extinction of the opacity stage, and
+    // per sample the table rows (species x nodes) and CIA rows it read
+    float *ext;                   // [B][L][Np]
+    int *arows;                   // [B][2]
     double *ymod;                 // [B][nbins]
     double *lnl;                  // [B]
     // adjoint
@@ -183,6 +187,11 @@ int launch_mixed_fused_forward(const Model &m, const Work &w, bool store, int wt
                                cudaStream_t st, const Hook &h);
 int launch_mixed_fused_backward(const Model &m, const Work &w, int wtiles, int sample_major, cudaStream_t st,
                                 const Hook &h);
+// One-vector transmission path: the opacity stage (extinction of every layer
+// and wavenumber from the raw table rows into w.ext) and the chord kernel
+// that reads it (transit depth; store_e keeps exp(-tau) for the adjoint)
+int launch_trans_alpha(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
+int launch_trans_chord_forward(const Model &m, const Work &w, bool store_e, cudaStream_t st, const Hook &h);
 // tiles per work item of the transmission kernels' heuristic
 int chunk_tiles(const Model &m, int B, int blocks, int tile);
 int launch_bins(const Model &m, const Work &w, bool want_adjoint, float *spectrum_out,

@@ -51,6 +51,40 @@ __global__ void __launch_bounds__(FWD_WARPS * 32, 1) k_trans_fwd(Model m, Work w
     e.teardown();
 }
 
+// The chord product, transit depth and exp(-tau) store of the one-vector
+// path: the forward's tiles with the extinction read from the buffer that
+// k_trans_alpha wrote (no interpolation, no layer constants).
+template <bool STORE_E, bool CLOUD>
+__global__ void __launch_bounds__(FWD_WARPS * 32, 1) k_trans_chord(Model m, Work w, int chunk_tiles) {
+    extern __shared__ float4 smem4[];
+    FwdSmem &sm = *reinterpret_cast<FwdSmem *>(smem4);
+    TransFwdEngine<4, STORE_E, CLOUD, FWD_WARPS> e(m, w, sm);
+    e.setup();
+    const int ntiles = (m.N + FT2 - 1) / FT2;
+    const ItemOrder order{w.B, (ntiles + chunk_tiles - 1) / chunk_tiles, 0};
+    int cur_b = -1;
+    for (long long item = blockIdx.x; item < order.total() && !e.abort; item += gridDim.x) {
+        int c, b;
+        order.at(item, c, b);
+        if (w.kind[b] != ES_KIND_TRANSMISSION) continue;
+        if (b != cur_b) {
+            e.drain();
+            if (sm.abort) {
+                e.abort = true;
+                break;
+            }
+            tc_fence_before();
+            __syncthreads();
+            e.stage_operands(b);
+            cur_b = b;
+            fence_async_smem();
+            __syncthreads();
+        }
+        e.tiles_from(b, c * chunk_tiles, min(ntiles, (c + 1) * chunk_tiles), w.ext);
+    }
+    e.teardown();
+}
+
 template <int SPL, bool CLOUD>
 __global__ void __launch_bounds__(BWD_WARPS * 32, 1) k_trans_bwd(Model m, Work w, int chunk_tiles, int sample_major) {
     extern __shared__ float4 smem4[];
@@ -148,6 +182,24 @@ int launch_trans_fused_forward(const Model &m, const Work &w, bool store_e, int 
     else { if (store_e) ES_FWD(8, true); else ES_FWD(8, false); }
 #undef ES_FWD1
 #undef ES_FWD
+    return 1;
+}
+
+int launch_trans_chord_forward(const Model &m, const Work &w, bool store_e, cudaStream_t st, const Hook &h) {
+    const int ntiles = (m.N + FT2 - 1) / FT2;
+    const int chunk = chunk_tiles(m, w.B, sm_count(), FT2);
+    const long long items = (long long)w.B * ((ntiles + chunk - 1) / chunk);
+    const int grid = (int)std::min<long long>(items, (long long)sm_count());
+    const size_t sm = fwd_smem();
+#define ES_CHORD(SE, CL)                                                                        \
+    do {                                                                                        \
+        cudaFuncSetAttribute(k_trans_chord<SE, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+        ES_LAUNCH(h, "k_trans_chord", st, k_trans_chord<SE, CL><<<grid, FWD_WARPS * 32, sm, st>>>(m, w, chunk)); \
+    } while (0)
+    const bool cloud = m.cloud_kind == ES_CLOUD_KH18;
+    if (store_e) { if (cloud) ES_CHORD(true, true); else ES_CHORD(true, false); }
+    else { if (cloud) ES_CHORD(false, true); else ES_CHORD(false, false); }
+#undef ES_CHORD
     return 1;
 }
 
