@@ -163,11 +163,11 @@ __device__ __forceinline__ void cia_rows(const Rows<BF16, false> &r, int h, int 
 // Extinction of layers [l0, l1) at the thread's wavenumber pair for species
 // [s0, s0 + ns), ns <= CH, by runs of layers with one cell and CIA bracket:
 // at a run's start the cell's coefficients of the species go to registers,
-// then each layer of the run sums the species' 2^e (slots j >= ns are exact
-// zeros). A part after
-// the FIRST adds the running sum read back from dst; the LAST adds CIA,
-// Rayleigh and n 2^-K and writes alpha; other parts store the running sum.
-// Run and loop bounds are broadcast from lane 0: warp-uniform for the compiler.
+// then each layer of the run sums the species' 2^e (slots j >= ns, in a last
+// part shorter than CH, are exact zeros). A part after the FIRST adds the
+// running sum read back from dst; the LAST adds CIA, Rayleigh and n 2^-K and
+// writes alpha; other parts store the running sum. Run and loop bounds are
+// broadcast from lane 0: warp-uniform for the compiler.
 template <bool BF16, bool STAGED, int CH, bool FIRST, bool LAST>
 __device__ __forceinline__ void layer_sums(const AlphaSmem &sa, const Rows<BF16, STAGED> &r, int s0, int ns, int l0,
                                            int l1, float2 nu4, float *dst, int Np) {
@@ -409,14 +409,14 @@ __global__ void __launch_bounds__(A_THREADS, 3) k_trans_alpha(Model m, Work w) {
         while (rper > 0 && part_bytes(rper) > avail) --rper;
     const bool staged = all || rper > 0;
     if (staged)
-        for (int l = tid; l < L; l += A_THREADS) {
-            int4 &ko = sa.lay[l].ko;
+        for (int q = tid; q < L; q += A_THREADS) {
+            int4 &ko = sa.lay[q].ko;
             ko.y = slot_of[ko.y];
             ko.z = slot_of[ko.z];
             ko.w = cslot[ko.w];
         }
 
-    // 3. the warp's layer group and the lane's wavenumber pair
+    // the warp's layer group and the lane's wavenumber pair
     const int n = n0 + 2 * lane;
     const int LG = (L + AG - 1) / AG, l0 = min(L, warp * LG), l1 = min(L, l0 + LG);
     const float2 nu = *reinterpret_cast<const float2 *>(m.nu + n);
@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(A_THREADS, 3) k_trans_alpha(Model m, Work w) {
             part_sums<BF16, false, 2>(sa, r, s0, ns, l0, l1, s0 == 0, s0 + 2 >= S, nu4, dst, Np);
         }
     } else {
-        // 2. staging
+        // 2. the rows into shared memory; 3.-4. the interpolation as each part lands
         const uint32_t sp = stage + cia_bytes;
         stage_rows<float>(stage, 2 * ncia, n0, Np,
                           [&](int q) { return m.cia + ((size_t)(q / ncia) * NTc + cnode_of[q % ncia]) * Np; });
