@@ -218,3 +218,31 @@ def test_one_vector_path_direct_reads():
     nodes = bracket_union_bytes(w, theta[0]) // (3 * 256 * 4)
     assert nodes >= 200, nodes
     _check(w, theta)
+
+
+def test_one_vector_path_high_resolution_shape():
+    """The high-resolution shape (60 layers, 4 absorbers, BF16 tables) at
+    44,000 wavenumbers, one transmission vector: against the oracle (spectrum
+    and ln L) and against the fused path (spectrum, ln L and gradient)."""
+    w = synth.workload("highres", batch=8, n_nu=44000)
+    b = next(k for k in range(8) if w.kind[k] == 0
+             and O.atmosphere(w.model, w.model.full_theta(w.theta[k])[0])["valid"])
+    theta = w.theta[b:b + 1]
+    ctx = binding.context_for(w)
+    one = run(ctx, w, theta)
+    assert one["launches"] == 4 and one["flags"][0] == 0
+    m, tabs = w.model, oracle_tables(w)
+    th = m.full_theta(theta[0])[0]
+    mem = O.bin_members(tabs.nu, w.bin_lo_um, w.bin_hi_um)
+    spec, _ = O.forward(m, tabs, th, 0, mem)
+    np.testing.assert_allclose(one["spec"][0], spec, rtol=1e-5, atol=0)
+    np.testing.assert_allclose(one["lnl"][0], O.loglike(m, tabs, th, 0, mem, w.y_obs[0], w.sigma[0]),
+                               rtol=1e-5, atol=1e-3)
+    two = run(ctx, w, np.vstack([theta, theta]))
+    for k in range(2):
+        np.testing.assert_allclose(two["spec"][k], one["spec"][0], rtol=2e-6, atol=0)
+        np.testing.assert_allclose(two["lnl"][k], one["lnl"][0], rtol=1e-6)
+        gt = 1e-5 * np.abs(one["grad"][0]) + 1e-6 * np.max(np.abs(one["grad"][0]))
+        assert np.all(np.abs(two["grad"][k] - one["grad"][0]) <= gt)
+    assert one["rows"] == bracket_union_bytes(w, theta[0])
+    ctx.es_destroy()
