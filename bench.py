@@ -389,6 +389,25 @@ def measured_traffic(name, n_vectors):
     return c["dram_bytes_per_launch"][name] * n_vectors / c["vectors"]
 
 
+def measured_instructions(name, n_vectors, n_layers, n_nu):
+    """Warp instructions per launch of `name` from the committed ncu opcode
+    capture (profiles/instructions_k_trans.json: per (vector, layer, 32
+    wavenumbers)), scaled to n_vectors x n_layers x n_nu; None when the
+    kernel sources changed since the capture."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "instructions_k_trans.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    for rel, digest in d["sources_sha256"].items():
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != digest:
+                return None
+    if name not in d["per_unit"]:
+        return None
+    return d["per_unit"][name] * n_vectors * n_layers * n_nu / 32.0
+
+
 def alu_peak(kind, sm_mhz):
     """Peaks from unit counts x clock (152 SMs): MUFU ex2 32/clk/SM on
     GB300; FP32 FMA 128 lanes x 2 flop/clk/SM."""
@@ -658,6 +677,19 @@ def run_gpu(args):
                                     "derived from unit counts x median SM clock %.0f MHz" % sm_mhz),
                     "nominal_peak": alu_peak(unit_kind, sm_mhz) / scale if alu_peak(unit_kind, sm_mhz) else None}
             if top in ("k_trans_fwd", "k_trans_bwd"):
+                # the launch's instruction issue: its warp instructions (committed ncu
+                # count, scaled) against one warp instruction per clock per SM
+                # sub-partition (4 per SM) at the median SM clock of the timed region
+                n_t = int(np.sum(w.kind[:n_valid] == 0))
+                inst = measured_instructions(top, n_t, w.model.n_layers, w.tables.nu.size)
+                if inst is not None:
+                    ipeak = 152 * 4 * sm_mhz * 1e6
+                    ach = inst / (ms_launch / 1e3)
+                    roof["issue"] = {"achieved": ach / 1e12, "peak": ipeak / 1e12, "unit": "T warp-instructions/s",
+                                     "frac": ach / ipeak, "instructions_per_launch": inst,
+                                     "peak_source": "152 SMs x 4 issue slots per clock x median SM clock %.0f MHz"
+                                                    % sm_mhz,
+                                     "count_source": "profiles/instructions_k_trans.json (ncu, same sources)"}
                 # the same launch as FP32 operations against the probed packed-FMA rate
                 ops = trans_fp32_ops(top, w, n_valid) / (ms_launch / 1e3)
                 roof["fp32"] = {"achieved": ops / 1e12, "peak": 2 * ffma2_rate / 1e12, "unit": "Top/s",
