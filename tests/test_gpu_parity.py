@@ -326,9 +326,13 @@ def test_maximum_layers_and_species():
     rng = np.random.default_rng(11)
     theta = np.concatenate([rng.uniform(-8, -4, S), [300.0, 1300.0, 0.3, -1.5, 0.6, 3.1, 1.1, -3.3, -5.0]])[None]
     ctx = binding.context_for(w)
-    out = gpu_eval(ctx, w, theta, np.zeros(1, np.int32))
     ref = oracle_eval(w, w.tables, theta[0], 0, grad=True)
+    # one vector (the one-vector path) and a batch of two copies (the fused kernels)
+    out = gpu_eval(ctx, w, theta, np.zeros(1, np.int32))
     check_sample(out, 0, ref, 0)
+    out2 = gpu_eval(ctx, w, np.vstack([theta, theta]), np.zeros(2, np.int32))
+    for b in range(2):
+        check_sample(out2, b, ref, 0)
 
 
 def test_bin_grid_errors():
