@@ -246,3 +246,30 @@ def test_one_vector_path_high_resolution_shape():
         assert np.all(np.abs(two["grad"][k] - one["grad"][0]) <= gt)
     assert one["rows"] == bracket_union_bytes(w, theta[0])
     ctx.es_destroy()
+
+
+def test_one_vector_path_over_prior_draws():
+    """48 draws from the batched transmission prior (BF16 tables, 2501
+    wavenumbers), invalid ones included: each vector alone (the one-vector
+    path) against the same vector in one fused batch of all 48 -- spectrum,
+    ln L and gradient, and the invalid samples' ln L = -1e300 with a zero
+    gradient on both paths."""
+    w = synth.workload("batched_trans", batch=48, n_nu=2501)
+    ctx = binding.context_for(w)
+    fused = run(ctx, w, w.theta)
+    assert fused["launches"] == 3
+    n_valid = 0
+    for b in range(w.theta.shape[0]):
+        one = run(ctx, w, w.theta[b:b + 1])
+        assert one["launches"] == 4
+        if fused["flags"][b] != 0:
+            assert one["flags"][0] == fused["flags"][b]
+            assert one["lnl"][0] == O.INVALID_LNL and np.all(one["grad"][0] == 0)
+            continue
+        n_valid += 1
+        np.testing.assert_allclose(one["spec"][0], fused["spec"][b], rtol=2e-6, atol=0)
+        np.testing.assert_allclose(one["lnl"][0], fused["lnl"][b], rtol=1e-6)
+        g = fused["grad"][b]
+        assert np.all(np.abs(one["grad"][0] - g) <= 1e-5 * np.abs(g) + 1e-6 * np.max(np.abs(g)))
+    assert n_valid >= 24
+    ctx.es_destroy()
