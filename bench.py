@@ -389,6 +389,24 @@ def measured_traffic(name, n_vectors):
     return c["dram_bytes_per_launch"][name] * n_vectors / c["vectors"]
 
 
+def measured_alpha_traffic(workload):
+    """DRAM bytes per launch of the one-vector opacity stage on `workload`
+    from the committed ncu capture (profiles/traffic_k_trans_alpha.json);
+    None for another workload or when the kernel sources changed since."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic_k_trans_alpha.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("workload") != workload:
+        return None
+    for rel, digest in d["sources_sha256"].items():
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != digest:
+                return None
+    return d["dram_bytes_per_launch"]
+
+
 def measured_instructions(name, n_vectors, n_layers, n_nu):
     """Warp instructions per launch of `name` from the committed ncu opcode
     capture (profiles/instructions_k_trans.json: per (vector, layer, 32
@@ -738,6 +756,8 @@ def run_gpu(args):
                 hbm_peak = float(peaks["hbm_gbs"])
                 rl = {"kernel": "k_trans_alpha", "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                       "frac": gbs / hbm_peak, "algorithmic_bytes": nbytes, "ms_per_launch": ms_a,
+                      "traffic": measured_alpha_traffic(wp.name),
+                      "traffic_unit": "DRAM bytes per launch (ncu capture, same sources)",
                       "bytes_source": "raw table and CIA rows bracketing the vector's layers (es_query 17), "
                                       "each read once",
                       "timing": "CUDA events around the launch in profiled steps, L2 flushed before each step",
