@@ -42,7 +42,12 @@ Readings taken where the paper is silent:
    edges) evaluated at the layer pressures; no grey deck in the same model;
    in emission a clear and a cloudy column mixed by the cloud fraction;
    a brown dwarf's hydrostatic reference radius is its R_bd = sqrt(G M_bd/g);
- - binning: equal-weight mean over native points with lambda in [lo, hi).
+ - binning: equal-weight mean over native points with lambda in [lo, hi);
+ - emission with scattering (Sect. 5 delta-EAA; emission_solver = RT_DELTA_EAA):
+   Rayleigh and cloud scattering, the cloud's single-scattering albedo and
+   asymmetry parameter constants of the model, delta-M with f = g^2, the
+   absorption approximation as the zeroth order and one scattering source
+   evaluated on it (emergent_flux_eaa).
 
 Parity status: every stage is pinned by tests/test_oracle_pins.py (closed forms,
 brute force, invariants); the complete discretised model (species sums, CIA,
@@ -297,10 +302,11 @@ def rayleigh_sigma(nu, sigma_ref, nu_ref):
     return sigma_ref * (nu / nu_ref) ** 4
 
 
-def extinction(tabs, model, x_trace, x_h2, x_he, t_lay, p_lay):
+def extinction(tabs, model, x_trace, x_h2, x_he, t_lay, p_lay, rayleigh=True):
     """alpha_l(nu) [cm^-1] = n_l sum_s X_s 10^{log10 sigma_s(T_l, p_l, nu)}
        + n_l^2 X_H2 (X_H2 k_H2H2 + X_He k_H2He)(T_l, nu)
-       + n_l (X_H2 sigma_R,H2 + X_He sigma_R,He)(nu),   n_l = p_l / (k_B T_l)."""
+       + n_l (X_H2 sigma_R,H2 + X_He sigma_R,He)(nu),   n_l = p_l / (k_B T_l);
+    without the Rayleigh term when rayleigh is False."""
     nu = tabs.nu
     ray = x_h2 * rayleigh_sigma(nu, model.ray_h2_cm2, model.ray_nu_ref) \
         + x_he * rayleigh_sigma(nu, model.ray_he_cm2, model.ray_nu_ref)
@@ -314,8 +320,17 @@ def extinction(tabs, model, x_trace, x_h2, x_he, t_lay, p_lay):
         k11 = 10.0 ** log10_cia_linear(tabs.cia_h2h2, tabs.cia_t_grid, t_lay[l])
         k12 = 10.0 ** log10_cia_linear(tabs.cia_h2he, tabs.cia_t_grid, t_lay[l])
         alpha[l] += n_l ** 2 * x_h2 * (x_h2 * k11 + x_he * k12)
-        alpha[l] += n_l * ray
+        if rayleigh:
+            alpha[l] += n_l * ray
     return alpha
+
+
+def rayleigh_extinction(model, x_h2, x_he, t_lay, p_lay, nu):
+    """The Rayleigh term of the extinction alone, n_l (X_H2 sigma_R,H2 + X_He sigma_R,He)(nu)."""
+    ray = x_h2 * rayleigh_sigma(nu, model.ray_h2_cm2, model.ray_nu_ref) \
+        + x_he * rayleigh_sigma(nu, model.ray_he_cm2, model.ray_nu_ref)
+    n_lay = p_lay / (K_B * t_lay)
+    return n_lay[:, None] * ray[None, :]
 
 
 # --------------------------------------------------------------------------
@@ -453,6 +468,110 @@ def emergent_flux(b_lev, dtau, n_mu=4, quadrature=QUAD_GAUSS_LEGENDRE):
 
 
 # --------------------------------------------------------------------------
+# emission with scattering (Sect. 5: linear-in-tau, delta-M scaled extended
+# absorption approximation). The paper names the scheme and cites its source
+# without printing its formulas; what follows is this library's reading:
+#  - scatterers: H2/He Rayleigh (omega = 1, g = 0) and the non-grey cloud
+#    with a single-scattering albedo omega_c and asymmetry parameter g_c that
+#    are constants of the model (Sect. 2.5 gives Q_ext alone);
+#  - delta-M scaling with the forward-peak fraction f = g^2 of the layer's
+#    scattering-weighted g (delta-Eddington truncation of a two-term phase
+#    function 1 + 3 g mu mu');
+#  - zeroth order (absorption approximation): absorption-only linear-in-tau
+#    RT in both directions on the scaled absorption depth (1 - omega') dtau';
+#  - extended step: the scattering integral evaluated on that zeroth-order
+#    field, J = 1/2 int I dmu and H = 1/2 int mu I dmu over both hemispheres
+#    (at the flux angles: H with the flux weights, J with the nodes'
+#    interpolatory weights of int_0^1 dmu),
+#    gives the source S(mu) = (1 - omega') B + omega' (J + 3 g' mu H) at the
+#    levels; one more upward linear-in-tau pass on the full scaled depth dtau'
+#    with that source gives the emergent intensity.
+# --------------------------------------------------------------------------
+RT_ABSORPTION, RT_DELTA_EAA = 0, 1
+
+
+def mean_intensity_weights(mu):
+    """Weights c_j of int_0^1 f(mu) dmu at the flux angles mu_j: the
+    interpolatory rule of those nodes (exact for polynomials of degree n-1;
+    at Gauss-Legendre nodes these are the Gauss-Legendre weights). The flux
+    weights of the Gauss-Jacobi rule divided by mu_j would not do: they
+    integrate f(mu) = 1 to 0.96 at 4 nodes."""
+    n = len(mu)
+    vander = np.vander(mu, n, increasing=True).T
+    return np.linalg.solve(vander, 1.0 / np.arange(1, n + 1))
+
+
+def delta_m_scaling(dtau_abs, dtau_ray, dtau_cld, omega_c, g_c):
+    """Layer optical properties and their delta-M scaling (Joseph, Wiscombe &
+    Weinman 1976). Inputs are the layer's absorption depth (gas and CIA), its
+    Rayleigh depth and its cloud extinction depth. With the scattering depth
+    dsca = dtau_ray + omega_c dtau_cld, the total dtau, omega = dsca / dtau,
+    the scattering-weighted asymmetry g = omega_c g_c dtau_cld / dsca (0 where
+    nothing scatters) and f = g^2:
+        dtau' = (1 - omega f) dtau,  omega' = (1 - f) omega / (1 - omega f),
+        g' = (g - f) / (1 - f).
+    Returns (dtau', omega', g')."""
+    dtau = dtau_abs + dtau_ray + dtau_cld
+    dsca = dtau_ray + omega_c * dtau_cld
+    some = _re(dsca) > 0
+    g = np.where(some, omega_c * g_c * dtau_cld / np.where(some, dsca, 1.0), 0.0)
+    omega = dsca / dtau
+    f = g * g
+    dtau_s = (1.0 - omega * f) * dtau
+    omega_s = (1.0 - f) * omega / (1.0 - omega * f)
+    g_s = (g - f) / (1.0 - f)
+    return dtau_s, omega_s, g_s
+
+
+def linear_in_tau_layer(i_in, s_entry, s_exit, x):
+    """Intensity leaving a layer of optical path x (along the ray) entered
+    with i_in, for a source linear in optical depth from s_entry (where the
+    ray enters) to s_exit (where it leaves):
+        i_in e^-x + s_exit (1 - e^-x) + (s_entry - s_exit) [(1 - e^-x)/x - e^-x]."""
+    e = np.exp(-x)
+    return i_in * e + s_exit * (1.0 - e) + (s_entry - s_exit) * linear_source_factor(x)
+
+
+def emergent_flux_eaa(b_lev, dtau_abs, dtau_ray, dtau_cld, omega_c, g_c, n_mu=4,
+                      quadrature=QUAD_GAUSS_LEGENDRE):
+    """Top-of-atmosphere flux of the delta-EAA (reading above). b_lev
+    [L+1, N] top to bottom; dtau_abs, dtau_ray, dtau_cld [L, N]. Angles mu_j
+    and flux weights a_j of the flux quadrature; mean_intensity_weights c_j
+    integrate over mu at the same nodes, so
+        J = 1/2 sum_j c_j (I_up,j + I_dn,j),  H = 1/2 sum_j a_j (I_up,j - I_dn,j).
+    Boundaries: no downward intensity at the top, I_up = B(bottom level) at
+    the bottom (both orders). F = 2 pi sum_j a_j I_j(top)."""
+    mu, a = flux_quadrature(quadrature, n_mu)
+    c = mean_intensity_weights(mu)
+    n = dtau_abs.shape[0]
+    dtau_s, om, gs = delta_m_scaling(dtau_abs, dtau_ray, dtau_cld, omega_c, g_c)
+    dtau_a = (1.0 - om) * dtau_s
+    j_lev = 0.0
+    h_lev = 0.0
+    for j in range(n_mu):
+        up = [None] * (n + 1)
+        dn = [None] * (n + 1)
+        dn[0] = np.zeros_like(b_lev[0])
+        for l in range(n):
+            dn[l + 1] = linear_in_tau_layer(dn[l], b_lev[l], b_lev[l + 1], dtau_a[l] / mu[j])
+        up[n] = b_lev[n]
+        for l in range(n - 1, -1, -1):
+            up[l] = linear_in_tau_layer(up[l + 1], b_lev[l + 1], b_lev[l], dtau_a[l] / mu[j])
+        up, dn = np.array(up), np.array(dn)
+        j_lev = j_lev + 0.5 * c[j] * (up + dn)
+        h_lev = h_lev + 0.5 * a[j] * (up - dn)
+    flux = 0.0
+    for j in range(n_mu):
+        inten = b_lev[n]
+        for l in range(n - 1, -1, -1):
+            s_top = (1.0 - om[l]) * b_lev[l] + om[l] * (j_lev[l] + 3.0 * gs[l] * mu[j] * h_lev[l])
+            s_bot = (1.0 - om[l]) * b_lev[l + 1] + om[l] * (j_lev[l + 1] + 3.0 * gs[l] * mu[j] * h_lev[l + 1])
+            inten = linear_in_tau_layer(inten, s_bot, s_top, dtau_s[l] / mu[j])
+        flux = flux + 2.0 * np.pi * a[j] * inten
+    return flux
+
+
+# --------------------------------------------------------------------------
 # instrument binning and Sect. 2.3 likelihood
 # --------------------------------------------------------------------------
 def bin_members(nu, bin_lo_um, bin_hi_um):
@@ -543,8 +662,9 @@ def forward(model, tabs, theta, kind, members):
         feature = None
         if getattr(model, "cloud_feature", 0):
             feature = (theta[s + P_FEAT_A], theta[s + P_FEAT_LAM0], theta[s + P_FEAT_W], theta[s + P_FEAT_XI])
-        alpha_cld = alpha + cloud_extinction(tabs.nu, rho_a, q_c, 10.0 ** theta[s + P_LOG_R_EFF] * 1.0e-4,
-                                             10.0 ** theta[s + P_LOG_Q0], theta[s + P_A_KH], feature)
+        alpha_c = cloud_extinction(tabs.nu, rho_a, q_c, 10.0 ** theta[s + P_LOG_R_EFF] * 1.0e-4,
+                                   10.0 ** theta[s + P_LOG_Q0], theta[s + P_A_KH], feature)
+        alpha_cld = alpha + alpha_c
         f_cld = theta[s + P_F_CLD]
     if kind == 0:
         P, dr, _ = path_matrix(r_lev)
@@ -560,12 +680,26 @@ def forward(model, tabs, theta, kind, members):
             spec = f_cld * spec_cld + (1.0 - f_cld) * spec
     else:
         dr = r_lev[:-1] - r_lev[1:]
-        dtau = alpha * dr[:, None]
         b_lev = planck_wavenumber(atm["t_lev"][:, None], tabs.nu[None, :])
         quad = getattr(model, "emission_quadrature", QUAD_GAUSS_LEGENDRE)
-        f_toa = emergent_flux(b_lev, dtau, quadrature=quad)
-        if cloudy:
-            f_toa = f_cld * emergent_flux(b_lev, alpha_cld * dr[:, None], quadrature=quad) + (1.0 - f_cld) * f_toa
+        if getattr(model, "emission_solver", RT_ABSORPTION) == RT_DELTA_EAA:
+            # Sect. 5 delta-EAA: absorption, Rayleigh and cloud depths kept apart
+            x_h2, x_he, t_lay, p_lay = atm["x_h2"], atm["x_he"], atm["t_lay"], atm["p_lay"]
+            alpha_abs = extinction(tabs, model, atm["x_trace"], x_h2, x_he, t_lay, p_lay, rayleigh=False)
+            d_abs = alpha_abs * dr[:, None]
+            d_ray = rayleigh_extinction(model, x_h2, x_he, t_lay, p_lay, tabs.nu) * dr[:, None]
+            ssa, gc = model.cloud_ssa, model.cloud_g
+            f_toa = emergent_flux_eaa(b_lev, d_abs, d_ray, np.zeros_like(d_abs), ssa, gc, quadrature=quad)
+            if cloudy:
+                d_cld = alpha_c * dr[:, None]
+                f_toa = f_cld * emergent_flux_eaa(b_lev, d_abs, d_ray, d_cld, ssa, gc, quadrature=quad) \
+                    + (1.0 - f_cld) * f_toa
+        else:
+            dtau = alpha * dr[:, None]
+            f_toa = emergent_flux(b_lev, dtau, quadrature=quad)
+            if cloudy:
+                f_toa = f_cld * emergent_flux(b_lev, alpha_cld * dr[:, None], quadrature=quad) \
+                    + (1.0 - f_cld) * f_toa
         if getattr(model, "emission_flux", FLUX_PLANET_STAR) == FLUX_BROWN_DWARF:
             # Sect. 5: F_bd = s F_toa (R_bd / D)^2
             spec = theta[s + P_DILUTION] * f_toa * (atm["r_ref"] / model.distance_cm) ** 2

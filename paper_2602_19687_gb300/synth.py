@@ -65,6 +65,9 @@ class Model:
     cloud_profile: int = QC_POWER_LAW
     cloud_feature: int = 0        # 1: the mid-infrared feature of the non-grey cloud
     emission_quadrature: int = 0  # 0: Gauss-Legendre, 1: Gauss-Jacobi flux angles
+    emission_solver: int = 0      # 0: absorption-only RT, 1: delta-EAA with scattering
+    cloud_ssa: float = 0.0        # delta-EAA: the cloud's single-scattering albedo
+    cloud_g: float = 0.0          # delta-EAA: the cloud's asymmetry parameter
 
     @property
     def n_species(self):
@@ -299,6 +302,10 @@ def workload(name: str, batch: int | None = None, seed: int = 42,
     cloudy_emis 512 emission vectors as batched_emis with the non-grey cloud
                 and cloud fraction: 20 free parameters (8 log-VMR, 4 Guillot,
                 log g, 7 cloud); a clear and a cloudy column per wavenumber.
+    scattering_emis 512 emission vectors as cloudy_emis solved with the
+                delta-EAA (Sect. 5): H2/He Rayleigh and cloud scattering with a
+                cloud single-scattering albedo of 0.9 and asymmetry parameter
+                of 0.6 (constants of the model).
     browndwarf  256 brown-dwarf emission vectors shaped like the paper's
                 Gliese 229 B setup: 15 free parameters (6 log-VMR, T_int,
                 log kappa_ir, T_ratio, log p_t, beta of the modified Milne
@@ -308,7 +315,7 @@ def workload(name: str, batch: int | None = None, seed: int = 42,
     `n_nu` shrinks the spectral grid (same physics) for fast tests.
     """
     S = {"tiny": 3, "jwst_plain": 6, "batched_trans": 8, "batched_emis": 8, "highres": 4,
-         "browndwarf": 6, "cloudy_trans": 8, "cloudy_emis": 8}[name]
+         "browndwarf": 6, "cloudy_trans": 8, "cloudy_emis": 8, "scattering_emis": 8}[name]
     s = S
     if name == "tiny":
         n = n_nu or 2000
@@ -364,7 +371,7 @@ def workload(name: str, batch: int | None = None, seed: int = 42,
         dtype, desc = "bf16", ("batched emission with adjoint, B=512, L=100, 8 absorbers, "
                                "20x15x20000 BF16 (1-12 um), 4 GL angles, 400 bins")
         level = 2.0e-3
-    elif name == "cloudy_emis":
+    elif name in ("cloudy_emis", "scattering_emis"):
         n = n_nu or 20000
         free = list(range(8)) + [s + P_T_INT, s + P_T_EQ, s + P_LOG_KAPPA, s + P_LOG_GAMMA, s + P_LOG_G,
                                  s + P_LOG_QC, s + P_LOG_PC_BASE, s + P_ALPHA_C, s + P_LOG_R_EFF,
@@ -378,6 +385,10 @@ def workload(name: str, batch: int | None = None, seed: int = 42,
         kind = np.ones(rows, np.int32)
         dtype, desc = "bf16", ("batched emission with a non-grey cloud and cloud fraction, with adjoint, B=512, "
                                "L=100, 8 absorbers, 20x15x20000 BF16 (1-12 um), 4 GL angles, 400 bins")
+        if name == "scattering_emis":
+            model.emission_solver, model.cloud_ssa, model.cloud_g = 1, 0.9, 0.6
+            desc = ("batched delta-EAA emission (Rayleigh and cloud scattering, omega_c = 0.9, g_c = 0.6) "
+                    "with adjoint, B=512, L=100, 8 absorbers, 20x15x20000 BF16 (1-12 um), 4 GL angles, 400 bins")
         level = 2.0e-3
     elif name == "highres":
         n = n_nu or 440000
@@ -434,9 +445,9 @@ def workload(name: str, batch: int | None = None, seed: int = 42,
         raise KeyError(name)
     y_obs, sigma = {}, {}
     nb = lo.size
+    emis_only = name in ("batched_emis", "cloudy_emis", "scattering_emis")
     y_obs[KIND_TRANSMISSION], sigma[KIND_TRANSMISSION] = make_data(nb, KIND_TRANSMISSION,
-                                                                   0.014 if name in ("batched_emis", "cloudy_emis")
-                                                                   else level)
+                                                                   0.014 if emis_only else level)
     if name == "browndwarf":
         y_obs[KIND_EMISSION], sigma[KIND_EMISSION] = make_data(nb, KIND_EMISSION, level, rel_sigma=0.05)
     else:
