@@ -63,6 +63,22 @@ enum { ES_QC_POWER_LAW = 0, ES_QC_SLAB = 1, ES_QC_SLAB_BAND = 2 };
  *   ES_QUAD_GAUSS_JACOBI    4-point Gauss-Jacobi rule of the weight mu on [0, 1]
  *                           ("8-stream": 4 angles per hemisphere), F = 2 pi sum W_j I_j */
 enum { ES_QUAD_GAUSS_LEGENDRE = 0, ES_QUAD_GAUSS_JACOBI = 1 };
+/* Emission solver (Sect. 5):
+ *   ES_RT_ABSORPTION  linear-in-tau Schwarzschild integration without
+ *                     scattering (Rayleigh extinction counted as absorption)
+ *   ES_RT_DELTA_EAA   the paper's delta-M scaled extended absorption
+ *                     approximation, linear in tau. The paper cites the scheme
+ *                     without its formulas; this library's reading: H2/He
+ *                     Rayleigh scatters (albedo 1, asymmetry 0) and the
+ *                     non-grey cloud scatters with the model constants
+ *                     cloud_ssa and cloud_g; delta-M scaling with the forward
+ *                     fraction f = g^2 of the layer's scattering-weighted
+ *                     asymmetry g; zeroth order: absorption-only RT in both
+ *                     directions on the scaled absorption depth; then one
+ *                     upward pass on the full scaled depth with the source
+ *                     (1 - w') B + w' (J + 3 g' mu H) of that field's mean
+ *                     intensity J and flux moment H. Cloud kinds NONE or KH18. */
+enum { ES_RT_ABSORPTION = 0, ES_RT_DELTA_EAA = 1 };
 enum { ES_KIND_TRANSMISSION = 0, ES_KIND_EMISSION = 1 };
 enum { ES_TABLE_F32 = 0, ES_TABLE_BF16 = 1 };
 enum { ES_MEM_HOST = 0, ES_MEM_DEVICE = 1 };
@@ -146,6 +162,11 @@ enum {
  * cloud_profile selects the non-grey cloud's q_c profile (ES_QC_*);
  * cloud_feature = 1 adds the mid-infrared feature to its Q_ext.
  * emission_quadrature selects the flux integral's angles (ES_QUAD_*).
+ * emission_solver selects the emission RT (ES_RT_*); with ES_RT_DELTA_EAA,
+ * cloud_ssa in [0, 1] and cloud_g in [0, 1) are the non-grey cloud's
+ * single-scattering albedo and asymmetry parameter (constant in wavenumber;
+ * the paper's cloud scheme gives Q_ext alone). These three trailing fields
+ * are zero in a zero-initialised description: absorption-only emission.
  */
 typedef struct {
     int n_layers;
@@ -164,6 +185,8 @@ typedef struct {
     int cloud_profile;           /* ES_QC_*          */
     int cloud_feature;           /* 0 or 1           */
     int emission_quadrature;     /* ES_QUAD_*        */
+    int emission_solver;         /* ES_RT_*          */
+    double cloud_ssa, cloud_g;   /* ES_RT_DELTA_EAA: cloud albedo, asymmetry */
 } es_model_desc;
 
 /*

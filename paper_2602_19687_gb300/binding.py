@@ -44,7 +44,8 @@ class es_model_desc(ctypes.Structure):
                 ("n_free", ctypes.c_int), ("free_idx", ctypes.c_int * ES_MAX_PARAMS),
                 ("emission_flux", ctypes.c_int), ("distance_cm", ctypes.c_double),
                 ("cloud_profile", ctypes.c_int), ("cloud_feature", ctypes.c_int),
-                ("emission_quadrature", ctypes.c_int)]
+                ("emission_quadrature", ctypes.c_int), ("emission_solver", ctypes.c_int),
+                ("cloud_ssa", ctypes.c_double), ("cloud_g", ctypes.c_double)]
 
 
 class es_tables_desc(ctypes.Structure):
@@ -147,6 +148,9 @@ def model_desc(model) -> es_model_desc:
     d.cloud_profile = int(getattr(model, "cloud_profile", 0))
     d.cloud_feature = int(getattr(model, "cloud_feature", 0))
     d.emission_quadrature = int(getattr(model, "emission_quadrature", 0))
+    d.emission_solver = int(getattr(model, "emission_solver", 0))
+    d.cloud_ssa = float(getattr(model, "cloud_ssa", 0.0))
+    d.cloud_g = float(getattr(model, "cloud_g", 0.0))
     return d
 
 

@@ -31,7 +31,9 @@ struct es_ctx {
     std::vector<double> y_host[2], s_host[2];
     std::vector<double> nu_host;      // FP64 wavenumber grid (bin membership)
     size_t ymod_cap = 0, alpha_cap = 0, estore_cap = 0;   // alpha_cap: the emission I_toa store
-    size_t ext_cap = 0;               // the one-vector path's extinction buffer
+    size_t ext_cap = 0;               // the extinction buffer (one-vector path; delta-EAA emission)
+    float *eaa_scr = nullptr;         // delta-EAA: the RT kernels' per-thread scratch array
+    size_t eaa_scr_cap = 0;
     double *d_data = nullptr;         // [2][nbins] y_obs then sigma
     double *d_lnl = nullptr, *d_grad = nullptr;
     // per-kernel CUDA-event profiling

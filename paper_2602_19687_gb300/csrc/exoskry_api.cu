@@ -346,12 +346,18 @@ es_status ensure_ymod(es_ctx *c) {
 // the extinction it wrote, instead of the fused interpolating forward.
 bool one_vector_path(const es_ctx *c) { return c->batch == 1 && c->n_kind[0] == 1; }
 
+// Emission samples solved by the delta-EAA (k_eaa.cu) instead of the fused
+// emission kernels.
+bool eaa_path(const es_ctx *c) { return c->m.emis_solver == ES_RT_DELTA_EAA && c->n_kind[1] > 0; }
+
 // Device buffers a call needs (allocated before any launch or capture).
 es_status prepare(es_ctx *c, bool adjoint) {
     es_status s;
     if ((s = ensure_ymod(c)) != ES_OK) return s;
-    if (one_vector_path(c) &&
+    if ((one_vector_path(c) || eaa_path(c)) &&
         (s = ensure_big(c, &c->w.ext, c->ext_cap, (size_t)c->batch * c->m.L * c->m.Np)) != ES_OK)
+        return s;
+    if (eaa_path(c) && (s = ensure_big(c, &c->eaa_scr, c->eaa_scr_cap, eaa_scratch_floats(c->m))) != ES_OK)
         return s;
 
     if (adjoint) {
@@ -386,7 +392,13 @@ es_status run_forward(es_ctx *c, bool adjoint, float *spec_out, double *binned_o
     launches += launch_setup(c->m, w, st, h);
     c->last_one_vector = false;
     const es_ctx::Shape *sh = c->shape;
-    if (c->n_kind[0] && c->n_kind[1]) {   // both kinds: one kernel over all items
+    if (eaa_path(c)) {   // emission by the delta-EAA; transmission samples by their fused kernel
+        if (c->n_kind[0]) {
+            const es_ctx::Shape &x = sh[es_ctx::FUSED_TRANS_FWD];
+            launches += launch_trans_fused_forward(c->m, w, adjoint, x.chunk, x.sample_major, st, h);
+        }
+        launches += launch_eaa_forward(c->m, w, c->eaa_scr, adjoint, st, h);
+    } else if (c->n_kind[0] && c->n_kind[1]) {   // both kinds: one kernel over all items
         const es_ctx::Shape &x = sh[es_ctx::FUSED_MIXED_FWD];
         launches += launch_mixed_fused_forward(c->m, w, adjoint, x.chunk, x.sample_major, st, h);
     } else if (one_vector_path(c)) {
@@ -427,6 +439,11 @@ es_status es_create(es_ctx **out, int device, const es_model_desc *d) {
     if (d->emission_quadrature != ES_QUAD_GAUSS_LEGENDRE && d->emission_quadrature != ES_QUAD_GAUSS_JACOBI)
         return ES_EINVAL;
     if (!(d->r_star_cm > 0) || !(d->t_star_k > 0)) return ES_EINVAL;
+    if (d->emission_solver != ES_RT_ABSORPTION && d->emission_solver != ES_RT_DELTA_EAA) return ES_EINVAL;
+    if (d->emission_solver == ES_RT_DELTA_EAA &&
+        (d->cloud_kind == ES_CLOUD_DECK || !(d->cloud_ssa >= 0.0 && d->cloud_ssa <= 1.0) ||
+         !(d->cloud_g >= 0.0 && d->cloud_g < 1.0)))
+        return ES_EINVAL;
     const int nfull = d->n_species + ES_P_N_EXTRA;
     if (d->n_free < 1 || d->n_free > 32 || d->n_free > nfull) return ES_EINVAL;
     for (int k = 0; k < d->n_free; ++k) {
@@ -476,6 +493,10 @@ es_status es_create(es_ctx **out, int device, const es_model_desc *d) {
     } else {
         gauss_legendre4_01(m.mu_gl, m.w_gl);
     }
+    m.emis_solver = d->emission_solver;
+    m.cloud_ssa = (float)d->cloud_ssa;
+    m.cloud_gasym = (float)d->cloud_g;
+    interp_weights_01(N_MU, m.mu_gl, m.c_mu);
     // pressure levels (top to bottom) and layers
     std::vector<double> p_lev(m.L + 1), p_lay(m.L);
     for (int k = 0; k <= m.L; ++k)
@@ -879,7 +900,13 @@ es_status enqueue_forward_backward(es_ctx *c, cudaStream_t st) {
     int launches = (int)c->last_launches;
     const Hook &h = c->hook;
     const es_ctx::Shape *sh = c->shape;
-    if (c->n_kind[0] && c->n_kind[1]) {
+    if (eaa_path(c)) {
+        if (c->n_kind[0]) {
+            const es_ctx::Shape &x = sh[es_ctx::FUSED_TRANS_BWD];
+            launches += launch_trans_fused_backward(m, w, x.chunk, x.sample_major, st, h);
+        }
+        launches += launch_eaa_backward(m, w, c->eaa_scr, st, h);
+    } else if (c->n_kind[0] && c->n_kind[1]) {
         const es_ctx::Shape &x = sh[es_ctx::FUSED_MIXED_BWD];
         launches += launch_mixed_fused_backward(m, w, x.chunk, x.sample_major, st, h);
     } else if (c->n_kind[0]) {
@@ -958,7 +985,14 @@ es_status es_autotune(es_ctx *c, es_stream_t stream) {
             }
     };
     const Model &m = c->m;
-    if (c->n_kind[0] && c->n_kind[1]) {
+    if (eaa_path(c)) {   // the delta-EAA kernels have fixed shapes: only a transmission part is tuned
+        if (c->n_kind[0]) {
+            tune(es_ctx::FUSED_TRANS_FWD, {2, 4, 8, 16, 32, 64, 128},
+                 [&](int ch, int o) { launch_trans_fused_forward(m, w, true, ch, o, st, none); });
+            tune(es_ctx::FUSED_TRANS_BWD, {2, 4, 8, 16, 32, 64},
+                 [&](int ch, int o) { launch_trans_fused_backward(m, w, ch, o, st, none); });
+        }
+    } else if (c->n_kind[0] && c->n_kind[1]) {
         const std::vector<int> win = {4, 8, 16, 32, 64};
         tune(es_ctx::FUSED_MIXED_FWD, win,
              [&](int ch, int o) { launch_mixed_fused_forward(m, w, true, ch, o, st, none); });
@@ -1107,6 +1141,7 @@ void es_destroy(es_ctx *c) {
     dev_free(c, c->w.itop);
     dev_free(c, c->w.estore);
     dev_free(c, c->w.ext);
+    dev_free(c, c->eaa_scr);
     if (c->h_err) cudaFreeHost(c->h_err);
     prof_resolve(c);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);

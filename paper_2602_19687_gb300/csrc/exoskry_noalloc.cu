@@ -112,6 +112,8 @@ extern "C" es_status es_loglike_noalloc(es_ctx *c, const double *theta, const in
     if (!c->have_data[ES_KIND_TRANSMISSION] || (kind && !c->have_data[ES_KIND_EMISSION]))
         return fail(c, ES_ESTATE, "es_loglike_noalloc needs transmission data, and emission data when kind is given");
     if (c->device < 0 || c->device >= MAX_DEVICES) return fail(c, ES_EINVAL, "device ordinal too large");
+    if (kind && c->m.emis_solver == ES_RT_DELTA_EAA)
+        return fail(c, ES_EINVAL, "es_loglike_noalloc: the delta-EAA emission solver needs es_loglike");
     es::Work w{};
     int *kind_slot = nullptr;
     const size_t need = carve(c->m, batch, nullptr, w, &kind_slot);

@@ -75,6 +75,11 @@ struct Model {
     int free_idx[ES_MAX_PARAMS];
     double theta_fixed[ES_MAX_PARAMS];
     double mu_gl[N_MU], w_gl[N_MU];   // flux angles mu_j and weights w_j (F = 2 pi sum w_j mu_j I_j)
+    // emission solver (ES_RT_*); the delta-EAA's interpolatory weights of
+    // int_0^1 dmu at the flux angles, and the cloud's albedo and asymmetry
+    int emis_solver;
+    double c_mu[N_MU];
+    float cloud_ssa, cloud_gasym;
     // device arrays
     const double *p_lev, *p_lay;  // [L+1], [L]
     const double *lnp_lev;        // [L+1] ln p_lev
@@ -176,6 +181,12 @@ int launch_setup(const Model &m, const Work &w, cudaStream_t st, const Hook &h);
 // fused emission: interpolation + Schwarzschild integration (store_i keeps I_toa for the adjoint)
 int launch_emis_fused_forward(const Model &m, const Work &w, bool store_i, int chunk, int sample_major,
                               cudaStream_t st, const Hook &h);
+// delta-EAA emission with scattering (k_eaa.cu): the extinction store and the
+// RT kernel; the RT adjoint and the interpolation adjoint. scr: a scratch
+// array of eaa_scratch_floats(m) floats.
+size_t eaa_scratch_floats(const Model &m);
+int launch_eaa_forward(const Model &m, const Work &w, float *scr, bool store_i, cudaStream_t st, const Hook &h);
+int launch_eaa_backward(const Model &m, const Work &w, float *scr, cudaStream_t st, const Hook &h);
 int launch_emis_fused_backward(const Model &m, const Work &w, int chunk, int sample_major, cudaStream_t st,
                                const Hook &h);
 int launch_trans_fused_forward(const Model &m, const Work &w, bool store_e, int chunk, int sample_major,

@@ -81,4 +81,36 @@ inline void gauss_jacobi_mu_01(int n, double *mu, double *W) {
     }
 }
 
+// Weights c_j of the interpolatory rule of int_0^1 f(mu) dmu at the n <= 8
+// nodes mu_j (exact for polynomials of degree n - 1): the solution of
+// sum_j c_j mu_j^k = 1 / (k + 1), k = 0 .. n-1, by Gaussian elimination with
+// partial pivoting. At Gauss-Legendre nodes these are the Gauss-Legendre
+// weights; the delta-EAA takes the mean intensity J with them.
+inline void interp_weights_01(int n, const double *mu, double *c) {
+    double a[8][9];
+    for (int k = 0; k < n; ++k) {
+        for (int j = 0; j < n; ++j) a[k][j] = std::pow(mu[j], (double)k);
+        a[k][n] = 1.0 / (k + 1.0);
+    }
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < n; ++r)
+            if (std::fabs(a[r][col]) > std::fabs(a[piv][col])) piv = r;
+        for (int j = 0; j <= n; ++j) {
+            const double t = a[col][j];
+            a[col][j] = a[piv][j];
+            a[piv][j] = t;
+        }
+        for (int r = col + 1; r < n; ++r) {
+            const double fct = a[r][col] / a[col][col];
+            for (int j = col; j <= n; ++j) a[r][j] -= fct * a[col][j];
+        }
+    }
+    for (int r = n - 1; r >= 0; --r) {
+        double acc = a[r][n];
+        for (int j = r + 1; j < n; ++j) acc -= a[r][j] * c[j];
+        c[r] = acc / a[r][r];
+    }
+}
+
 }  // namespace es

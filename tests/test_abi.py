@@ -48,10 +48,13 @@ def test_struct_layout_matches_c_header():
 #include <stddef.h>
 #include "exoskry.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(es_model_desc), offsetof(es_model_desc, theta_fixed),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(es_model_desc),
+         offsetof(es_model_desc, theta_fixed),
          offsetof(es_model_desc, free_idx), offsetof(es_model_desc, emission_flux),
          offsetof(es_model_desc, distance_cm), offsetof(es_model_desc, cloud_profile),
          offsetof(es_model_desc, cloud_feature), offsetof(es_model_desc, emission_quadrature),
+         offsetof(es_model_desc, emission_solver), offsetof(es_model_desc, cloud_ssa),
+         offsetof(es_model_desc, cloud_g),
          sizeof(es_tables_desc), offsetof(es_tables_desc, cia_h2he),
          offsetof(es_tables_desc, storage));
   return 0;
@@ -66,7 +69,8 @@ int main(void) {
     M, T = binding.es_model_desc, binding.es_tables_desc
     assert vals == [ctypes.sizeof(M), M.theta_fixed.offset, M.free_idx.offset, M.emission_flux.offset,
                     M.distance_cm.offset, M.cloud_profile.offset, M.cloud_feature.offset,
-                    M.emission_quadrature.offset, ctypes.sizeof(T),
+                    M.emission_quadrature.offset, M.emission_solver.offset, M.cloud_ssa.offset,
+                    M.cloud_g.offset, ctypes.sizeof(T),
                     T.cia_h2he.offset, T.storage.offset]
 
 
@@ -85,9 +89,23 @@ def test_null_context_calls(lib):
                                          ("n_species", 17), ("p_top_bar", -1.0), ("tp_kind", 7),
                                          ("cloud_kind", 3), ("n_free", 0), ("r_star_cm", 0.0),
                                          ("emission_flux", 2), ("cloud_profile", 3), ("cloud_profile", -1),
-                                         ("cloud_feature", 2), ("emission_quadrature", 2)])
+                                         ("cloud_feature", 2), ("emission_quadrature", 2),
+                                         ("emission_solver", 2), ("emission_solver", 1)])
 def test_create_rejects_bad_descriptions_before_touching_cuda(lib, field, value):
     w = synth.workload("tiny", n_nu=64)
+    d = binding.model_desc(w.model)
+    setattr(d, field, value)
+    h = ctypes.c_void_p()
+    assert lib.es_create(ctypes.byref(h), 0, ctypes.byref(d)) == binding.ES_EINVAL
+    assert not h.value
+
+
+@pytest.mark.parametrize("field,value", [("cloud_ssa", -0.1), ("cloud_ssa", 1.5), ("cloud_g", 1.0),
+                                         ("cloud_g", -0.2), ("cloud_ssa", float("nan"))])
+def test_create_rejects_bad_scattering_constants(lib, field, value):
+    """The delta-EAA solver takes a cloud albedo in [0, 1] and an asymmetry
+    parameter in [0, 1) (and no grey deck: the tiny workload above)."""
+    w = synth.workload("scattering_emis", n_nu=64, batch=1)
     d = binding.model_desc(w.model)
     setattr(d, field, value)
     h = ctypes.c_void_p()
