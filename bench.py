@@ -317,6 +317,19 @@ def kernel_work(name, w, n_valid):
         # Planck function at the level (1); the adjoint recomputes all of them.
         # The non-grey cloud's second column adds 4 attenuations.
         return n_e * L * (S + 7 + 4 * cloud) * N, "ex2", "alu"
+    if name in ("k_eaa_ext", "k_eaa_abar"):
+        # delta-EAA: the interpolation's S + 2 exponentials per (emission
+        # vector, layer, wavenumber), stored (ext) or recomputed (abar)
+        return n_e * L * (S + 2) * N, "ex2", "alu"
+    if name == "k_eaa_rt":
+        # delta-EAA RT per column (clear, and cloudy with the non-grey cloud)
+        # and layer: going up, 4 zeroth-order attenuations and the Planck
+        # value; going down, 4 zeroth-order and 4 first-order attenuations
+        return n_e * L * 13 * (1 + cloud) * N, "ex2", "alu"
+    if name == "k_eaa_rt_bwd":
+        # its adjoint: the forward's 13 and, in the third pass, 4 zeroth-order
+        # attenuations and dB/dT at the level
+        return n_e * L * 18 * (1 + cloud) * N, "ex2", "alu"
     if name == "k_trans_fwd":
         # one ex2 per (vector, layer, species or CIA pair, wavenumber) of the
         # interpolation, plus exp(-tau_i) per (vector, impact parameter,
@@ -496,6 +509,13 @@ def measure_workload(name, device, steps=5, warmup=3, out_vectors=None, probe=No
                        "fp32": {"achieved": fp32 / 1e12, "peak": 2 * probe[1] / 1e12, "unit": "Top/s",
                                 "frac": fp32 / (2 * probe[1]),
                                 "peak_source": "measured: es_probe_rates packed FFMA2 rate x 2 lanes"}}
+    for k in ("k_eaa_ext", "k_eaa_rt", "k_eaa_rt_bwd", "k_eaa_abar"):
+        if k in kernels and probe:
+            sec = kernels[k]["ms_per_launch"] / 1e3
+            ex2 = kernel_work(k, w, B)[0] / sec
+            roof[k] = {"bound": "alu", "ms_per_launch": kernels[k]["ms_per_launch"],
+                       "ex2": {"achieved": ex2 / 1e12, "peak": probe[0] / 1e12, "unit": "Tex2/s",
+                               "frac": ex2 / probe[0]}}
     gpu_out = None
     if out_vectors:
         N, nb = w.tables.nu.size, w.bin_lo_um.size
@@ -780,7 +800,7 @@ def run_gpu(args):
     extra, extra_out, roof_emis = None, {}, None
     if rank == 0 and not args.no_extra:
         extra = []
-        for n in ("batched_emis", "highres", "browndwarf", "cloudy_trans", "cloudy_emis"):
+        for n in ("batched_emis", "highres", "browndwarf", "cloudy_trans", "cloudy_emis", "scattering_emis"):
             want = list(range(8)) if (n in ("batched_emis", "highres") and not args.no_cpu) else None
             rec, wx, gx = measure_workload(n, local, out_vectors=want, probe=(ex2_rate, ffma2_rate))
             extra.append(rec)

@@ -47,6 +47,7 @@ namespace {
 
 constexpr int EA_THREADS = 128;     // one column per thread
 constexpr int EA_BLOCKS_PER_SM = 4; // resident RT blocks per SM (the scratch array's size follows)
+constexpr int EA_BWD_BLOCKS_PER_SM = 3;   // the adjoint's: measured best (164 registers, no spills; 4 spill, 2 idle)
 constexpr int EA_SUB = 8;           // 128-wavenumber sub-chunks per RT work item
 constexpr int EA_FIELDS = 9;        // scratch values per level and thread (adjoint)
 
@@ -189,43 +190,50 @@ __device__ __forceinline__ void layer_factors_fp(const EaaAngles &ang, int p, fl
     fp = lin_fp(x, e, fma2(e, f2(-1.f), f2(1.f)), ix);
 }
 
+// Reciprocal (MUFU, relative error ~2^-23); zero for a zero argument (where
+// the callers' products are zero or discarded).
+__device__ __forceinline__ float rcpa(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return x != 0.f ? y : 0.f;
+}
+
 // Layer optical properties of the reading above from its absorption,
 // Rayleigh and cloud depths: the zeroth-order depth da = A + (1 - w_c) C, the
-// scaled depth dp = dtau', w' and g'; sca, g and f kept for the adjoint.
+// scaled depth dp = dtau', w' and g'; sca, g, f and the reciprocals of da,
+// dp, sca and 1 + g kept for the layer factors and the adjoint.
 struct LayerOpt {
-    float da, dp, om, gp, sca, g, f;
+    float da, dp, om, gp, sca, g, f, rda, rdp, rsca, r1g;
 };
 __device__ __forceinline__ LayerOpt layer_opt(float A, float R, float C, float wc, float gcl) {
     LayerOpt o;
     o.sca = fmaf(wc, C, R);
-    o.g = o.sca > 0.f ? wc * gcl * C / o.sca : 0.f;
+    o.rsca = rcpa(o.sca);
+    o.g = wc * gcl * C * o.rsca;
     o.f = o.g * o.g;
     o.da = fmaf(1.f - wc, C, A);
+    o.rda = rcpa(o.da);
     const float ssc = (1.f - o.f) * o.sca;
     o.dp = o.da + ssc;
-    o.om = o.dp > 0.f ? ssc / o.dp : 0.f;
-    o.gp = o.g / (1.f + o.g);
+    o.rdp = rcpa(o.dp);
+    o.om = ssc * o.rdp;
+    o.r1g = rcpa(1.f + o.g);
+    o.gp = o.g * o.r1g;
     return o;
 }
 // Adjoint of layer_opt: from the adjoints of (da, dp, w', g') those of A, R, C.
 __device__ __forceinline__ void layer_opt_bwd(const LayerOpt &o, float wc, float gcl, float dab, float dpb,
                                               float omb, float gpb, float &Ab, float &Rb, float &Cb) {
-    float sscb = 0.f;
-    if (o.dp > 0.f) {
-        sscb = omb / o.dp;
-        dpb -= omb * o.om / o.dp;
-    }
+    float sscb = omb * o.rdp;
+    dpb -= sscb * o.om;
     dab += dpb;
     sscb += dpb;
-    float gb = gpb / ((1.f + o.g) * (1.f + o.g));
+    float gb = gpb * o.r1g * o.r1g;
     const float fb = -sscb * o.sca;
     float scab = sscb * (1.f - o.f);
     gb = fmaf(2.f * o.g, fb, gb);
-    Cb = (1.f - wc) * dab;
-    if (o.sca > 0.f) {
-        Cb = fmaf(gb, wc * gcl / o.sca, Cb);
-        scab -= gb * o.g / o.sca;
-    }
+    Cb = fmaf(gb, wc * gcl * o.rsca, (1.f - wc) * dab);
+    scab -= gb * o.g * o.rsca;
     Ab = dab;
     Rb = scab;
     Cb = fmaf(wc, scab, Cb);
@@ -298,16 +306,21 @@ __global__ void __launch_bounds__(EA_THREADS, EA_BLOCKS_PER_SM) k_eaa_rt(Model m
             for (int col = 0; col < (CLOUD ? 2 : 1); ++col) {
                 const float cg = col ? gnu : 0.f;   // cloud depth C = C_l g(nu) dr in the cloudy column
                 // pass 1: zeroth order upward, its moments and B to the scratch array
+                // (the extinction of the layers two ahead already in flight)
                 {
                     float bb = pl.value(ss.inv_t[L]);
                     float2 up[2] = {f2(bb), f2(bb)};
                     sc.at(L, 0) = dot4(ang.hc, up);
                     sc.at(L, 1) = dot4(ang.ha, up);
                     sc.at(L, 2) = bb;
+                    float xa = ex[(size_t)(L - 1) * Np], xb = ex[(size_t)(L - 2) * Np];
                     for (int l = L - 1; l >= 0; --l) {
+                        const float alpha = xa;
+                        xa = xb;
+                        if (l >= 2) xb = ex[(size_t)(l - 2) * Np];
                         const float dr = ss.dr[l];
                         const float C = CLOUD ? ss.ccl[l] * cg * dr : 0.f;
-                        const float da = fmaf(1.f - wc, C, ex[(size_t)l * Np] * dr), rda = __frcp_rn(da);
+                        const float da = fmaf(1.f - wc, C, alpha * dr), rda = rcpa(da);
                         const float bt = pl.value(ss.inv_t[l]);
 #pragma unroll
                         for (int p = 0; p < 2; ++p) {
@@ -321,23 +334,31 @@ __global__ void __launch_bounds__(EA_THREADS, EA_BLOCKS_PER_SM) k_eaa_rt(Model m
                         bb = bt;
                     }
                 }
-                // pass 2: zeroth order downward, first order summed top-down
+                // pass 2: zeroth order downward, first order summed top-down (the
+                // next layer's extinction and level values loaded one layer ahead)
                 float2 dn[2] = {f2(0.f), f2(0.f)}, tr[2] = {f2(1.f), f2(1.f)}, v[2] = {f2(0.f), f2(0.f)};
                 float bt = sc.at(0, 2), jt = sc.at(0, 0), ht = sc.at(0, 1);
+                float nx = ex[0], nj = sc.at(1, 0), nh = sc.at(1, 1), nb = sc.at(1, 2);
                 for (int l = 0; l < L; ++l) {
+                    const float alpha = nx, ju = nj, hu = nh, bb = nb;
+                    if (l + 1 < L) {
+                        nx = ex[(size_t)(l + 1) * Np];
+                        nj = sc.at(l + 2, 0);
+                        nh = sc.at(l + 2, 1);
+                        nb = sc.at(l + 2, 2);
+                    }
                     const float dr = ss.dr[l];
-                    const float A = ex[(size_t)l * Np] * dr, R = ss.ray[l] * nr4 * dr;
+                    const float A = alpha * dr, R = ss.ray[l] * nr4 * dr;
                     const float C = CLOUD ? ss.ccl[l] * cg * dr : 0.f;
                     const LayerOpt o = layer_opt(A, R, C, wc, gcl);
-                    const float bb = sc.at(l + 1, 2);
-                    const float rda = __frcp_rn(o.da), rdp = __frcp_rn(o.dp);
+                    const float rda = o.rda, rdp = o.rdp;
 #pragma unroll
                     for (int p = 0; p < 2; ++p) {
                         float2 e, ome, f;
                         layer_factors(ang, p, o.da, rda, e, ome, f);
                         dn[p] = fma2(dn[p], e, fma2(f2(bb), ome, mul2(f2(bt - bb), f)));
                     }
-                    const float jb = sc.at(l + 1, 0) + dot4(ang.hc, dn), hb = sc.at(l + 1, 1) - dot4(ang.ha, dn);
+                    const float jb = ju + dot4(ang.hc, dn), hb = hu - dot4(ang.ha, dn);
 #pragma unroll
                     for (int p = 0; p < 2; ++p) {
                         float2 e, ome, f;
@@ -421,7 +442,7 @@ __device__ __forceinline__ void load4(const Scratch &sc, int k, float2 (&v)[2]) 
 // of pass 2, 8 A_bar of the layer below the level (pass 2's part; then the
 // cloudy column's total, which the clear column's pass 2 adds to its own).
 template <bool CLOUD>
-__global__ void __launch_bounds__(EA_THREADS, EA_BLOCKS_PER_SM) k_eaa_rt_bwd(Model m, Work w, float *scr) {
+__global__ void __launch_bounds__(EA_THREADS, EA_BWD_BLOCKS_PER_SM) k_eaa_rt_bwd(Model m, Work w, float *scr) {
     __shared__ EaaSample ss;
     __shared__ EaaRed rd;
     const EaaAngles ang(m);
@@ -465,16 +486,20 @@ __global__ void __launch_bounds__(EA_THREADS, EA_BLOCKS_PER_SM) k_eaa_rt_bwd(Mod
                 const float4 vt = it4[col];
                 const float2 v0[2] = {make_float2(vt.x, vt.y), make_float2(vt.z, vt.w)};
                 const float2 vb[2] = {mul2(f2(fbar * wcol), ang.wt[0]), mul2(f2(fbar * wcol), ang.wt[1])};
-                // pass 1: upward zeroth order
+                // pass 1: upward zeroth order (the extinction two layers ahead in flight)
                 {
                     float bb = pl.value(ss.inv_t[L]);
                     float2 up[2] = {f2(bb), f2(bb)};
                     store4(sc, L, up);
                     sc.at(L, 6) = bb;
+                    float xa = ex[(size_t)(L - 1) * Np], xb = ex[(size_t)(L - 2) * Np];
                     for (int l = L - 1; l >= 0; --l) {
+                        const float alpha = xa;
+                        xa = xb;
+                        if (l >= 2) xb = ex[(size_t)(l - 2) * Np];
                         const float dr = ss.dr[l];
                         const float C = CLOUD ? ss.ccl[l] * cg * dr : 0.f;
-                        const float da = fmaf(1.f - wc, C, ex[(size_t)l * Np] * dr), rda = __frcp_rn(da);
+                        const float da = fmaf(1.f - wc, C, alpha * dr), rda = rcpa(da);
                         const float bt = pl.value(ss.inv_t[l]);
 #pragma unroll
                         for (int p = 0; p < 2; ++p) {
@@ -499,15 +524,23 @@ __global__ void __launch_bounds__(EA_THREADS, EA_BLOCKS_PER_SM) k_eaa_rt_bwd(Mod
                     ht = dot4(ang.ha, u0);
                 }
                 float jbt = 0.f, hbt = 0.f, bbt = 0.f;   // adjoints of the top level's J, H, B from the layer above
+                // the next layer's extinction and the level below it (U, B) loaded one layer ahead
+                float nx = ex[0], nbv = sc.at(1, 6);
+                float2 nu2[2];
+                load4(sc, 1, nu2);
                 for (int l = 0; l < L; ++l) {
+                    const float alpha = nx, bb = nbv;
+                    const float2 ub[2] = {nu2[0], nu2[1]};
+                    if (l + 1 < L) {
+                        nx = ex[(size_t)(l + 1) * Np];
+                        nbv = sc.at(l + 2, 6);
+                        load4(sc, l + 2, nu2);
+                    }
                     const float dr = ss.dr[l];
-                    const float A = ex[(size_t)l * Np] * dr, R = ss.ray[l] * nr4 * dr;
+                    const float A = alpha * dr, R = ss.ray[l] * nr4 * dr;
                     const float C = CLOUD ? ss.ccl[l] * cg * dr : 0.f;
                     const LayerOpt o = layer_opt(A, R, C, wc, gcl);
-                    const float bb = sc.at(l + 1, 6);
-                    float2 ub[2];
-                    load4(sc, l + 1, ub);
-                    const float rda = __frcp_rn(o.da), rdp = __frcp_rn(o.dp);
+                    const float rda = o.rda, rdp = o.rdp;
                     float2 ea[2], omea[2], fa[2], fpa[2], dnb[2];
 #pragma unroll
                     for (int p = 0; p < 2; ++p) {
@@ -599,14 +632,22 @@ __global__ void __launch_bounds__(EA_THREADS, EA_BLOCKS_PER_SM) k_eaa_rt_bwd(Mod
                     for (int p = 0; p < 2; ++p) ld[p] = fma2(ang.hc[p], f2(jl), mul2(ang.ha[p], f2(-hl)));
                 }
                 float bb = sc.at(L, 6), bbs = 0.f;   // bbs: this pass's B_bar of level l+1 from layer l+1
+                // the layer's extinction and its top level's D and B loaded one layer ahead
+                float px = ex[(size_t)(L - 1) * Np], nbt = sc.at(L - 1, 6);
+                float2 nd[2];
+                load4(sc, L - 1, nd);
                 for (int l = L - 1; l >= 0; --l) {
+                    const float alpha = px, btl = nbt;
+                    const float2 dl[2] = {nd[0], nd[1]};
+                    if (l >= 1) {
+                        px = ex[(size_t)(l - 1) * Np];
+                        nbt = sc.at(l - 1, 6);
+                        load4(sc, l - 1, nd);
+                    }
                     const float dr = ss.dr[l];
-                    const float alpha = ex[(size_t)l * Np];
                     const float C = CLOUD ? ss.ccl[l] * cg * dr : 0.f;
-                    const float da = fmaf(1.f - wc, C, alpha * dr), rda = __frcp_rn(da);
-                    const float btl = sc.at(l, 6);
-                    float2 dl[2], ea[2];
-                    load4(sc, l, dl);
+                    const float da = fmaf(1.f - wc, C, alpha * dr), rda = rcpa(da);
+                    float2 ea[2];
                     float da3 = 0.f, bte = 0.f;
 #pragma unroll
                     for (int p = 0; p < 2; ++p) {
@@ -819,9 +860,9 @@ int eaa_chunk(const Model &m, int B) {
     return (int)std::max<long long>(1, std::min<long long>(8, c));
 }
 
-int eaa_rt_grid(const Model &m, int B) {
+int eaa_rt_grid(const Model &m, int B, int per_sm) {
     const long long items = (long long)B * ((m.Np + 128 * EA_SUB - 1) / (128 * EA_SUB));
-    return (int)std::max<long long>(1, std::min<long long>(items, (long long)sm_count_a() * EA_BLOCKS_PER_SM));
+    return (int)std::max<long long>(1, std::min<long long>(items, (long long)sm_count_a() * per_sm));
 }
 
 }  // namespace
@@ -840,7 +881,7 @@ int launch_eaa_forward(const Model &m, const Work &w, float *scr, bool store_i, 
     if (spl == 2) ES_LAUNCH(h, "k_eaa_ext", st, k_eaa_ext<2><<<grid, EM_THREADS, sm, st>>>(m, w, chunk));
     else if (spl == 4) ES_LAUNCH(h, "k_eaa_ext", st, k_eaa_ext<4><<<grid, EM_THREADS, sm, st>>>(m, w, chunk));
     else ES_LAUNCH(h, "k_eaa_ext", st, k_eaa_ext<8><<<grid, EM_THREADS, sm, st>>>(m, w, chunk));
-    const int g2 = eaa_rt_grid(m, w.B);
+    const int g2 = eaa_rt_grid(m, w.B, EA_BLOCKS_PER_SM);
 #define ES_ER(CL, SI) ES_LAUNCH(h, "k_eaa_rt", st, k_eaa_rt<CL, SI><<<g2, EA_THREADS, 0, st>>>(m, w, scr))
     if (m.cloud_kind == ES_CLOUD_KH18) {
         if (store_i) ES_ER(true, true); else ES_ER(true, false);
@@ -852,7 +893,7 @@ int launch_eaa_forward(const Model &m, const Work &w, float *scr, bool store_i, 
 }
 
 int launch_eaa_backward(const Model &m, const Work &w, float *scr, cudaStream_t st, const Hook &h) {
-    const int g2 = eaa_rt_grid(m, w.B);
+    const int g2 = eaa_rt_grid(m, w.B, EA_BWD_BLOCKS_PER_SM);
     if (m.cloud_kind == ES_CLOUD_KH18)
         ES_LAUNCH(h, "k_eaa_rt_bwd", st, k_eaa_rt_bwd<true><<<g2, EA_THREADS, 0, st>>>(m, w, scr));
     else
