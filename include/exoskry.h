@@ -254,7 +254,10 @@ es_status es_set_batch(es_ctx *ctx, const double *theta, const int32_t *kind, in
  * opacity stage (Sect. 3) as a kernel of its own: the raw table rows that
  * bracket the vector's layers, each read once, into the layer extinction,
  * which the chord kernel (Sect. 4) then reads (es_query key 17 gives the
- * row bytes); larger batches interpolate inside the fused kernels. */
+ * row bytes); larger batches interpolate inside the fused kernels. With
+ * ES_RT_DELTA_EAA the emission samples run through kernels of their own:
+ * their extinction is stored per (sample, layer, wavenumber), then solved
+ * column by column (the context holds that buffer and a scratch array). */
 es_status es_forward(es_ctx *ctx, float *spectrum, double *binned, double *lnL,
                      int mem, es_stream_t stream);
 
@@ -321,7 +324,9 @@ es_status es_set_graphs(es_ctx *ctx, int on);
  * ES_KIND_EMISSION makes that sample invalid (ln L = -1e300). A kernel that
  * gives up on a bounded wait makes every ln L of the call -1e300.
  * A batch whose workspace exceeds 32 MiB is rejected with ES_EINVAL
- * (the message gives the bytes needed). The first call on a device looks up
+ * (the message gives the bytes needed), and so is an emission batch (kind
+ * given) of a model with ES_RT_DELTA_EAA, whose per-batch extinction buffer
+ * does not fit the fixed array. The first call on a device looks up
  * the array's device address; make that first call before any stream
  * capture. All calls on a device share the array and leave their contents in
  * it: calls that overlap on the GPU race and must be serialised. */
