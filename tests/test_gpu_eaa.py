@@ -199,6 +199,40 @@ def test_eaa_invalid_samples_and_replay():
     np.testing.assert_allclose(l0[valid[0]], ref["lnl"], rtol=1e-5, atol=1e-3)
 
 
+def test_eaa_brown_dwarf_gauss_jacobi():
+    """A brown dwarf's absolute flux at distance D (modified Milne profile,
+    mass and gravity through R_bd) by the delta-EAA with Rayleigh scattering
+    and the Gauss-Jacobi flux angles: spectra, ln L and all 15 gradient
+    components against the oracle."""
+    w = synth.workload("browndwarf", batch=2, n_nu=1500)
+    w.model = dataclasses.replace(w.model, emission_solver=O.RT_DELTA_EAA,
+                                  emission_quadrature=O.QUAD_GAUSS_JACOBI)
+    tabs = oracle_tables(w)
+    ctx = binding.context_for(w)
+    out = gpu_eval(ctx, w, w.theta, np.ones(2, np.int32))
+    for b in range(2):
+        ref = oracle_eval(w, tabs, w.theta[b], 1, grad=(b == 0))
+        assert ref["valid"]
+        check_sample(out, b, ref, 1, grad=(b == 0))
+
+
+def test_eaa_autotune_mixed_batch():
+    """es_autotune on a mixed batch of a delta-EAA model tunes the
+    transmission kernels' shapes only; the results with the tuned shapes equal
+    the built-in ones to FP32 rounding of the atomically summed adjoint."""
+    w = _scattering(batch=4, n_nu=1500)
+    kind = np.array([0, 1, 0, 1], np.int32)
+    ctx = binding.context_for(w)
+    before = gpu_eval(ctx, w, w.theta, kind)
+    shapes = ctx.es_autotune()
+    for k, (size, _) in shapes.items():
+        assert (size >= 1) == (k in ("trans_fwd", "trans_bwd")), (k, size)
+    after = gpu_eval(ctx, w, w.theta, kind)
+    np.testing.assert_allclose(after["spec"], before["spec"], rtol=1e-6, atol=0)
+    np.testing.assert_allclose(after["lnl"], before["lnl"], rtol=1e-9)
+    np.testing.assert_allclose(after["grad"], before["grad"], rtol=1e-5, atol=1e-7 * np.abs(before["grad"]).max())
+
+
 @pytest.mark.slow
 def test_eaa_full_size_sampled():
     """The scattering workload at its full size (512 vectors, 20000

@@ -130,3 +130,21 @@ def test_no_alloc_rejects_a_batch_beyond_the_fixed_workspace():
     out = torch.empty(400, dtype=torch.float64, device=DEV)
     with pytest.raises(binding.ExoskryError, match="EINVAL.*bytes of workspace"):
         ctx.es_loglike_noalloc(theta, None, out)
+
+
+def test_no_alloc_rejects_delta_eaa_emission():
+    """A model with the delta-EAA emission solver: an all-transmission call
+    runs (and matches es_loglike); a call with emission samples is rejected
+    with ES_EINVAL before any launch, since the solver's extinction buffer
+    does not fit the fixed array."""
+    w = synth.workload("scattering_emis", batch=2, n_nu=1000)
+    ctx = binding.context_for(w)
+    theta = torch.tensor(w.theta, dtype=torch.float64, device=DEV)
+    ref = _reference(ctx, theta, None)
+    out = torch.full((2,), float("nan"), dtype=torch.float64, device=DEV)
+    ctx.es_loglike_noalloc(theta, None, out)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-5, atol=1e-3)
+    kind = torch.ones(2, dtype=torch.int32, device=DEV)
+    with pytest.raises(binding.ExoskryError, match="ES_EINVAL"):
+        ctx.es_loglike_noalloc(theta, kind, out)
