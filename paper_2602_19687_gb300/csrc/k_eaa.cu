@@ -25,8 +25,9 @@
 //   k_eaa_ext     alpha_gas of every (sample, layer, wavenumber), interpolated
 //                 by the fused kernels' lane pairs (no Rayleigh: it scatters);
 //   k_eaa_rt      one thread per (sample, wavenumber) column: the zeroth-order
-//                 downward pass (its moments to a scratch array), then the
-//                 zeroth- and first-order upward passes together;
+//                 upward pass (its moments to a scratch array), then the
+//                 zeroth-order downward pass with the first order summed
+//                 top-down;
 //   k_eaa_rt_bwd  the adjoint of k_eaa_rt (three passes per column), which
 //                 overwrites w.ext with d lnL / d alpha_gas and sums the other
 //                 adjoints per layer (dr, the levels' T, the Rayleigh weight,
@@ -47,7 +48,7 @@ namespace {
 
 constexpr int EA_THREADS = 128;     // one column per thread
 constexpr int EA_BLOCKS_PER_SM = 4; // resident RT blocks per SM (the scratch array's size follows)
-constexpr int EA_BWD_BLOCKS_PER_SM = 3;   // the adjoint's: measured best (164 registers, no spills; 4 spill, 2 idle)
+constexpr int EA_BWD_BLOCKS_PER_SM = 3;   // the adjoint's (164 registers, no spills): at 4 it spills, at 2 it is slower
 constexpr int EA_SUB = 8;           // 128-wavenumber sub-chunks per RT work item
 constexpr int EA_FIELDS = 9;        // scratch values per level and thread (adjoint)
 
