@@ -804,13 +804,15 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_eaa_abar(Model m, Work w, int
             float2 qa[SPL];
 #pragma unroll
             for (int j = 0; j < SPL; ++j) qa[j] = f2(0.f);
+            float2 ab_next = abp[0];   // alpha_bar of the pair's two wavenumbers, one layer ahead
             for (int l = 0; l < L;) {
                 const int end = __shfl_sync(0xffffffffu, sm.sc.lay[l].run_end, 0);
                 pi.load(sm.sc, sm.sc.lay[l].cell, sm.sc.lay[l].itc);
                 if (end < L) pi.prefetch(sm.sc.lay[end].cell, sm.sc.lay[end].itc);
                 for (; l < end; ++l) {
                     const LayerConst &lc = sm.sc.lay[l];
-                    const float2 ab = abp[(size_t)l * (m.Np / 2)];   // alpha_bar of the pair's two wavenumbers
+                    const float2 ab = ab_next;
+                    if (l + 1 < L) ab_next = abp[(size_t)(l + 1) * (m.Np / 2)];
                     float2 p[SPL];
                     float2 sum = f2(0.f), pt = f2(0.f);
 #pragma unroll
