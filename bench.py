@@ -420,13 +420,14 @@ def measured_alpha_traffic(workload):
     return d["dram_bytes_per_launch"]
 
 
-def measured_instructions(name, n_vectors, n_layers, n_nu):
-    """Warp instructions per launch of `name` from the committed ncu opcode
-    capture (profiles/instructions_k_trans.json: per (vector, layer, 32
-    wavenumbers)), scaled to n_vectors x n_layers x n_nu; None when the
-    kernel sources changed since the capture."""
+def measured_instructions(name, n_vectors, n_layers, n_nu, record="instructions_k_trans.json"):
+    """Warp instructions per launch of `name` from a committed ncu capture
+    (profiles/instructions_k_trans.json for the transmission kernels,
+    profiles/instructions_k_eaa.json for the delta-EAA kernels: per (vector,
+    layer, 32 wavenumbers)), scaled to n_vectors x n_layers x n_nu; None when
+    the kernel sources changed since the capture."""
     import hashlib
-    p = os.path.join(ROOT, "profiles", "instructions_k_trans.json")
+    p = os.path.join(ROOT, "profiles", record)
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
@@ -452,7 +453,7 @@ def alu_peak(kind, sm_mhz):
 
 # --------------------------------------------------------------------------- main arms
 # --------------------------------------------------------------------------- other workloads
-def measure_workload(name, device, steps=5, warmup=3, out_vectors=None, probe=None):
+def measure_workload(name, device, steps=5, warmup=3, out_vectors=None, probe=None, sm_mhz=2070.0):
     """Forward+gradient and forward-only throughput of another synthetic
     workload (graph replay, device-resident inputs, CUDA events): spectra/s
     and ms/step; per-kernel times of two directly launched steps (with the
@@ -512,10 +513,20 @@ def measure_workload(name, device, steps=5, warmup=3, out_vectors=None, probe=No
     for k in ("k_eaa_ext", "k_eaa_rt", "k_eaa_rt_bwd", "k_eaa_abar"):
         if k in kernels and probe:
             sec = kernels[k]["ms_per_launch"] / 1e3
-            ex2 = kernel_work(k, w, B)[0] / sec
+            # the forward kernels run every emission vector, the adjoint ones the valid vectors
+            nvec = B if k in ("k_eaa_ext", "k_eaa_rt") else n_valid
+            ex2 = kernel_work(k, w, nvec)[0] / sec
             roof[k] = {"bound": "alu", "ms_per_launch": kernels[k]["ms_per_launch"],
                        "ex2": {"achieved": ex2 / 1e12, "peak": probe[0] / 1e12, "unit": "Tex2/s",
                                "frac": ex2 / probe[0]}}
+            inst = measured_instructions(k, nvec, w.model.n_layers, w.tables.nu.size, "instructions_k_eaa.json")
+            if inst is not None and name == "scattering_emis":
+                # warp instructions against one per clock per SM sub-partition at the median SM clock
+                ipeak = 152 * 4 * sm_mhz * 1e6
+                roof[k]["issue"] = {"achieved": inst / sec / 1e12, "peak": ipeak / 1e12,
+                                    "unit": "T warp-instructions/s", "frac": inst / sec / ipeak,
+                                    "instructions_per_launch": inst,
+                                    "count_source": "profiles/instructions_k_eaa.json (ncu, same sources)"}
     gpu_out = None
     if out_vectors:
         N, nb = w.tables.nu.size, w.bin_lo_um.size
@@ -802,7 +813,7 @@ def run_gpu(args):
         extra = []
         for n in ("batched_emis", "highres", "browndwarf", "cloudy_trans", "cloudy_emis", "scattering_emis"):
             want = list(range(8)) if (n in ("batched_emis", "highres") and not args.no_cpu) else None
-            rec, wx, gx = measure_workload(n, local, out_vectors=want, probe=(ex2_rate, ffma2_rate))
+            rec, wx, gx = measure_workload(n, local, out_vectors=want, probe=(ex2_rate, ffma2_rate), sm_mhz=sm_mhz)
             extra.append(rec)
             if gx is not None:
                 extra_out[n] = (wx, gx)
