@@ -169,6 +169,44 @@ int main() {
         np.testing.assert_allclose(v[rows, 1], w, rtol=0, atol=1e-14)
 
 
+def test_host_mean_intensity_weights_match_the_oracle():
+    """The delta-EAA's weights of int_0^1 dmu at the flux angles, as the
+    library computes them on the host (csrc/quadrature.h interp_weights_01,
+    Gaussian elimination), against the oracle's (numpy solve) at the
+    Gauss-Legendre and Gauss-Jacobi nodes, and against the closed forms
+    int_0^1 mu^k dmu = 1/(k+1) they integrate exactly."""
+    from oracle import exoskry_oracle as O
+    src = r'''
+#include <cstdio>
+#include "quadrature.h"
+int main() {
+  double mu[8], w[8], c[8];
+  es::gauss_legendre4_01(mu, w);
+  es::interp_weights_01(4, mu, c);
+  for (int j = 0; j < 4; ++j) std::printf("%.17g %.17g\n", mu[j], c[j]);
+  es::gauss_jacobi_mu_01(4, mu, w);
+  es::interp_weights_01(4, mu, c);
+  for (int j = 0; j < 4; ++j) std::printf("%.17g %.17g\n", mu[j], c[j]);
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        cpp = os.path.join(d, "w.cpp")
+        exe = os.path.join(d, "w")
+        open(cpp, "w").write(src)
+        subprocess.run(["g++", "-O2", "-I", os.path.join(ROOT, "paper_2602_19687_gb300", "csrc"), cpp, "-o", exe],
+                       check=True)
+        v = np.array([[float(x) for x in line.split()] for line in
+                      subprocess.run([exe], capture_output=True, text=True, check=True).stdout.splitlines()])
+    for rows, kind in ((slice(0, 4), O.QUAD_GAUSS_LEGENDRE), (slice(4, 8), O.QUAD_GAUSS_JACOBI)):
+        mu, c = v[rows, 0], v[rows, 1]
+        np.testing.assert_allclose(c, O.mean_intensity_weights(O.flux_quadrature(kind, 4)[0]), rtol=0, atol=1e-14)
+        for k in range(4):
+            assert np.sum(c * mu ** k) == pytest.approx(1.0 / (k + 1), rel=1e-13)
+    # at the Gauss-Legendre nodes they are the Gauss-Legendre weights
+    np.testing.assert_allclose(v[:4, 1], O.gauss_legendre_01(4)[1], rtol=0, atol=1e-14)
+
+
 def test_parameter_slots_agree_across_header_binding_synth_and_oracle():
     """The canonical parameter slots (include/exoskry.h ES_P_*) in the same order
     and number in the binding, the synthetic-input module and the oracle."""
